@@ -1,0 +1,252 @@
+/*
+ * gb300_ipm.h -- C ABI of the GB300-native pivoting-free interior-point solver.
+ *
+ * The method (arXiv 2508.16094): problem (1)  min f(x) s.t. g(x) >= 0  is solved
+ * by a primal-dual interior-point method. Every iteration linearises the KKT
+ * conditions (2) into the regularised Newton system (3) and condenses it into
+ * the primal condensed system (5)
+ *
+ *     K d_x = -r_p,   K = W + delta_p I + J^T D J,   D = (delta_d I + Lambda^{-1} S)^{-1},
+ *
+ * which is symmetric positive definite (Sec. 3, "Pivoting-Free IPM"), so it is
+ * factored by a supernodal Cholesky that never pivots after a fill-reducing
+ * ordering computed once on the host and reused (Sec. 2, "GPU Direct Solvers
+ * for Optimization"), followed by triangular solves and iterative refinement
+ * (Sec. 2, "Numerical Pivoting": perturbation error corrected by refinement).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an ipm_status and never aborts the process; on error
+ *    ipm_last_error(ctx) returns a message owned by the context.
+ *  - Pointers named h_* are host memory, d_* are device memory of the GPU the
+ *    context was created on. Device buffers are owned by the caller; they are
+ *    read or written only during the call, on the context's stream.
+ *  - Index arrays are int32 (int64 for CSR/CSC offsets), values float64.
+ *  - J is the m x n constraint Jacobian pattern in CSR (rows sorted ascending,
+ *    no duplicates). W (optional) is the pattern of the Hessian of the
+ *    Lagrangian, lower triangle, CSC. Value arrays follow these patterns' nnz
+ *    order.
+ *  - Bounds l <= x <= u (+-INFINITY for none) are rows of g with Jacobian rows
+ *    +-e_i. Their D entries act on the diagonal of K only. The constraint
+ *    vector has m_tot = m + (#finite l) + (#finite u) rows, ordered: the m rows
+ *    of J, then the finite lower bounds by ascending variable, then the finite
+ *    upper bounds by ascending variable. s, lambda and D have length m_tot.
+ *  - Orderings are new->old: perm[k] is the original index of the k-th
+ *    eliminated variable.
+ *  - Call order: ipm_create -> kkt_analyze -> ipm_set_workspace -> kkt_assemble
+ *    -> kkt_factor -> kkt_solve (any number of times). ipm_solve runs the whole
+ *    method after ipm_set_workspace. A call out of order returns IPM_ERR_STATE.
+ */
+#ifndef GB300_IPM_H
+#define GB300_IPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IPM_API __attribute__((visibility("default")))
+#else
+#define IPM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipm_ctx ipm_ctx;
+
+typedef enum {
+  IPM_OK = 0,
+  IPM_ERR_ARG = 1,         /* invalid argument (null pointer, size, pattern) */
+  IPM_ERR_STATE = 2,       /* call out of order */
+  IPM_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+  IPM_ERR_NOMEM = 4,       /* workspace too small, or the factor does not fit the device */
+  IPM_ERR_NOT_SPD = 5,     /* a pivot of the Cholesky factorisation was not positive */
+  IPM_ERR_NUMERIC = 6,     /* NaN/Inf met, or refinement could not reach its tolerance */
+  IPM_ERR_MAXITER = 7,     /* interior-point iteration limit reached */
+  IPM_ERR_TIMEOUT = 8,     /* a bounded device-side wait ran out */
+  IPM_ERR_STALL = 9,       /* the interior-point method stopped making progress */
+  IPM_ERR_UNSUPPORTED = 10 /* feature not available in this build / configuration */
+} ipm_status;
+
+/* Arithmetic of the numeric factorisation (storage type in brackets). */
+typedef enum {
+  IPM_FP64 = 0, /* FP64 FMA                                             [FP64] */
+  IPM_FP32 = 1, /* FP32 FMA                                             [FP32] */
+  IPM_TF32 = 2, /* TF32 tensor cores (tcgen05), FP32 accumulate (TMEM)  [FP32] */
+  IPM_BF16 = 3  /* BF16 tensor cores (tcgen05), FP32 accumulate (TMEM)  [FP32] */
+} ipm_precision;
+
+typedef enum {
+  IPM_REFINE_NONE = 0, /* one solve with the factor */
+  IPM_REFINE_IR = 1,   /* FP64 iterative refinement, then PCG if it stalls */
+  IPM_REFINE_PCG = 2   /* FP64 conjugate gradients preconditioned by the factor */
+} ipm_refine;
+
+typedef struct {
+  int32_t max_iter;      /* interior-point iteration limit (500) */
+  double tol;            /* scaled KKT residual tolerance (1e-8) */
+  double delta_p;        /* primal regularisation of (3) (1e-8) */
+  double delta_d;        /* dual regularisation of (3) (1e-8) */
+  int32_t precision;     /* ipm_precision of kkt_factor inside ipm_solve (IPM_FP64) */
+  int32_t storage_fp64;  /* 1: size the factor storage for FP64 values (needed by IPM_FP64
+                            and by fallback_fp64); 0: FP32 storage only. -1: automatic */
+  int32_t refine;        /* ipm_refine used inside ipm_solve (IPM_REFINE_IR) */
+  int32_t ir_max;        /* refinement steps per solve (10) */
+  double ir_tol;         /* stop once ||b - K x||_inf <= ir_tol ||b||_inf (1e-10) */
+  int32_t pcg_max;       /* PCG iterations per solve (100) */
+  int32_t fallback_fp64; /* refactor in FP64 when refinement misses ir_tol (0) */
+  double accept_tol;     /* a solve that misses ir_tol but reaches accept_tol is used (1e-6) */
+  int32_t verbose;       /* print one line per interior-point iteration to stderr */
+  int32_t warm_start;    /* 1: ipm_solve starts from the x, s, lambda it is given (0) */
+} ipm_options;
+
+/* Default options (values in brackets above). */
+IPM_API void ipm_default_options(ipm_options *opts);
+
+typedef struct {
+  int64_t n;               /* variables */
+  int64_t m_tot;           /* rows of g including finite bounds */
+  int64_t nnz_k;           /* entries of the lower triangle of K (diagonal included) */
+  int64_t nnz_l;           /* entries of L (sum of column counts) */
+  int32_t nsuper;          /* supernodes after relaxed amalgamation */
+  int32_t nlevels;         /* levels of the supernodal elimination tree */
+  int32_t max_front;       /* largest frontal matrix order */
+  int32_t max_ncol;        /* widest supernode */
+  double flops;            /* algorithmic factor flops: sum over columns of colcount^2 */
+  int64_t factor_entries;  /* stored entries of the supernodal panels (with padding) */
+  int64_t update_entries;  /* stored entries of all update matrices */
+  int64_t workspace_bytes; /* bytes ipm_set_workspace needs (from the storage option) */
+} ipm_symbolic_info;
+
+typedef struct {
+  int32_t iterations;   /* refinement or PCG iterations */
+  int32_t used_pcg;     /* 1 if PCG ran */
+  double rel_residual;  /* final ||b - K x||_inf / ||b||_inf in FP64 */
+} ipm_solve_info;
+
+typedef struct {
+  int32_t status;           /* ipm_status of the solve */
+  int32_t iterations;       /* interior-point iterations */
+  int32_t factorizations;   /* numeric factorisations (including retries) */
+  int32_t regularizations;  /* delta_p increases after a non-positive pivot */
+  int32_t refine_steps;     /* total refinement steps */
+  int32_t pcg_steps;        /* total PCG iterations */
+  int32_t fp64_fallbacks;   /* refactorisations in FP64 after a missed tolerance */
+  int32_t perturbed_pivots; /* low-precision pivots replaced (static pivoting) */
+  double objective;         /* f(x) at the returned point */
+  double kkt;               /* scaled KKT residual (see ipm_solve) */
+  double primal_res, dual_res, compl_res, mu;
+  double worst_rel_residual;/* largest linear-solve residual accepted */
+  double time_total_ms, time_assemble_ms, time_factor_ms, time_solve_ms, time_other_ms;
+} ipm_result;
+
+/* Create a solver context for a problem with n variables and m general
+ * constraint rows (Sec. 1, problem (1); Sec. 3, KKT conditions (2)).
+ * j_rowptr/j_col: host CSR pattern of J (m x n). w_colptr/w_row: host lower
+ * CSC pattern of W (NULL for an LP). l/u: host bounds, length n (NULL = none).
+ * stream: a cudaStream_t (NULL = default stream) on the current device.
+ * Copies everything it needs; keeps no caller pointer. Touches no GPU memory.
+ * Errors: IPM_ERR_ARG for a malformed pattern (unsorted or out-of-range). */
+IPM_API ipm_status ipm_create(int32_t n, int32_t m, const int64_t *h_j_rowptr, const int32_t *h_j_col,
+                      const int64_t *h_w_colptr, const int32_t *h_w_row, const double *h_l,
+                      const double *h_u, const ipm_options *opts, void *stream, ipm_ctx **out);
+
+/* Symbolic analysis with the ordering given (Sec. 2: the fill-reducing
+ * reordering is computed once on the host and reused): pattern of
+ * K = W + J^T J + I, elimination tree, postorder, column counts, supernodes
+ * with relaxed amalgamation, supernode row structures, level sets and every
+ * index map the numeric phase uses. Host only; no GPU work.
+ * h_perm: length n, new->old, or NULL for the identity.
+ * info (may be NULL) receives sizes and the workspace the numeric phase needs.
+ * Errors: IPM_ERR_ARG if h_perm is not a permutation. */
+IPM_API ipm_status kkt_analyze(ipm_ctx *ctx, const int32_t *h_perm, ipm_symbolic_info *info);
+
+/* Hand the context a caller-owned device buffer of at least
+ * info.workspace_bytes bytes (256-byte aligned). Uploads the symbolic data.
+ * The buffer must stay valid until ipm_destroy or the next call of this
+ * function. Errors: IPM_ERR_NOMEM if too small, IPM_ERR_CUDA on upload failure. */
+IPM_API ipm_status ipm_set_workspace(ipm_ctx *ctx, void *d_buf, size_t bytes);
+
+/* Assembly of the primal condensed matrix, Eq. (5):
+ *   K = W + J^T diag(D_J) J + diag(D_bounds) + delta_p I
+ * on the fixed pattern, in FP64 (products summed in ascending J row).
+ * d_wvals: W values (NULL if no W). d_jvals: J values. d_D: length m_tot.
+ * The values are copied into the workspace (kkt_solve's refinement evaluates
+ * K x from them), so the caller's buffers may be released after the call.
+ * Errors: IPM_ERR_STATE before ipm_set_workspace. */
+IPM_API ipm_status kkt_assemble(ipm_ctx *ctx, const double *d_wvals, const double *d_jvals,
+                        const double *d_D, double delta_p);
+
+/* Supernodal multifrontal Cholesky P K P^T = L L^T without pivoting (Sec. 2,
+ * "LDL^T Factorization"; Sec. 3, SPD condensed system), level by level over
+ * the elimination tree (Sec. 2: tree-level parallelism), in the given
+ * ipm_precision. FP64 reports the first non-positive pivot: returns
+ * IPM_ERR_NOT_SPD with *bad_col = that column in the final ordering (the
+ * smallest such column). Lower precisions replace a non-positive pivot by a
+ * large value (static pivoting; counted in ipm_last_perturbed) and return
+ * IPM_OK; refinement in kkt_solve corrects the perturbation.
+ * Errors: IPM_ERR_STATE before kkt_assemble; IPM_ERR_NOMEM if the storage was
+ * sized for FP32 and FP64 is requested. */
+IPM_API ipm_status kkt_factor(ipm_ctx *ctx, int32_t precision, int32_t *bad_col);
+
+/* Solve K x = b with the current factor: x = P^T L^{-T} L^{-1} P b, then FP64
+ * refinement on the residual b - K x computed matrix-free from W, J, D
+ * (Sec. 2, refinement; ipm_refine). d_b, d_x: length n, original numbering
+ * (may alias). info may be NULL.
+ * Errors: IPM_ERR_STATE before kkt_factor; IPM_ERR_NUMERIC if the residual
+ * misses accept_tol. */
+IPM_API ipm_status kkt_solve(ipm_ctx *ctx, const double *d_b, double *d_x, int32_t refine,
+                     ipm_solve_info *info);
+
+/* The whole method on the LP/QP  min c^T x + 1/2 x^T W x  s.t.  J x >= b,
+ * l <= x <= u  (Sec. 3): Mehrotra predictor-corrector on the primal condensed
+ * system (5), fraction-to-the-boundary step lengths and the barrier update as
+ * device map/reduce kernels (Sec. 1: "map or reduce operations").
+ * d_jvals, d_b (length m), d_c (length n), d_wvals (NULL for an LP): problem
+ * data. d_x (n), d_s and d_lambda (m_tot): outputs. res may be NULL.
+ * Scaled KKT residual: max(||g - s||_inf / max(1, ||bfull||_inf),
+ * ||grad f - J^T lambda||_inf / max(1, ||c||_inf), ||s .* lambda||_inf /
+ * max(1, |f(x)|)), bfull = [b; l_finite; -u_finite].
+ * Returns IPM_OK when it reaches opts.tol, else IPM_ERR_MAXITER/NUMERIC/... */
+IPM_API ipm_status ipm_solve(ipm_ctx *ctx, const double *d_jvals, const double *d_b, const double *d_c,
+                     const double *d_wvals, double *d_x, double *d_s, double *d_lambda,
+                     ipm_result *res);
+
+/* One Newton direction of (3) at (x, s, lambda) with complementarity target w
+ * (length m_tot; w = mu e for the barrier step), through D, assembly, factor,
+ * solve with refinement and the recovery d_lambda = D (w/lambda - g - J d_x),
+ * d_s = -s + w/lambda - (s/lambda) d_lambda. All arrays are device memory.
+ * Used to check one step of the method in isolation. */
+IPM_API ipm_status ipm_newton_direction(ipm_ctx *ctx, const double *d_jvals, const double *d_b,
+                                const double *d_c, const double *d_wvals, const double *d_x,
+                                const double *d_s, const double *d_lambda, const double *d_w,
+                                double *d_dx, double *d_ds, double *d_dlambda);
+
+/* --- inspection (host copies; for tests and tools) --------------------- */
+
+/* Copy the symbolic analysis to host arrays (each may be NULL). Sizes: perm,
+ * parent, colcount: n; super: nsuper+1; sparent, slevel: nsuper; srp: nsuper+1;
+ * sri: srp[nsuper]. Numbering is the final one (given ordering + postorder). */
+IPM_API ipm_status kkt_symbolic_export(const ipm_ctx *ctx, int32_t *h_perm, int32_t *h_parent,
+                               int32_t *h_colcount, int32_t *h_super, int32_t *h_sparent,
+                               int32_t *h_slevel, int64_t *h_srp, int32_t *h_sri);
+
+/* Assembled K values in the order of the lower CSC pattern of K in the
+ * ORIGINAL numbering (columns ascending, rows ascending): h_out has nnz_k. */
+IPM_API ipm_status kkt_export_assembled(ipm_ctx *ctx, double *h_out);
+
+/* Entries L(i, j) of the current factor for count (i, j) pairs in the final
+ * numbering (h_rows, h_cols; 0 for entries outside the structure), as FP64. */
+IPM_API ipm_status kkt_factor_entries(ipm_ctx *ctx, int64_t count, const int32_t *h_rows,
+                              const int32_t *h_cols, double *h_out);
+
+/* Low-precision pivots replaced by the last kkt_factor. */
+IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);
+
+IPM_API const char *ipm_last_error(const ipm_ctx *ctx);
+IPM_API void ipm_destroy(ipm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_IPM_H */

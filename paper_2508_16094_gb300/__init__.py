@@ -1,0 +1,266 @@
+"""GB300-native pivoting-free interior-point solver (arXiv 2508.16094).
+
+Thin ctypes binding of the C ABI in ``include/gb300_ipm.h``: argument
+marshalling only, every step of the method runs in ``libgb300ipm.so``. PyTorch
+provides device memory (the workspace and the vectors) and the stream.
+
+There is no CPU fallback: if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["IpmError", "IpmContext", "Options", "load", "build", "lib_path",
+           "IPM_FP64", "IPM_FP32", "IPM_TF32", "IPM_BF16",
+           "IPM_REFINE_NONE", "IPM_REFINE_IR", "IPM_REFINE_PCG"]
+
+IPM_FP64, IPM_FP32, IPM_TF32, IPM_BF16 = 0, 1, 2, 3
+IPM_REFINE_NONE, IPM_REFINE_IR, IPM_REFINE_PCG = 0, 1, 2
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_NOMEM", 5: "ERR_NOT_SPD",
+          6: "ERR_NUMERIC", 7: "ERR_MAXITER", 8: "ERR_TIMEOUT", 9: "ERR_STALL",
+          10: "ERR_UNSUPPORTED"}
+EXPORTED = ["ipm_default_options", "ipm_create", "kkt_analyze", "ipm_set_workspace",
+            "kkt_assemble", "kkt_factor", "kkt_solve", "ipm_solve", "ipm_newton_direction",
+            "kkt_symbolic_export", "kkt_export_assembled", "kkt_factor_entries",
+            "ipm_last_perturbed", "ipm_last_error", "ipm_destroy"]
+
+
+class IpmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Options(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("delta_p", C.c_double),
+                ("delta_d", C.c_double), ("precision", C.c_int32), ("storage_fp64", C.c_int32),
+                ("refine", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
+                ("pcg_max", C.c_int32), ("fallback_fp64", C.c_int32), ("accept_tol", C.c_double),
+                ("verbose", C.c_int32), ("warm_start", C.c_int32)]
+
+
+class SymbolicInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m_tot", C.c_int64), ("nnz_k", C.c_int64),
+                ("nnz_l", C.c_int64), ("nsuper", C.c_int32), ("nlevels", C.c_int32),
+                ("max_front", C.c_int32), ("max_ncol", C.c_int32), ("flops", C.c_double),
+                ("factor_entries", C.c_int64), ("update_entries", C.c_int64),
+                ("workspace_bytes", C.c_int64)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("used_pcg", C.c_int32), ("rel_residual", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("factorizations", C.c_int32),
+                ("regularizations", C.c_int32), ("refine_steps", C.c_int32),
+                ("pcg_steps", C.c_int32), ("fp64_fallbacks", C.c_int32),
+                ("perturbed_pivots", C.c_int32), ("objective", C.c_double), ("kkt", C.c_double),
+                ("primal_res", C.c_double), ("dual_res", C.c_double), ("compl_res", C.c_double),
+                ("mu", C.c_double), ("worst_rel_residual", C.c_double),
+                ("time_total_ms", C.c_double), ("time_assemble_ms", C.c_double),
+                ("time_factor_ms", C.c_double), ("time_solve_ms", C.c_double),
+                ("time_other_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def load() -> C.CDLL:
+    """Load libgb300ipm.so (built in-tree by ``build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"{_build.LIB} is missing: run paper_2508_16094_gb300.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback")
+    lib = C.CDLL(_build.LIB)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "ipm_default_options": (None, [P]),
+        "ipm_create": (I32, [I32, I32, P, P, P, P, P, P, P, P, P]),
+        "kkt_analyze": (I32, [P, P, P]),
+        "ipm_set_workspace": (I32, [P, P, C.c_size_t]),
+        "kkt_assemble": (I32, [P, P, P, P, D]),
+        "kkt_factor": (I32, [P, I32, P]),
+        "kkt_solve": (I32, [P, P, P, I32, P]),
+        "ipm_solve": (I32, [P, P, P, P, P, P, P, P, P]),
+        "ipm_newton_direction": (I32, [P] * 12),
+        "kkt_symbolic_export": (I32, [P] * 9),
+        "kkt_export_assembled": (I32, [P, P]),
+        "kkt_factor_entries": (I32, [P, I64, P, P, P]),
+        "ipm_last_perturbed": (I32, [P]),
+        "ipm_last_error": (C.c_char_p, [P]),
+        "ipm_destroy": (None, [P]),
+    }
+    for name, (rt, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = rt
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().ipm_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _np(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dp(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class IpmContext:
+    """One solver context; methods are named after the C entry points they call."""
+
+    def __init__(self, n, m, j_rowptr, j_col, l=None, u=None, w_colptr=None, w_row=None,
+                 options: Options | None = None, stream=None):
+        lib = load()
+        self._lib = lib
+        self.n, self.m = int(n), int(m)
+        self.options = options if options is not None else default_options()
+        self._keep = [_np(j_rowptr, np.int64), _np(j_col, np.int32), _np(w_colptr, np.int64),
+                      _np(w_row, np.int32), _np(l, np.float64), _np(u, np.float64)]
+        h = C.c_void_p()
+        st = self._keep
+        self._check(lib.ipm_create(self.n, self.m, _hp(st[0]), _hp(st[1]), _hp(st[2]), _hp(st[3]),
+                                   _hp(st[4]), _hp(st[5]), C.byref(self.options),
+                                   C.c_void_p(stream) if stream else None, C.byref(h)), None)
+        self.handle = h
+        self.info: SymbolicInfo | None = None
+        self.workspace = None
+        lf = np.isfinite(st[4]).sum() if st[4] is not None else 0
+        uf = np.isfinite(st[5]).sum() if st[5] is not None else 0
+        self.m_tot = self.m + int(lf) + int(uf)
+
+    def _check(self, status, handle="self"):
+        if status != 0:
+            h = self.handle if handle == "self" else None
+            msg = self._lib.ipm_last_error(h).decode() if h else ""
+            raise IpmError(status, msg)
+        return status
+
+    # --- C entry points -----------------------------------------------------
+    def kkt_analyze(self, perm=None) -> SymbolicInfo:
+        info = SymbolicInfo()
+        p = _np(perm, np.int32)
+        self._check(self._lib.kkt_analyze(self.handle, _hp(p), C.byref(info)))
+        self.info = info
+        return info
+
+    def ipm_set_workspace(self, buf=None):
+        """Hand over a device buffer (torch uint8 tensor); allocates one if None."""
+        import torch
+        if buf is None:
+            buf = torch.empty(int(self.info.workspace_bytes) + 256, dtype=torch.uint8, device="cuda")
+        self.workspace = buf
+        self._check(self._lib.ipm_set_workspace(self.handle, C.c_void_p(buf.data_ptr()),
+                                                buf.numel()))
+        return buf
+
+    def kkt_assemble(self, jvals, D, delta_p, wvals=None):
+        self._check(self._lib.kkt_assemble(self.handle, _dp(wvals), _dp(jvals), _dp(D),
+                                           float(delta_p)))
+
+    def kkt_factor(self, precision=IPM_FP64, raise_on_error=True):
+        bad = C.c_int32(-1)
+        st = self._lib.kkt_factor(self.handle, int(precision), C.byref(bad))
+        if raise_on_error:
+            self._check(st)
+        return st, bad.value
+
+    def kkt_solve(self, b, x, refine=IPM_REFINE_IR, raise_on_error=True) -> SolveInfo:
+        info = SolveInfo()
+        st = self._lib.kkt_solve(self.handle, _dp(b), _dp(x), int(refine), C.byref(info))
+        if raise_on_error:
+            self._check(st)
+        return info
+
+    def ipm_solve(self, jvals, b, c, x, s, lam, wvals=None, raise_on_error=False) -> Result:
+        res = Result()
+        st = self._lib.ipm_solve(self.handle, _dp(jvals), _dp(b), _dp(c), _dp(wvals), _dp(x),
+                                 _dp(s), _dp(lam), C.byref(res))
+        if raise_on_error:
+            self._check(st)
+        return res
+
+    def ipm_newton_direction(self, jvals, b, c, x, s, lam, w, dx, ds, dl, wvals=None):
+        self._check(self._lib.ipm_newton_direction(self.handle, _dp(jvals), _dp(b), _dp(c),
+                                                   _dp(wvals), _dp(x), _dp(s), _dp(lam), _dp(w),
+                                                   _dp(dx), _dp(ds), _dp(dl)))
+
+    def kkt_symbolic_export(self) -> dict:
+        n, ns = self.n, self.info.nsuper
+        out = dict(perm=np.empty(n, np.int32), parent=np.empty(n, np.int32),
+                   colcount=np.empty(n, np.int32), super=np.empty(ns + 1, np.int32),
+                   sparent=np.empty(ns, np.int32), slevel=np.empty(ns, np.int32),
+                   srp=np.empty(ns + 1, np.int64))
+        self._check(self._lib.kkt_symbolic_export(self.handle, *[_hp(out[k]) for k in
+                                                                 ["perm", "parent", "colcount",
+                                                                  "super", "sparent", "slevel",
+                                                                  "srp"]], None))
+        out["sri"] = np.empty(int(out["srp"][-1]), np.int32)
+        self._check(self._lib.kkt_symbolic_export(self.handle, None, None, None, None, None,
+                                                  None, None, _hp(out["sri"])))
+        return out
+
+    def kkt_export_assembled(self) -> np.ndarray:
+        out = np.empty(int(self.info.nnz_k), np.float64)
+        self._check(self._lib.kkt_export_assembled(self.handle, _hp(out)))
+        return out
+
+    def kkt_factor_entries(self, rows, cols) -> np.ndarray:
+        r = _np(rows, np.int32)
+        c = _np(cols, np.int32)
+        out = np.empty(len(r), np.float64)
+        self._check(self._lib.kkt_factor_entries(self.handle, len(r), _hp(r), _hp(c), _hp(out)))
+        return out
+
+    def ipm_last_perturbed(self) -> int:
+        return int(self._lib.ipm_last_perturbed(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ipm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

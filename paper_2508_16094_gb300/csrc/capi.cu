@@ -1,0 +1,781 @@
+// C ABI of the solver (declared in include/gb300_ipm.h): context, workspace,
+// assembly/factor/solve drivers with FP64 refinement and PCG, and the
+// interior-point iteration.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "../../include/gb300_ipm.h"
+#include "ipm_kernels.h"
+#include "launch.h"
+#include "tc.h"
+
+using namespace gipm;
+
+struct ipm_ctx {
+  Problem P;
+  Symbolic S;
+  Plan plan;
+  ipm_options opts;
+  cudaStream_t st = nullptr;
+  int state = 0;  // 0 created, 1 analysed, 2 workspace, 3 assembled, 4 factored
+  std::string err;
+  // workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0, ws_need = 0;
+  int storage_bytes = 8;  // bytes per stored factor entry
+  DevPlan dp{};
+  double *kval = nullptr;
+  void *L = nullptr, *U = nullptr;
+  double *yv = nullptr, *tv = nullptr;  // solve scratch (doubles; float views)
+  double *vx = nullptr, *vr = nullptr, *vc = nullptr, *vz = nullptr, *vp = nullptr,
+         *vq = nullptr, *vb = nullptr, *vdx = nullptr, *vrd = nullptr, *vwx = nullptr;
+  double *vg = nullptr, *vD = nullptr, *vw = nullptr, *vds = nullptr, *vdl = nullptr,
+         *vt = nullptr, *vjd = nullptr, *vjx = nullptr, *vtA = nullptr;
+  double *dl_ = nullptr, *du_ = nullptr;
+  double *jv_copy = nullptr, *D_copy = nullptr, *wv_copy = nullptr;  // inputs kept for refinement
+  double *scal = nullptr, *partial = nullptr;
+  IpmScalars *sc = nullptr;
+  int32_t *status = nullptr, *col2s = nullptr;
+  TcPlan tcp;
+  // inputs of the last assembly (device pointers, used by the residual)
+  const double *cur_jvals = nullptr, *cur_D = nullptr, *cur_wvals = nullptr;
+  double cur_delta_p = 0.0;
+  int factor_prec = -1;
+  int32_t last_perturbed = 0;
+  int64_t refine_steps = 0, pcg_steps = 0;
+  double last_rel = 0.0;
+  VecOps vec() const { return VecOps{dp, st, partial}; }
+};
+
+namespace {
+
+struct Fail {
+  ipm_status code;
+  std::string msg;
+};
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw Fail{IPM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};       \
+  } while (0)
+
+template <typename F>
+ipm_status guarded(ipm_ctx *ctx, F &&f) {
+  try {
+    return f();
+  } catch (const Fail &e) {
+    if (ctx) ctx->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    if (ctx) ctx->err = "host allocation failed";
+    return IPM_ERR_NOMEM;
+  } catch (const std::exception &e) {
+    if (ctx) ctx->err = e.what();
+    return IPM_ERR_ARG;
+  }
+}
+
+// Bump allocator over the workspace (base == nullptr: size only).
+struct Carve {
+  char *base;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+template <typename T>
+const T *upload(Carve &cv, const std::vector<T> &v, cudaStream_t st) {
+  T *p = cv.take<T>(std::max<size_t>(v.size(), 1));
+  if (cv.base && !v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return p;
+}
+
+// Full symmetric W in CSR with the index of each entry's value in the caller's lower CSC.
+void w_full(const Problem &P, std::vector<int64_t> &fp, std::vector<int32_t> &fi,
+            std::vector<int64_t> &src) {
+  const int32_t n = P.n;
+  fp.assign(n + 1, 0);
+  fi.clear();
+  src.clear();
+  if (P.wp.empty()) return;
+  for (int32_t j = 0; j < n; j++)
+    for (int64_t e = P.wp[j]; e < P.wp[j + 1]; e++) {
+      fp[P.wi[e] + 1]++;
+      if (P.wi[e] != j) fp[j + 1]++;
+    }
+  for (int32_t j = 0; j < n; j++) fp[j + 1] += fp[j];
+  fi.resize(fp[n]);
+  src.resize(fp[n]);
+  std::vector<int64_t> f(fp.begin(), fp.end() - 1);
+  for (int32_t j = 0; j < n; j++)
+    for (int64_t e = P.wp[j]; e < P.wp[j + 1]; e++) {
+      const int32_t i = P.wi[e];
+      fi[f[i]] = j; src[f[i]++] = e;
+      if (i != j) { fi[f[j]] = i; src[f[j]++] = e; }
+    }
+}
+
+// Assign every device pointer of the context inside the workspace.
+void layout(ipm_ctx *c, char *base) {
+  Carve cv{base};
+  const Plan &pl = c->plan;
+  const Problem &P = c->P;
+  const cudaStream_t st = c->st;
+  DevPlan &d = c->dp;
+  d.fronts = upload(cv, pl.fronts, st);
+  d.children = upload(cv, pl.children, st);
+  d.inv = upload(cv, pl.inv, st);
+  d.relpos = upload(cv, pl.relpos, st);
+  d.sri = upload(cv, c->S.sri, st);
+  d.build = upload(cv, pl.build_tasks, st);
+  d.gemm = upload(cv, pl.gemm_tasks, st);
+  d.potrf = upload(cv, pl.potrf_tasks, st);
+  d.trsm = upload(cv, pl.trsm_tasks, st);
+  d.syrk = upload(cv, pl.syrk_tasks, st);
+  d.gath = upload(cv, pl.gath_tasks, st);
+  d.sdiag = upload(cv, pl.sdiag_tasks, st);
+  d.sgemv = upload(cv, pl.sgemv_tasks, st);
+  d.rgemv = upload(cv, pl.rgemv_tasks, st);
+  d.toff = upload(cv, pl.toff, st);
+  d.k_slot = upload(cv, pl.k_slot, st);
+  d.k_poff = upload(cv, pl.k_poff, st);
+  d.k_w = upload(cv, pl.k_w, st);
+  d.k_orig = upload(cv, pl.k_orig, st);
+  d.k_pa = upload(cv, pl.k_pa, st);
+  d.k_pb = upload(cv, pl.k_pb, st);
+  d.k_diag = upload(cv, pl.k_diag, st);
+  d.perm = upload(cv, c->S.perm, st);
+  d.jp = upload(cv, P.jp, st);
+  d.jtp = upload(cv, P.jtp, st);
+  d.ji = upload(cv, P.ji, st);
+  d.jrow = upload(cv, P.jrow, st);
+  d.jtpos = upload(cv, P.jtpos, st);
+  {
+    std::vector<int64_t> fp, src;
+    std::vector<int32_t> fi;
+    w_full(P, fp, fi, src);
+    if (fp.empty()) fp.assign(P.n + 1, 0);
+    d.wfp = upload(cv, fp, st);
+    d.wfi = upload(cv, fi, st);
+    d.wfsrc = upload(cv, src, st);
+  }
+  d.lpos = upload(cv, P.lpos, st);
+  d.upos = upload(cv, P.upos, st);
+  d.lidx = upload(cv, P.lidx, st);
+  d.uidx = upload(cv, P.uidx, st);
+  {
+    std::vector<int32_t> col2s(P.n);
+    for (int32_t s = 0; s < c->S.nsuper; s++)
+      for (int32_t j = c->S.super[s]; j < c->S.super[s + 1]; j++) col2s[j] = s;
+    c->col2s = const_cast<int32_t *>(upload(cv, col2s, st));
+  }
+  c->dl_ = const_cast<double *>(upload(cv, P.l, st));
+  c->du_ = const_cast<double *>(upload(cv, P.u, st));
+  c->tcp.layout(cv.base ? &cv : nullptr, c->plan, st);
+  d.n = P.n;
+  d.m = P.m;
+  d.nl = P.nl;
+  d.nu = P.nu;
+  d.mt = P.mt;
+  d.nk = (int64_t)pl.k_slot.size();
+  const size_t n = std::max<int64_t>(P.n, 1), mt = std::max<int64_t>(P.mt, 1),
+               m = std::max<int32_t>(P.m, 1);
+  c->kval = cv.take<double>(std::max<int64_t>(d.nk, 1));
+  c->yv = cv.take<double>(n);
+  c->tv = cv.take<double>(pl.t_entries);
+  for (double **v : {&c->vx, &c->vr, &c->vc, &c->vz, &c->vp, &c->vq, &c->vb, &c->vdx, &c->vrd,
+                     &c->vwx})
+    *v = cv.take<double>(n);
+  for (double **v : {&c->vg, &c->vD, &c->vw, &c->vds, &c->vdl, &c->vt, &c->vjd})
+    *v = cv.take<double>(mt);
+  c->jv_copy = cv.take<double>(std::max<int64_t>(P.jp.back(), 1));
+  c->D_copy = cv.take<double>(mt);
+  c->wv_copy = cv.take<double>(std::max<int64_t>(P.wp.empty() ? 0 : P.wp.back(), 1));
+  c->vjx = cv.take<double>(m);
+  c->vtA = cv.take<double>(m);
+  c->scal = cv.take<double>(64);
+  c->partial = cv.take<double>(kRedBlocks * 8);
+  c->sc = cv.take<IpmScalars>(1);
+  c->status = cv.take<int32_t>(ST_COUNT);
+  c->L = cv.take<char>((size_t)pl.l_entries * c->storage_bytes);
+  c->U = cv.take<char>((size_t)pl.u_entries * c->storage_bytes);
+  c->ws_need = cv.off + 256;
+}
+
+double d2h_scalar(ipm_ctx *c, const double *p) {
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return v;
+}
+
+// ---- factor ----------------------------------------------------------------
+ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
+  if (c->state < 3) throw Fail{IPM_ERR_STATE, "kkt_factor before kkt_assemble"};
+  if (prec < IPM_FP64 || prec > IPM_BF16) throw Fail{IPM_ERR_ARG, "unknown precision"};
+  if (prec == IPM_FP64 && c->storage_bytes < 8)
+    throw Fail{IPM_ERR_NOMEM, "factor storage sized for FP32; FP64 factor needs storage_fp64"};
+  int32_t init[ST_COUNT] = {INT32_MAX, 0, 0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(c->status, init, sizeof(init), cudaMemcpyHostToDevice, c->st));
+  if (prec == IPM_FP64) {
+    launch_factor_simt<double>(c->dp, c->plan, c->kval, (double *)c->L, (double *)c->U, c->status,
+                               false, c->st);
+  } else if (prec == IPM_FP32) {
+    launch_factor_simt<float>(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->status,
+                              true, c->st);
+  } else {
+    if (!c->tcp.ready()) throw Fail{IPM_ERR_UNSUPPORTED, "tensor-core factor not prepared"};
+    c->tcp.factor(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->status,
+                  prec == IPM_BF16, c->st);
+  }
+  CK(cudaGetLastError());
+  int32_t out[ST_COUNT];
+  CK(cudaMemcpyAsync(out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->last_perturbed = out[ST_PERTURBED];
+  c->factor_prec = prec;
+  c->state = 4;
+  if (bad_col) *bad_col = out[ST_FAIL_COL] == INT32_MAX ? -1 : out[ST_FAIL_COL];
+  if (out[ST_FAIL_COL] != INT32_MAX) {
+    c->err = "non-positive pivot at column " + std::to_string(out[ST_FAIL_COL]);
+    return IPM_ERR_NOT_SPD;
+  }
+  return IPM_OK;
+}
+
+// out = M^{-1} b with the current factor (b, out: original numbering, device)
+void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
+  VecOps V = c->vec();
+  if (c->storage_bytes == 8 && c->factor_prec == IPM_FP64) {
+    V.permute_in<double>(b, nullptr, c->yv);
+    launch_solve<double, double>(c->dp, c->plan, (const double *)c->L, c->yv, c->tv, c->st);
+    V.permute_out<double>(c->yv, nullptr, out, accumulate);
+  } else {
+    double *scale = c->scal + 8, *amax = c->scal + 9;
+    V.absmax(c->P.n, b, amax);
+    V.inv_scale(amax, scale);
+    float *y = reinterpret_cast<float *>(c->yv);
+    float *t = reinterpret_cast<float *>(c->tv);
+    V.permute_in<float>(b, scale, y);
+    launch_solve<float, float>(c->dp, c->plan, (const float *)c->L, y, t, c->st);
+    V.permute_out<float>(y, scale, out, accumulate);
+  }
+}
+
+// ---- solve with refinement / PCG ----------------------------------------------
+ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solve_info *info) {
+  if (c->state < 4) throw Fail{IPM_ERR_STATE, "kkt_solve before kkt_factor"};
+  VecOps V = c->vec();
+  const int64_t n = c->P.n;
+  const ipm_options &o = c->opts;
+  double *bb = c->vb, *r = c->vr, *z = c->vz, *p = c->vp, *q = c->vq, *xx = c->vx;
+  CK(cudaMemcpyAsync(bb, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  double *sN = c->scal;  // scalars: 0 |b|, 1 |r|, 2 rz, 3 pq, 4 rz_new
+  V.absmax(n, bb, sN + 0);
+  const double bn = d2h_scalar(c, sN + 0);
+  if (info) *info = ipm_solve_info{0, 0, 0.0};
+  if (bn == 0.0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->st));
+    c->last_rel = 0.0;
+    return IPM_OK;
+  }
+  auto residual = [&](const double *xv) {
+    V.residual(c->cur_jvals, c->cur_D, c->cur_wvals, c->cur_delta_p, xv, bb, r, c->vtA);
+    V.absmax(n, r, sN + 1);
+    return d2h_scalar(c, sN + 1) / bn;
+  };
+  apply_factor(c, bb, xx, false);
+  double rel = residual(xx);
+  int iters = 0, used_pcg = 0;
+  if (refine != IPM_REFINE_NONE && refine != IPM_REFINE_PCG) {
+    double prev = rel;
+    int slow = 0;
+    while (rel > o.ir_tol && iters < o.ir_max) {
+      apply_factor(c, r, xx, true);
+      iters++;
+      rel = residual(xx);
+      if (!(rel < 0.5 * prev)) slow++;
+      else slow = 0;
+      prev = std::min(prev, rel);
+      if (slow >= 2 || !std::isfinite(rel)) break;
+    }
+    c->refine_steps += iters;
+  }
+  if ((refine == IPM_REFINE_PCG || refine == IPM_REFINE_IR) && (rel > o.ir_tol || !std::isfinite(rel))) {
+    // PCG on K x = b preconditioned by the factor, from the current x
+    if (!std::isfinite(rel)) {
+      CK(cudaMemsetAsync(xx, 0, n * sizeof(double), c->st));
+      rel = residual(xx);
+    }
+    used_pcg = 1;
+    CK(cudaMemsetAsync(c->vc, 0, n * sizeof(double), c->st));  // zero right-hand side for q = K p
+    apply_factor(c, r, z, false);
+    CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    V.dot(n, r, z, sN + 2);
+    int k = 0;
+    for (; k < o.pcg_max && rel > o.ir_tol; k++) {
+      // q = K p  (residual of b = 0 gives -K p)
+      V.residual(c->cur_jvals, c->cur_D, c->cur_wvals, c->cur_delta_p, p, c->vc, q, c->vtA);
+      V.negate(n, q);
+      V.dot(n, p, q, sN + 3);
+      V.axpy_ratio(n, sN + 2, sN + 3, +1, p, xx);
+      V.axpy_ratio(n, sN + 2, sN + 3, -1, q, r);
+      V.absmax(n, r, sN + 1);
+      rel = d2h_scalar(c, sN + 1) / bn;
+      if (rel <= o.ir_tol || !std::isfinite(rel)) { k++; break; }
+      apply_factor(c, r, z, false);
+      V.dot(n, r, z, sN + 4);
+      V.xpby_ratio(n, sN + 4, sN + 2, z, p);
+      CK(cudaMemcpyAsync(sN + 2, sN + 4, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    }
+    c->pcg_steps += k;
+    iters += k;
+    rel = residual(xx);  // true residual of the returned iterate
+  }
+  CK(cudaMemcpyAsync(x, xx, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaGetLastError());
+  c->last_rel = rel;
+  if (info) *info = ipm_solve_info{iters, used_pcg, rel};
+  if (!(rel <= o.accept_tol)) {
+    c->err = "linear solve residual " + std::to_string(rel) + " above accept_tol";
+    return IPM_ERR_NUMERIC;
+  }
+  return IPM_OK;
+}
+
+void set_assembly(ipm_ctx *c, const double *wv, const double *jv, const double *D, double dp) {
+  c->cur_jvals = jv;
+  c->cur_D = D;
+  c->cur_wvals = wv;
+  c->cur_delta_p = dp;
+  launch_assemble(c->dp, jv, D, wv, dp, c->kval, c->st);
+  CK(cudaGetLastError());
+  if (c->state < 3) c->state = 3;
+}
+
+// Newton direction at (x, s, lambda) with target w (w == nullptr: zero), reusing
+// the factor held by the context (assembled with D = (delta_d + s/lambda)^{-1}).
+ipm_status direction(ipm_ctx *c, const double *jvals, const double *b, const double *cc,
+                     const double *wvals, const double *x, const double *s, const double *lam,
+                     const double *w, double *dx, double *ds, double *dl, ipm_solve_info *si) {
+  VecOps V = c->vec();
+  V.rhs_rows(c->vD, c->vg, w, lam, c->vt);
+  V.jtv(jvals, c->vt, 1.0, wvals, x, cc, c->vrd);  // r_p = c + W x + J^T (D (g - w/lam) - lam)
+  V.negate(c->P.n, c->vrd);
+  ipm_status stt = do_solve(c, c->vrd, dx, c->opts.refine, si);
+  V.jv(jvals, dx, c->vjx);
+  V.jfull(c->vjx, dx, c->vjd);
+  V.recover(c->vD, c->vg, w, s, lam, c->vjd, ds, dl);
+  (void)b;
+  return stt;
+}
+
+void eval_g(ipm_ctx *c, const double *jvals, const double *b, const double *x) {
+  VecOps V = c->vec();
+  V.jv(jvals, x, c->vjx);
+  V.g(c->vjx, x, b, c->dl_, c->du_, c->vg);
+}
+
+// Factor with the regularisation raised after a non-positive pivot (inertia
+// correction reduced to "Cholesky succeeds" for the SPD condensed system).
+ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jvals, int prec,
+                             double &delta_p, ipm_result *res) {
+  for (int tries = 0;; tries++) {
+    set_assembly(c, wvals, jvals, c->vD, delta_p);
+    int32_t bad = -1;
+    ipm_status stt = do_factor(c, prec, &bad);
+    if (res) {
+      res->factorizations++;
+      res->perturbed_pivots += c->last_perturbed;
+    }
+    if (stt == IPM_OK) return IPM_OK;
+    if (stt != IPM_ERR_NOT_SPD || tries >= 12) return stt;
+    delta_p = delta_p > 0 ? delta_p * 100.0 : 1e-8;
+    if (res) res->regularizations++;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void ipm_default_options(ipm_options *o) {
+  if (!o) return;
+  o->max_iter = 500;
+  o->tol = 1e-8;
+  o->delta_p = 1e-8;
+  o->delta_d = 1e-8;
+  o->precision = IPM_FP64;
+  o->storage_fp64 = -1;
+  o->refine = IPM_REFINE_IR;
+  o->ir_max = 10;
+  o->ir_tol = 1e-10;
+  o->pcg_max = 100;
+  o->fallback_fp64 = 0;
+  o->accept_tol = 1e-6;
+  o->verbose = 0;
+  o->warm_start = 0;
+}
+
+ipm_status ipm_create(int32_t n, int32_t m, const int64_t *jp, const int32_t *ji,
+                      const int64_t *wp, const int32_t *wi, const double *l, const double *u,
+                      const ipm_options *opts, void *stream, ipm_ctx **out) {
+  if (!out || n < 0 || m < 0 || (m > 0 && (!jp || !ji)) || ((wp == nullptr) != (wi == nullptr)))
+    return IPM_ERR_ARG;
+  *out = nullptr;
+  ipm_ctx *c = new (std::nothrow) ipm_ctx();
+  if (!c) return IPM_ERR_NOMEM;
+  ipm_status st = guarded(c, [&]() -> ipm_status {
+    if (opts) c->opts = *opts;
+    else ipm_default_options(&c->opts);
+    c->st = (cudaStream_t)stream;
+    Problem &P = c->P;
+    P.n = n;
+    P.m = m;
+    P.jp.assign(jp ? jp : nullptr, jp ? jp + m + 1 : nullptr);
+    if (m == 0) P.jp.assign(1, 0);
+    if (P.jp[0] != 0) throw Fail{IPM_ERR_ARG, "J row pointer must start at 0"};
+    const int64_t nnz = P.jp[m];
+    P.ji.assign(ji ? ji : nullptr, ji ? ji + nnz : nullptr);
+    P.jrow.resize(nnz);
+    for (int32_t r = 0; r < m; r++) {
+      if (P.jp[r + 1] < P.jp[r]) throw Fail{IPM_ERR_ARG, "J row pointer not monotone"};
+      for (int64_t e = P.jp[r]; e < P.jp[r + 1]; e++) {
+        if (P.ji[e] < 0 || P.ji[e] >= n) throw Fail{IPM_ERR_ARG, "J column index out of range"};
+        if (e > P.jp[r] && P.ji[e] <= P.ji[e - 1])
+          throw Fail{IPM_ERR_ARG, "J columns must be strictly ascending within a row"};
+        P.jrow[e] = r;
+      }
+    }
+    P.jtp.assign(n + 1, 0);
+    for (int64_t e = 0; e < nnz; e++) P.jtp[P.ji[e] + 1]++;
+    for (int32_t j = 0; j < n; j++) P.jtp[j + 1] += P.jtp[j];
+    P.jtpos.resize(nnz);
+    {
+      std::vector<int64_t> f(P.jtp.begin(), P.jtp.end() - 1);
+      for (int64_t e = 0; e < nnz; e++) P.jtpos[f[P.ji[e]]++] = (int32_t)e;
+    }
+    if (wp) {
+      P.wp.assign(wp, wp + n + 1);
+      P.wi.assign(wi, wi + wp[n]);
+      for (int32_t j = 0; j < n; j++)
+        for (int64_t e = wp[j]; e < wp[j + 1]; e++)
+          if (wi[e] < j || wi[e] >= n) throw Fail{IPM_ERR_ARG, "W must be lower CSC"};
+    }
+    P.l.assign(n, -INFINITY);
+    P.u.assign(n, INFINITY);
+    if (l) P.l.assign(l, l + n);
+    if (u) P.u.assign(u, u + n);
+    P.lpos.assign(n, -1);
+    P.upos.assign(n, -1);
+    P.lidx.clear();
+    P.uidx.clear();
+    for (int32_t i = 0; i < n; i++) if (std::isfinite(P.l[i])) P.lidx.push_back(i);
+    for (int32_t i = 0; i < n; i++) if (std::isfinite(P.u[i])) P.uidx.push_back(i);
+    P.nl = (int32_t)P.lidx.size();
+    P.nu = (int32_t)P.uidx.size();
+    P.mt = (int64_t)m + P.nl + P.nu;
+    for (int32_t k = 0; k < P.nl; k++) P.lpos[P.lidx[k]] = m + k;
+    for (int32_t k = 0; k < P.nu; k++) P.upos[P.uidx[k]] = m + P.nl + k;
+    c->state = 0;
+    return IPM_OK;
+  });
+  if (st != IPM_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return IPM_OK;
+}
+
+ipm_status kkt_analyze(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info) {
+  if (!c) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    const int32_t n = c->P.n;
+    if (perm) {
+      std::vector<char> seen(n, 0);
+      for (int32_t k = 0; k < n; k++) {
+        if (perm[k] < 0 || perm[k] >= n || seen[perm[k]]) throw Fail{IPM_ERR_ARG, "perm is not a permutation"};
+        seen[perm[k]] = 1;
+      }
+    }
+    analyze_symbolic(c->P, perm, c->S);
+    build_plan(c->P, c->S, c->plan, 64, 64);
+    validate_plan(c->P, c->S, c->plan);
+    c->tcp.build(c->plan);
+    const int so = c->opts.storage_fp64;
+    c->storage_bytes = (so == 1 || (so < 0 && (c->opts.precision == IPM_FP64 || c->opts.fallback_fp64))) ? 8 : 4;
+    layout(c, nullptr);
+    c->state = 1;
+    if (info) {
+      info->n = n;
+      info->m_tot = c->P.mt;
+      info->nnz_k = (int64_t)c->S.koi.size();
+      info->nnz_l = c->S.nnz_l;
+      info->nsuper = c->S.nsuper;
+      info->nlevels = c->S.nlevels;
+      info->max_front = c->plan.max_front;
+      info->max_ncol = c->plan.max_ncol;
+      info->flops = c->S.flops;
+      info->factor_entries = c->plan.l_entries;
+      info->update_entries = c->plan.u_entries;
+      info->workspace_bytes = (int64_t)c->ws_need;
+    }
+    return IPM_OK;
+  });
+}
+
+ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
+  if (!c || !buf) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 1) throw Fail{IPM_ERR_STATE, "ipm_set_workspace before kkt_analyze"};
+    if (bytes < c->ws_need)
+      throw Fail{IPM_ERR_NOMEM, "workspace of " + std::to_string(bytes) + " bytes, need " +
+                                    std::to_string(c->ws_need)};
+    char *base = (char *)(((uintptr_t)buf + 255) & ~uintptr_t(255));
+    if ((size_t)(base - (char *)buf) + c->ws_need - 256 > bytes) throw Fail{IPM_ERR_NOMEM, "workspace misaligned"};
+    c->ws = base;
+    c->ws_bytes = bytes;
+    layout(c, base);
+    CK(cudaStreamSynchronize(c->st));
+    c->state = 2;
+    return IPM_OK;
+  });
+}
+
+ipm_status kkt_assemble(ipm_ctx *c, const double *wv, const double *jv, const double *D,
+                        double delta_p) {
+  if (!c) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 2) throw Fail{IPM_ERR_STATE, "kkt_assemble before ipm_set_workspace"};
+    if ((!jv && c->P.jp.back() > 0) || (!D && c->P.mt > 0)) throw Fail{IPM_ERR_ARG, "null values"};
+    // keep copies: refinement in kkt_solve evaluates K x from J, D and W
+    const int64_t nj = c->P.jp.back(), nw = c->P.wp.empty() ? 0 : c->P.wp.back();
+    if (nj > 0) CK(cudaMemcpyAsync(c->jv_copy, jv, nj * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (c->P.mt > 0) CK(cudaMemcpyAsync(c->D_copy, D, c->P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (wv && nw > 0) CK(cudaMemcpyAsync(c->wv_copy, wv, nw * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    set_assembly(c, wv ? c->wv_copy : nullptr, c->jv_copy, c->D_copy, delta_p);
+    c->state = 3;
+    return IPM_OK;
+  });
+}
+
+ipm_status kkt_factor(ipm_ctx *c, int32_t precision, int32_t *bad_col) {
+  if (!c) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status { return do_factor(c, precision, bad_col); });
+}
+
+ipm_status kkt_solve(ipm_ctx *c, const double *b, double *x, int32_t refine, ipm_solve_info *info) {
+  if (!c || !b || !x) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status { return do_solve(c, b, x, refine, info); });
+}
+
+ipm_status ipm_newton_direction(ipm_ctx *c, const double *jv, const double *b, const double *cc,
+                                const double *wv, const double *x, const double *s,
+                                const double *lam, const double *w, double *dx, double *ds,
+                                double *dl) {
+  if (!c) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 2) throw Fail{IPM_ERR_STATE, "ipm_newton_direction before ipm_set_workspace"};
+    VecOps V = c->vec();
+    eval_g(c, jv, b, x);
+    V.scaling(s, lam, c->opts.delta_d, c->vD);
+    double delta_p = c->opts.delta_p;
+    ipm_status stt = factor_with_retry(c, wv, jv, c->opts.precision, delta_p, nullptr);
+    if (stt != IPM_OK) return stt;
+    return direction(c, jv, b, cc, wv, x, s, lam, w, dx, ds, dl, nullptr);
+  });
+}
+
+ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double *cc,
+                     const double *wv, double *x, double *s, double *lam, ipm_result *res_out) {
+  if (!c || !x || !s || !lam || !cc) return IPM_ERR_ARG;
+  ipm_result res{};
+  ipm_status rs = guarded(c, [&]() -> ipm_status {
+    if (c->state < 2) throw Fail{IPM_ERR_STATE, "ipm_solve before ipm_set_workspace"};
+    const auto t_start = std::chrono::steady_clock::now();
+    const Problem &P = c->P;
+    const ipm_options &o = c->opts;
+    VecOps V = c->vec();
+    c->refine_steps = c->pcg_steps = 0;
+    // starting point (unless warm-started from the caller's x, s, lambda)
+    if (!o.warm_start) {
+      std::vector<double> x0(P.n);
+      for (int32_t i = 0; i < P.n; i++) {
+        const bool fl = std::isfinite(P.l[i]), fu = std::isfinite(P.u[i]);
+        if (fl && fu) x0[i] = 0.5 * (P.l[i] + P.u[i]);
+        else if (fl) x0[i] = std::max(0.0, P.l[i] + 1.0);
+        else if (fu) x0[i] = std::min(0.0, P.u[i] - 1.0);
+        else x0[i] = 0.0;
+      }
+      CK(cudaMemcpyAsync(x, x0.data(), P.n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      eval_g(c, jv, b, x);
+      V.init_slack(c->vg, s, lam);
+    }
+    // scales of the KKT residual
+    double bscale = 1.0, cscale = 1.0;
+    {
+      V.absmax(P.m, b, c->scal + 20);
+      V.absmax(P.n, cc, c->scal + 21);
+      double bm = P.m > 0 ? d2h_scalar(c, c->scal + 20) : 0.0, cm = d2h_scalar(c, c->scal + 21);
+      for (int32_t k = 0; k < P.nl; k++) bm = std::max(bm, std::fabs(P.l[P.lidx[k]]));
+      for (int32_t k = 0; k < P.nu; k++) bm = std::max(bm, std::fabs(P.u[P.uidx[k]]));
+      bscale = std::max(1.0, bm);
+      cscale = std::max(1.0, cm);
+    }
+    cudaEvent_t ev[6];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    double delta_p = o.delta_p;
+    res.status = IPM_ERR_MAXITER;
+    ipm_status stt = IPM_OK;
+    int it = 0;
+    for (it = 0; it <= o.max_iter; it++) {
+      eval_g(c, jv, b, x);
+      V.jtv(jv, lam, -1.0, wv, x, cc, c->vrd);  // rd = c + W x - J^T lambda
+      if (wv) V.jtv(jv, lam, 0.0, wv, x, nullptr, c->vwx);  // W x
+      V.kkt(c->vg, s, lam, c->vrd, cc, wv ? c->vwx : nullptr, x, c->scal + 24, c->sc);
+      IpmScalars h;
+      CK(cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      const double fs = std::max(1.0, std::fabs(h.fx));
+      res.primal_res = h.primal_inf / bscale;
+      res.dual_res = h.dual_inf / cscale;
+      res.compl_res = h.compl_inf / fs;
+      res.kkt = std::max(res.primal_res, std::max(res.dual_res, res.compl_res));
+      res.objective = h.fx;
+      res.mu = h.mu;
+      if (o.verbose)
+        std::fprintf(stderr, "ipm it %3d f % .10e kkt %.3e (p %.2e d %.2e c %.2e) mu %.2e\n", it,
+                     h.fx, res.kkt, res.primal_res, res.dual_res, res.compl_res, h.mu);
+      if (!std::isfinite(res.kkt)) { res.status = IPM_ERR_NUMERIC; break; }
+      if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
+      if (it == o.max_iter) break;
+      CK(cudaEventRecord(ev[0], c->st));
+      V.scaling(s, lam, o.delta_d, c->vD);
+      CK(cudaEventRecord(ev[1], c->st));
+      stt = factor_with_retry(c, wv, jv, o.precision, delta_p, &res);
+      CK(cudaEventRecord(ev[2], c->st));
+      if (stt != IPM_OK) { res.status = stt; break; }
+      // predictor (w = 0)
+      ipm_solve_info si{};
+      stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
+      res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
+      if (stt != IPM_OK && o.fallback_fp64 && o.precision != IPM_FP64 && c->storage_bytes == 8) {
+        res.fp64_fallbacks++;
+        stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
+        if (stt == IPM_OK)
+          stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
+      }
+      if (stt != IPM_OK) { res.status = stt; break; }
+      V.ftb(s, c->vds, lam, c->vdl, c->scal + 32, c->sc, true);
+      V.muaff(s, c->vds, lam, c->vdl, c->scal + 34, c->sc);
+      // corrector: w = sigma mu - ds_aff .* dl_aff
+      V.corrector_target(c->vds, c->vdl, c->sc, c->vw);
+      stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+      res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
+      if (stt != IPM_OK) { res.status = stt; break; }
+      CK(cudaEventRecord(ev[3], c->st));
+      V.ftb(s, c->vds, lam, c->vdl, c->scal + 32, c->sc, false);
+      V.update(c->sc, x, c->vdx, s, c->vds, lam, c->vdl);
+      CK(cudaEventRecord(ev[4], c->st));
+      CK(cudaEventSynchronize(ev[4]));
+      float ms[4];
+      for (int k = 0; k < 4; k++) CK(cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]));
+      res.time_assemble_ms += ms[0];
+      res.time_factor_ms += ms[1];
+      res.time_solve_ms += ms[2];
+      res.time_other_ms += ms[3];
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    CK(cudaStreamSynchronize(c->st));
+    res.iterations = it;
+    res.refine_steps = (int32_t)c->refine_steps;
+    res.pcg_steps = (int32_t)c->pcg_steps;
+    res.time_total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    return (ipm_status)res.status;
+  });
+  if (rs != IPM_OK && res.status == IPM_OK) res.status = rs;
+  if (res_out) *res_out = res;
+  return rs;
+}
+
+ipm_status kkt_symbolic_export(const ipm_ctx *c, int32_t *perm, int32_t *parent, int32_t *colcount,
+                               int32_t *super, int32_t *sparent, int32_t *slevel, int64_t *srp,
+                               int32_t *sri) {
+  if (!c || c->state < 1) return c ? IPM_ERR_STATE : IPM_ERR_ARG;
+  const Symbolic &S = c->S;
+  auto cp = [](auto *dst, const auto &v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
+  cp(perm, S.perm);
+  cp(parent, S.parent);
+  cp(colcount, S.colcount);
+  cp(super, S.super);
+  cp(sparent, S.sparent);
+  cp(slevel, S.slevel);
+  cp(srp, S.srp);
+  cp(sri, S.sri);
+  return IPM_OK;
+}
+
+ipm_status kkt_export_assembled(ipm_ctx *c, double *h_out) {
+  if (!c || !h_out) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 3) throw Fail{IPM_ERR_STATE, "nothing assembled"};
+    const int64_t nk = c->dp.nk;
+    std::vector<double> tmp(nk);
+    CK(cudaMemcpyAsync(tmp.data(), c->kval, nk * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int64_t q = 0; q < nk; q++) h_out[c->plan.k_orig[q]] = tmp[q];
+    return IPM_OK;
+  });
+}
+
+ipm_status kkt_factor_entries(ipm_ctx *c, int64_t count, const int32_t *rows, const int32_t *cols,
+                              double *out) {
+  if (!c || count < 0 || (count > 0 && (!rows || !cols || !out))) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 4) throw Fail{IPM_ERR_STATE, "no factor"};
+    if (count == 0) return IPM_OK;
+    int32_t *dr = nullptr, *dc = nullptr;
+    double *dout = nullptr;
+    CK(cudaMallocAsync(&dr, count * sizeof(int32_t), c->st));
+    CK(cudaMallocAsync(&dc, count * sizeof(int32_t), c->st));
+    CK(cudaMallocAsync(&dout, count * sizeof(double), c->st));
+    CK(cudaMemcpyAsync(dr, rows, count * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(dc, cols, count * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+    if (c->factor_prec == IPM_FP64)
+      launch_factor_entries<double>(c->dp, (const double *)c->L, c->col2s, count, dr, dc, dout, c->st);
+    else
+      launch_factor_entries<float>(c->dp, (const float *)c->L, c->col2s, count, dr, dc, dout, c->st);
+    CK(cudaMemcpyAsync(out, dout, count * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaFreeAsync(dr, c->st));
+    CK(cudaFreeAsync(dc, c->st));
+    CK(cudaFreeAsync(dout, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return IPM_OK;
+  });
+}
+
+int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0; }
+
+const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void ipm_destroy(ipm_ctx *c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,51 @@
+// Device-side views shared by the kernels and the host launchers.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gipm {
+
+// Device pointers of the plan and problem structure (all inside the caller's workspace).
+struct DevPlan {
+  const FrontInfo *fronts;
+  const int32_t *children, *inv, *relpos, *sri;
+  const Task *build, *gemm, *potrf, *trsm, *syrk, *gath, *sdiag, *sgemv, *rgemv;
+  const int64_t *toff;
+  const int64_t *k_slot, *k_poff, *k_w, *k_orig;
+  const int32_t *k_pa, *k_pb, *k_diag;
+  const int32_t *perm;  // final new -> old
+  // problem structure
+  const int64_t *jp, *jtp;
+  const int32_t *ji, *jrow, *jtpos;
+  const int64_t *wfp;    // W, both triangles, CSR (for matrix-free products)
+  const int32_t *wfi;
+  const int64_t *wfsrc;  // index of each full-W entry in the caller's lower-CSC values
+  const int32_t *lpos, *upos;  // per variable: row of its bound in g, or -1
+  const int32_t *lidx, *uidx;  // per bound row: its variable
+  int32_t n, m, nl, nu;
+  int64_t mt, nk;
+};
+
+// Status words written by kernels (one int32 array in device memory).
+enum StatusWord : int {
+  ST_FAIL_COL = 0,   // smallest column with a non-positive pivot (INT32_MAX if none)
+  ST_PERTURBED = 1,  // pivots replaced by the low-precision factorisation
+  ST_COUNT = 8
+};
+
+constexpr int kBuildTile = 32;
+constexpr int kGemmTile = 64;
+constexpr int kTrsmRows = 128;
+constexpr int kGathPos = 256;
+constexpr int kSolveRows = 128;
+constexpr int kSolveCols = 256;
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+}  // namespace gipm

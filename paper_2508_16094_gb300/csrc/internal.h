@@ -1,0 +1,116 @@
+// Internal data structures of the solver library (host + device).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace gipm {
+
+// ---------------------------------------------------------------------------
+// Symbolic analysis (host). Final numbering = given ordering + etree postorder.
+// ---------------------------------------------------------------------------
+struct Symbolic {
+  int32_t n = 0;
+  std::vector<int32_t> perm, iperm;       // final new->old, old->new
+  std::vector<int32_t> parent, colcount;  // elimination tree, column counts (incl. diagonal)
+  // lower CSC pattern of K in the ORIGINAL numbering (export order)
+  std::vector<int64_t> kop;
+  std::vector<int32_t> koi;
+  // supernodes
+  int32_t nsuper = 0, nlevels = 0;
+  std::vector<int32_t> super, sparent, slevel;
+  std::vector<int64_t> srp;  // row structure of each supernode (rows below its columns)
+  std::vector<int32_t> sri;
+  int64_t nnz_l = 0;
+  double flops = 0.0;
+};
+
+// Per-supernode layout of the frontal matrices (device-visible, 64 bytes).
+// Front of supernode s: order nf = ncol + nrow; local index p < ncol is column
+// first + p, p >= ncol is row sri[rows_off + p - ncol]. The first ncol columns
+// live in the panel (row-major, nf rows x ld), the trailing nrow x nrow block
+// (the update matrix handed to the parent) lives in U storage (row-major, uld).
+struct FrontInfo {
+  int64_t loff;      // panel offset in the factor storage (elements)
+  int64_t uoff;      // update matrix offset in the update storage (elements)
+  int64_t rows_off;  // offset of the row structure in sri
+  int64_t inv_off;   // offset of this front's map into its parent's front (length nf(parent))
+  int32_t first, ncol, nrow, ld;
+  int32_t uld, child_begin, child_end, parent;
+};
+static_assert(sizeof(FrontInfo) == 64, "FrontInfo layout");
+
+// A unit of work of a batched kernel: meaning of a/b depends on the kernel.
+struct Task {
+  int32_t front, a, b, c;
+};
+
+// Work of one level of the supernodal tree, as ranges into the task arrays.
+struct StepRange {
+  int32_t gemm_b, gemm_e, potrf_b, potrf_e, trsm_b, trsm_e;
+};
+struct LevelPlan {
+  int32_t front_b = 0, front_e = 0;  // into the level-ordered front list
+  int32_t build_b = 0, build_e = 0;  // front-assembly tiles
+  int64_t k_b = 0, k_e = 0;          // K entries of this level's fronts
+  int32_t syrk_b = 0, syrk_e = 0;    // update-matrix tiles
+  int32_t gath_b = 0, gath_e = 0;    // solve gather tasks
+  int32_t rg_b = 0, rg_e = 0;        // backward-solve tasks on the rows below the block
+  int32_t sdiag_b = 0, sdiag_e = 0;  // solve diagonal-block tasks, by step: see solve_steps
+  std::vector<StepRange> steps;      // factor steps (block columns)
+  std::vector<int32_t> sstep_b;      // solve steps: [sstep_b[j], sstep_b[j+1]) in stasks
+  std::vector<int32_t> sgemv_b;      // solve update tasks per step
+  int32_t max_ncol = 0;
+};
+
+// Numeric plan: everything the kernels need, built on the host by analysis.
+struct Plan {
+  int nb = 64;                       // factor block width
+  int nbs = 64;                      // solve block width
+  std::vector<FrontInfo> fronts;     // by supernode index
+  std::vector<int32_t> sched;        // schedule level of each supernode (parent = child + 1)
+  std::vector<int32_t> level_fronts; // supernodes sorted by (schedule level, index)
+  std::vector<int32_t> children;     // child lists (ascending), ranges in FrontInfo
+  std::vector<int32_t> inv;          // child -> parent-front inverse maps
+  std::vector<int32_t> relpos;       // child row -> position in parent's front (by sri offset)
+  std::vector<LevelPlan> levels;
+  std::vector<Task> build_tasks, gemm_tasks, potrf_tasks, trsm_tasks, syrk_tasks;
+  std::vector<Task> gath_tasks, sdiag_tasks, sgemv_tasks, rgemv_tasks;
+  std::vector<int64_t> toff;         // per front: offset of its solve update vector (length nrow)
+  int64_t t_entries = 0;
+  // K entries in level-major order
+  std::vector<int64_t> k_slot;   // element offset of L(i, j) in the factor storage
+  std::vector<int64_t> k_poff;   // products [k_poff[q], k_poff[q+1])
+  std::vector<int32_t> k_pa, k_pb;  // CSR positions of the two J factors of each product
+  std::vector<int64_t> k_w;      // W value index or -1
+  std::vector<int32_t> k_diag;   // original variable index for a diagonal entry, else -1
+  std::vector<int64_t> k_orig;   // original lower-CSC entry index (export order)
+  int64_t l_entries = 0, u_entries = 0;
+  int32_t max_front = 0, max_ncol = 0;
+};
+
+// Problem description kept by the context (host copies).
+struct Problem {
+  int32_t n = 0, m = 0;
+  std::vector<int64_t> jp;
+  std::vector<int32_t> ji;
+  std::vector<int32_t> jrow;         // row of each CSR position
+  std::vector<int64_t> jtp;          // CSC of J: column pointers
+  std::vector<int32_t> jtpos;        // CSR position of each CSC entry
+  std::vector<int64_t> wp;
+  std::vector<int32_t> wi;
+  std::vector<double> l, u;
+  int32_t nl = 0, nu = 0;
+  int64_t mt = 0;
+  std::vector<int32_t> lidx, uidx;   // variables with a finite lower/upper bound
+  std::vector<int32_t> lpos, upos;   // per variable: row of its bound in g (or -1)
+};
+
+void analyze_symbolic(const Problem &P, const int32_t *perm, Symbolic &S);
+void build_plan(const Problem &P, const Symbolic &S, Plan &plan, int nb, int nbs);
+void validate_plan(const Problem &P, const Symbolic &S, const Plan &plan);
+
+}  // namespace gipm

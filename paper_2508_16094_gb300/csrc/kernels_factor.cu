@@ -1,0 +1,351 @@
+// Assembly of the primal condensed matrix (Eq. 5) and the level-scheduled
+// multifrontal supernodal Cholesky (Sec. 2: pivoting-free factorisation with
+// elimination-tree parallelism), SIMT FMA path for FP64 and FP32.
+//
+// Per level of the supernodal tree: build every frontal matrix of the level
+// (gather of the children's update matrices, each entry written once), add the
+// K entries owned by the level, then factor the fronts' panels block column by
+// block column (left-looking GEMM update, Cholesky of the diagonal block,
+// triangular solve of the rows below) and form their update matrices
+// U = F22 - L21 L21^T (SYRK). No atomics on values: results are bit-reproducible.
+#include <cfloat>
+#include <climits>
+
+#include "launch.h"
+
+namespace gipm {
+
+namespace {
+
+__global__ void assemble_kernel(DevPlan dp, const double *__restrict__ jv,
+                                const double *__restrict__ D, const double *__restrict__ wv,
+                                double delta_p, double *__restrict__ kval) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < dp.nk;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    const int64_t p1 = dp.k_poff[q + 1];
+    for (int64_t p = dp.k_poff[q]; p < p1; p++) {
+      const int32_t a = dp.k_pa[p], b = dp.k_pb[p];
+      v = fma(jv[a] * D[dp.jrow[a]], jv[b], v);
+    }
+    const int64_t w = dp.k_w[q];
+    if (w >= 0 && wv) v += wv[w];
+    const int32_t i = dp.k_diag[q];
+    if (i >= 0) {
+      double d = delta_p;
+      if (dp.lpos[i] >= 0) d += D[dp.lpos[i]];
+      if (dp.upos[i] >= 0) d += D[dp.upos[i]];
+      v += d;
+    }
+    kval[q] = v;
+  }
+}
+
+// Front assembly: one 32x32 tile of a front's lower triangle per block. Each
+// entry is the sum, over the children in ascending order, of the matching
+// entry of the child's update matrix (through the child->front inverse map).
+template <typename T>
+__global__ void __launch_bounds__(256) build_front_kernel(DevPlan dp, int32_t task0,
+                                                          T *__restrict__ L, T *__restrict__ U) {
+  const Task tk = dp.build[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow;
+  const int r0 = tk.a, c0 = tk.b;
+  __shared__ int32_t rinv[kBuildTile], cinv[kBuildTile];
+  T acc[4] = {0, 0, 0, 0};
+  const int tid = threadIdx.x;
+  for (int ci = F.child_begin; ci < F.child_end; ci++) {
+    const FrontInfo C = dp.fronts[dp.children[ci]];
+    __syncthreads();
+    if (tid < kBuildTile) {
+      rinv[tid] = (r0 + tid < nf) ? dp.inv[C.inv_off + r0 + tid] : -1;
+    } else if (tid < 2 * kBuildTile) {
+      const int c = c0 + tid - kBuildTile;
+      cinv[tid - kBuildTile] = (c < nf) ? dp.inv[C.inv_off + c] : -1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int e = tid + 256 * q, rr = e / kBuildTile, cc = e % kBuildTile;
+      const int a = rinv[rr], b = cinv[cc];
+      if (a >= 0 && b >= 0 && r0 + rr >= c0 + cc) acc[q] += U[C.uoff + (int64_t)a * C.uld + b];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int e = tid + 256 * q, r = r0 + e / kBuildTile, c = c0 + e % kBuildTile;
+    if (r >= nf || c >= nf) continue;
+    if (c < F.ncol) {
+      L[F.loff + (int64_t)r * F.ld + c] = (r >= c) ? acc[q] : T(0);
+    } else if (r >= c) {
+      U[F.uoff + (int64_t)(r - F.ncol) * F.uld + (c - F.ncol)] = acc[q];
+    }
+  }
+}
+
+template <typename T>
+__global__ void kadd_kernel(DevPlan dp, int64_t q0, int64_t q1, const double *__restrict__ kval,
+                            T *__restrict__ L) {
+  for (int64_t q = q0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < q1;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = dp.k_slot[q];
+    L[s] = T((double)L[s] + kval[q]);
+  }
+}
+
+// C[M x N] -= A[M x K] * B[N x K]^T for one 64x64 tile (rows of A and B are
+// contiguous along K), 256 threads, 4x4 outputs per thread.
+template <typename T>
+__device__ __forceinline__ void gemm_nt_tile(T *C, int64_t ldc, const T *A, int64_t lda,
+                                             const T *B, int64_t ldb, int M, int N, int K) {
+  constexpr int BK = 16;
+  __shared__ T As[BK][kGemmTile + 4], Bs[BK][kGemmTile + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int e = tid + 256 * q, r = e / BK, kk = e % BK;
+      As[kk][r] = (r < M && k0 + kk < K) ? A[(int64_t)r * lda + k0 + kk] : T(0);
+      Bs[kk][r] = (r < N && k0 + kk < K) ? B[(int64_t)r * ldb + k0 + kk] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk++) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int r = ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int c = tx + 16 * j;
+      if (c < N) C[(int64_t)r * ldc + c] -= acc[i][j];
+    }
+  }
+}
+
+// Left-looking update of block column k of a panel: rows i0..i0+63 of
+// F[:, k:k+kb] -= L[:, 0:k] * L[k:k+kb, 0:k]^T.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_ll_kernel(DevPlan dp, int32_t task0, int nb,
+                                                      T *__restrict__ L) {
+  const Task tk = dp.gemm[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow, i0 = tk.a, k = tk.b;
+  const int kb = min(nb, F.ncol - k), M = min(kGemmTile, nf - i0);
+  T *P = L + F.loff;
+  gemm_nt_tile<T>(P + (int64_t)i0 * F.ld + k, F.ld, P + (int64_t)i0 * F.ld, F.ld,
+                  P + (int64_t)k * F.ld, F.ld, M, kb, k);
+}
+
+// Update matrix U = F22 - L21 L21^T, one 64x64 lower tile per block.
+template <typename T>
+__global__ void __launch_bounds__(256) syrk_kernel(DevPlan dp, int32_t task0,
+                                                   const T *__restrict__ L, T *__restrict__ U) {
+  const Task tk = dp.syrk[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int i0 = tk.a, j0 = tk.b;
+  const int M = min(kGemmTile, F.nrow - i0), N = min(kGemmTile, F.nrow - j0);
+  const T *P = L + F.loff + (int64_t)F.ncol * F.ld;
+  gemm_nt_tile<T>(U + F.uoff + (int64_t)i0 * F.uld + j0, F.uld, P + (int64_t)i0 * F.ld, F.ld,
+                  P + (int64_t)j0 * F.ld, F.ld, M, N, F.ncol);
+}
+
+template <typename T> __device__ __forceinline__ T big_pivot();
+template <> __device__ __forceinline__ float big_pivot<float>() { return 1e30f; }
+template <> __device__ __forceinline__ double big_pivot<double>() { return 1e64; }
+
+// Cholesky of one diagonal block (kb <= 64) in shared memory. A pivot that is
+// not positive is either reported (smallest failing column kept) or replaced
+// by a large value (static pivoting) and counted.
+template <typename T>
+__global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, int32_t task0, int nb,
+                                                    T *__restrict__ L, int32_t *status,
+                                                    int perturb) {
+  const Task tk = dp.potrf[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int k = tk.a, kb = min(nb, F.ncol - k);
+  T *A = L + F.loff + (int64_t)k * F.ld + k;
+  __shared__ T Ad[64][65];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    if (r >= c) Ad[r][c] = A[(int64_t)r * F.ld + c];
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; j++) {
+    if (tid == 0) {
+      T d = Ad[j][j];
+      if (!(d > T(0)) || !(d < big_pivot<T>() * big_pivot<T>())) {
+        if (perturb) {
+          d = big_pivot<T>();
+          atomicAdd(&status[ST_PERTURBED], 1);
+        } else {
+          atomicMin(&status[ST_FAIL_COL], F.first + k + j);
+          d = T(1);
+        }
+      }
+      Ad[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const T ljj = Ad[j][j];
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i][j] /= ljj;
+    __syncthreads();
+    const int w = kb - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = j + 1 + e / w, c = j + 1 + e % w;
+      if (c <= i) Ad[i][c] = fma(-Ad[i][j], Ad[c][j], Ad[i][c]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    if (r >= c) A[(int64_t)r * F.ld + c] = Ad[r][c];
+  }
+}
+
+// Rows below the diagonal block: X <- X L_kk^{-T} (row-wise forward substitution).
+template <typename T>
+__global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, int32_t task0, int nb,
+                                                         T *__restrict__ L) {
+  const Task tk = dp.trsm[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow, i0 = tk.a, k = tk.b;
+  const int kb = min(nb, F.ncol - k), rows = min(kTrsmRows, nf - i0);
+  extern __shared__ unsigned char smem_raw[];
+  T *Lk = reinterpret_cast<T *>(smem_raw);  // [64][65]
+  T *X = Lk + 64 * 65;                      // [kTrsmRows][65]
+  const T *A = L + F.loff + (int64_t)k * F.ld + k;
+  T *Xg = L + F.loff + (int64_t)i0 * F.ld + k;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    Lk[r * 65 + c] = (r >= c) ? A[(int64_t)r * F.ld + c] : T(0);
+  }
+  for (int e = tid; e < rows * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    X[r * 65 + c] = Xg[(int64_t)r * F.ld + c];
+  }
+  __syncthreads();
+  if (tid < rows) {
+    T *x = X + tid * 65;
+    for (int c = 0; c < kb; c++) {
+      T v = x[c];
+      for (int c2 = 0; c2 < c; c2++) v = fma(-x[c2], Lk[c * 65 + c2], v);
+      x[c] = v / Lk[c * 65 + c];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    Xg[(int64_t)r * F.ld + c] = X[r * 65 + c];
+  }
+}
+
+template <typename T>
+__global__ void entries_kernel(DevPlan dp, const T *__restrict__ L, const int32_t *col2s,
+                               int64_t count, const int32_t *rows, const int32_t *cols,
+                               double *out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = rows[e], j = cols[e];
+    double v = 0.0;
+    if (i >= j && j >= 0 && i < dp.n) {
+      const FrontInfo F = dp.fronts[col2s[j]];
+      int32_t p = -1;
+      if (i < F.first + F.ncol) {
+        p = i - F.first;
+      } else {
+        int lo = 0, hi = F.nrow;  // binary search in the row structure
+        const int32_t *rs = dp.sri + F.rows_off;
+        while (lo < hi) {
+          int mid = (lo + hi) / 2;
+          if (rs[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        if (lo < F.nrow && rs[lo] == i) p = F.ncol + lo;
+      }
+      if (p >= 0) v = (double)L[F.loff + (int64_t)p * F.ld + (j - F.first)];
+    }
+    out[e] = v;
+  }
+}
+
+inline int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
+}  // namespace
+
+void launch_assemble(const DevPlan &dp, const double *jv, const double *D, const double *wv,
+                     double delta_p, double *kval, cudaStream_t st) {
+  if (dp.nk == 0) return;
+  assemble_kernel<<<grid_for(dp.nk, 256), 256, 0, st>>>(dp, jv, D, wv, delta_p, kval);
+}
+
+template <typename T>
+void launch_factor_simt(const DevPlan &dp, const Plan &plan, const double *kval, T *L, T *U,
+                        int32_t *status, bool perturb, cudaStream_t st) {
+  const size_t trsm_smem = (size_t)(64 * 65 + kTrsmRows * 65) * sizeof(T);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)trsm_smem);
+    attr_done = true;
+  }
+  const int nb = plan.nb;
+  for (const LevelPlan &LP : plan.levels) {
+    if (LP.build_e > LP.build_b)
+      build_front_kernel<T><<<LP.build_e - LP.build_b, 256, 0, st>>>(dp, LP.build_b, L, U);
+    if (LP.k_e > LP.k_b)
+      kadd_kernel<T><<<grid_for(LP.k_e - LP.k_b, 256), 256, 0, st>>>(dp, LP.k_b, LP.k_e, kval, L);
+    for (const StepRange &S : LP.steps) {
+      if (S.gemm_e > S.gemm_b)
+        gemm_ll_kernel<T><<<S.gemm_e - S.gemm_b, 256, 0, st>>>(dp, S.gemm_b, nb, L);
+      if (S.potrf_e > S.potrf_b)
+        potrf_kernel<T><<<S.potrf_e - S.potrf_b, 256, 0, st>>>(dp, S.potrf_b, nb, L, status,
+                                                               perturb ? 1 : 0);
+      if (S.trsm_e > S.trsm_b)
+        trsm_kernel<T><<<S.trsm_e - S.trsm_b, kTrsmRows, trsm_smem, st>>>(dp, S.trsm_b, nb, L);
+    }
+    if (LP.syrk_e > LP.syrk_b)
+      syrk_kernel<T><<<LP.syrk_e - LP.syrk_b, 256, 0, st>>>(dp, LP.syrk_b, L, U);
+  }
+}
+
+template <typename T>
+void launch_factor_entries(const DevPlan &dp, const T *L, const int32_t *col2s, int64_t count,
+                           const int32_t *rows, const int32_t *cols, double *out,
+                           cudaStream_t st) {
+  if (count <= 0) return;
+  entries_kernel<T><<<grid_for(count, 256), 256, 0, st>>>(dp, L, col2s, count, rows, cols, out);
+}
+
+template void launch_factor_simt<double>(const DevPlan &, const Plan &, const double *, double *,
+                                         double *, int32_t *, bool, cudaStream_t);
+template void launch_factor_simt<float>(const DevPlan &, const Plan &, const double *, float *,
+                                        float *, int32_t *, bool, cudaStream_t);
+template void launch_factor_entries<double>(const DevPlan &, const double *, const int32_t *,
+                                            int64_t, const int32_t *, const int32_t *, double *,
+                                            cudaStream_t);
+template void launch_factor_entries<float>(const DevPlan &, const float *, const int32_t *,
+                                           int64_t, const int32_t *, const int32_t *, double *,
+                                           cudaStream_t);
+
+}  // namespace gipm

@@ -1,0 +1,192 @@
+// Supernodal triangular solves with the multifrontal factor (Sec. 2: once
+// pivoting is gone, the triangular solves run on the GPU; level scheduling
+// over the elimination tree, Naumov's parallel sparse triangular solve).
+//
+// Forward (L y = b), levels ascending. Each front first gathers its children's
+// update vectors (entries on its own columns are subtracted from y, entries on
+// its rows below are summed into its own update vector), then block column by
+// block column: solve the diagonal block, then warp-cooperative dot products
+// with the rows below (its own later columns -> y, rows below -> update vector).
+// Backward (L^T x = y), levels descending: subtract L21^T x(rows below) with a
+// fixed-order reduction, then block columns from last to first: solve the
+// transposed diagonal block and update the columns to its left.
+#include "launch.h"
+
+namespace gipm {
+
+namespace {
+
+template <typename V>
+__global__ void __launch_bounds__(kGathPos) gather_fwd_kernel(DevPlan dp, int32_t task0,
+                                                              V *__restrict__ y,
+                                                              V *__restrict__ t) {
+  const Task tk = dp.gath[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int p = tk.a + threadIdx.x;
+  if (p >= F.ncol + F.nrow) return;
+  V v = V(0);
+  for (int ci = F.child_begin; ci < F.child_end; ci++) {
+    const int32_t c = dp.children[ci];
+    const int32_t a = dp.inv[dp.fronts[c].inv_off + p];
+    if (a >= 0) v += t[dp.toff[c] + a];
+  }
+  if (p < F.ncol) y[F.first + p] -= v;
+  else t[dp.toff[tk.front] + p - F.ncol] = v;
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(64) diag_fwd_kernel(DevPlan dp, int32_t task0, int nbs,
+                                                      const T *__restrict__ L,
+                                                      V *__restrict__ y) {
+  const Task tk = dp.sdiag[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int j = tk.a, jb = min(nbs, F.ncol - j), tid = threadIdx.x;
+  __shared__ V Lb[64][65];
+  __shared__ V yb[64];
+  const T *A = L + F.loff + (int64_t)j * F.ld + j;
+  for (int e = tid; e < jb * jb; e += 64) {
+    const int r = e / jb, c = e % jb;
+    if (r >= c) Lb[r][c] = (V)A[(int64_t)r * F.ld + c];
+  }
+  if (tid < jb) yb[tid] = y[F.first + j + tid];
+  __syncthreads();
+  for (int c = 0; c < jb; c++) {
+    if (tid == c) yb[c] /= Lb[c][c];
+    __syncthreads();
+    if (tid > c && tid < jb) yb[tid] = fma(-Lb[tid][c], yb[c], yb[tid]);
+    __syncthreads();
+  }
+  if (tid < jb) y[F.first + j + tid] = yb[tid];
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) upd_fwd_kernel(DevPlan dp, int32_t task0, int nbs,
+                                                      const T *__restrict__ L,
+                                                      V *__restrict__ y, V *__restrict__ t) {
+  const Task tk = dp.sgemv[task0 + blockIdx.x];
+  if (tk.c != 0) return;
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow, i0 = tk.a, j = tk.b, jb = min(nbs, F.ncol - j);
+  __shared__ V yj[64];
+  if (threadIdx.x < jb) yj[threadIdx.x] = y[F.first + j + threadIdx.x];
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int r1 = min(i0 + kSolveRows, nf);
+  for (int r = i0 + warp; r < r1; r += 8) {
+    const T *row = L + F.loff + (int64_t)r * F.ld + j;
+    V v = V(0);
+    for (int c = lane; c < jb; c += 32) v = fma((V)row[c], yj[c], v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      if (r < F.ncol) y[F.first + r] -= v;
+      else t[dp.toff[tk.front] + r - F.ncol] += v;
+    }
+  }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) rows_bwd_kernel(DevPlan dp, int32_t task0,
+                                                       const T *__restrict__ L,
+                                                       V *__restrict__ y) {
+  const Task tk = dp.rgemv[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int c0 = tk.a, warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = c0 + lane;
+  __shared__ V part[8][33];
+  V acc = V(0);
+  if (c < F.ncol) {
+    const T *P = L + F.loff + (int64_t)F.ncol * F.ld + c;
+    const int32_t *rs = dp.sri + F.rows_off;
+    for (int r = warp; r < F.nrow; r += 8) acc = fma((V)P[(int64_t)r * F.ld], y[rs[r]], acc);
+  }
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && c < F.ncol) {
+    V s = part[0][lane];
+    for (int w = 1; w < 8; w++) s += part[w][lane];
+    y[F.first + c] -= s;
+  }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(64) diag_bwd_kernel(DevPlan dp, int32_t task0, int nbs,
+                                                      const T *__restrict__ L,
+                                                      V *__restrict__ y) {
+  const Task tk = dp.sdiag[task0 + blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int j = tk.a, jb = min(nbs, F.ncol - j), tid = threadIdx.x;
+  __shared__ V Lb[64][65];
+  __shared__ V yb[64];
+  const T *A = L + F.loff + (int64_t)j * F.ld + j;
+  for (int e = tid; e < jb * jb; e += 64) {
+    const int r = e / jb, c = e % jb;
+    if (r >= c) Lb[r][c] = (V)A[(int64_t)r * F.ld + c];
+  }
+  if (tid < jb) yb[tid] = y[F.first + j + tid];
+  __syncthreads();
+  for (int c = jb - 1; c >= 0; c--) {
+    if (tid == c) yb[c] /= Lb[c][c];
+    __syncthreads();
+    if (tid < c) yb[tid] = fma(-Lb[c][tid], yb[c], yb[tid]);
+    __syncthreads();
+  }
+  if (tid < jb) y[F.first + j + tid] = yb[tid];
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) upd_bwd_kernel(DevPlan dp, int32_t task0, int nbs,
+                                                      const T *__restrict__ L,
+                                                      V *__restrict__ y) {
+  const Task tk = dp.sgemv[task0 + blockIdx.x];
+  if (tk.c != 1) return;
+  const FrontInfo F = dp.fronts[tk.front];
+  const int c0 = tk.a, j = tk.b, jb = min(nbs, F.ncol - j);
+  __shared__ V xj[64];
+  if (threadIdx.x < jb) xj[threadIdx.x] = y[F.first + j + threadIdx.x];
+  __syncthreads();
+  const int c = c0 + threadIdx.x;
+  if (c >= j) return;
+  const T *P = L + F.loff + (int64_t)j * F.ld + c;
+  V v = V(0);
+  for (int r = 0; r < jb; r++) v = fma((V)P[(int64_t)r * F.ld], xj[r], v);
+  y[F.first + c] -= v;
+}
+
+}  // namespace
+
+template <typename T, typename V>
+void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st) {
+  const int nbs = plan.nbs;
+  const int nlev = (int)plan.levels.size();
+  for (int li = 0; li < nlev; li++) {
+    const LevelPlan &LP = plan.levels[li];
+    if (LP.gath_e > LP.gath_b)
+      gather_fwd_kernel<V><<<LP.gath_e - LP.gath_b, kGathPos, 0, st>>>(dp, LP.gath_b, y, t);
+    for (size_t si = 0; si + 1 < LP.sstep_b.size(); si++) {
+      const int d0 = LP.sstep_b[si], d1 = LP.sstep_b[si + 1];
+      const int g0 = LP.sgemv_b[si], g1 = LP.sgemv_b[si + 1];
+      if (d1 > d0) diag_fwd_kernel<T, V><<<d1 - d0, 64, 0, st>>>(dp, d0, nbs, L, y);
+      if (g1 > g0) upd_fwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y, t);
+    }
+  }
+  for (int li = nlev - 1; li >= 0; li--) {
+    const LevelPlan &LP = plan.levels[li];
+    if (LP.rg_e > LP.rg_b)
+      rows_bwd_kernel<T, V><<<LP.rg_e - LP.rg_b, 256, 0, st>>>(dp, LP.rg_b, L, y);
+    for (int si = (int)LP.sstep_b.size() - 2; si >= 0; si--) {
+      const int d0 = LP.sstep_b[si], d1 = LP.sstep_b[si + 1];
+      const int g0 = LP.sgemv_b[si], g1 = LP.sgemv_b[si + 1];
+      if (d1 > d0) diag_bwd_kernel<T, V><<<d1 - d0, 64, 0, st>>>(dp, d0, nbs, L, y);
+      if (g1 > g0) upd_bwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y);
+    }
+  }
+}
+
+template void launch_solve<double, double>(const DevPlan &, const Plan &, const double *,
+                                           double *, double *, cudaStream_t);
+template void launch_solve<float, float>(const DevPlan &, const Plan &, const float *, float *,
+                                         float *, cudaStream_t);
+template void launch_solve<float, double>(const DevPlan &, const Plan &, const float *, double *,
+                                          double *, cudaStream_t);
+
+}  // namespace gipm

@@ -1,0 +1,30 @@
+// Host launchers of the device kernels (one stream, no synchronisation inside).
+#pragma once
+
+#include "dev.cuh"
+
+namespace gipm {
+
+// K = W + J^T diag(D_J) J + diag(D_bounds) + delta_p I into the compact FP64
+// array kval (level-major order of the plan).
+void launch_assemble(const DevPlan &dp, const double *jv, const double *D, const double *wv,
+                     double delta_p, double *kval, cudaStream_t st);
+
+// Multifrontal factorisation of all levels with SIMT FMA kernels. status must
+// be initialised by the caller (ST_FAIL_COL = INT32_MAX, ST_PERTURBED = 0).
+template <typename T>
+void launch_factor_simt(const DevPlan &dp, const Plan &plan, const double *kval, T *L, T *U,
+                        int32_t *status, bool perturb, cudaStream_t st);
+
+// Triangular solves with the factor: y (final numbering, length n) is
+// overwritten by L^{-T} L^{-1} y. t: update-vector scratch (plan.t_entries).
+template <typename T, typename V>
+void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st);
+
+// Sampled entries of L (final numbering).
+template <typename T>
+void launch_factor_entries(const DevPlan &dp, const T *L, const int32_t *col2s, int64_t count,
+                           const int32_t *rows, const int32_t *cols, double *out,
+                           cudaStream_t st);
+
+}  // namespace gipm

@@ -1,0 +1,97 @@
+"""The C-ABI library loads, exports every declared entry point, and its host
+symbolic analysis matches the oracle bit for bit. CPU only (no compute call
+touches a GPU: ipm_create and kkt_analyze are host-only)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2508_16094_gb300 as gb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gb.build()
+    return gb.load()
+
+
+def _declared_symbols():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^IPM_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_symbols()
+    assert len(names) >= 15
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(gb.EXPORTED) <= set(names)
+
+
+def _cases():
+    yield "grid5", gen.grid_lp(5, seed=2), gen.nd_order_grid3d(5, leaf=16)
+    yield "grid6x4x3", gen.grid_lp(6, 4, 3, seed=3), gen.nd_order_grid3d(6, 4, 3, leaf=8)
+    yield "grid9", gen.grid_lp(9, seed=4), gen.nd_order_grid3d(9)
+    lp = gen.random_lp(300, 150, 5, seed=5)
+    yield "random300_md", lp, gen.lp_ordering(lp)
+    lp = gen.random_lp(120, 200, 3, seed=6)
+    yield "random120_id", lp, None
+
+
+@pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
+def test_symbolic_bit_exact_vs_oracle(lib, case):
+    _, lp, perm = case
+    ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u)
+    info = ctx.kkt_analyze(perm)
+    got = ctx.kkt_symbolic_export()
+    S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
+    for k in ["perm", "parent", "colcount", "super", "sparent", "slevel", "srp", "sri"]:
+        np.testing.assert_array_equal(got[k], getattr(S, k), err_msg=k)
+    assert info.nnz_l == S.nnz_l
+    assert info.flops == S.flops
+    assert info.nsuper == S.nsuper
+    assert info.nnz_k == len(S.koi)
+    assert info.m_tot == lp.m + 2 * lp.n
+    ctx.close()
+
+
+def test_symbolic_special_patterns(lib):
+    n = 9
+    # diagonal only
+    ctx = gb.IpmContext(n, 0, np.zeros(1, np.int64), np.zeros(0, np.int32))
+    info = ctx.kkt_analyze()
+    assert info.nnz_l == n and info.nsuper >= 1
+    # dense row: one supernode of n columns
+    ctx = gb.IpmContext(n, 1, np.array([0, n], np.int64), np.arange(n, dtype=np.int32))
+    info = ctx.kkt_analyze()
+    assert info.nsuper == 1 and info.nnz_l == n * (n + 1) // 2 and info.max_ncol == n
+
+
+def test_argument_errors(lib):
+    lp = gen.grid_lp(3, seed=1)
+    # unsorted row
+    col = lp.col.copy()
+    col[0], col[1] = col[1], col[0]
+    with pytest.raises(gb.IpmError) as e:
+        gb.IpmContext(lp.n, lp.m, lp.rowptr, col)
+    assert e.value.status == 1
+    ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u)
+    with pytest.raises(gb.IpmError) as e:
+        ctx.kkt_analyze(np.zeros(lp.n, np.int32))  # not a permutation
+    assert e.value.status == 1
+    # out-of-order: factor before anything
+    st, _ = ctx.kkt_factor(gb.IPM_FP64, raise_on_error=False)
+    assert st == 2
+    # workspace size is reported and covers the FP64 factor
+    info = ctx.kkt_analyze(None)
+    assert info.workspace_bytes >= 8 * info.factor_entries
