@@ -151,6 +151,10 @@ IPM_API ipm_status ipm_create(int32_t n, int32_t m, const int64_t *h_j_rowptr, c
                       const int64_t *h_w_colptr, const int32_t *h_w_row, const double *h_l,
                       const double *h_u, const ipm_options *opts, void *stream, ipm_ctx **out);
 
+/* Replace the options of a context (copied). Takes effect at the next call;
+ * storage_fp64 is read by kkt_analyze only. Errors: IPM_ERR_ARG for NULL. */
+IPM_API ipm_status ipm_set_options(ipm_ctx *ctx, const ipm_options *opts);
+
 /* Symbolic analysis with the ordering given (Sec. 2: the fill-reducing
  * reordering is computed once on the host and reused): pattern of
  * K = W + J^T J + I, elimination tree, postorder, column counts, supernodes
@@ -242,6 +246,10 @@ IPM_API ipm_status kkt_factor_entries(ipm_ctx *ctx, int64_t count, const int32_t
 
 /* Low-precision pivots replaced by the last kkt_factor. */
 IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts). Read it before and after a call to count that call's launches. */
+IPM_API int64_t ipm_kernel_launches(void);
 
 IPM_API const char *ipm_last_error(const ipm_ctx *ctx);
 IPM_API void ipm_destroy(ipm_ctx *ctx);

@@ -256,7 +256,6 @@ static void postorder(int32_t n, const int32_t *parent, int32_t *post) {
  * ncol: merged column count; nrow: rows below the merged block;
  * ztrue: sum of the true column counts of both groups. */
 static int amalgamate_ok(int64_t ncol, int64_t nrow, int64_t ztrue) {
-  if (ncol > 256) return 0;
   int64_t nz = ncol * (ncol + 1) / 2 + ncol * nrow;
   int64_t z = nz - ztrue;
   if (ncol <= 4) return 1;

@@ -24,10 +24,10 @@ IPM_REFINE_NONE, IPM_REFINE_IR, IPM_REFINE_PCG = 0, 1, 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_NOMEM", 5: "ERR_NOT_SPD",
           6: "ERR_NUMERIC", 7: "ERR_MAXITER", 8: "ERR_TIMEOUT", 9: "ERR_STALL",
           10: "ERR_UNSUPPORTED"}
-EXPORTED = ["ipm_default_options", "ipm_create", "kkt_analyze", "ipm_set_workspace",
+EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze", "ipm_set_workspace",
             "kkt_assemble", "kkt_factor", "kkt_solve", "ipm_solve", "ipm_newton_direction",
             "kkt_symbolic_export", "kkt_export_assembled", "kkt_factor_entries",
-            "ipm_last_perturbed", "ipm_last_error", "ipm_destroy"]
+            "ipm_last_perturbed", "ipm_kernel_launches", "ipm_last_error", "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -96,6 +96,7 @@ def load() -> C.CDLL:
     sig = {
         "ipm_default_options": (None, [P]),
         "ipm_create": (I32, [I32, I32, P, P, P, P, P, P, P, P, P]),
+        "ipm_set_options": (I32, [P, P]),
         "kkt_analyze": (I32, [P, P, P]),
         "ipm_set_workspace": (I32, [P, P, C.c_size_t]),
         "kkt_assemble": (I32, [P, P, P, P, D]),
@@ -107,6 +108,7 @@ def load() -> C.CDLL:
         "kkt_export_assembled": (I32, [P, P]),
         "kkt_factor_entries": (I32, [P, I64, P, P, P]),
         "ipm_last_perturbed": (I32, [P]),
+        "ipm_kernel_launches": (I64, []),
         "ipm_last_error": (C.c_char_p, [P]),
         "ipm_destroy": (None, [P]),
     }
@@ -116,6 +118,11 @@ def load() -> C.CDLL:
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().ipm_kernel_launches())
 
 
 def default_options(**kw) -> Options:
@@ -176,6 +183,14 @@ class IpmContext:
         return status
 
     # --- C entry points -----------------------------------------------------
+    def ipm_set_options(self, options: Options | None = None, **kw):
+        """Push options to the library (the context keeps its own copy)."""
+        if options is not None:
+            self.options = options
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        self._check(self._lib.ipm_set_options(self.handle, C.byref(self.options)))
+
     def kkt_analyze(self, perm=None) -> SymbolicInfo:
         info = SymbolicInfo()
         p = _np(perm, np.int32)

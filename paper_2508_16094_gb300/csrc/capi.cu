@@ -53,6 +53,13 @@ struct ipm_ctx {
   VecOps vec() const { return VecOps{dp, st, partial}; }
 };
 
+namespace gipm {
+int64_t &launch_counter() {
+  static int64_t count = 0;
+  return count;
+}
+}  // namespace gipm
+
 namespace {
 
 struct Fail {
@@ -82,19 +89,6 @@ ipm_status guarded(ipm_ctx *ctx, F &&f) {
     return IPM_ERR_ARG;
   }
 }
-
-// Bump allocator over the workspace (base == nullptr: size only).
-struct Carve {
-  char *base;
-  size_t off = 0;
-  template <typename T>
-  T *take(size_t count) {
-    off = (off + 255) & ~size_t(255);
-    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
-    off += count * sizeof(T);
-    return p;
-  }
-};
 
 template <typename T>
 const T *upload(Carve &cv, const std::vector<T> &v, cudaStream_t st) {
@@ -184,7 +178,7 @@ void layout(ipm_ctx *c, char *base) {
   }
   c->dl_ = const_cast<double *>(upload(cv, P.l, st));
   c->du_ = const_cast<double *>(upload(cv, P.u, st));
-  c->tcp.layout(cv.base ? &cv : nullptr, c->plan, st);
+  c->tcp.layout(cv, st);
   d.n = P.n;
   d.m = P.m;
   d.nl = P.nl;
@@ -248,6 +242,10 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   c->last_perturbed = out[ST_PERTURBED];
   c->factor_prec = prec;
   c->state = 4;
+  if (out[ST_TIMEOUT]) {
+    c->state = 3;
+    throw Fail{IPM_ERR_TIMEOUT, "a bounded wait of the tensor-core factorisation ran out"};
+  }
   if (bad_col) *bad_col = out[ST_FAIL_COL] == INT32_MAX ? -1 : out[ST_FAIL_COL];
   if (out[ST_FAIL_COL] != INT32_MAX) {
     c->err = "non-positive pivot at column " + std::to_string(out[ST_FAIL_COL]);
@@ -502,6 +500,12 @@ ipm_status ipm_create(int32_t n, int32_t m, const int64_t *jp, const int32_t *ji
   return IPM_OK;
 }
 
+ipm_status ipm_set_options(ipm_ctx *c, const ipm_options *o) {
+  if (!c || !o) return IPM_ERR_ARG;
+  c->opts = *o;
+  return IPM_OK;
+}
+
 ipm_status kkt_analyze(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info) {
   if (!c) return IPM_ERR_ARG;
   return guarded(c, [&]() -> ipm_status {
@@ -552,6 +556,11 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     c->ws_bytes = bytes;
     layout(c, base);
     CK(cudaStreamSynchronize(c->st));
+    try {  // tensor maps of the FP32 panels for the tensor-core path
+      c->tcp.encode(c->plan, (float *)c->L, c->st);
+    } catch (const std::exception &e) {
+      c->err = std::string("tensor-core path unavailable: ") + e.what();
+    }
     c->state = 2;
     return IPM_OK;
   });
@@ -773,6 +782,8 @@ ipm_status kkt_factor_entries(ipm_ctx *c, int64_t count, const int32_t *rows, co
 }
 
 int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0; }
+
+int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }
 
 const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
 

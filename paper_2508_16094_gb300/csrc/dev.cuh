@@ -34,7 +34,21 @@ struct DevPlan {
 enum StatusWord : int {
   ST_FAIL_COL = 0,   // smallest column with a non-positive pivot (INT32_MAX if none)
   ST_PERTURBED = 1,  // pivots replaced by the low-precision factorisation
+  ST_TIMEOUT = 2,    // a bounded device-side wait ran out
   ST_COUNT = 8
+};
+
+// Bump allocator over the caller's workspace (base == nullptr: size only).
+struct Carve {
+  char *base;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
 };
 
 constexpr int kBuildTile = 32;
@@ -43,6 +57,10 @@ constexpr int kTrsmRows = 128;
 constexpr int kGathPos = 256;
 constexpr int kSolveRows = 128;
 constexpr int kSolveCols = 256;
+
+// Kernel launches issued by this library (host-side count, single stream of work).
+int64_t &launch_counter();
+inline void note_launch() { launch_counter() += 1; }
 
 template <typename T> struct Acc;
 template <> struct Acc<double> { using type = double; };

@@ -171,27 +171,28 @@ template <typename T> __device__ __forceinline__ T big_pivot();
 template <> __device__ __forceinline__ float big_pivot<float>() { return 1e30f; }
 template <> __device__ __forceinline__ double big_pivot<double>() { return 1e64; }
 
-// Cholesky of one diagonal block (kb <= 64) in shared memory. A pivot that is
-// not positive is either reported (smallest failing column kept) or replaced
-// by a large value (static pivoting) and counted.
+// Cholesky of one diagonal block (kb <= nb <= 128) in shared memory. A pivot
+// that is not positive is either reported (smallest failing column kept) or
+// replaced by a large value (static pivoting) and counted.
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, int32_t task0, int nb,
-                                                    T *__restrict__ L, int32_t *status,
+__global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__restrict__ tasks,
+                                                    int nb, T *__restrict__ L, int32_t *status,
                                                     int perturb) {
-  const Task tk = dp.potrf[task0 + blockIdx.x];
+  const Task tk = tasks[blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
-  const int k = tk.a, kb = min(nb, F.ncol - k);
+  const int k = tk.a, kb = min(nb, F.ncol - k), ls = nb + 1;
   T *A = L + F.loff + (int64_t)k * F.ld + k;
-  __shared__ T Ad[64][65];
+  extern __shared__ unsigned char smem_raw[];
+  T *Ad = reinterpret_cast<T *>(smem_raw);  // [nb][nb + 1]
   const int tid = threadIdx.x;
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
-    if (r >= c) Ad[r][c] = A[(int64_t)r * F.ld + c];
+    if (r >= c) Ad[r * ls + c] = A[(int64_t)r * F.ld + c];
   }
   __syncthreads();
   for (int j = 0; j < kb; j++) {
     if (tid == 0) {
-      T d = Ad[j][j];
+      T d = Ad[j * ls + j];
       if (!(d > T(0)) || !(d < big_pivot<T>() * big_pivot<T>())) {
         if (perturb) {
           d = big_pivot<T>();
@@ -201,60 +202,61 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, int32_t task0, i
           d = T(1);
         }
       }
-      Ad[j][j] = sqrt(d);
+      Ad[j * ls + j] = sqrt(d);
     }
     __syncthreads();
-    const T ljj = Ad[j][j];
-    for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i][j] /= ljj;
+    const T ljj = Ad[j * ls + j];
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i * ls + j] /= ljj;
     __syncthreads();
     const int w = kb - j - 1;
     for (int e = tid; e < w * w; e += blockDim.x) {
       const int i = j + 1 + e / w, c = j + 1 + e % w;
-      if (c <= i) Ad[i][c] = fma(-Ad[i][j], Ad[c][j], Ad[i][c]);
+      if (c <= i) Ad[i * ls + c] = fma(-Ad[i * ls + j], Ad[c * ls + j], Ad[i * ls + c]);
     }
     __syncthreads();
   }
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
-    if (r >= c) A[(int64_t)r * F.ld + c] = Ad[r][c];
+    if (r >= c) A[(int64_t)r * F.ld + c] = Ad[r * ls + c];
   }
 }
 
-// Rows below the diagonal block: X <- X L_kk^{-T} (row-wise forward substitution).
+// Rows below the diagonal block: X <- X L_kk^{-T} (row-wise forward
+// substitution), kTrsmRows rows per block, kb <= nb <= 128.
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, int32_t task0, int nb,
-                                                         T *__restrict__ L) {
-  const Task tk = dp.trsm[task0 + blockIdx.x];
+__global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, const Task *__restrict__ tasks,
+                                                         int nb, T *__restrict__ L) {
+  const Task tk = tasks[blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
-  const int nf = F.ncol + F.nrow, i0 = tk.a, k = tk.b;
+  const int nf = F.ncol + F.nrow, i0 = tk.a, k = tk.b, ls = nb + 1;
   const int kb = min(nb, F.ncol - k), rows = min(kTrsmRows, nf - i0);
   extern __shared__ unsigned char smem_raw[];
-  T *Lk = reinterpret_cast<T *>(smem_raw);  // [64][65]
-  T *X = Lk + 64 * 65;                      // [kTrsmRows][65]
+  T *Lk = reinterpret_cast<T *>(smem_raw);  // [nb][nb + 1]
+  T *X = Lk + nb * ls;                      // [kTrsmRows][nb + 1]
   const T *A = L + F.loff + (int64_t)k * F.ld + k;
   T *Xg = L + F.loff + (int64_t)i0 * F.ld + k;
   const int tid = threadIdx.x;
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
-    Lk[r * 65 + c] = (r >= c) ? A[(int64_t)r * F.ld + c] : T(0);
+    Lk[r * ls + c] = (r >= c) ? A[(int64_t)r * F.ld + c] : T(0);
   }
   for (int e = tid; e < rows * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
-    X[r * 65 + c] = Xg[(int64_t)r * F.ld + c];
+    X[r * ls + c] = Xg[(int64_t)r * F.ld + c];
   }
   __syncthreads();
   if (tid < rows) {
-    T *x = X + tid * 65;
+    T *x = X + tid * ls;
     for (int c = 0; c < kb; c++) {
       T v = x[c];
-      for (int c2 = 0; c2 < c; c2++) v = fma(-x[c2], Lk[c * 65 + c2], v);
-      x[c] = v / Lk[c * 65 + c];
+      for (int c2 = 0; c2 < c; c2++) v = fma(-x[c2], Lk[c * ls + c2], v);
+      x[c] = v / Lk[c * ls + c];
     }
   }
   __syncthreads();
   for (int e = tid; e < rows * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
-    Xg[(int64_t)r * F.ld + c] = X[r * 65 + c];
+    Xg[(int64_t)r * F.ld + c] = X[r * ls + c];
   }
 }
 
@@ -296,36 +298,51 @@ inline int grid_for(int64_t n, int block) {
 void launch_assemble(const DevPlan &dp, const double *jv, const double *D, const double *wv,
                      double delta_p, double *kval, cudaStream_t st) {
   if (dp.nk == 0) return;
-  assemble_kernel<<<grid_for(dp.nk, 256), 256, 0, st>>>(dp, jv, D, wv, delta_p, kval);
+  { note_launch(); assemble_kernel<<<grid_for(dp.nk, 256), 256, 0, st>>>(dp, jv, D, wv, delta_p, kval); }
+}
+
+template <typename T>
+void launch_build_level(const DevPlan &dp, const LevelPlan &LP, const double *kval, T *L, T *U,
+                        cudaStream_t st) {
+  if (LP.build_e > LP.build_b)
+    { note_launch(); build_front_kernel<T><<<LP.build_e - LP.build_b, 256, 0, st>>>(dp, LP.build_b, L, U); }
+  if (LP.k_e > LP.k_b)
+    { note_launch(); kadd_kernel<T><<<grid_for(LP.k_e - LP.k_b, 256), 256, 0, st>>>(dp, LP.k_b, LP.k_e, kval, L); }
+}
+
+template <typename T>
+void launch_potrf(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L, int32_t *status,
+                  bool perturb, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)nb * (nb + 1) * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  { note_launch(); potrf_kernel<T><<<ntasks, 256, smem, st>>>(dp, tasks, nb, L, status, perturb ? 1 : 0); }
+}
+
+template <typename T>
+void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)(nb + kTrsmRows) * (nb + 1) * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  { note_launch(); trsm_kernel<T><<<ntasks, kTrsmRows, smem, st>>>(dp, tasks, nb, L); }
 }
 
 template <typename T>
 void launch_factor_simt(const DevPlan &dp, const Plan &plan, const double *kval, T *L, T *U,
                         int32_t *status, bool perturb, cudaStream_t st) {
-  const size_t trsm_smem = (size_t)(64 * 65 + kTrsmRows * 65) * sizeof(T);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)trsm_smem);
-    attr_done = true;
-  }
   const int nb = plan.nb;
   for (const LevelPlan &LP : plan.levels) {
-    if (LP.build_e > LP.build_b)
-      build_front_kernel<T><<<LP.build_e - LP.build_b, 256, 0, st>>>(dp, LP.build_b, L, U);
-    if (LP.k_e > LP.k_b)
-      kadd_kernel<T><<<grid_for(LP.k_e - LP.k_b, 256), 256, 0, st>>>(dp, LP.k_b, LP.k_e, kval, L);
+    launch_build_level<T>(dp, LP, kval, L, U, st);
     for (const StepRange &S : LP.steps) {
       if (S.gemm_e > S.gemm_b)
-        gemm_ll_kernel<T><<<S.gemm_e - S.gemm_b, 256, 0, st>>>(dp, S.gemm_b, nb, L);
-      if (S.potrf_e > S.potrf_b)
-        potrf_kernel<T><<<S.potrf_e - S.potrf_b, 256, 0, st>>>(dp, S.potrf_b, nb, L, status,
-                                                               perturb ? 1 : 0);
-      if (S.trsm_e > S.trsm_b)
-        trsm_kernel<T><<<S.trsm_e - S.trsm_b, kTrsmRows, trsm_smem, st>>>(dp, S.trsm_b, nb, L);
+        { note_launch(); gemm_ll_kernel<T><<<S.gemm_e - S.gemm_b, 256, 0, st>>>(dp, S.gemm_b, nb, L); }
+      launch_potrf<T>(dp, dp.potrf + S.potrf_b, S.potrf_e - S.potrf_b, nb, L, status, perturb, st);
+      launch_trsm<T>(dp, dp.trsm + S.trsm_b, S.trsm_e - S.trsm_b, nb, L, st);
     }
     if (LP.syrk_e > LP.syrk_b)
-      syrk_kernel<T><<<LP.syrk_e - LP.syrk_b, 256, 0, st>>>(dp, LP.syrk_b, L, U);
+      { note_launch(); syrk_kernel<T><<<LP.syrk_e - LP.syrk_b, 256, 0, st>>>(dp, LP.syrk_b, L, U); }
   }
 }
 
@@ -334,9 +351,14 @@ void launch_factor_entries(const DevPlan &dp, const T *L, const int32_t *col2s, 
                            const int32_t *rows, const int32_t *cols, double *out,
                            cudaStream_t st) {
   if (count <= 0) return;
-  entries_kernel<T><<<grid_for(count, 256), 256, 0, st>>>(dp, L, col2s, count, rows, cols, out);
+  { note_launch(); entries_kernel<T><<<grid_for(count, 256), 256, 0, st>>>(dp, L, col2s, count, rows, cols, out); }
 }
 
+template void launch_build_level<float>(const DevPlan &, const LevelPlan &, const double *,
+                                        float *, float *, cudaStream_t);
+template void launch_potrf<float>(const DevPlan &, const Task *, int, int, float *, int32_t *, bool,
+                                  cudaStream_t);
+template void launch_trsm<float>(const DevPlan &, const Task *, int, int, float *, cudaStream_t);
 template void launch_factor_simt<double>(const DevPlan &, const Plan &, const double *, double *,
                                          double *, int32_t *, bool, cudaStream_t);
 template void launch_factor_simt<float>(const DevPlan &, const Plan &, const double *, float *,

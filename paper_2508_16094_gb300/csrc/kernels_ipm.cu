@@ -342,48 +342,48 @@ __global__ void xpby_dev_kernel(int64_t n, const double *num, const double *den,
 // ---------------------------------------------------------------------------
 void VecOps::reduce_final(int ns, const RedOps &ops, double *out) const {
   switch (ns) {
-    case 1: final_reduce_kernel<1><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); break;
-    case 2: final_reduce_kernel<2><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); break;
-    case 5: final_reduce_kernel<5><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); break;
+    case 1: { note_launch(); final_reduce_kernel<1><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); } break;
+    case 2: { note_launch(); final_reduce_kernel<2><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); } break;
+    case 5: { note_launch(); final_reduce_kernel<5><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); } break;
     default: break;
   }
 }
 void VecOps::absmax(int64_t n, const double *v, double *out) const {
-  absmax_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(n, v, partial);
+  { note_launch(); absmax_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(n, v, partial); }
   reduce_final(1, RedOps{{RED_MAX}}, out);
 }
 void VecOps::dot(int64_t n, const double *a, const double *b, double *out) const {
-  dot_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(n, a, b, partial);
+  { note_launch(); dot_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(n, a, b, partial); }
   reduce_final(1, RedOps{{RED_SUM}}, out);
 }
 void VecOps::inv_scale(const double *absmax_v, double *scale) const {
-  inv_scale_kernel<<<1, 1, 0, st>>>(absmax_v, scale);
+  { note_launch(); inv_scale_kernel<<<1, 1, 0, st>>>(absmax_v, scale); }
 }
 void VecOps::jv(const double *jvals, const double *x, double *out) const {
-  if (dp.m > 0) jv_kernel<<<grid_of(dp.m), 256, 0, st>>>(dp, jvals, x, out);
+  if (dp.m > 0) { note_launch(); jv_kernel<<<grid_of(dp.m), 256, 0, st>>>(dp, jvals, x, out); }
 }
 void VecOps::jfull(const double *jx, const double *x, double *out) const {
-  if (dp.mt > 0) jfull_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp, jx, x, out);
+  if (dp.mt > 0) { note_launch(); jfull_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp, jx, x, out); }
 }
 void VecOps::jtv(const double *jvals, const double *v, double sgn, const double *wv,
                  const double *x, const double *base, double *out) const {
-  jtv_kernel<<<grid_of(dp.n), 256, 0, st>>>(dp, jvals, v, sgn, wv, x, base, out);
+  { note_launch(); jtv_kernel<<<grid_of(dp.n), 256, 0, st>>>(dp, jvals, v, sgn, wv, x, base, out); }
 }
 void VecOps::init_slack(const double *gv, double *s, double *lam) const {
-  if (dp.mt > 0) init_slack_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, gv, s, lam);
+  if (dp.mt > 0) { note_launch(); init_slack_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, gv, s, lam); }
 }
 void VecOps::residual(const double *jvals, const double *D, const double *wv, double delta_p,
                       const double *x, const double *b, double *r, double *tA) const {
-  if (dp.m > 0) resid_rows_kernel<<<grid_of(dp.m), 256, 0, st>>>(dp, jvals, D, x, tA);
-  resid_cols_kernel<<<grid_of(dp.n), 256, 0, st>>>(dp, jvals, D, wv, delta_p, tA, x, b, r);
+  if (dp.m > 0) { note_launch(); resid_rows_kernel<<<grid_of(dp.m), 256, 0, st>>>(dp, jvals, D, x, tA); }
+  { note_launch(); resid_cols_kernel<<<grid_of(dp.n), 256, 0, st>>>(dp, jvals, D, wv, delta_p, tA, x, b, r); }
 }
 template <typename V>
 void VecOps::permute_in(const double *b, const double *scale, V *y) const {
-  permute_in_kernel<V><<<grid_of(dp.n), 256, 0, st>>>(dp.n, dp.perm, b, scale, y);
+  { note_launch(); permute_in_kernel<V><<<grid_of(dp.n), 256, 0, st>>>(dp.n, dp.perm, b, scale, y); }
 }
 template <typename V>
 void VecOps::permute_out(const V *y, const double *scale, double *x, bool accumulate) const {
-  permute_out_kernel<V><<<grid_of(dp.n), 256, 0, st>>>(dp.n, dp.perm, y, scale, x, accumulate);
+  { note_launch(); permute_out_kernel<V><<<grid_of(dp.n), 256, 0, st>>>(dp.n, dp.perm, y, scale, x, accumulate); }
 }
 template void VecOps::permute_in<double>(const double *, const double *, double *) const;
 template void VecOps::permute_in<float>(const double *, const double *, float *) const;
@@ -393,56 +393,56 @@ template void VecOps::permute_out<float>(const float *, const double *, double *
 void VecOps::kkt(const double *g, const double *s, const double *lam, const double *rd,
                  const double *c, const double *wx, const double *x, double *red5,
                  IpmScalars *sc) const {
-  kkt_reduce_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(dp, g, s, lam, rd, c, wx, x, partial);
+  { note_launch(); kkt_reduce_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(dp, g, s, lam, rd, c, wx, x, partial); }
   reduce_final(5, RedOps{{RED_SUM, RED_MAX, RED_MAX, RED_MAX, RED_SUM}}, red5);
-  finish_kkt_kernel<<<1, 1, 0, st>>>(red5, dp.mt, sc);
+  { note_launch(); finish_kkt_kernel<<<1, 1, 0, st>>>(red5, dp.mt, sc); }
 }
 void VecOps::g(const double *jx, const double *x, const double *b, const double *l,
                const double *u, double *gout) const {
-  if (dp.mt > 0) g_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp, jx, x, b, l, u, gout);
+  if (dp.mt > 0) { note_launch(); g_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp, jx, x, b, l, u, gout); }
 }
 void VecOps::scaling(const double *s, const double *lam, double delta_d, double *D) const {
-  if (dp.mt > 0) scaling_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, s, lam, delta_d, D);
+  if (dp.mt > 0) { note_launch(); scaling_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, s, lam, delta_d, D); }
 }
 void VecOps::rhs_rows(const double *D, const double *gv, const double *w, const double *lam,
                       double *t) const {
-  if (dp.mt > 0) rhs_rows_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, D, gv, w, lam, t);
+  if (dp.mt > 0) { note_launch(); rhs_rows_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, D, gv, w, lam, t); }
 }
 void VecOps::negate(int64_t n, double *v) const {
-  negate_kernel<<<grid_of(n), 256, 0, st>>>(n, v);
+  { note_launch(); negate_kernel<<<grid_of(n), 256, 0, st>>>(n, v); }
 }
 void VecOps::recover(const double *D, const double *gv, const double *w, const double *s,
                      const double *lam, const double *jdx, double *ds, double *dl) const {
   if (dp.mt > 0)
-    recover_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, D, gv, w, s, lam, jdx, ds, dl);
+    { note_launch(); recover_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, D, gv, w, s, lam, jdx, ds, dl); }
 }
 void VecOps::ftb(const double *s, const double *ds, const double *lam, const double *dl,
                  double *red2, IpmScalars *sc, bool affine) const {
-  ftb_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(dp.mt, s, ds, lam, dl, partial);
+  { note_launch(); ftb_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(dp.mt, s, ds, lam, dl, partial); }
   reduce_final(2, RedOps{{RED_MIN, RED_MIN}}, red2);
-  finish_ftb_kernel<<<1, 1, 0, st>>>(red2, sc, affine ? 1 : 0);
+  { note_launch(); finish_ftb_kernel<<<1, 1, 0, st>>>(red2, sc, affine ? 1 : 0); }
 }
 void VecOps::muaff(const double *s, const double *ds, const double *lam, const double *dl,
                    double *red1, IpmScalars *sc) const {
-  muaff_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(dp.mt, s, ds, lam, dl, sc, partial);
+  { note_launch(); muaff_kernel<<<kRedBlocks, kRedBlock, 0, st>>>(dp.mt, s, ds, lam, dl, sc, partial); }
   reduce_final(1, RedOps{{RED_SUM}}, red1);
-  finish_muaff_kernel<<<1, 1, 0, st>>>(red1, dp.mt, sc);
+  { note_launch(); finish_muaff_kernel<<<1, 1, 0, st>>>(red1, dp.mt, sc); }
 }
 void VecOps::corrector_target(const double *ds, const double *dl, IpmScalars *sc,
                               double *w) const {
-  corrector_target_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, ds, dl, sc, w);
+  { note_launch(); corrector_target_kernel<<<grid_of(dp.mt), 256, 0, st>>>(dp.mt, ds, dl, sc, w); }
 }
 void VecOps::update(const IpmScalars *sc, double *x, const double *dx, double *s,
                     const double *ds, double *lam, const double *dl) const {
-  update_kernel<<<grid_of(dp.n + dp.mt), 256, 0, st>>>(dp.n, dp.mt, sc, x, dx, s, ds, lam, dl);
+  { note_launch(); update_kernel<<<grid_of(dp.n + dp.mt), 256, 0, st>>>(dp.n, dp.mt, sc, x, dx, s, ds, lam, dl); }
 }
 void VecOps::axpy_ratio(int64_t n, const double *num, const double *den, int sign,
                         const double *x, double *y) const {
-  axpy_dev_kernel<<<grid_of(n), 256, 0, st>>>(n, num, den, sign, x, y);
+  { note_launch(); axpy_dev_kernel<<<grid_of(n), 256, 0, st>>>(n, num, den, sign, x, y); }
 }
 void VecOps::xpby_ratio(int64_t n, const double *num, const double *den, const double *x,
                         double *p) const {
-  xpby_dev_kernel<<<grid_of(n), 256, 0, st>>>(n, num, den, x, p);
+  { note_launch(); xpby_dev_kernel<<<grid_of(n), 256, 0, st>>>(n, num, den, x, p); }
 }
 
 }  // namespace gipm

@@ -161,23 +161,23 @@ void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, c
   for (int li = 0; li < nlev; li++) {
     const LevelPlan &LP = plan.levels[li];
     if (LP.gath_e > LP.gath_b)
-      gather_fwd_kernel<V><<<LP.gath_e - LP.gath_b, kGathPos, 0, st>>>(dp, LP.gath_b, y, t);
+      { note_launch(); gather_fwd_kernel<V><<<LP.gath_e - LP.gath_b, kGathPos, 0, st>>>(dp, LP.gath_b, y, t); }
     for (size_t si = 0; si + 1 < LP.sstep_b.size(); si++) {
       const int d0 = LP.sstep_b[si], d1 = LP.sstep_b[si + 1];
       const int g0 = LP.sgemv_b[si], g1 = LP.sgemv_b[si + 1];
-      if (d1 > d0) diag_fwd_kernel<T, V><<<d1 - d0, 64, 0, st>>>(dp, d0, nbs, L, y);
-      if (g1 > g0) upd_fwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y, t);
+      if (d1 > d0) { note_launch(); diag_fwd_kernel<T, V><<<d1 - d0, 64, 0, st>>>(dp, d0, nbs, L, y); }
+      if (g1 > g0) { note_launch(); upd_fwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y, t); }
     }
   }
   for (int li = nlev - 1; li >= 0; li--) {
     const LevelPlan &LP = plan.levels[li];
     if (LP.rg_e > LP.rg_b)
-      rows_bwd_kernel<T, V><<<LP.rg_e - LP.rg_b, 256, 0, st>>>(dp, LP.rg_b, L, y);
+      { note_launch(); rows_bwd_kernel<T, V><<<LP.rg_e - LP.rg_b, 256, 0, st>>>(dp, LP.rg_b, L, y); }
     for (int si = (int)LP.sstep_b.size() - 2; si >= 0; si--) {
       const int d0 = LP.sstep_b[si], d1 = LP.sstep_b[si + 1];
       const int g0 = LP.sgemv_b[si], g1 = LP.sgemv_b[si + 1];
-      if (d1 > d0) diag_bwd_kernel<T, V><<<d1 - d0, 64, 0, st>>>(dp, d0, nbs, L, y);
-      if (g1 > g0) upd_bwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y);
+      if (d1 > d0) { note_launch(); diag_bwd_kernel<T, V><<<d1 - d0, 64, 0, st>>>(dp, d0, nbs, L, y); }
+      if (g1 > g0) { note_launch(); upd_bwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y); }
     }
   }
 }

@@ -16,6 +16,18 @@ template <typename T>
 void launch_factor_simt(const DevPlan &dp, const Plan &plan, const double *kval, T *L, T *U,
                         int32_t *status, bool perturb, cudaStream_t st);
 
+// Pieces of a level of the factorisation, shared with the tensor-core path:
+// front assembly (+ K entries), diagonal-block Cholesky (nb <= 128) and the
+// triangular solve of the rows below (nb <= 128).
+template <typename T>
+void launch_build_level(const DevPlan &dp, const LevelPlan &LP, const double *kval, T *L, T *U,
+                        cudaStream_t st);
+template <typename T>
+void launch_potrf(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L, int32_t *status,
+                  bool perturb, cudaStream_t st);
+template <typename T>
+void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L, cudaStream_t st);
+
 // Triangular solves with the factor: y (final numbering, length n) is
 // overwritten by L^{-T} L^{-1} y. t: update-vector scratch (plan.t_entries).
 template <typename T, typename V>

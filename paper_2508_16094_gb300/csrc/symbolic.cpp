@@ -116,12 +116,13 @@ std::vector<int32_t> postorder_of(const std::vector<int32_t> &parent) {
   return order;
 }
 
-// Amalgamation rule: a child group may merge into its parent when the merged
-// block has at most 256 columns and its explicit zeros z (relative to the
-// merged trapezoid nz) satisfy: ncol <= 4, or ncol <= 16 and z <= 0.8 nz, or
-// ncol <= 48 and z <= 0.1 nz, or z <= 0.05 nz.
+// Amalgamation rule: a child group may merge into its parent when the explicit
+// zeros z of the merged block (relative to the merged trapezoid nz) satisfy:
+// ncol <= 4, or ncol <= 16 and z <= 0.8 nz, or ncol <= 48 and z <= 0.1 nz, or
+// z <= 0.05 nz. No width cap: a separator whose column counts shrink by more
+// than one per column still becomes one wide supernode, not a chain of narrow
+// ones each handing a full update matrix to the next.
 bool may_merge(int64_t ncol, int64_t nrow, int64_t true_nnz) {
-  if (ncol > 256) return false;
   const int64_t nz = ncol * (ncol + 1) / 2 + ncol * nrow;
   const int64_t z = nz - true_nnz;
   return ncol <= 4 || (ncol <= 16 && 10 * z <= 8 * nz) || (ncol <= 48 && 10 * z <= nz) ||

@@ -1,11 +1,389 @@
-// Tensor-core factorisation path (placeholder until the tcgen05 kernels land).
+// Tensor-core GEMM for the supernodal factorisation on sm_103a (tcgen05 + TMA).
+//
+// One CTA computes one 128 x 128 tile of C -= A B^T, where A and B are row
+// blocks of a front's panel (row-major, K contiguous: "K-major") and C is
+// either the panel itself (left-looking update of a block column) or the
+// front's update matrix (SYRK). Warp 0 streams 128 x 32 FP32 tiles of A and B
+// through a 4-stage ring of 128B-swizzled shared memory with TMA, warp 1
+// issues tcgen05.mma kind::tf32 (M=128, N=128, K=8) into a 128-column FP32
+// accumulator in tensor memory, warps 2-5 read the accumulator back with
+// tcgen05.ld and subtract it from C. Every wait on an mbarrier is bounded by a
+// clock limit; on expiry the CTA records ST_TIMEOUT, skips the epilogue and
+// still releases its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "launch.h"
 #include "tc.h"
 
 namespace gipm {
 
-void TcPlan::build(const Plan &) { ready_ = false; }
+namespace {
 
-void TcPlan::factor(const DevPlan &, const Plan &, const double *, float *, float *, int32_t *,
-                    bool, cudaStream_t) {}
+constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kStages = 4;
+constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per operand tile
+constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kSmemBytes = 2 * kStages * kTileBytes + 1024 /*barriers*/ + 1024 /*alignment*/;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and ST_TIMEOUT recorded) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *status) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kSpinCycles) {
+      atomicExch(&status[ST_TIMEOUT], 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::tf32: FP32 accumulator, TF32 A
+// and B, both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t tf32_idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+         ((uint32_t)(kTileM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Task: front, a = first row of the A tile (block-local), b = k (mode 0) or j0
+// (mode 1), c = mode. Mode 0: C = panel[a:a+128, k:k+kb], A = panel rows a..,
+// B = panel rows k.., K = k. Mode 1: C = U[a:a+128, b:b+128], A = panel rows
+// ncol+a.., B = panel rows ncol+b.., K = ncol.
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, const CUtensorMap *__restrict__ maps,
+                   float *__restrict__ L, float *__restrict__ U, int nb, int32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  uint8_t *sA = base;
+  uint8_t *sB = base + kStages * kTileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + 2 * kStages * kTileBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *accum = empty + kStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const Task tk = tasks[blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow;
+  int arow, brow, K, M, N;
+  float *C;
+  int64_t ldc;
+  if (tk.c == 0) {
+    const int k = tk.b;
+    arow = tk.a;
+    brow = k;
+    K = k;
+    M = min(kTileM, nf - tk.a);
+    N = min(nb, F.ncol - k);
+    C = L + F.loff + (int64_t)tk.a * F.ld + k;
+    ldc = F.ld;
+  } else {
+    arow = F.ncol + tk.a;
+    brow = F.ncol + tk.b;
+    K = F.ncol;
+    M = min(kTileM, F.nrow - tk.a);
+    N = min(kTileN, F.nrow - tk.b);
+    C = U + F.uoff + (int64_t)tk.a * F.uld + tk.b;
+    ldc = F.uld;
+  }
+  const CUtensorMap *tmap = maps + tk.front;
+  const int nk = (K + kTileK - 1) / kTileK;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTileN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kt = 0; kt < nk; kt++) {
+        const int s = kt % kStages, round = kt / kStages;
+        if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
+        mbar_arrive_expect_tx(&full[s], 2 * kTileBytes);
+        tma_load_2d(sA + s * kTileBytes, tmap, &full[s], kt * kTileK, arow);
+        tma_load_2d(sB + s * kTileBytes, tmap, &full[s], kt * kTileK, brow);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc();
+      for (int kt = 0; kt < nk; kt++) {
+        const int s = kt % kStages, round = kt / kStages;
+        if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ad = sw128_desc(smem_u32(sA + s * kTileBytes));
+        const uint64_t bd = sw128_desc(smem_u32(sB + s * kTileBytes));
+#pragma unroll
+        for (int k4 = 0; k4 < kTileK / 8; k4++)  // 8 TF32 = 32 bytes per MMA along K
+          mma_tf32(tmem, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accum);
+    }
+  } else {
+    const bool ok = mbar_wait(accum, 0, status);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp % 4;  // tensor-memory lane quarter this warp may access
+    const int row = q * 32 + lane;
+    if (ok && !*abort_flag) {
+      for (int cb = 0; cb < (N + 31) / 32; cb++) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), v);
+        if (row < M) {
+          float *crow = C + (int64_t)row * ldc + cb * 32;
+          const int nc = min(32, N - cb * 32);
+#pragma unroll
+          for (int c = 0; c < 32; c++)
+            if (c < nc) crow[c] -= v[c];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTileN));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      throw std::runtime_error("cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+void TcPlan::build(const Plan &plan) {
+  gemm_.clear();
+  potrf_.clear();
+  trsm_.clear();
+  syrk_.clear();
+  levels_.assign(plan.levels.size(), Level{});
+  nfronts_ = (int)plan.fronts.size();
+  for (size_t li = 0; li < plan.levels.size(); li++) {
+    const LevelPlan &LP = plan.levels[li];
+    Level &lv = levels_[li];
+    for (int32_t k = 0; k < LP.max_ncol; k += kNb) {
+      Step st{};
+      st.gemm_b = (int)gemm_.size();
+      for (int32_t t = LP.front_b; t < LP.front_e && k > 0; t++) {
+        const int32_t s = plan.level_fronts[t];
+        const FrontInfo &F = plan.fronts[s];
+        if (F.ncol <= k) continue;
+        for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, k, 0});
+      }
+      st.gemm_e = (int)gemm_.size();
+      st.potrf_b = (int)potrf_.size();
+      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+        const int32_t s = plan.level_fronts[t];
+        if (plan.fronts[s].ncol > k) potrf_.push_back({s, k, 0, 0});
+      }
+      st.potrf_e = (int)potrf_.size();
+      st.trsm_b = (int)trsm_.size();
+      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+        const int32_t s = plan.level_fronts[t];
+        const FrontInfo &F = plan.fronts[s];
+        if (F.ncol <= k) continue;
+        const int32_t kb = std::min(kNb, F.ncol - k);
+        for (int32_t i0 = k + kb; i0 < F.ncol + F.nrow; i0 += kTrsmRows) trsm_.push_back({s, i0, k, 0});
+      }
+      st.trsm_e = (int)trsm_.size();
+      lv.steps.push_back(st);
+    }
+    lv.syrk_b = (int)syrk_.size();
+    for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+      const int32_t s = plan.level_fronts[t];
+      const FrontInfo &F = plan.fronts[s];
+      for (int32_t i0 = 0; i0 < F.nrow; i0 += kTileM)
+        for (int32_t j0 = 0; j0 <= i0; j0 += kTileN) syrk_.push_back({s, i0, j0, 1});
+    }
+    lv.syrk_e = (int)syrk_.size();
+  }
+  // range checks of the tasks against the fronts (the kernel masks only the tile edges)
+  auto fail = [](const char *w) { throw std::runtime_error(std::string("tc plan check: ") + w); };
+  for (const Task &t : gemm_) {
+    const FrontInfo &F = plan.fronts[t.front];
+    if (!(t.b > 0 && t.b < F.ncol && t.a >= t.b && t.a < F.ncol + F.nrow && t.c == 0)) fail("gemm");
+  }
+  for (const Task &t : syrk_) {
+    const FrontInfo &F = plan.fronts[t.front];
+    if (!(t.a >= 0 && t.a < F.nrow && t.b >= 0 && t.b <= t.a && t.c == 1)) fail("syrk");
+  }
+  for (const Task &t : trsm_) {
+    const FrontInfo &F = plan.fronts[t.front];
+    const int kb = std::min(kNb, F.ncol - t.b);
+    if (!(t.b >= 0 && t.b < F.ncol && t.a >= t.b + kb && t.a < F.ncol + F.nrow)) fail("trsm");
+  }
+  for (const Task &t : potrf_)
+    if (!(t.a >= 0 && t.a < plan.fronts[t.front].ncol)) fail("potrf");
+  ready_ = false;
+}
+
+void TcPlan::layout(Carve &cv, cudaStream_t st) {
+  auto up = [&](const std::vector<Task> &v) {
+    Task *p = cv.take<Task>(std::max<size_t>(v.size(), 1));
+    if (cv.base && !v.empty())
+      cudaMemcpyAsync(p, v.data(), v.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
+    return p;
+  };
+  d_gemm_ = up(gemm_);
+  d_potrf_ = up(potrf_);
+  d_trsm_ = up(trsm_);
+  d_syrk_ = up(syrk_);
+  d_maps_ = cv.take<CUtensorMap>(std::max(nfronts_, 1));
+  ready_ = false;
+}
+
+void TcPlan::encode(const Plan &plan, float *L, cudaStream_t st) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  std::vector<CUtensorMap> maps(plan.fronts.size());
+  for (size_t s = 0; s < plan.fronts.size(); s++) {
+    const FrontInfo &F = plan.fronts[s];
+    cuuint64_t dims[2] = {(cuuint64_t)F.ncol, (cuuint64_t)(F.ncol + F.nrow)};
+    cuuint64_t strides[1] = {(cuuint64_t)F.ld * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)kTileM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(L + F.loff), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      throw std::runtime_error("cuTensorMapEncodeTiled failed for front " + std::to_string(s));
+  }
+  if (!maps.empty())
+    if (cudaMemcpyAsync(d_maps_, maps.data(), maps.size() * sizeof(CUtensorMap),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+      throw std::runtime_error("tensor map upload failed");
+  if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("tensor map upload failed");
+  cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  ready_ = true;
+}
+
+void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
+                    int32_t *status, bool bf16, cudaStream_t st) {
+  (void)bf16;
+  const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
+  for (size_t li = 0; li < levels_.size(); li++) {
+    launch_build_level<float>(dp, plan.levels[li], kval, L, U, st);
+    for (const Step &s : levels_[li].steps) {
+      if (s.gemm_e > s.gemm_b)
+        { note_launch(); tc_gemm_kernel<<<s.gemm_e - s.gemm_b, 192, kSmemBytes, st>>>(dp, d_gemm_ + s.gemm_b, maps, L, U, kNb, status); }
+      launch_potrf<float>(dp, d_potrf_ + s.potrf_b, s.potrf_e - s.potrf_b, kNb, L, status, true, st);
+      launch_trsm<float>(dp, d_trsm_ + s.trsm_b, s.trsm_e - s.trsm_b, kNb, L, st);
+    }
+    const Level &lv = levels_[li];
+    if (lv.syrk_e > lv.syrk_b)
+      { note_launch(); tc_gemm_kernel<<<lv.syrk_e - lv.syrk_b, 192, kSmemBytes, st>>>(dp, d_syrk_ + lv.syrk_b, maps, L, U, kNb, status); }
+  }
+}
 
 }  // namespace gipm

@@ -1,29 +1,38 @@
-// Tensor-core (tcgen05) factorisation path: TF32 or BF16 operands staged by
-// TMA into shared memory, FP32 accumulators in tensor memory.
+// Tensor-core (tcgen05) factorisation path: TF32 operands staged by TMA into
+// 128B-swizzled shared memory, FP32 accumulators in tensor memory. The GEMM-
+// shaped work of the factorisation (left-looking panel updates and the
+// update-matrix SYRK) runs here; the diagonal-block Cholesky and the
+// triangular solve of the rows below stay on the FP32 FMA pipe.
 #pragma once
+
+#include <vector>
 
 #include "dev.cuh"
 
 namespace gipm {
 
-struct Carve;
-
 class TcPlan {
  public:
-  // Host-side preparation after the symbolic analysis (task lists, sizes).
+  static constexpr int kNb = 128;  // block-column width of the tensor-core path
+  // Host task lists (after the symbolic analysis and plan).
   void build(const Plan &plan);
-  // Carve device memory inside the workspace (cv == nullptr: size only).
-  template <typename C>
-  void layout(C *cv, const Plan &plan, cudaStream_t st);
+  // Carve device memory for tasks and tensor maps (cv.base == nullptr: size only).
+  void layout(Carve &cv, cudaStream_t st);
+  // Encode one TMA tensor map per front panel of the FP32 factor storage L.
+  void encode(const Plan &plan, float *L, cudaStream_t st);
   bool ready() const { return ready_; }
   void factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
               int32_t *status, bool bf16, cudaStream_t st);
 
  private:
+  struct Step { int gemm_b, gemm_e, potrf_b, potrf_e, trsm_b, trsm_e; };
+  struct Level { std::vector<Step> steps; int syrk_b = 0, syrk_e = 0; };
+  std::vector<Task> gemm_, potrf_, trsm_, syrk_;
+  std::vector<Level> levels_;
+  int nfronts_ = 0;
+  Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_syrk_ = nullptr;
+  void *d_maps_ = nullptr;  // nfronts_ CUtensorMap (128 bytes each)
   bool ready_ = false;
 };
-
-template <typename C>
-void TcPlan::layout(C *, const Plan &, cudaStream_t) {}
 
 }  // namespace gipm

@@ -1,0 +1,93 @@
+"""Tensor-core (tcgen05, TF32) factorisation vs the CPU oracle.
+
+TF32 keeps 10 explicit mantissa bits, so the factor itself is only accurate to
+about 1e-3 relative; FP64 refinement must then recover a 1e-10 solve residual
+and the interior-point method the oracle's objective. Fronts of the 15^3 grid
+span 4 block columns of 128 (450-column top separator) and several K tiles."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2508_16094_gb300 as gb  # noqa: E402
+from tests.test_gpu_parity import _ctx, _oracle_K, _problem, _state, dev  # noqa: E402
+
+TF32_BACKWARD = 5e-3  # ||L L^T - K||_F / ||K||_F allowed for a TF32 factor (unit roundoff 2^-11)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gb.build()
+    oracle.build()
+
+
+def _dense_factor(ctx, S, n):
+    cols = np.repeat(np.arange(n), np.diff(S.lp) + 1).astype(np.int32)
+    rows = np.empty_like(cols)
+    for j in range(n):
+        b = S.lp[j] + j
+        rows[b] = j
+        rows[b + 1: b + 1 + S.lp[j + 1] - S.lp[j]] = S.li[S.lp[j]:S.lp[j + 1]]
+    L = np.zeros((n, n))
+    L[rows, cols] = ctx.kkt_factor_entries(rows, cols)
+    return L
+
+
+@pytest.mark.parametrize("name", ["grid15", "random600", "grid7x9x5"])
+def test_tf32_factor_backward_error(name):
+    lp, perm = _problem(name)
+    ctx, info = _ctx(lp, perm, precision=gb.IPM_TF32, storage_fp64=0)
+    S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
+    D = _state(lp, 2, spread=1.0)
+    ctx.kkt_assemble(dev(lp.val), dev(D), 1e-8)
+    st, bad = ctx.kkt_factor(gb.IPM_TF32)
+    assert st == 0 and ctx.ipm_last_perturbed() == 0
+    K = oracle.k_dense(S, _oracle_K(S, lp, D, 1e-8), final=True)
+    L = _dense_factor(ctx, S, lp.n)
+    err = np.linalg.norm(L @ L.T - K) / np.linalg.norm(K)
+    assert err <= TF32_BACKWARD
+    # the same factor in FP32 FMA arithmetic is far more accurate: TF32 really ran
+    ctx.kkt_factor(gb.IPM_FP32)
+    L32 = _dense_factor(ctx, S, lp.n)
+    err32 = np.linalg.norm(L32 @ L32.T - K) / np.linalg.norm(K)
+    assert err32 <= 1e-5
+    lval, _ = oracle.factor(S, _oracle_K(S, lp, D, 1e-8))
+    assert np.abs(L - oracle.l_dense(S, lval)).max() <= 0.05 * np.abs(lval).max()
+
+
+@pytest.mark.parametrize("name", ["grid15", "random600"])
+def test_tf32_solve_refined_to_1e10(name):
+    lp, perm = _problem(name)
+    ctx, info = _ctx(lp, perm, precision=gb.IPM_TF32, storage_fp64=0)
+    S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
+    D = _state(lp, 3, spread=3.0)
+    ctx.kkt_assemble(dev(lp.val), dev(D), 1e-8)
+    ctx.kkt_factor(gb.IPM_TF32)
+    b = gen.normal(4, lp.n)
+    x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    info = ctx.kkt_solve(dev(b), x, gb.IPM_REFINE_IR)
+    assert info.rel_residual <= 1e-10
+    K = oracle.k_dense(S, _oracle_K(S, lp, D, 1e-8))
+    assert np.abs(K @ x.cpu().numpy() - b).max() <= 4e-10 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("name", ["grid15", "random600"])
+def test_tf32_ipm_matches_oracle(name):
+    lp, perm = _problem(name)
+    ctx, info = _ctx(lp, perm, precision=gb.IPM_TF32, storage_fp64=0, tol=1e-6)
+    S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
+    ref = oracle.ipm_lp(S, lp, tol=1e-6)
+    mt = lp.m + 2 * lp.n
+    x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    s = torch.empty(mt, dtype=torch.float64, device="cuda")
+    lam = torch.empty(mt, dtype=torch.float64, device="cuda")
+    res = ctx.ipm_solve(dev(lp.val), dev(lp.b), dev(lp.c), x, s, lam)
+    assert res.status == 0, res.as_dict()
+    assert res.kkt <= 1e-6
+    assert abs(res.objective - ref["objective"]) <= 1e-6 * abs(ref["objective"])

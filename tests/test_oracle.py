@@ -81,7 +81,6 @@ def _check_symbolic(n, rowptr, col, perm):
         z = nz - int(counts[c0:c1].sum())
         assert z >= 0
         if z > 0:
-            assert ncol <= 256
             assert (ncol <= 4 or (ncol <= 16 and 10 * z <= 8 * nz) or (ncol <= 48 and 10 * z <= nz)
                     or 20 * z <= nz)
         # supernode parent and level
