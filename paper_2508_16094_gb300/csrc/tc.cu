@@ -127,13 +127,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// Task: front, a = first row of the A tile (block-local), b = k (mode 0) or j0
-// (mode 1), c = mode. Mode 0: C = panel[a:a+128, k:k+kb], A = panel rows a..,
-// B = panel rows k.., K = k. Mode 1: C = U[a:a+128, b:b+128], A = panel rows
-// ncol+a.., B = panel rows ncol+b.., K = ncol.
+// Task: front, a = first row of the A tile (front-local), b = k (modes 0, 2) or
+// j0 (mode 1), c = mode | slot << 2.
+//  Mode 0 (left-looking update): C = panel[a:a+128, k:k+kb] -= A B^T with
+//    A = panel rows a.., B = panel rows k.., K = k.
+//  Mode 1 (update matrix): C = U[a:a+128, b:b+128] -= A B^T with
+//    A = panel rows ncol+a.., B = panel rows ncol+b.., K = ncol.
+//  Mode 2 (triangular solve of the rows below a diagonal block, as a product
+//    with its inverse): C = panel[a:a+128, k:k+kb] = A B^T with A = the same
+//    panel rows and columns, B = L_kk^{-1} from scratch slot `slot`, K = kb.
+//    The tile's rows are read completely before its epilogue overwrites them.
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, const CUtensorMap *__restrict__ maps,
-                   float *__restrict__ L, float *__restrict__ U, int nb, int32_t *status) {
+                   const CUtensorMap *__restrict__ inv_map, float *__restrict__ L,
+                   float *__restrict__ U, int nb, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -148,16 +155,29 @@ __global__ void __launch_bounds__(192, 1)
   const Task tk = tasks[blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
   const int nf = F.ncol + F.nrow;
-  int arow, brow, K, M, N;
+  const int mode = tk.c & 3;
+  int arow, brow, K, M, N, ax0 = 0;
   float *C;
   int64_t ldc;
-  if (tk.c == 0) {
+  const CUtensorMap *amap = maps + tk.front, *bmap = amap;
+  if (mode == 0) {
     const int k = tk.b;
     arow = tk.a;
     brow = k;
     K = k;
     M = min(kTileM, nf - tk.a);
     N = min(nb, F.ncol - k);
+    C = L + F.loff + (int64_t)tk.a * F.ld + k;
+    ldc = F.ld;
+  } else if (mode == 2) {
+    const int k = tk.b;
+    arow = tk.a;
+    ax0 = k;
+    brow = (tk.c >> 2) * kTileN;
+    bmap = inv_map;
+    N = min(nb, F.ncol - k);
+    K = N;
+    M = min(kTileM, nf - tk.a);
     C = L + F.loff + (int64_t)tk.a * F.ld + k;
     ldc = F.ld;
   } else {
@@ -169,7 +189,6 @@ __global__ void __launch_bounds__(192, 1)
     C = U + F.uoff + (int64_t)tk.a * F.uld + tk.b;
     ldc = F.uld;
   }
-  const CUtensorMap *tmap = maps + tk.front;
   const int nk = (K + kTileK - 1) / kTileK;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -200,8 +219,8 @@ __global__ void __launch_bounds__(192, 1)
         const int s = kt % kStages, round = kt / kStages;
         if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
         mbar_arrive_expect_tx(&full[s], 2 * kTileBytes);
-        tma_load_2d(sA + s * kTileBytes, tmap, &full[s], kt * kTileK, arow);
-        tma_load_2d(sB + s * kTileBytes, tmap, &full[s], kt * kTileK, brow);
+        tma_load_2d(sA + s * kTileBytes, amap, &full[s], ax0 + kt * kTileK, arow);
+        tma_load_2d(sB + s * kTileBytes, bmap, &full[s], kt * kTileK, brow);
       }
     }
   } else if (warp == 1) {
@@ -232,9 +251,15 @@ __global__ void __launch_bounds__(192, 1)
         if (row < M) {
           float *crow = C + (int64_t)row * ldc + cb * 32;
           const int nc = min(32, N - cb * 32);
+          if (mode == 2) {
 #pragma unroll
-          for (int c = 0; c < 32; c++)
-            if (c < nc) crow[c] -= v[c];
+            for (int c = 0; c < 32; c++)
+              if (c < nc) crow[c] = v[c];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+              if (c < nc) crow[c] -= v[c];
+          }
         }
       }
     }
@@ -245,6 +270,70 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTileN));
 }
+
+// Cholesky of one diagonal block (kb <= 128) in FP32 and the explicit inverse
+// of its factor, written row-major (128 x 128, zero outside the lower kb x kb
+// triangle) to scratch slot `b` for the triangular solve of the rows below as
+// a tensor-core product. Division-free 2D thread mapping for the trailing
+// update; a non-positive pivot is replaced by a large value (static pivoting)
+// and counted.
+__global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *__restrict__ tasks,
+                                                        float *__restrict__ L,
+                                                        float *__restrict__ Linv,
+                                                        int32_t *status) {
+  constexpr int LS = 129;
+  const Task tk = tasks[blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int k = tk.a, slot = tk.b, kb = min(TcPlan::kNb, F.ncol - k);
+  extern __shared__ float smf[];
+  float *A = smf;            // [128][129]
+  float *X = smf + 128 * LS;  // [128][129]
+  float *g = L + F.loff + (int64_t)k * F.ld + k;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int e = tid; e < 128 * 128; e += 256) {
+    const int r = e >> 7, c = e & 127;
+    A[r * LS + c] = (r < kb && c <= r) ? g[(int64_t)r * F.ld + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; j++) {
+    if (tid == 0) {
+      float d = A[j * LS + j];
+      if (!(d > 0.f) || !(d < 3.0e38f)) {
+        d = 1e30f;
+        atomicAdd(&status[ST_PERTURBED], 1);
+      }
+      A[j * LS + j] = sqrtf(d);
+    }
+    __syncthreads();
+    const float ljj = A[j * LS + j];
+    if (tid > j && tid < kb) A[tid * LS + j] /= ljj;
+    __syncthreads();
+    for (int r = j + 1 + ty; r < kb; r += 16) {
+      const float arj = A[r * LS + j];
+      for (int c = j + 1 + tx; c <= r; c += 16) A[r * LS + c] = fmaf(-arj, A[c * LS + j], A[r * LS + c]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += 256) {
+    const int r = e / kb, c = e % kb;
+    if (c <= r) g[(int64_t)r * F.ld + c] = A[r * LS + c];
+  }
+  if (tid < 128) {  // column c of the inverse by forward substitution
+    const int c = tid;
+    for (int i = 0; i < 128; i++) X[i * LS + c] = 0.f;
+    if (c < kb)
+      for (int i = c; i < kb; i++) {
+        float s = (i == c) ? 1.f : 0.f;
+        for (int m = c; m < i; m++) s = fmaf(-A[i * LS + m], X[m * LS + c], s);
+        X[i * LS + c] = s / A[i * LS + i];
+      }
+  }
+  __syncthreads();
+  float *out = Linv + (int64_t)slot * 128 * 128;
+  for (int e = tid; e < 128 * 128; e += 256) out[e] = X[(e >> 7) * LS + (e & 127)];
+}
+
+constexpr int kPotrfInvSmem = 2 * 128 * 129 * 4;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -269,6 +358,7 @@ void TcPlan::build(const Plan &plan) {
   syrk_.clear();
   levels_.assign(plan.levels.size(), Level{});
   nfronts_ = (int)plan.fronts.size();
+  max_slots_ = 1;
   for (size_t li = 0; li < plan.levels.size(); li++) {
     const LevelPlan &LP = plan.levels[li];
     Level &lv = levels_[li];
@@ -283,18 +373,22 @@ void TcPlan::build(const Plan &plan) {
       }
       st.gemm_e = (int)gemm_.size();
       st.potrf_b = (int)potrf_.size();
+      int32_t slot = 0;
       for (int32_t t = LP.front_b; t < LP.front_e; t++) {
         const int32_t s = plan.level_fronts[t];
-        if (plan.fronts[s].ncol > k) potrf_.push_back({s, k, 0, 0});
+        if (plan.fronts[s].ncol > k) potrf_.push_back({s, k, slot++, 0});
       }
       st.potrf_e = (int)potrf_.size();
+      max_slots_ = std::max(max_slots_, slot);
       st.trsm_b = (int)trsm_.size();
+      slot = 0;
       for (int32_t t = LP.front_b; t < LP.front_e; t++) {
         const int32_t s = plan.level_fronts[t];
         const FrontInfo &F = plan.fronts[s];
         if (F.ncol <= k) continue;
         const int32_t kb = std::min(kNb, F.ncol - k);
-        for (int32_t i0 = k + kb; i0 < F.ncol + F.nrow; i0 += kTrsmRows) trsm_.push_back({s, i0, k, 0});
+        for (int32_t i0 = k + kb; i0 < F.ncol + F.nrow; i0 += kTileM) trsm_.push_back({s, i0, k, 2 | (slot << 2)});
+        slot++;
       }
       st.trsm_e = (int)trsm_.size();
       lv.steps.push_back(st);
@@ -321,10 +415,12 @@ void TcPlan::build(const Plan &plan) {
   for (const Task &t : trsm_) {
     const FrontInfo &F = plan.fronts[t.front];
     const int kb = std::min(kNb, F.ncol - t.b);
-    if (!(t.b >= 0 && t.b < F.ncol && t.a >= t.b + kb && t.a < F.ncol + F.nrow)) fail("trsm");
+    if (!(t.b >= 0 && t.b < F.ncol && t.a >= t.b + kb && t.a < F.ncol + F.nrow && (t.c & 3) == 2 &&
+          (t.c >> 2) < max_slots_))
+      fail("trsm");
   }
   for (const Task &t : potrf_)
-    if (!(t.a >= 0 && t.a < plan.fronts[t.front].ncol)) fail("potrf");
+    if (!(t.a >= 0 && t.a < plan.fronts[t.front].ncol && t.b >= 0 && t.b < max_slots_)) fail("potrf");
   ready_ = false;
 }
 
@@ -339,7 +435,8 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_potrf_ = up(potrf_);
   d_trsm_ = up(trsm_);
   d_syrk_ = up(syrk_);
-  d_maps_ = cv.take<CUtensorMap>(std::max(nfronts_, 1));
+  d_maps_ = cv.take<CUtensorMap>(std::max(nfronts_, 1) + 1);  // + the inverse-scratch map
+  d_inv_ = cv.take<float>((size_t)max_slots_ * kTileM * kTileN);
   ready_ = false;
 }
 
@@ -359,12 +456,25 @@ void TcPlan::encode(const Plan &plan, float *L, cudaStream_t st) {
     if (r != CUDA_SUCCESS)
       throw std::runtime_error("cuTensorMapEncodeTiled failed for front " + std::to_string(s));
   }
+  {
+    CUtensorMap im;
+    cuuint64_t dims[2] = {(cuuint64_t)kTileN, (cuuint64_t)max_slots_ * kTileM};
+    cuuint64_t strides[1] = {(cuuint64_t)kTileN * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)kTileN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&im, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d_inv_, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed for the inverse scratch");
+    maps.push_back(im);
+  }
   if (!maps.empty())
     if (cudaMemcpyAsync(d_maps_, maps.data(), maps.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
       throw std::runtime_error("tensor map upload failed");
   if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("tensor map upload failed");
   cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfInvSmem);
   ready_ = true;
 }
 
@@ -372,17 +482,20 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
                     int32_t *status, bool bf16, cudaStream_t st) {
   (void)bf16;
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
+  const CUtensorMap *inv_map = maps + nfronts_;
   for (size_t li = 0; li < levels_.size(); li++) {
     launch_build_level<float>(dp, plan.levels[li], kval, L, U, st);
     for (const Step &s : levels_[li].steps) {
       if (s.gemm_e > s.gemm_b)
-        { note_launch(); tc_gemm_kernel<<<s.gemm_e - s.gemm_b, 192, kSmemBytes, st>>>(dp, d_gemm_ + s.gemm_b, maps, L, U, kNb, status); }
-      launch_potrf<float>(dp, d_potrf_ + s.potrf_b, s.potrf_e - s.potrf_b, kNb, L, status, true, st);
-      launch_trsm<float>(dp, d_trsm_ + s.trsm_b, s.trsm_e - s.trsm_b, kNb, L, st);
+        { note_launch(); tc_gemm_kernel<<<s.gemm_e - s.gemm_b, 192, kSmemBytes, st>>>(dp, d_gemm_ + s.gemm_b, maps, inv_map, L, U, kNb, status); }
+      if (s.potrf_e > s.potrf_b)
+        { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, kPotrfInvSmem, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, status); }
+      if (s.trsm_e > s.trsm_b)
+        { note_launch(); tc_gemm_kernel<<<s.trsm_e - s.trsm_b, 192, kSmemBytes, st>>>(dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, kNb, status); }
     }
     const Level &lv = levels_[li];
     if (lv.syrk_e > lv.syrk_b)
-      { note_launch(); tc_gemm_kernel<<<lv.syrk_e - lv.syrk_b, 192, kSmemBytes, st>>>(dp, d_syrk_ + lv.syrk_b, maps, L, U, kNb, status); }
+      { note_launch(); tc_gemm_kernel<<<lv.syrk_e - lv.syrk_b, 192, kSmemBytes, st>>>(dp, d_syrk_ + lv.syrk_b, maps, inv_map, L, U, kNb, status); }
   }
 }
 

@@ -29,7 +29,8 @@ class TcPlan {
   struct Level { std::vector<Step> steps; int syrk_b = 0, syrk_e = 0; };
   std::vector<Task> gemm_, potrf_, trsm_, syrk_;
   std::vector<Level> levels_;
-  int nfronts_ = 0;
+  int nfronts_ = 0, max_slots_ = 1;
+  float *d_inv_ = nullptr;  // inverses of the diagonal blocks of one step (max_slots_ x 128 x 128)
   Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_syrk_ = nullptr;
   void *d_maps_ = nullptr;  // nfronts_ CUtensorMap (128 bytes each)
   bool ready_ = false;
