@@ -247,6 +247,32 @@ IPM_API ipm_status kkt_factor_entries(ipm_ctx *ctx, int64_t count, const int32_t
 /* Low-precision pivots replaced by the last kkt_factor. */
 IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);
 
+/* --- allocation-free solve -------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they need a solve (code running while a
+ * memory pool is locked or exhausted, allocation-free callbacks of another
+ * library, or a framework whose allocator must not be re-entered).
+ *
+ * kkt_solve_noalloc: x = P^T L^{-T} L^{-1} P b with the current factor, like
+ * kkt_solve(..., IPM_REFINE_NONE, ...), but its working vectors live in a
+ * static device array of kkt_solve_noalloc_capacity() doubles (8 MiB) that
+ * every GPU loading this library holds until the process exits. It calls no
+ * cudaMalloc/cudaFree and no allocating library routine.
+ *  - d_b, d_x: device, length n, original numbering (may not alias).
+ *  - Size limit: n + (update-vector entries of the plan) + 2464 doubles must fit
+ *    the array, else IPM_ERR_NOMEM with the sizes in ipm_last_error (checked
+ *    right after kkt_analyze, before any GPU work).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array, which keeps the last call's
+ *    contents; calls that overlap on the GPU (other streams, other contexts,
+ *    other threads) race on it and must be serialised by the caller.
+ * Errors: IPM_ERR_STATE before kkt_factor, IPM_ERR_CUDA if the address lookup
+ * or a launch fails. */
+IPM_API ipm_status kkt_solve_noalloc(ipm_ctx *ctx, const double *d_b, double *d_x);
+IPM_API int64_t kkt_solve_noalloc_capacity(void);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts). Read it before and after a call to count that call's launches. */
 IPM_API int64_t ipm_kernel_launches(void);

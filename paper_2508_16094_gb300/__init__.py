@@ -27,7 +27,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_NOMEM", 
 EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze", "ipm_set_workspace",
             "kkt_assemble", "kkt_factor", "kkt_solve", "ipm_solve", "ipm_newton_direction",
             "kkt_symbolic_export", "kkt_export_assembled", "kkt_factor_entries",
-            "ipm_last_perturbed", "ipm_kernel_launches", "ipm_last_error", "ipm_destroy"]
+            "ipm_last_perturbed", "ipm_kernel_launches", "kkt_solve_noalloc",
+            "kkt_solve_noalloc_capacity", "ipm_last_error", "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -109,6 +110,8 @@ def load() -> C.CDLL:
         "kkt_factor_entries": (I32, [P, I64, P, P, P]),
         "ipm_last_perturbed": (I32, [P]),
         "ipm_kernel_launches": (I64, []),
+        "kkt_solve_noalloc": (I32, [P, P, P]),
+        "kkt_solve_noalloc_capacity": (I64, []),
         "ipm_last_error": (C.c_char_p, [P]),
         "ipm_destroy": (None, [P]),
     }
@@ -265,6 +268,14 @@ class IpmContext:
         out = np.empty(len(r), np.float64)
         self._check(self._lib.kkt_factor_entries(self.handle, len(r), _hp(r), _hp(c), _hp(out)))
         return out
+
+    def kkt_solve_noalloc(self, b, x, raise_on_error=True) -> int:
+        """Factor-only solve whose working vectors sit in the library's static
+        device array (no device allocation; see the header for its limits)."""
+        st = self._lib.kkt_solve_noalloc(self.handle, _dp(b), _dp(x))
+        if raise_on_error:
+            self._check(st)
+        return st
 
     def ipm_last_perturbed(self) -> int:
         return int(self._lib.ipm_last_perturbed(self.handle))

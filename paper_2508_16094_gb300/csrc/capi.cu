@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <stdexcept>
 
 #include "../../include/gb300_ipm.h"
@@ -788,5 +789,90 @@ int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }
 const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 void ipm_destroy(ipm_ctx *c) { delete c; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Solve without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// solve: code running while a memory pool is locked or exhausted, code inside
+// another library's allocation-free callback, or a process whose allocator
+// belongs to a framework it must not re-enter. kkt_solve_noalloc gives them
+// the factor-only solve x = P^T L^{-T} L^{-1} P b with its working vectors
+// (the permuted right-hand side, the children's update vectors, a scale and
+// the reduction partials) in the file-scope array below instead of the
+// context workspace. The caller still passes b and x.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocDoubles = size_t(1) << 20;  // 8 MiB per device, held until exit
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device (set up once per device).
+double *noalloc_scratch() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) throw Fail{IPM_ERR_UNSUPPORTED, "device index too large"};
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  return g_noalloc_addr[dev];
+}
+
+size_t noalloc_need(const ipm_ctx *c) {
+  // partials + 32 scalars + y (n) + update vectors (plan.t_entries), in doubles
+  return (size_t)kRedBlocks * 8 + 32 + (size_t)std::max<int32_t>(c->P.n, 1) +
+         (size_t)c->plan.t_entries;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t kkt_solve_noalloc_capacity(void) { return (int64_t)kNoAllocDoubles; }
+
+ipm_status kkt_solve_noalloc(ipm_ctx *c, const double *b, double *x) {
+  if (!c || !b || !x) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 1) throw Fail{IPM_ERR_STATE, "kkt_solve_noalloc before kkt_analyze"};
+    const size_t need = noalloc_need(c);
+    if (need > kNoAllocDoubles)
+      throw Fail{IPM_ERR_NOMEM, "kkt_solve_noalloc needs " + std::to_string(need) +
+                                    " doubles of static scratch (n + update-vector entries + " +
+                                    std::to_string(kRedBlocks * 8 + 32) + "); the limit is " +
+                                    std::to_string(kNoAllocDoubles)};
+    if (c->state < 4) throw Fail{IPM_ERR_STATE, "kkt_solve_noalloc before kkt_factor"};
+    double *base = noalloc_scratch();
+    double *partial = base;
+    double *scal = base + (size_t)kRedBlocks * 8;
+    double *y = scal + 32;
+    double *t = y + std::max<int32_t>(c->P.n, 1);
+    // every entry of y and t is written before it is read (permutation in,
+    // then the gathers initialise each front's update vector): nothing to clear
+    VecOps V{c->dp, c->st, partial};
+    if (c->factor_prec == IPM_FP64) {
+      V.permute_in<double>(b, nullptr, y);
+      launch_solve<double, double>(c->dp, c->plan, (const double *)c->L, y, t, c->st);
+      V.permute_out<double>(y, nullptr, x, false);
+    } else {
+      V.absmax(c->P.n, b, scal + 1);
+      V.inv_scale(scal + 1, scal);
+      float *yf = reinterpret_cast<float *>(y), *tf = reinterpret_cast<float *>(t);
+      V.permute_in<float>(b, scal, yf);
+      launch_solve<float, float>(c->dp, c->plan, (const float *)c->L, yf, tf, c->st);
+      V.permute_out<float>(yf, scal, x, false);
+    }
+    CK(cudaGetLastError());
+    return IPM_OK;
+  });
+}
 
 }  // extern "C"
