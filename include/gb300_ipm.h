@@ -73,7 +73,9 @@ typedef enum {
   IPM_FP64 = 0, /* FP64 FMA                                             [FP64] */
   IPM_FP32 = 1, /* FP32 FMA                                             [FP32] */
   IPM_TF32 = 2, /* TF32 tensor cores (tcgen05), FP32 accumulate (TMEM)  [FP32] */
-  IPM_BF16 = 3  /* BF16 tensor cores (tcgen05), FP32 accumulate (TMEM)  [FP32] */
+  IPM_BF16 = 3, /* BF16 tensor cores (tcgen05), FP32 accumulate (TMEM)  [FP32] */
+  IPM_TF32X3 = 4 /* TF32 tensor cores, 3-term split A_lo B + A B_lo + A B: about
+                    FP32-accurate products; FP32 accumulate (TMEM)      [FP32] */
 } ipm_precision;
 
 typedef enum {

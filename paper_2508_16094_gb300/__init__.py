@@ -16,10 +16,10 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["IpmError", "IpmContext", "Options", "load", "build", "lib_path",
-           "IPM_FP64", "IPM_FP32", "IPM_TF32", "IPM_BF16",
+           "IPM_FP64", "IPM_FP32", "IPM_TF32", "IPM_BF16", "IPM_TF32X3",
            "IPM_REFINE_NONE", "IPM_REFINE_IR", "IPM_REFINE_PCG"]
 
-IPM_FP64, IPM_FP32, IPM_TF32, IPM_BF16 = 0, 1, 2, 3
+IPM_FP64, IPM_FP32, IPM_TF32, IPM_BF16, IPM_TF32X3 = 0, 1, 2, 3, 4
 IPM_REFINE_NONE, IPM_REFINE_IR, IPM_REFINE_PCG = 0, 1, 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_NOMEM", 5: "ERR_NOT_SPD",
           6: "ERR_NUMERIC", 7: "ERR_MAXITER", 8: "ERR_TIMEOUT", 9: "ERR_STALL",

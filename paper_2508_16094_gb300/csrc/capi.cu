@@ -220,7 +220,8 @@ double d2h_scalar(ipm_ctx *c, const double *p) {
 // ---- factor ----------------------------------------------------------------
 ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   if (c->state < 3) throw Fail{IPM_ERR_STATE, "kkt_factor before kkt_assemble"};
-  if (prec < IPM_FP64 || prec > IPM_BF16) throw Fail{IPM_ERR_ARG, "unknown precision"};
+  if (prec < IPM_FP64 || prec > IPM_TF32X3) throw Fail{IPM_ERR_ARG, "unknown precision"};
+  if (prec == IPM_BF16) throw Fail{IPM_ERR_UNSUPPORTED, "BF16 factorisation not available"};
   if (prec == IPM_FP64 && c->storage_bytes < 8)
     throw Fail{IPM_ERR_NOMEM, "factor storage sized for FP32; FP64 factor needs storage_fp64"};
   int32_t init[ST_COUNT] = {INT32_MAX, 0, 0, 0, 0, 0, 0, 0};
@@ -234,7 +235,7 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   } else {
     if (!c->tcp.ready()) throw Fail{IPM_ERR_UNSUPPORTED, "tensor-core factor not prepared"};
     c->tcp.factor(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->status,
-                  prec == IPM_BF16, c->st);
+                  prec == IPM_TF32X3 ? 3 : 1, c->st);
   }
   CK(cudaGetLastError());
   int32_t out[ST_COUNT];

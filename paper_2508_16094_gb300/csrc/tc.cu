@@ -26,7 +26,12 @@ namespace {
 constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kStages = 4;
 constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per operand tile
 constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
-constexpr int kSmemBytes = 2 * kStages * kTileBytes + 1024 /*barriers*/ + 1024 /*alignment*/;
+template <int SPLIT> struct StagesOf { static constexpr int value = SPLIT == 3 ? 3 : kStages; };
+template <int SPLIT>
+constexpr int smem_bytes() {
+  return (SPLIT == 3 ? 4 : 2) * StagesOf<SPLIT>::value * kTileBytes + 1024 /*barriers*/ +
+         1024 /*alignment*/;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -52,6 +57,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// x - tf32(x): what the tensor core drops from an FP32 operand (low 13 mantissa bits)
+__device__ __forceinline__ float lo1(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float4 lo_part(float4 v) {
+  return make_float4(lo1(v.x), lo1(v.y), lo1(v.z), lo1(v.w));
 }
 
 // Bounded wait on an mbarrier phase; false (and ST_TIMEOUT recorded) on expiry.
@@ -137,6 +154,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 //    with its inverse): C = panel[a:a+128, k:k+kb] = A B^T with A = the same
 //    panel rows and columns, B = L_kk^{-1} from scratch slot `slot`, K = kb.
 //    The tile's rows are read completely before its epilogue overwrites them.
+template <int SPLIT>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, const CUtensorMap *__restrict__ maps,
                    const CUtensorMap *__restrict__ inv_map, float *__restrict__ L,
@@ -144,11 +162,15 @@ __global__ void __launch_bounds__(192, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
+  constexpr int S = StagesOf<SPLIT>::value;
   uint8_t *sA = base;
-  uint8_t *sB = base + kStages * kTileBytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + 2 * kStages * kTileBytes);
-  uint64_t *empty = full + kStages;
-  uint64_t *accum = empty + kStages;
+  uint8_t *sB = base + S * kTileBytes;
+  uint8_t *sAl = base + 2 * S * kTileBytes;  // low parts (SPLIT == 3 only)
+  uint8_t *sBl = base + 3 * S * kTileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + (SPLIT == 3 ? 4 : 2) * S * kTileBytes);
+  uint64_t *empty = full + S;
+  uint64_t *lofull = empty + S;
+  uint64_t *accum = lofull + S;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -193,9 +215,10 @@ __global__ void __launch_bounds__(192, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; s++) {
+    for (int s = 0; s < S; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&lofull[s], 4);  // one arrival per converting warp
     }
     mbar_init(accum, 1);
     *abort_flag = 0;
@@ -216,7 +239,7 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) {
     if (lane == 0) {
       for (int kt = 0; kt < nk; kt++) {
-        const int s = kt % kStages, round = kt / kStages;
+        const int s = kt % S, round = kt / S;
         if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
         mbar_arrive_expect_tx(&full[s], 2 * kTileBytes);
         tma_load_2d(sA + s * kTileBytes, amap, &full[s], ax0 + kt * kTileK, arow);
@@ -227,19 +250,48 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = tf32_idesc();
       for (int kt = 0; kt < nk; kt++) {
-        const int s = kt % kStages, round = kt / kStages;
+        const int s = kt % S, round = kt / S;
         if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
+        if (SPLIT == 3 && !mbar_wait(&lofull[s], round & 1, status)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint64_t ad = sw128_desc(smem_u32(sA + s * kTileBytes));
         const uint64_t bd = sw128_desc(smem_u32(sB + s * kTileBytes));
+        const uint64_t ald = sw128_desc(smem_u32(sAl + s * kTileBytes));
+        const uint64_t bld = sw128_desc(smem_u32(sBl + s * kTileBytes));
 #pragma unroll
-        for (int k4 = 0; k4 < kTileK / 8; k4++)  // 8 TF32 = 32 bytes per MMA along K
-          mma_tf32(tmem, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+        for (int k4 = 0; k4 < kTileK / 8; k4++) {  // 8 TF32 = 32 bytes per MMA along K
+          if (SPLIT == 3) {  // small terms first: A_lo B + A B_lo, then A B
+            mma_tf32(tmem, ald + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+            mma_tf32(tmem, ad + 2 * k4, bld + 2 * k4, idesc, 1);
+            mma_tf32(tmem, ad + 2 * k4, bd + 2 * k4, idesc, 1);
+          } else {
+            mma_tf32(tmem, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+          }
+        }
         mma_commit(&empty[s]);
       }
       mma_commit(accum);
     }
   } else {
+    if (SPLIT == 3) {
+      // low parts x - tf32(x) of both operand tiles (tf32 keeps the top 19 bits)
+      const int t = threadIdx.x - 64;
+      for (int kt = 0; kt < nk && !*abort_flag; kt++) {
+        const int s = kt % S, round = kt / S;
+        if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
+        const float4 *a = reinterpret_cast<const float4 *>(sA + s * kTileBytes);
+        const float4 *b = reinterpret_cast<const float4 *>(sB + s * kTileBytes);
+        float4 *al = reinterpret_cast<float4 *>(sAl + s * kTileBytes);
+        float4 *bl = reinterpret_cast<float4 *>(sBl + s * kTileBytes);
+        for (int i = t; i < kTileBytes / 16; i += 128) {
+          al[i] = lo_part(a[i]);
+          bl[i] = lo_part(b[i]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&lofull[s]);
+      }
+    }
     const bool ok = mbar_wait(accum, 0, status);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int q = warp % 4;  // tensor-memory lane quarter this warp may access
@@ -473,29 +525,39 @@ void TcPlan::encode(const Plan &plan, float *L, cudaStream_t st) {
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
       throw std::runtime_error("tensor map upload failed");
   if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("tensor map upload failed");
-  cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
+  cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<3>());
   cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfInvSmem);
   ready_ = true;
 }
 
+template <int SPLIT>
+static void gemm_launch(int ntask, const DevPlan &dp, const Task *tasks, const CUtensorMap *maps,
+                        const CUtensorMap *inv_map, float *L, float *U, int32_t *status,
+                        cudaStream_t st) {
+  note_launch();
+  tc_gemm_kernel<SPLIT><<<ntask, 192, smem_bytes<SPLIT>(), st>>>(dp, tasks, maps, inv_map, L, U,
+                                                                 TcPlan::kNb, status);
+}
+
 void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
-                    int32_t *status, bool bf16, cudaStream_t st) {
-  (void)bf16;
+                    int32_t *status, int split, cudaStream_t st) {
+  auto gemm = split == 3 ? gemm_launch<3> : gemm_launch<1>;
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
   const CUtensorMap *inv_map = maps + nfronts_;
   for (size_t li = 0; li < levels_.size(); li++) {
     launch_build_level<float>(dp, plan.levels[li], kval, L, U, st);
     for (const Step &s : levels_[li].steps) {
       if (s.gemm_e > s.gemm_b)
-        { note_launch(); tc_gemm_kernel<<<s.gemm_e - s.gemm_b, 192, kSmemBytes, st>>>(dp, d_gemm_ + s.gemm_b, maps, inv_map, L, U, kNb, status); }
+        gemm(s.gemm_e - s.gemm_b, dp, d_gemm_ + s.gemm_b, maps, inv_map, L, U, status, st);
       if (s.potrf_e > s.potrf_b)
         { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, kPotrfInvSmem, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, status); }
       if (s.trsm_e > s.trsm_b)
-        { note_launch(); tc_gemm_kernel<<<s.trsm_e - s.trsm_b, 192, kSmemBytes, st>>>(dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, kNb, status); }
+        gemm(s.trsm_e - s.trsm_b, dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, status, st);
     }
     const Level &lv = levels_[li];
     if (lv.syrk_e > lv.syrk_b)
-      { note_launch(); tc_gemm_kernel<<<lv.syrk_e - lv.syrk_b, 192, kSmemBytes, st>>>(dp, d_syrk_ + lv.syrk_b, maps, inv_map, L, U, kNb, status); }
+      gemm(lv.syrk_e - lv.syrk_b, dp, d_syrk_ + lv.syrk_b, maps, inv_map, L, U, status, st);
   }
 }
 

@@ -21,8 +21,10 @@ class TcPlan {
   // Encode one TMA tensor map per front panel of the FP32 factor storage L.
   void encode(const Plan &plan, float *L, cudaStream_t st);
   bool ready() const { return ready_; }
+  // split = 1: plain TF32 products; split = 3: A_lo B + A B_lo + A B with the
+  // low parts formed in shared memory (FP32-accurate products on tensor cores)
   void factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
-              int32_t *status, bool bf16, cudaStream_t st);
+              int32_t *status, int split, cudaStream_t st);
 
  private:
   struct Step { int gemm_b, gemm_e, potrf_b, potrf_e, trsm_b, trsm_e; };

@@ -39,19 +39,26 @@ def _dense_factor(ctx, S, n):
     return L
 
 
+TF32X3_BACKWARD = 2e-6  # 3-term split: products about as accurate as FP32 FMA
+
+
+@pytest.mark.parametrize("prec,bound", [(gb.IPM_TF32, TF32_BACKWARD), (gb.IPM_TF32X3, TF32X3_BACKWARD)],
+                         ids=["tf32", "tf32x3"])
 @pytest.mark.parametrize("name", ["grid15", "random600", "grid7x9x5"])
-def test_tf32_factor_backward_error(name):
+def test_tf32_factor_backward_error(name, prec, bound):
     lp, perm = _problem(name)
-    ctx, info = _ctx(lp, perm, precision=gb.IPM_TF32, storage_fp64=0)
+    ctx, info = _ctx(lp, perm, precision=prec, storage_fp64=0)
     S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
     D = _state(lp, 2, spread=1.0)
     ctx.kkt_assemble(dev(lp.val), dev(D), 1e-8)
-    st, bad = ctx.kkt_factor(gb.IPM_TF32)
+    st, bad = ctx.kkt_factor(prec)
     assert st == 0 and ctx.ipm_last_perturbed() == 0
     K = oracle.k_dense(S, _oracle_K(S, lp, D, 1e-8), final=True)
     L = _dense_factor(ctx, S, lp.n)
     err = np.linalg.norm(L @ L.T - K) / np.linalg.norm(K)
-    assert err <= TF32_BACKWARD
+    assert err <= bound
+    if prec == gb.IPM_TF32:
+        assert err >= 1e-5  # the products really ran in TF32
     # the same factor in FP32 FMA arithmetic is far more accurate: TF32 really ran
     ctx.kkt_factor(gb.IPM_FP32)
     L32 = _dense_factor(ctx, S, lp.n)
@@ -61,14 +68,15 @@ def test_tf32_factor_backward_error(name):
     assert np.abs(L - oracle.l_dense(S, lval)).max() <= 0.05 * np.abs(lval).max()
 
 
+@pytest.mark.parametrize("prec", [gb.IPM_TF32, gb.IPM_TF32X3], ids=["tf32", "tf32x3"])
 @pytest.mark.parametrize("name", ["grid15", "random600"])
-def test_tf32_solve_refined_to_1e10(name):
+def test_tf32_solve_refined_to_1e10(name, prec):
     lp, perm = _problem(name)
-    ctx, info = _ctx(lp, perm, precision=gb.IPM_TF32, storage_fp64=0)
+    ctx, info = _ctx(lp, perm, precision=prec, storage_fp64=0)
     S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
     D = _state(lp, 3, spread=3.0)
     ctx.kkt_assemble(dev(lp.val), dev(D), 1e-8)
-    ctx.kkt_factor(gb.IPM_TF32)
+    ctx.kkt_factor(prec)
     b = gen.normal(4, lp.n)
     x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
     info = ctx.kkt_solve(dev(b), x, gb.IPM_REFINE_IR)
@@ -77,10 +85,11 @@ def test_tf32_solve_refined_to_1e10(name):
     assert np.abs(K @ x.cpu().numpy() - b).max() <= 4e-10 * np.abs(b).max()
 
 
+@pytest.mark.parametrize("prec", [gb.IPM_TF32, gb.IPM_TF32X3], ids=["tf32", "tf32x3"])
 @pytest.mark.parametrize("name", ["grid15", "random600"])
-def test_tf32_ipm_matches_oracle(name):
+def test_tf32_ipm_matches_oracle(name, prec):
     lp, perm = _problem(name)
-    ctx, info = _ctx(lp, perm, precision=gb.IPM_TF32, storage_fp64=0, tol=1e-6)
+    ctx, info = _ctx(lp, perm, precision=prec, storage_fp64=0, tol=1e-6)
     S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
     ref = oracle.ipm_lp(S, lp, tol=1e-6)
     mt = lp.m + 2 * lp.n
