@@ -40,6 +40,9 @@ struct ipm_ctx {
          *vt = nullptr, *vjd = nullptr, *vjx = nullptr, *vtA = nullptr;
   double *dl_ = nullptr, *du_ = nullptr;
   double *jv_copy = nullptr, *D_copy = nullptr, *wv_copy = nullptr;  // inputs kept for refinement
+  float *dinv = nullptr, *fsa = nullptr, *fsb = nullptr, *fsx = nullptr;  // fused FP32 solve
+  cudaGraphExec_t solve_graph = nullptr;  // captured fused solve (fixed buffers)
+  int solve_graph_launches = 0;
   double *scal = nullptr, *partial = nullptr;
   IpmScalars *sc = nullptr;
   int32_t *status = nullptr, *col2s = nullptr;
@@ -145,6 +148,10 @@ void layout(ipm_ctx *c, char *base) {
   d.sgemv = upload(cv, pl.sgemv_tasks, st);
   d.rgemv = upload(cv, pl.rgemv_tasks, st);
   d.toff = upload(cv, pl.toff, st);
+  d.fs_fwd = upload(cv, pl.fs_fwd, st);
+  d.fs_bwd = upload(cv, pl.fs_bwd, st);
+  d.fs_inv = upload(cv, pl.fs_inv, st);
+  d.fs_dinv_off = upload(cv, pl.fs_dinv_off, st);
   d.k_slot = upload(cv, pl.k_slot, st);
   d.k_poff = upload(cv, pl.k_poff, st);
   d.k_w = upload(cv, pl.k_w, st);
@@ -201,6 +208,10 @@ void layout(ipm_ctx *c, char *base) {
   c->wv_copy = cv.take<double>(std::max<int64_t>(P.wp.empty() ? 0 : P.wp.back(), 1));
   c->vjx = cv.take<double>(m);
   c->vtA = cv.take<double>(m);
+  c->dinv = cv.take<float>(pl.fs_dinv_entries);
+  c->fsa = cv.take<float>(n);
+  c->fsb = cv.take<float>(n);
+  c->fsx = cv.take<float>(n);
   c->scal = cv.take<double>(64);
   c->partial = cv.take<double>(kRedBlocks * 8);
   c->sc = cv.take<IpmScalars>(1);
@@ -237,6 +248,8 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
     c->tcp.factor(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->status,
                   prec == IPM_TF32X3 ? 3 : 1, c->st);
   }
+  if (prec != IPM_FP64)  // explicit inverses of the diagonal blocks for the fused solve
+    launch_dinv(c->dp, c->plan, (const float *)c->L, c->dinv, c->st);
   CK(cudaGetLastError());
   int32_t out[ST_COUNT];
   CK(cudaMemcpyAsync(out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
@@ -267,11 +280,24 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
     double *scale = c->scal + 8, *amax = c->scal + 9;
     V.absmax(c->P.n, b, amax);
     V.inv_scale(amax, scale);
-    float *y = reinterpret_cast<float *>(c->yv);
     float *t = reinterpret_cast<float *>(c->tv);
-    V.permute_in<float>(b, scale, y);
-    launch_solve<float, float>(c->dp, c->plan, (const float *)c->L, y, t, c->st);
-    V.permute_out<float>(y, scale, out, accumulate);
+    V.permute_in<float>(b, scale, c->fsa);
+    if (!c->solve_graph) {  // capture the fixed launch sequence once
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      c->solve_graph_launches = launch_solve_fused(c->dp, c->plan, (const float *)c->L, c->dinv,
+                                                   c->fsa, c->fsb, c->fsx, t, cs);
+      CK(cudaStreamEndCapture(cs, &g));
+      CK(cudaGraphInstantiate(&c->solve_graph, g, 0));
+      CK(cudaGraphDestroy(g));
+      CK(cudaStreamDestroy(cs));
+    } else {
+      for (int k = 0; k < c->solve_graph_launches; k++) note_launch();
+    }
+    CK(cudaGraphLaunch(c->solve_graph, c->st));
+    V.permute_out<float>(c->fsx, scale, out, accumulate);
   }
 }
 
@@ -522,6 +548,7 @@ ipm_status kkt_analyze(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info)
     analyze_symbolic(c->P, perm, c->S);
     build_plan(c->P, c->S, c->plan, 64, 64);
     validate_plan(c->P, c->S, c->plan);
+    build_fused_solve(c->plan);
     c->tcp.build(c->plan);
     const int so = c->opts.storage_fp64;
     c->storage_bytes = (so == 1 || (so < 0 && (c->opts.precision == IPM_FP64 || c->opts.fallback_fp64))) ? 8 : 4;
@@ -556,6 +583,10 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     if ((size_t)(base - (char *)buf) + c->ws_need - 256 > bytes) throw Fail{IPM_ERR_NOMEM, "workspace misaligned"};
     c->ws = base;
     c->ws_bytes = bytes;
+    if (c->solve_graph) {  // captured against the previous buffers
+      CK(cudaGraphExecDestroy(c->solve_graph));
+      c->solve_graph = nullptr;
+    }
     layout(c, base);
     CK(cudaStreamSynchronize(c->st));
     try {  // tensor maps of the FP32 panels for the tensor-core path
@@ -789,7 +820,10 @@ int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }
 
 const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
-void ipm_destroy(ipm_ctx *c) { delete c; }
+void ipm_destroy(ipm_ctx *c) {
+  if (c && c->solve_graph) cudaGraphExecDestroy(c->solve_graph);
+  delete c;
+}
 
 }  // extern "C"
 

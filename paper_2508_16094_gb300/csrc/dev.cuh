@@ -15,6 +15,8 @@ struct DevPlan {
   const int32_t *children, *inv, *relpos, *sri;
   const Task *build, *gemm, *potrf, *trsm, *syrk, *gath, *sdiag, *sgemv, *rgemv;
   const int64_t *toff;
+  const Task *fs_fwd, *fs_bwd, *fs_inv;  // fused FP32 solve
+  const int64_t *fs_dinv_off;
   const int64_t *k_slot, *k_poff, *k_w, *k_orig;
   const int32_t *k_pa, *k_pb, *k_diag;
   const int32_t *perm;  // final new -> old

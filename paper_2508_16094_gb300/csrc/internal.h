@@ -63,6 +63,7 @@ struct LevelPlan {
   std::vector<StepRange> steps;      // factor steps (block columns)
   std::vector<int32_t> sstep_b;      // solve steps: [sstep_b[j], sstep_b[j+1]) in stasks
   std::vector<int32_t> sgemv_b;      // solve update tasks per step
+  std::vector<int32_t> ffwd_b, fbwd_b;  // fused FP32 solve: task ranges per 128-wide step
   int32_t max_ncol = 0;
 };
 
@@ -81,6 +82,10 @@ struct Plan {
   std::vector<Task> gath_tasks, sdiag_tasks, sgemv_tasks, rgemv_tasks;
   std::vector<int64_t> toff;         // per front: offset of its solve update vector (length nrow)
   int64_t t_entries = 0;
+  // fused FP32 solve: explicit inverses of the 128-wide diagonal blocks
+  std::vector<Task> fs_fwd, fs_bwd, fs_inv;  // c = block slot
+  std::vector<int64_t> fs_dinv_off;          // per block slot: offset of its jb x jb inverse
+  int64_t fs_dinv_entries = 0;
   // K entries in level-major order
   std::vector<int64_t> k_slot;   // element offset of L(i, j) in the factor storage
   std::vector<int64_t> k_poff;   // products [k_poff[q], k_poff[q+1])
@@ -112,5 +117,7 @@ struct Problem {
 void analyze_symbolic(const Problem &P, const int32_t *perm, Symbolic &S);
 void build_plan(const Problem &P, const Symbolic &S, Plan &plan, int nb, int nbs);
 void validate_plan(const Problem &P, const Symbolic &S, const Plan &plan);
+// Task lists of the fused FP32 solve (128-wide blocks), appended to the plan.
+void build_fused_solve(Plan &plan);
 
 }  // namespace gipm

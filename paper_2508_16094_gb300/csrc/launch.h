@@ -33,6 +33,14 @@ void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L,
 template <typename T, typename V>
 void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st);
 
+// Fused FP32 solve: inverses of the 128-wide diagonal blocks (after each FP32
+// factorisation), then x = L^{-T} L^{-1} a with b as the forward result and t
+// the update vectors (all fixed buffers, so the launch sequence can be captured
+// in a CUDA graph). Returns the number of kernels launched.
+void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Dinv, cudaStream_t st);
+int launch_solve_fused(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv,
+                       float *a, float *b, float *x, float *t, cudaStream_t st);
+
 // Sampled entries of L (final numbering).
 template <typename T>
 void launch_factor_entries(const DevPlan &dp, const T *L, const int32_t *col2s, int64_t count,

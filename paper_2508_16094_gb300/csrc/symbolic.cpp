@@ -709,3 +709,73 @@ void validate_plan(const Problem &P, const Symbolic &S, const Plan &pl) {
 }
 
 }  // namespace gipm
+
+namespace gipm {
+
+// Fused FP32 solve: for every front and 128-wide block column j, one inverse
+// task (the diagonal block's inverse, jb x jb, at fs_dinv_off[slot]), forward
+// tasks over the rows [j, nf) in chunks of 128 (the chunk starting at j also
+// publishes the solved block), backward tasks over the columns [0, j) in
+// chunks of 256 (at least one, which publishes the solved block).
+void build_fused_solve(Plan &pl) {
+  constexpr int B = 128, FR = 128, BC = 256;
+  pl.fs_fwd.clear();
+  pl.fs_bwd.clear();
+  pl.fs_inv.clear();
+  pl.fs_dinv_off.clear();
+  pl.fs_dinv_entries = 0;
+  std::vector<std::vector<int32_t>> slot_of(pl.fronts.size());
+  for (size_t s = 0; s < pl.fronts.size(); s++) {
+    const FrontInfo &F = pl.fronts[s];
+    for (int32_t j = 0; j < F.ncol; j += B) {
+      const int32_t jb = std::min(B, F.ncol - j);
+      const int32_t slot = (int32_t)pl.fs_dinv_off.size();
+      slot_of[s].push_back(slot);
+      pl.fs_dinv_off.push_back(pl.fs_dinv_entries);
+      pl.fs_dinv_entries += (int64_t)jb * jb;
+      pl.fs_inv.push_back({(int32_t)s, j, slot, 0});
+    }
+  }
+  pl.fs_dinv_entries = std::max<int64_t>(pl.fs_dinv_entries, 1);
+  for (LevelPlan &LP : pl.levels) {
+    LP.ffwd_b.clear();
+    LP.fbwd_b.clear();
+    for (int32_t j = 0; j < LP.max_ncol; j += B) {
+      LP.ffwd_b.push_back((int32_t)pl.fs_fwd.size());
+      LP.fbwd_b.push_back((int32_t)pl.fs_bwd.size());
+      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+        const int32_t s = pl.level_fronts[t];
+        const FrontInfo &F = pl.fronts[s];
+        if (F.ncol <= j) continue;
+        const int32_t slot = slot_of[s][j / B];
+        for (int32_t i0 = j; i0 < F.ncol + F.nrow; i0 += FR) pl.fs_fwd.push_back({s, i0, j, slot});
+        for (int32_t c0 = 0; c0 < std::max(j, 1); c0 += BC) pl.fs_bwd.push_back({s, c0, j, slot});
+      }
+    }
+    LP.ffwd_b.push_back((int32_t)pl.fs_fwd.size());
+    LP.fbwd_b.push_back((int32_t)pl.fs_bwd.size());
+  }
+  // range checks (the kernels mask only the chunk edges)
+  auto need = [](bool ok, const char *w) {
+    if (!ok) throw std::runtime_error(std::string("fused solve plan check failed: ") + w);
+  };
+  const int32_t nslot = (int32_t)pl.fs_dinv_off.size();
+  for (const Task &t : pl.fs_inv) {
+    const FrontInfo &F = pl.fronts[t.front];
+    const int32_t jb = std::min(B, F.ncol - t.a);
+    need(t.a >= 0 && t.a < F.ncol && t.b >= 0 && t.b < nslot &&
+         pl.fs_dinv_off[t.b] + (int64_t)jb * jb <= pl.fs_dinv_entries, "inverse task");
+  }
+  for (const Task &t : pl.fs_fwd) {
+    const FrontInfo &F = pl.fronts[t.front];
+    need(t.b >= 0 && t.b < F.ncol && t.a >= t.b && t.a < F.ncol + F.nrow && t.c >= 0 && t.c < nslot,
+         "forward task");
+  }
+  for (const Task &t : pl.fs_bwd) {
+    const FrontInfo &F = pl.fronts[t.front];
+    need(t.b >= 0 && t.b < F.ncol && t.a >= 0 && t.a < std::max(t.b, 1) && t.c >= 0 && t.c < nslot,
+         "backward task");
+  }
+}
+
+}  // namespace gipm
