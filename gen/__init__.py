@@ -278,3 +278,105 @@ def sgm10(times, shift: float = 10.0) -> float:
     solve times (Sec. 5, Table 1 caption)."""
     t = np.asarray(times, dtype=np.float64)
     return float(np.exp(np.mean(np.log(t + shift))) - shift)
+
+
+@dataclass
+class MPCBatch:
+    """Batch of linear MPC QPs (one per instance), stage k = 0..T-1:
+
+        min 1/2 sum_k (x_{k+1}^T Q x_{k+1} + u_k^T R u_k)
+        s.t. x_{k+1} = A_k x_k + B_k u_k  (x_0 given),  |u| <= u_max,  |x| <= x_max.
+
+    Arrays are stacked over instances; instance i owns stages
+    stage_off[i] .. stage_off[i] + T[i] - 1 of A (12x12) and B (12x4)."""
+
+    T: np.ndarray          # int32, horizons
+    stage_off: np.ndarray  # int64, first stage of each instance
+    A: np.ndarray          # (sum T, nx, nx)
+    B: np.ndarray          # (sum T, nx, nu)
+    Q: np.ndarray          # (count, nx) diagonal
+    R: np.ndarray          # (count, nu) diagonal
+    x0: np.ndarray         # (count, nx)
+    u_max: float = 1.0
+    x_max: float = 5.0
+
+    @property
+    def count(self) -> int:
+        return len(self.T)
+
+    def instance(self, i: int):
+        s0, t = int(self.stage_off[i]), int(self.T[i])
+        return (self.A[s0:s0 + t], self.B[s0:s0 + t], self.Q[i], self.R[i], self.x0[i])
+
+
+def mpc_batch(count: int = 4096, seed: int = 3, t_min: int = 10, t_max: int = 100,
+              nx: int = 12, nu: int = 4, rho: float = 0.95, u_max: float = 1.0,
+              x_max: float = 5.0) -> MPCBatch:
+    """Instance i uses sub-seed (seed, i): T ~ U{t_min..t_max}; A_k = rho G_k /
+    spectral_radius(G_k) with G_k ~ N(0,1); B_k ~ N(0,1); Q, R diagonal ~ U(0.1, 10)
+    shared by the stages of an instance; x0 ~ U(-1,1), redrawn (next sub-seed
+    draw) until the u = 0 trajectory stays within |x| <= x_max."""
+    Ts, As, Bs, Qs, Rs, X0 = [], [], [], [], [], []
+    for i in range(count):
+        si = stream_seed(seed, 1000 + i)
+        T = t_min + int(splitmix64(stream_seed(si, 1), 1)[0] % np.uint64(t_max - t_min + 1))
+        G = normal(stream_seed(si, 2), T * nx * nx).reshape(T, nx, nx)
+        A = np.empty_like(G)
+        for k in range(T):
+            A[k] = rho * G[k] / np.max(np.abs(np.linalg.eigvals(G[k])))
+        B = normal(stream_seed(si, 3), T * nx * nu).reshape(T, nx, nu)
+        Q = uniform(stream_seed(si, 4), nx, 0.1, 10.0)
+        R = uniform(stream_seed(si, 5), nu, 0.1, 10.0)
+        for draw in range(1000):
+            x0 = uniform(stream_seed(si, 100 + draw), nx, -1.0, 1.0)
+            x, ok = x0.copy(), True
+            for k in range(T):
+                x = A[k] @ x
+                if np.abs(x).max() > x_max:
+                    ok = False
+                    break
+            if ok:
+                break
+        Ts.append(T); As.append(A); Bs.append(B); Qs.append(Q); Rs.append(R); X0.append(x0)
+    T = np.array(Ts, dtype=np.int32)
+    off = np.zeros(count, dtype=np.int64)
+    off[1:] = np.cumsum(T)[:-1]
+    return MPCBatch(T=T, stage_off=off, A=np.concatenate(As), B=np.concatenate(Bs),
+                    Q=np.array(Qs), R=np.array(Rs), x0=np.array(X0), u_max=u_max, x_max=x_max)
+
+
+def mpc_instance_qp(A, B, Q, R, x0, u_max=1.0, x_max=5.0):
+    """One MPC instance as  min c^T z + 1/2 z^T W z,  J z >= b,  l <= z <= u  with
+    z = (u_0, x_1, u_1, x_2, ...): the dynamics are the row pairs h >= 0, -h >= 0,
+    h_k = x_{k+1} - A_k x_k - B_k u_k (x_0 moves to the right-hand side).
+    Returns (LP-shaped data, W as lower CSC (diagonal))."""
+    T, nx, nu = A.shape[0], A.shape[1], B.shape[2]
+    ns = nu + nx
+    n = ns * T
+    rows, cols, vals, b = [], [], [], []
+    for k in range(T):
+        for sign in (1.0, -1.0):
+            for r in range(nx):
+                ent = {}
+                if k > 0:
+                    for j in range(nx):
+                        ent[(k - 1) * ns + nu + j] = -A[k][r, j]
+                for j in range(nu):
+                    ent[k * ns + j] = ent.get(k * ns + j, 0.0) - B[k][r, j]
+                ent[k * ns + nu + r] = ent.get(k * ns + nu + r, 0.0) + 1.0
+                rhs = (A[0][r] @ x0) if k == 0 else 0.0
+                cs = sorted(ent)
+                rows.append(cs)
+                vals.append([sign * ent[c] for c in cs])
+                b.append(sign * rhs)
+    m = len(rows)
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([c for r in rows for c in r], dtype=np.int32)
+    val = np.array([v for r in vals for v in r])
+    lo = np.concatenate([np.r_[np.full(nu, -u_max), np.full(nx, -x_max)] for _ in range(T)])
+    wdiag = np.concatenate([np.r_[R, Q] for _ in range(T)])
+    lp = LP(n, m, rowptr, col, val, np.array(b), np.zeros(n), lo, -lo, name=f"mpc_T{T}")
+    wp = np.arange(n + 1, dtype=np.int64)
+    wi = np.arange(n, dtype=np.int32)
+    return lp, (wp, wi, wdiag)

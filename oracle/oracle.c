@@ -621,6 +621,9 @@ typedef struct {
   const int64_t *ap;
   const int32_t *ai;
   const double *av, *b, *c, *l, *u;
+  const int64_t *wp;  /* Hessian W of f (lower CSC), NULL for an LP */
+  const int32_t *wi;
+  const double *wv;
   int32_t *lidx, *uidx;
 } lp_rows;
 
@@ -628,6 +631,7 @@ static void lp_rows_init(lp_rows *P, int32_t n, int32_t m, const int64_t *ap, co
                          const double *av, const double *b, const double *c, const double *l,
                          const double *u) {
   P->n = n; P->m = m; P->ap = ap; P->ai = ai; P->av = av; P->b = b; P->c = c; P->l = l; P->u = u;
+  P->wp = NULL; P->wi = NULL; P->wv = NULL;
   P->nl = P->nu = 0;
   for (int32_t i = 0; i < n; i++) { if (isfinite(l[i])) P->nl++; if (isfinite(u[i])) P->nu++; }
   P->mt = (int64_t)m + P->nl + P->nu;
@@ -656,6 +660,18 @@ static void lp_jtv(const lp_rows *P, const double *v, double *out) {
   for (int32_t k = 0; k < P->nl; k++) out[P->lidx[k]] += v[P->m + k];
   for (int32_t k = 0; k < P->nu; k++) out[P->uidx[k]] -= v[P->m + P->nl + k];
 }
+/* out (length n) = W x for the symmetric W given by its lower triangle (0 without W) */
+static void lp_wx(const lp_rows *P, const double *x, double *out) {
+  for (int32_t i = 0; i < P->n; i++) out[i] = 0.0;
+  if (!P->wp) return;
+  for (int32_t j = 0; j < P->n; j++)
+    for (int64_t e = P->wp[j]; e < P->wp[j + 1]; e++) {
+      const int32_t i = P->wi[e];
+      out[i] += P->wv[e] * x[j];
+      if (i != j) out[j] += P->wv[e] * x[i];
+    }
+}
+
 /* g(x) = J x - bfull */
 static void lp_g(const lp_rows *P, const double *x, double *g) {
   lp_jv(P, x, g);
@@ -695,7 +711,7 @@ static void lp_scaling(const lp_rows *P, const double *s, const double *lam, dou
  *   d_lambda = D (w ./ lambda - g - J d_x),
  *   d_s = -s + w ./ lambda - (s ./ lambda) .* d_lambda. */
 static void lp_direction(const orc_sym *S, const lp_rows *P, const double *kval,
-                         const double *lval, const double *g, const double *s,
+                         const double *lval, const double *xcur, const double *g, const double *s,
                          const double *lam, const double *D, const double *w, int32_t ir_max,
                          double ir_tol, double *dx, double *ds, double *dl, double *work_n3,
                          double *work_mt) {
@@ -704,7 +720,8 @@ static void lp_direction(const orc_sym *S, const lp_rows *P, const double *kval,
   double *rp = work_n3, *r = work_n3 + n, *cx = work_n3 + 2 * (int64_t)n;
   for (int64_t k = 0; k < mt; k++) work_mt[k] = D[k] * (g[k] - w[k] / lam[k]) - lam[k];
   lp_jtv(P, work_mt, rp); /* J^T (D (g - w/lambda) - lambda) */
-  for (int32_t i = 0; i < n; i++) rp[i] = -(P->c[i] + rp[i]);
+  lp_wx(P, xcur, r);      /* grad f = c + W x */
+  for (int32_t i = 0; i < n; i++) rp[i] = -(P->c[i] + r[i] + rp[i]);
   orc_solve(S, lval, rp, dx);
   double bn = inf_norm(rp, n);
   for (int32_t ir = 0; ir < ir_max; ir++) {
@@ -728,9 +745,11 @@ ORC_EXPORT int32_t orc_lp_direction(const orc_sym *S, int32_t m, const int64_t *
                                     const double *c, const double *l, const double *u,
                                     const double *x, const double *s, const double *lam,
                                     const double *w, double delta_p, double delta_d,
-                                    int32_t ir_max, double *dx, double *ds, double *dl) {
+                                    int32_t ir_max, const int64_t *wp, const int32_t *wi,
+                                    const double *wv, double *dx, double *ds, double *dl) {
   lp_rows P;
   lp_rows_init(&P, S->n, m, ap, ai, av, b, c, l, u);
+  P.wp = wp; P.wi = wi; P.wv = wv;
   int32_t n = S->n;
   double *g = (double *)xmalloc(sizeof(double) * (size_t)P.mt);
   double *D = (double *)xmalloc(sizeof(double) * (size_t)P.mt);
@@ -741,9 +760,9 @@ ORC_EXPORT int32_t orc_lp_direction(const orc_sym *S, int32_t m, const int64_t *
   double *lval = (double *)xmalloc(sizeof(double) * (size_t)S->nnz_l);
   lp_g(&P, x, g);
   lp_scaling(&P, s, lam, delta_d, D, dextra);
-  orc_assemble(S, m, ap, ai, av, D, NULL, NULL, NULL, dextra, delta_p, kval);
+  orc_assemble(S, m, ap, ai, av, D, wp, wi, wv, dextra, delta_p, kval);
   int32_t bad = orc_factor(S, kval, lval);
-  if (!bad) lp_direction(S, &P, kval, lval, g, s, lam, D, w, ir_max, 1e-14, dx, ds, dl, wn3, wmt);
+  if (!bad) lp_direction(S, &P, kval, lval, x, g, s, lam, D, w, ir_max, 1e-14, dx, ds, dl, wn3, wmt);
   free(g); free(D); free(wmt); free(dextra); free(wn3); free(kval); free(lval);
   lp_rows_free(&P);
   return bad;
@@ -767,12 +786,14 @@ ORC_EXPORT int32_t orc_lp_direction(const orc_sym *S, int32_t m, const int64_t *
  * times per iteration). */
 ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const int32_t *ai,
                           const double *av, const double *b, const double *c, const double *l,
-                          const double *u, const orc_ipm_opts *o, double *x, double *s_out,
+                          const double *u, const int64_t *wp, const int32_t *wi,
+                          const double *wv, const orc_ipm_opts *o, double *x, double *s_out,
                           double *lam_out, orc_ipm_result *res, double *log_mu,
                           double *log_kkt) {
   int32_t n = S->n;
   lp_rows P;
   lp_rows_init(&P, n, m, ap, ai, av, b, c, l, u);
+  P.wp = wp; P.wi = wi; P.wv = wv;
   int64_t mt = P.mt;
   size_t zmt = (size_t)(mt > 0 ? mt : 1), zn = (size_t)(n > 0 ? n : 1);
   double *s = (double *)xmalloc(sizeof(double) * zmt), *lam = (double *)xmalloc(sizeof(double) * zmt);
@@ -809,7 +830,8 @@ ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const 
   for (it = 0; it <= o->max_iter; it++) {
     lp_g(&P, x, g);
     lp_jtv(&P, lam, rd);
-    for (int32_t i = 0; i < n; i++) rd[i] = c[i] - rd[i];
+    lp_wx(&P, x, dx); /* dx used as scratch for W x here */
+    for (int32_t i = 0; i < n; i++) rd[i] = c[i] + dx[i] - rd[i];
     double mu = 0.0, fx = 0.0, pr = 0.0, cr = 0.0;
     for (int64_t k = 0; k < mt; k++) {
       mu += s[k] * lam[k];
@@ -817,7 +839,7 @@ ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const 
       double q = fabs(s[k] * lam[k]); if (q > cr) cr = q;
     }
     mu /= (double)(mt ? mt : 1);
-    for (int32_t i = 0; i < n; i++) fx += c[i] * x[i];
+    for (int32_t i = 0; i < n; i++) fx += (c[i] + 0.5 * dx[i]) * x[i]; /* c^T x + x^T W x / 2 */
     double dr = inf_norm(rd, n);
     double fs = fabs(fx) > 1.0 ? fabs(fx) : 1.0;
     double kkt = pr / bscale;
@@ -833,7 +855,7 @@ ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const 
     lp_scaling(&P, s, lam, o->delta_d, D, dextra);
     int32_t bad = 1, tries = 0;
     while (bad) {
-      orc_assemble(S, m, ap, ai, av, D, NULL, NULL, NULL, dextra, delta_p, kval);
+      orc_assemble(S, m, ap, ai, av, D, wp, wi, wv, dextra, delta_p, kval);
       bad = orc_factor(S, kval, lval);
       if (bad) {
         res->refactorizations++;
@@ -843,7 +865,7 @@ ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const 
     }
     /* predictor: w = 0 */
     for (int64_t k = 0; k < mt; k++) w[k] = 0.0;
-    lp_direction(S, &P, kval, lval, g, s, lam, D, w, o->ir_max, o->ir_tol, dx, ds, dl, wn3, wmt);
+    lp_direction(S, &P, kval, lval, x, g, s, lam, D, w, o->ir_max, o->ir_tol, dx, ds, dl, wn3, wmt);
     double apa = step_to_boundary(s, ds, mt, 1.0), ada = step_to_boundary(lam, dl, mt, 1.0);
     double mua = 0.0;
     for (int64_t k = 0; k < mt; k++) mua += (s[k] + apa * ds[k]) * (lam[k] + ada * dl[k]);
@@ -852,7 +874,7 @@ ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const 
     sigma = sigma * sigma * sigma;
     /* corrector: w = sigma mu - d_s_aff .* d_lambda_aff */
     for (int64_t k = 0; k < mt; k++) w[k] = sigma * mu - ds[k] * dl[k];
-    lp_direction(S, &P, kval, lval, g, s, lam, D, w, o->ir_max, o->ir_tol, dx, ds, dl, wn3, wmt);
+    lp_direction(S, &P, kval, lval, x, g, s, lam, D, w, o->ir_max, o->ir_tol, dx, ds, dl, wn3, wmt);
     double tau = 1.0 - mu > 0.99 ? 1.0 - mu : 0.99;
     double alpha_p = step_to_boundary(s, ds, mt, tau), alpha_d = step_to_boundary(lam, dl, mt, tau);
     for (int32_t i = 0; i < n; i++) x[i] += alpha_p * dx[i];

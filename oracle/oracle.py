@@ -55,9 +55,9 @@ def _load():
         lib.orc_kmatvec.argtypes = [P, P, P, P]
         lib.orc_lp_direction.restype = C.c_int32
         lib.orc_lp_direction.argtypes = [P, C.c_int32] + [P] * 11 + [C.c_double, C.c_double,
-                                                                     C.c_int32, P, P, P]
+                                                                     C.c_int32, P, P, P, P, P, P]
         lib.orc_ipm_lp.restype = C.c_int
-        lib.orc_ipm_lp.argtypes = [P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_ipm_lp.argtypes = [P, C.c_int32] + [P] * 17
         _lib = lib
     return _lib
 
@@ -201,9 +201,11 @@ class _Res(C.Structure):
                 ("compl_res", C.c_double), ("mu", C.c_double)]
 
 
-def lp_direction(S: OracleSymbolic, lp, x, s, lam, w, delta_p=1e-8, delta_d=1e-8, ir_max=3):
+def lp_direction(S: OracleSymbolic, lp, x, s, lam, w, delta_p=1e-8, delta_d=1e-8, ir_max=3,
+                 W=None):
     """Newton direction (d_x, d_s, d_lambda) of system (3) at (x, s, lambda) with
-    complementarity target w, computed through the condensed system (5)."""
+    complementarity target w, computed through the condensed system (5).
+    W = (colptr, rowidx, values) of the lower triangle of the Hessian, or None."""
     lib = _load()
     mt = len(s)
     dx = np.empty(lp.n)
@@ -213,16 +215,20 @@ def lp_direction(S: OracleSymbolic, lp, x, s, lam, w, delta_p=1e-8, delta_d=1e-8
             _c(lp.b, np.float64), _c(lp.c, np.float64), _c(lp.l, np.float64),
             _c(lp.u, np.float64), _c(x, np.float64), _c(s, np.float64), _c(lam, np.float64),
             _c(w, np.float64)]
+    w3 = [None, None, None] if W is None else [_c(W[0], np.int64), _c(W[1], np.int32),
+                                              _c(W[2], np.float64)]
     bad = lib.orc_lp_direction(C.c_void_p(S.handle), lp.m, *[_p(a) for a in arrs],
-                               float(delta_p), float(delta_d), int(ir_max), _p(dx), _p(ds), _p(dl))
+                               float(delta_p), float(delta_d), int(ir_max),
+                               *[_p(a) for a in w3], _p(dx), _p(ds), _p(dl))
     if bad:
         raise ArithmeticError(f"non-positive pivot at column {bad - 1}")
     return dx, ds, dl
 
 
 def ipm_lp(S: OracleSymbolic, lp, tol=1e-8, max_iter=500, delta_p=1e-8, delta_d=1e-8,
-           ir_max=3, ir_tol=1e-12) -> dict:
-    """Mehrotra predictor-corrector IPM on  min c^T x, A x >= b, l <= x <= u,
+           ir_max=3, ir_tol=1e-12, W=None) -> dict:
+    """Mehrotra predictor-corrector IPM on  min c^T x + x^T W x / 2, A x >= b,
+    l <= x <= u (W = (colptr, rowidx, values) lower CSC, or None for an LP),
     solving the primal condensed system (5) at every iteration."""
     lib = _load()
     n, m = lp.n, lp.m
@@ -237,8 +243,10 @@ def ipm_lp(S: OracleSymbolic, lp, tol=1e-8, max_iter=500, delta_p=1e-8, delta_d=
     arrs = [_c(lp.rowptr, np.int64), _c(lp.col, np.int32), _c(lp.val, np.float64),
             _c(lp.b, np.float64), _c(lp.c, np.float64), _c(lp.l, np.float64),
             _c(lp.u, np.float64)]
-    lib.orc_ipm_lp(C.c_void_p(S.handle), m, *[_p(a) for a in arrs], C.byref(o), _p(x), _p(s),
-                   _p(lam), C.byref(r), _p(log_mu), _p(log_kkt))
+    w3 = [None, None, None] if W is None else [_c(W[0], np.int64), _c(W[1], np.int32),
+                                              _c(W[2], np.float64)]
+    lib.orc_ipm_lp(C.c_void_p(S.handle), m, *[_p(a) for a in arrs], *[_p(a) for a in w3],
+                   C.byref(o), _p(x), _p(s), _p(lam), C.byref(r), _p(log_mu), _p(log_kkt))
     it = r.iterations
     return dict(status=r.status, iterations=it, refactorizations=r.refactorizations,
                 objective=r.objective, kkt=r.kkt, primal_res=r.primal_res,
