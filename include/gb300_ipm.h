@@ -228,6 +228,55 @@ IPM_API ipm_status ipm_newton_direction(ipm_ctx *ctx, const double *d_jvals, con
                                 const double *d_s, const double *d_lambda, const double *d_w,
                                 double *d_dx, double *d_ds, double *d_dlambda);
 
+/* --- batched MPC QPs (Sec. 6: batch solvers) ------------------------------
+ * Many small QPs of one family solved by one persistent launch: instance i is
+ *   min 1/2 sum_k (x_{k+1}^T Q_i x_{k+1} + u_k^T R_i u_k)
+ *   s.t. x_{k+1} = A_k x_k + B_k u_k (k = 0..T_i-1, x_0 given), |u| <= u_max, |x| <= x_max,
+ * with 12 states and 4 inputs, the dynamics written as pairs of inequalities
+ * (Sec. 1: equalities as pairs of inequalities). Each instance runs the same
+ * Mehrotra method on the condensed system (5), which is block tridiagonal
+ * with 16 x 16 blocks (stage variables (u_k, x_{k+1})) and factored by a
+ * sequential block Cholesky without pivoting. */
+typedef struct {
+  int32_t count;          /* instances */
+  const int32_t *h_T;     /* host, horizons T_i >= 1 */
+  const double *d_A;      /* device, (sum T) x 12 x 12, stages of instance 0 first */
+  const double *d_B;      /* device, (sum T) x 12 x 4 */
+  const double *d_Q;      /* device, count x 12 (diagonal of Q_i) */
+  const double *d_R;      /* device, count x 4 (diagonal of R_i) */
+  const double *d_x0;     /* device, count x 12 */
+  double u_max, x_max;    /* box bounds */
+} ipm_mpc_batch;
+
+typedef struct {
+  int32_t precision;          /* IPM_FP64, or IPM_FP32: FP32 block factor and solves with
+                                 two FP64 refinement steps per solve */
+  int32_t instances_per_cta;  /* 2, 4, 8 or 16 (16 lanes per instance) */
+  int32_t ctas;               /* persistent grid size, 0 = automatic */
+} ipm_mpc_config;
+
+/* Workspace bytes for a batch (host only). */
+IPM_API ipm_status ipm_mpc_workspace_bytes(const ipm_mpc_batch *b, size_t *bytes);
+/* Upload the horizons, stage offsets and the longest-first instance queue into
+ * the workspace (256-byte aligned device buffer). Call once per batch shape. */
+IPM_API ipm_status ipm_mpc_prepare(const ipm_mpc_batch *b, void *d_work, size_t bytes, void *stream);
+/* Solve every instance to the scaled KKT residual tol (same definition as
+ * ipm_solve, with c = 0). Launches only kernels (a queue reset and the
+ * persistent solver) on stream, so the call can be captured in a CUDA graph.
+ * Outputs (device): d_z ((sum T) x 16, may be NULL), d_obj, d_kkt, d_iters,
+ * d_status (ipm_status per instance). */
+IPM_API ipm_status ipm_solve_batched(const ipm_mpc_batch *b, const ipm_mpc_config *cfg,
+                                     void *d_work, size_t bytes, double tol, int32_t max_iter,
+                                     void *stream, double *d_z, double *d_obj, double *d_kkt,
+                                     int32_t *d_iters, int32_t *d_status);
+/* Autotuner: times instances_per_cta in {2, 4, 8, 16} x two grid sizes for the
+ * precision in best->precision on this batch and writes the fastest shape to
+ * best; h_ms (may be NULL) receives the 8 timings in that order. */
+IPM_API ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t bytes, double tol,
+                                    int32_t max_iter, void *stream, double *d_z, double *d_obj,
+                                    double *d_kkt, int32_t *d_iters, int32_t *d_status,
+                                    ipm_mpc_config *best, float *h_ms);
+
 /* --- inspection (host copies; for tests and tools) --------------------- */
 
 /* Copy the symbolic analysis to host arrays (each may be NULL). Sizes: perm,

@@ -28,7 +28,8 @@ EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze
             "kkt_assemble", "kkt_factor", "kkt_solve", "ipm_solve", "ipm_newton_direction",
             "kkt_symbolic_export", "kkt_export_assembled", "kkt_factor_entries",
             "ipm_last_perturbed", "ipm_kernel_launches", "kkt_solve_noalloc",
-            "kkt_solve_noalloc_capacity", "ipm_last_error", "ipm_destroy"]
+            "kkt_solve_noalloc_capacity", "ipm_mpc_workspace_bytes", "ipm_mpc_prepare",
+            "ipm_solve_batched", "ipm_mpc_autotune", "ipm_last_error", "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -112,6 +113,10 @@ def load() -> C.CDLL:
         "ipm_kernel_launches": (I64, []),
         "kkt_solve_noalloc": (I32, [P, P, P]),
         "kkt_solve_noalloc_capacity": (I64, []),
+        "ipm_mpc_workspace_bytes": (I32, [P, P]),
+        "ipm_mpc_prepare": (I32, [P, P, C.c_size_t, P]),
+        "ipm_solve_batched": (I32, [P, P, P, C.c_size_t, D, I32, P, P, P, P, P, P]),
+        "ipm_mpc_autotune": (I32, [P, P, C.c_size_t, D, I32, P, P, P, P, P, P, P, P]),
         "ipm_last_error": (C.c_char_p, [P]),
         "ipm_destroy": (None, [P]),
     }
@@ -290,3 +295,66 @@ class IpmContext:
             self.close()
         except Exception:
             pass
+
+
+class MpcBatch(C.Structure):
+    _fields_ = [("count", C.c_int32), ("h_T", C.c_void_p), ("d_A", C.c_void_p),
+                ("d_B", C.c_void_p), ("d_Q", C.c_void_p), ("d_R", C.c_void_p),
+                ("d_x0", C.c_void_p), ("u_max", C.c_double), ("x_max", C.c_double)]
+
+
+class MpcConfig(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("instances_per_cta", C.c_int32), ("ctas", C.c_int32)]
+
+
+class BatchedMPC:
+    """Batched MPC QPs (ipm_mpc_* entry points). ``mb`` holds numpy arrays
+    T, A, B, Q, R, x0 (stacked over instances) and the box bounds."""
+
+    def __init__(self, mb, stream=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+        self.T = np.ascontiguousarray(mb.T, dtype=np.int32)
+        self.count = len(self.T)
+        self.total_stages = int(self.T.sum())
+        self._t = [dev(mb.A), dev(mb.B), dev(mb.Q), dev(mb.R), dev(mb.x0)]
+        self.batch = MpcBatch(self.count, _hp(self.T), *[C.c_void_p(t.data_ptr()) for t in self._t],
+                              float(mb.u_max), float(mb.x_max))
+        nb = C.c_size_t()
+        self._check(lib.ipm_mpc_workspace_bytes(C.byref(self.batch), C.byref(nb)))
+        self.work = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        self.wptr = (self.work.data_ptr() + 255) // 256 * 256
+        self.wbytes = nb.value
+        self.stream = stream
+        self._check(lib.ipm_mpc_prepare(C.byref(self.batch), C.c_void_p(self.wptr), self.wbytes,
+                                        C.c_void_p(stream) if stream else None))
+        self.z = torch.empty(self.total_stages * 16, dtype=torch.float64, device="cuda")
+        self.obj = torch.empty(self.count, dtype=torch.float64, device="cuda")
+        self.kkt = torch.empty(self.count, dtype=torch.float64, device="cuda")
+        self.iters = torch.empty(self.count, dtype=torch.int32, device="cuda")
+        self.status = torch.empty(self.count, dtype=torch.int32, device="cuda")
+
+    @staticmethod
+    def _check(st):
+        if st != 0:
+            raise IpmError(st, "batched MPC call failed")
+
+    def ipm_solve_batched(self, precision=IPM_FP64, instances_per_cta=8, ctas=0, tol=1e-6,
+                          max_iter=100, stream=None):
+        cfg = MpcConfig(precision, instances_per_cta, ctas)
+        st = stream if stream is not None else self.stream
+        self._check(self._lib.ipm_solve_batched(
+            C.byref(self.batch), C.byref(cfg), C.c_void_p(self.wptr), self.wbytes, float(tol),
+            int(max_iter), C.c_void_p(st) if st else None, _dp(self.z), _dp(self.obj),
+            _dp(self.kkt), _dp(self.iters), _dp(self.status)))
+
+    def ipm_mpc_autotune(self, precision=IPM_FP64, tol=1e-6, max_iter=100):
+        cfg = MpcConfig(precision, 8, 0)
+        ms = (C.c_float * 8)()
+        self._check(self._lib.ipm_mpc_autotune(
+            C.byref(self.batch), C.c_void_p(self.wptr), self.wbytes, float(tol), int(max_iter),
+            C.c_void_p(self.stream) if self.stream else None, _dp(self.z), _dp(self.obj),
+            _dp(self.kkt), _dp(self.iters), _dp(self.status), C.byref(cfg), ms))
+        return cfg, list(ms)

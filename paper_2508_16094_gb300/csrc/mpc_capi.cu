@@ -1,0 +1,163 @@
+// C ABI of the batched MPC solver: workspace sizing, preparation, the
+// persistent solve launch and the autotuner over launch shapes.
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/gb300_ipm.h"
+#include "mpc_batch.h"
+
+using namespace gipm;
+
+namespace {
+
+struct MpcLayout {
+  int32_t *T;
+  int64_t *soff;
+  int32_t *order;
+  int *counter;
+  double *work;
+  size_t bytes;
+};
+
+MpcLayout mpc_layout(char *base, int32_t count, int64_t total_stages) {
+  Carve cv{base};
+  MpcLayout L;
+  L.T = cv.take<int32_t>(std::max(count, 1));
+  L.soff = cv.take<int64_t>(std::max(count, 1));
+  L.order = cv.take<int32_t>(std::max(count, 1));
+  L.counter = cv.take<int>(64);
+  L.work = cv.take<double>((size_t)std::max<int64_t>(total_stages, 1) * kMpcStageDoubles);
+  L.bytes = cv.off + 256;
+  return L;
+}
+
+bool valid_batch(const ipm_mpc_batch *b) {
+  return b && b->count > 0 && b->h_T && b->d_A && b->d_B && b->d_Q && b->d_R && b->d_x0;
+}
+
+int64_t total_stages(const ipm_mpc_batch *b) {
+  int64_t t = 0;
+  for (int32_t i = 0; i < b->count; i++) t += b->h_T[i];
+  return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+ipm_status ipm_mpc_workspace_bytes(const ipm_mpc_batch *b, size_t *bytes) {
+  if (!valid_batch(b) || !bytes) return IPM_ERR_ARG;
+  for (int32_t i = 0; i < b->count; i++)
+    if (b->h_T[i] < 1) return IPM_ERR_ARG;
+  *bytes = mpc_layout(nullptr, b->count, total_stages(b)).bytes;
+  return IPM_OK;
+}
+
+ipm_status ipm_mpc_prepare(const ipm_mpc_batch *b, void *d_work, size_t bytes, void *stream) {
+  if (!valid_batch(b) || !d_work) return IPM_ERR_ARG;
+  const int64_t ts = total_stages(b);
+  const MpcLayout L = mpc_layout(static_cast<char *>(d_work), b->count, ts);
+  if ((uintptr_t)d_work % 256 != 0 || L.bytes > bytes) return IPM_ERR_NOMEM;
+  std::vector<int64_t> soff(b->count);
+  std::vector<int32_t> order(b->count);
+  int64_t acc = 0;
+  for (int32_t i = 0; i < b->count; i++) {
+    soff[i] = acc;
+    acc += b->h_T[i];
+  }
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t x, int32_t y) { return b->h_T[x] > b->h_T[y]; });
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(L.T, b->h_T, b->count * sizeof(int32_t), cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(L.soff, soff.data(), b->count * sizeof(int64_t), cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(L.order, order.data(), b->count * sizeof(int32_t), cudaMemcpyHostToDevice, st) ||
+      cudaStreamSynchronize(st))
+    return IPM_ERR_CUDA;
+  return IPM_OK;
+}
+
+ipm_status ipm_solve_batched(const ipm_mpc_batch *b, const ipm_mpc_config *cfg, void *d_work,
+                             size_t bytes, double tol, int32_t max_iter, void *stream, double *d_z,
+                             double *d_obj, double *d_kkt, int32_t *d_iters, int32_t *d_status) {
+  if (!valid_batch(b) || !cfg || !d_work || !d_obj || !d_kkt || !d_iters || !d_status)
+    return IPM_ERR_ARG;
+  const int ipc = cfg->instances_per_cta;
+  if (!(ipc == 2 || ipc == 4 || ipc == 8 || ipc == 16)) return IPM_ERR_ARG;
+  if (cfg->precision != IPM_FP64 && cfg->precision != IPM_FP32) return IPM_ERR_UNSUPPORTED;
+  const MpcLayout L = mpc_layout(static_cast<char *>(d_work), b->count, total_stages(b));
+  if (L.bytes > bytes) return IPM_ERR_NOMEM;
+  MpcArgs a{};
+  a.count = b->count;
+  a.T = L.T;
+  a.soff = L.soff;
+  a.order = L.order;
+  a.A = b->d_A;
+  a.B = b->d_B;
+  a.Q = b->d_Q;
+  a.R = b->d_R;
+  a.x0 = b->d_x0;
+  a.umax = b->u_max;
+  a.xmax = b->x_max;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.delta_p = 1e-8;
+  a.delta_d = 1e-8;
+  a.work = L.work;
+  a.counter = L.counter;
+  a.zout = d_z;
+  a.obj = d_obj;
+  a.kkt = d_kkt;
+  a.iters = d_iters;
+  a.status = d_status;
+  int ctas = cfg->ctas;
+  if (ctas <= 0) ctas = 152 * std::max(1, 64 / ipc);
+  launch_mpc(a, cfg->precision == IPM_FP64 ? 0 : 1, ipc, ctas, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? IPM_OK : IPM_ERR_CUDA;
+}
+
+ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t bytes, double tol,
+                            int32_t max_iter, void *stream, double *d_z, double *d_obj,
+                            double *d_kkt, int32_t *d_iters, int32_t *d_status,
+                            ipm_mpc_config *best, float *h_ms) {
+  if (!best) return IPM_ERR_ARG;
+  const int ipcs[4] = {2, 4, 8, 16};
+  const int occ[2] = {1, 2};  // persistent CTAs per SM relative to the lane budget
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return IPM_ERR_CUDA;
+  float best_ms = 1e30f;
+  ipm_mpc_config winner = *best;
+  int idx = 0;
+  for (int ipc : ipcs)
+    for (int o : occ) {
+      ipm_mpc_config c = *best;
+      c.instances_per_cta = ipc;
+      c.ctas = 152 * o * std::max(1, 32 / ipc);
+      // warm once, then time
+      ipm_status s = ipm_solve_batched(b, &c, d_work, bytes, tol, max_iter, stream, d_z, d_obj,
+                                       d_kkt, d_iters, d_status);
+      if (s != IPM_OK) return s;
+      cudaEventRecord(e0, st);
+      ipm_solve_batched(b, &c, d_work, bytes, tol, max_iter, stream, d_z, d_obj, d_kkt, d_iters,
+                        d_status);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return IPM_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (h_ms) h_ms[idx] = ms;
+      idx++;
+      if (ms < best_ms) {
+        best_ms = ms;
+        winner = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best = winner;
+  return IPM_OK;
+}
+
+}  // extern "C"
