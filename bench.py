@@ -120,6 +120,40 @@ def oracle_direction_sample(grid: int, reps: int = 1):
     return float(np.mean(ts)), S.flops, lp.n
 
 
+def mpc_measure(steps: int = 3):
+    """Batched MPC QPs (4096 instances, T ~ U{10..100}, 12 states, 4 inputs):
+    autotuned launch shape, one persistent launch per batch replayed from a CUDA
+    graph; solves per second for the FP32-factor (FP64-refined) and FP64 kernels."""
+    import torch
+    import paper_2508_16094_gb300 as gb
+    mb = gen.mpc_batch(4096, seed=3)
+    b = gb.BatchedMPC(mb)
+    out = {"instances": mb.count, "stages": int(mb.T.sum())}
+    for name, prec in (("fp32", gb.IPM_FP32), ("fp64", gb.IPM_FP64)):
+        cfg, ms = b.ipm_mpc_autotune(precision=prec, tol=1e-6)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.ipm_solve_batched(precision=prec, instances_per_cta=cfg.instances_per_cta,
+                                ctas=cfg.ctas, tol=1e-6, stream=s.cuda_stream)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / steps
+        st = b.status.cpu().numpy()
+        out[name] = {"ms_per_batch": t, "solves_per_s": mb.count / (t * 1e-3),
+                     "converged": int((st == 0).sum()), "max_kkt": float(b.kkt.max().item()),
+                     "mean_iters": float(b.iters.float().mean().item()),
+                     "instances_per_cta": int(cfg.instances_per_cta), "ctas": int(cfg.ctas),
+                     "autotune_ms": [round(x, 3) for x in ms]}
+    return out
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,6 +324,10 @@ def run_ours(args, ws, rank, local):
                "fp64_fallbacks": int(rt.fp64_fallbacks),
                "time_factor_s": rt.time_factor_ms / 1e3, "time_solve_s": rt.time_solve_ms / 1e3}
 
+    mpc = None
+    if rank == 0 and not args.no_mpc:
+        mpc = mpc_measure()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sec, oflops, on = oracle_direction_sample(ORACLE_GRID, reps=3)
@@ -321,6 +359,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "time_to_kkt_1e-6": tti,
+            "mpc_batch": mpc,
             "ipm_step": {"refine_steps": int(res.refine_steps), "pcg_steps": int(res.pcg_steps),
                          "factor_ms": res.time_factor_ms / steps_done,
                          "solve_ms": res.time_solve_ms / steps_done},
@@ -336,10 +375,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=100)
-    ap.add_argument("--precision", choices=list(PREC), default="fp32")
+    ap.add_argument("--precision", choices=list(PREC), default="tf32x3")
     ap.add_argument("--no-tti", dest="tti", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vary-seed", action="store_true")
+    ap.add_argument("--no-mpc", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank, local = dist_init()
