@@ -100,6 +100,12 @@ typedef struct {
   double accept_tol;     /* a solve that misses ir_tol but reaches accept_tol is used (1e-6) */
   int32_t verbose;       /* print one line per interior-point iteration to stderr */
   int32_t warm_start;    /* 1: ipm_solve starts from the x, s, lambda it is given (0) */
+  int32_t learned;       /* stale-factor reuse inside ipm_solve (needs an FP32-storage factor):
+                            0 off; 1 PCG with the learned correction; 2 PCG with the stale
+                            factor alone (E = 0 ablation) (0) */
+  int32_t learned_probes;/* probes per training sample (1..8); > 0 also reserves the learned
+                            buffers when learned = 0 (0) */
+  int32_t learned_pcg_max; /* PCG iterations allowed before falling back to refactoring (30) */
 } ipm_options;
 
 /* Default options (values in brackets above). */
@@ -140,6 +146,8 @@ typedef struct {
   double primal_res, dual_res, compl_res, mu;
   double worst_rel_residual;/* largest linear-solve residual accepted */
   double time_total_ms, time_assemble_ms, time_factor_ms, time_solve_ms, time_other_ms;
+  int32_t learned_skips;     /* iterations that reused the held factor (no factorisation) */
+  int32_t learned_pcg_steps; /* PCG iterations spent with the held factor */
 } ipm_result;
 
 /* Create a solver context for a problem with n variables and m general
@@ -276,6 +284,33 @@ IPM_API ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t
                                     int32_t max_iter, void *stream, double *d_z, double *d_obj,
                                     double *d_kkt, int32_t *d_iters, int32_t *d_status,
                                     ipm_mpc_config *best, float *h_ms);
+
+/* --- learned correction of a stale factor --------------------------------
+ * Not in the paper. A per-variable network (8 features -> 32 -> 32 -> 17, tanh)
+ * maps the change between the matrix a held factor L_s was computed from and
+ * the current K to Delta = diag(exp(o_0)) and U (n x 16, rank 16) so that
+ * M^{-1} = P^T L_s^{-T} (Delta + U U^T)^{-1} L_s^{-1} P preconditions PCG on K
+ * (Woodbury identity with a 16 x 16 capacitance). Training minimises
+ * sum_z ||w_z - Delta z - U (U^T z)||^2 / (probes n) with w_z = L_s^{-1} P K P^T
+ * L_s^{-T} z on iterates of the method itself. Features, targets, loss,
+ * gradients and Adam run in this library's kernels. Requires learned_probes > 0
+ * (or learned != 0) at kkt_analyze and an FP32-storage factor. */
+IPM_API int32_t ipm_learned_param_count(void);
+/* Copy the weights out (h_get, may be NULL) and/or in (h_set, may be NULL). */
+IPM_API ipm_status ipm_learned_weights(ipm_ctx *ctx, float *h_get, const float *h_set);
+/* One training sample for the held factor and the current iterate: features
+ * (d_feat, n x 8, permuted index) and targets d_w (probes x n) for the probes
+ * d_z (probes x n, permuted index). All device memory. */
+IPM_API ipm_status ipm_learned_sample(ipm_ctx *ctx, const double *d_jvals, const double *d_x,
+                                      const double *d_s, const double *d_lambda,
+                                      const float *d_z, float *d_feat, float *d_w);
+/* Loss and its gradient w.r.t. the weights for one sample (no update). */
+IPM_API ipm_status ipm_learned_loss_grad(ipm_ctx *ctx, const float *d_feat, const float *d_z,
+                                         const float *d_w, double *h_loss, float *h_grad);
+/* steps Adam updates (learning rate lr) on one sample; h_loss: loss before
+ * the last update. */
+IPM_API ipm_status ipm_learned_train(ipm_ctx *ctx, const float *d_feat, const float *d_z,
+                                     const float *d_w, float lr, int32_t steps, double *h_loss);
 
 /* --- inspection (host copies; for tests and tools) --------------------- */
 

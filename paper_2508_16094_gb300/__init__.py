@@ -29,7 +29,9 @@ EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze
             "kkt_symbolic_export", "kkt_export_assembled", "kkt_factor_entries",
             "ipm_last_perturbed", "ipm_kernel_launches", "kkt_solve_noalloc",
             "kkt_solve_noalloc_capacity", "ipm_mpc_workspace_bytes", "ipm_mpc_prepare",
-            "ipm_solve_batched", "ipm_mpc_autotune", "ipm_last_error", "ipm_destroy"]
+            "ipm_solve_batched", "ipm_mpc_autotune", "ipm_learned_param_count",
+            "ipm_learned_weights", "ipm_learned_sample", "ipm_learned_loss_grad",
+            "ipm_learned_train", "ipm_last_error", "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -44,7 +46,8 @@ class Options(C.Structure):
                 ("delta_d", C.c_double), ("precision", C.c_int32), ("storage_fp64", C.c_int32),
                 ("refine", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
                 ("pcg_max", C.c_int32), ("fallback_fp64", C.c_int32), ("accept_tol", C.c_double),
-                ("verbose", C.c_int32), ("warm_start", C.c_int32)]
+                ("verbose", C.c_int32), ("warm_start", C.c_int32), ("learned", C.c_int32),
+                ("learned_probes", C.c_int32), ("learned_pcg_max", C.c_int32)]
 
 
 class SymbolicInfo(C.Structure):
@@ -68,7 +71,8 @@ class Result(C.Structure):
                 ("mu", C.c_double), ("worst_rel_residual", C.c_double),
                 ("time_total_ms", C.c_double), ("time_assemble_ms", C.c_double),
                 ("time_factor_ms", C.c_double), ("time_solve_ms", C.c_double),
-                ("time_other_ms", C.c_double)]
+                ("time_other_ms", C.c_double), ("learned_skips", C.c_int32),
+                ("learned_pcg_steps", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +118,11 @@ def load() -> C.CDLL:
         "kkt_solve_noalloc": (I32, [P, P, P]),
         "kkt_solve_noalloc_capacity": (I64, []),
         "ipm_mpc_workspace_bytes": (I32, [P, P]),
+        "ipm_learned_param_count": (I32, []),
+        "ipm_learned_weights": (I32, [P, P, P]),
+        "ipm_learned_sample": (I32, [P] * 8),
+        "ipm_learned_loss_grad": (I32, [P] * 6),
+        "ipm_learned_train": (I32, [P, P, P, P, C.c_float, I32, P]),
         "ipm_mpc_prepare": (I32, [P, P, C.c_size_t, P]),
         "ipm_solve_batched": (I32, [P, P, P, C.c_size_t, D, I32, P, P, P, P, P, P]),
         "ipm_mpc_autotune": (I32, [P, P, C.c_size_t, D, I32, P, P, P, P, P, P, P, P]),
@@ -281,6 +290,31 @@ class IpmContext:
         if raise_on_error:
             self._check(st)
         return st
+
+    # --- learned correction ---------------------------------------------------
+    def ipm_learned_weights(self, set_to=None) -> np.ndarray:
+        n = int(self._lib.ipm_learned_param_count())
+        out = np.empty(n, np.float32)
+        inp = None if set_to is None else np.ascontiguousarray(set_to, dtype=np.float32)
+        self._check(self._lib.ipm_learned_weights(self.handle, _hp(out), _hp(inp)))
+        return out
+
+    def ipm_learned_sample(self, jvals, x, s, lam, z, feat, w):
+        self._check(self._lib.ipm_learned_sample(self.handle, _dp(jvals), _dp(x), _dp(s), _dp(lam),
+                                                 _dp(z), _dp(feat), _dp(w)))
+
+    def ipm_learned_loss_grad(self, feat, z, w):
+        loss = C.c_double()
+        grad = np.empty(int(self._lib.ipm_learned_param_count()), np.float32)
+        self._check(self._lib.ipm_learned_loss_grad(self.handle, _dp(feat), _dp(z), _dp(w),
+                                                    C.byref(loss), _hp(grad)))
+        return loss.value, grad
+
+    def ipm_learned_train(self, feat, z, w, lr=1e-3, steps=1) -> float:
+        loss = C.c_double()
+        self._check(self._lib.ipm_learned_train(self.handle, _dp(feat), _dp(z), _dp(w),
+                                                C.c_float(lr), int(steps), C.byref(loss)))
+        return loss.value
 
     def ipm_last_perturbed(self) -> int:
         return int(self._lib.ipm_last_perturbed(self.handle))

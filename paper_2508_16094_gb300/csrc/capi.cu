@@ -14,6 +14,7 @@
 #include "../../include/gb300_ipm.h"
 #include "ipm_kernels.h"
 #include "launch.h"
+#include "learned.h"
 #include "tc.h"
 
 using namespace gipm;
@@ -43,6 +44,14 @@ struct ipm_ctx {
   float *dinv = nullptr, *fsa = nullptr, *fsb = nullptr, *fsx = nullptr;  // fused FP32 solve
   cudaGraphExec_t solve_graph = nullptr;  // captured fused solve (fixed buffers)
   int solve_graph_launches = 0;
+  cudaGraphExec_t fwd_graph = nullptr, bwd_graph = nullptr;  // its two sweeps alone
+  int fwd_graph_launches = 0, bwd_graph_launches = 0;
+  // learned correction of a stale factor
+  LearnedBufs lb;
+  bool learned_active = false;  // PCG preconditioner = corrected stale factor
+  bool have_stale = false;      // lb.D_old / diag_old / mu[0] describe the held factor
+  int refine_override = -1, pcg_override = -1;
+  double *lb_loss = nullptr;
   double *scal = nullptr, *partial = nullptr;
   IpmScalars *sc = nullptr;
   int32_t *status = nullptr, *col2s = nullptr;
@@ -212,6 +221,36 @@ void layout(ipm_ctx *c, char *base) {
   c->fsa = cv.take<float>(n);
   c->fsb = cv.take<float>(n);
   c->fsx = cv.take<float>(n);
+  {  // learned-correction buffers (only when enabled)
+    LearnedBufs &B = c->lb;
+    const bool on = c->opts.learned != 0 || c->opts.learned_probes > 0;
+    B.n = P.n;
+    B.mt = P.mt;
+    B.P = std::min(8, std::max(1, c->opts.learned_probes));
+    const size_t nn = on ? n : 1, mm = on ? mt : 1;
+    B.w = cv.take<float>(kNParams);
+    B.m = cv.take<float>(kNParams);
+    B.v = cv.take<float>(kNParams);
+    B.grad = cv.take<float>(kNParams);
+    B.feat = cv.take<float>(nn * kNF);
+    B.h1 = cv.take<float>(nn * kNH);
+    B.h2 = cv.take<float>(nn * kNH);
+    B.out = cv.take<float>(nn * kNO);
+    B.gout = cv.take<float>(nn * (kNO + 2 * kNH));
+    B.delta = cv.take<float>(nn);
+    B.U = cv.take<float>(nn * kNR);
+    B.diag_old = cv.take<double>(nn);
+    B.diag_new = cv.take<double>(nn);
+    B.D_old = cv.take<double>(mm);
+    B.mu = cv.take<double>(2);
+    B.partial = cv.take<float>((size_t)kLRedBlocks * kNParams);
+    B.dpart = cv.take<double>((size_t)kLRedBlocks * 256);
+    B.probe_t = cv.take<float>(8 * kNR);
+    B.probe_q = cv.take<float>(8 * kNR);
+    B.cap = cv.take<double>(kNR * kNR);
+    B.ts = cv.take<float>(kNR);
+    c->lb_loss = cv.take<double>(2);
+  }
   c->scal = cv.take<double>(64);
   c->partial = cv.take<double>(kRedBlocks * 8);
   c->sc = cv.take<IpmScalars>(1);
@@ -270,8 +309,42 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
 }
 
 // out = M^{-1} b with the current factor (b, out: original numbering, device)
+// capture (once) and launch one of the fused-solve graphs: which = 0 both
+// sweeps, 1 forward only, 2 backward only
+void launch_fused_graph(ipm_ctx *c, int which) {
+  cudaGraphExec_t *g = which == 0 ? &c->solve_graph : which == 1 ? &c->fwd_graph : &c->bwd_graph;
+  int *nl = which == 0 ? &c->solve_graph_launches
+                       : which == 1 ? &c->fwd_graph_launches : &c->bwd_graph_launches;
+  if (!*g) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t gr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    *nl = launch_solve_fused(c->dp, c->plan, (const float *)c->L, c->dinv, c->fsa, c->fsb, c->fsx,
+                             reinterpret_cast<float *>(c->tv), cs, which != 2, which != 1);
+    CK(cudaStreamEndCapture(cs, &gr));
+    CK(cudaGraphInstantiate(g, gr, 0));
+    CK(cudaGraphDestroy(gr));
+    CK(cudaStreamDestroy(cs));
+  } else {
+    for (int k = 0; k < *nl; k++) note_launch();
+  }
+  CK(cudaGraphLaunch(*g, c->st));
+}
+
 void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
   VecOps V = c->vec();
+  if (c->learned_active) {  // P^T L_s^{-T} (Delta + U U^T)^{-1} L_s^{-1} P b
+    double *scale = c->scal + 8, *amax = c->scal + 9;
+    V.absmax(c->P.n, b, amax);
+    V.inv_scale(amax, scale);
+    V.permute_in<float>(b, scale, c->fsa);
+    launch_fused_graph(c, 1);
+    learned_apply(c->lb, c->fsb, c->st);
+    launch_fused_graph(c, 2);
+    V.permute_out<float>(c->fsx, scale, out, accumulate);
+    return;
+  }
   if (c->storage_bytes == 8 && c->factor_prec == IPM_FP64) {
     V.permute_in<double>(b, nullptr, c->yv);
     launch_solve<double, double>(c->dp, c->plan, (const double *)c->L, c->yv, c->tv, c->st);
@@ -281,22 +354,9 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
     V.absmax(c->P.n, b, amax);
     V.inv_scale(amax, scale);
     float *t = reinterpret_cast<float *>(c->tv);
+    (void)t;
     V.permute_in<float>(b, scale, c->fsa);
-    if (!c->solve_graph) {  // capture the fixed launch sequence once
-      cudaStream_t cs;
-      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-      cudaGraph_t g;
-      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      c->solve_graph_launches = launch_solve_fused(c->dp, c->plan, (const float *)c->L, c->dinv,
-                                                   c->fsa, c->fsb, c->fsx, t, cs);
-      CK(cudaStreamEndCapture(cs, &g));
-      CK(cudaGraphInstantiate(&c->solve_graph, g, 0));
-      CK(cudaGraphDestroy(g));
-      CK(cudaStreamDestroy(cs));
-    } else {
-      for (int k = 0; k < c->solve_graph_launches; k++) note_launch();
-    }
-    CK(cudaGraphLaunch(c->solve_graph, c->st));
+    launch_fused_graph(c, 0);
     V.permute_out<float>(c->fsx, scale, out, accumulate);
   }
 }
@@ -310,6 +370,7 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
   double *bb = c->vb, *r = c->vr, *z = c->vz, *p = c->vp, *q = c->vq, *xx = c->vx;
   CK(cudaMemcpyAsync(bb, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   double *sN = c->scal;  // scalars: 0 |b|, 1 |r|, 2 rz, 3 pq, 4 rz_new
+  const int pcg_max = c->pcg_override >= 0 ? c->pcg_override : o.pcg_max;
   V.absmax(n, bb, sN + 0);
   const double bn = d2h_scalar(c, sN + 0);
   if (info) *info = ipm_solve_info{0, 0, 0.0};
@@ -352,7 +413,7 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
     CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     V.dot(n, r, z, sN + 2);
     int k = 0;
-    for (; k < o.pcg_max && rel > o.ir_tol; k++) {
+    for (; k < pcg_max && rel > o.ir_tol; k++) {
       // q = K p  (residual of b = 0 gives -K p)
       V.residual(c->cur_jvals, c->cur_D, c->cur_wvals, c->cur_delta_p, p, c->vc, q, c->vtA);
       V.negate(n, q);
@@ -401,7 +462,8 @@ ipm_status direction(ipm_ctx *c, const double *jvals, const double *b, const dou
   V.rhs_rows(c->vD, c->vg, w, lam, c->vt);
   V.jtv(jvals, c->vt, 1.0, wvals, x, cc, c->vrd);  // r_p = c + W x + J^T (D (g - w/lam) - lam)
   V.negate(c->P.n, c->vrd);
-  ipm_status stt = do_solve(c, c->vrd, dx, c->opts.refine, si);
+  ipm_status stt = do_solve(c, c->vrd, dx,
+                            c->refine_override >= 0 ? c->refine_override : c->opts.refine, si);
   V.jv(jvals, dx, c->vjx);
   V.jfull(c->vjx, dx, c->vjd);
   V.recover(c->vD, c->vg, w, s, lam, c->vjd, ds, dl);
@@ -434,6 +496,52 @@ ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jval
   }
 }
 
+// After a fresh factorisation: remember what it was computed from (features of
+// later iterations compare against it).
+void save_stale(ipm_ctx *c, const double *jv) {
+  LearnedBufs &B = c->lb;
+  if (!(c->opts.learned != 0 || c->opts.learned_probes > 0)) return;
+  CK(cudaMemcpyAsync(B.D_old, c->cur_D, c->P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  learned_diag(c->dp, jv, c->cur_D, c->cur_delta_p, B.diag_old, c->st);
+  CK(cudaMemcpyAsync(B.mu, &c->sc->mu, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  c->have_stale = true;
+}
+
+// Features of the current D against the held factor, network forward (or the
+// E = 0 ablation) and the Woodbury capacitance.
+void learned_prepare(ipm_ctx *c, const double *jv, const double *x, double delta_p, bool ablate) {
+  LearnedBufs &B = c->lb;
+  CK(cudaMemcpyAsync(B.mu + 1, &c->sc->mu, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  learned_diag(c->dp, jv, c->vD, delta_p, B.diag_new, c->st);
+  learned_features(c->dp, B, jv, c->vD, x, c->st);
+  learned_forward(B, ablate, c->st);
+  learned_capacitance(B, c->st);
+}
+
+// Deterministic initial weights: uniform Glorot ranges for the hidden layers
+// (SplitMix64 stream), zero output layer, so the untrained network is the
+// E = 0 correction (Delta = 1, U = 0).
+void learned_init_weights(ipm_ctx *c) {
+  std::vector<float> w(kNParams, 0.f);
+  uint64_t st = 0x9E3779B97F4A7C15ull * 77u;
+  auto next = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  const float a1 = std::sqrt(6.f / (kNF + kNH)), a2 = std::sqrt(6.f / (kNH + kNH));
+  for (int p = kW1; p < kB1; p++) w[p] = (float)((2 * next() - 1) * a1);
+  for (int p = kW2; p < kB2; p++) w[p] = (float)((2 * next() - 1) * a2);
+  CK(cudaMemcpyAsync(c->lb.w, w.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->lb.m, 0, kNParams * sizeof(float), c->st));
+  CK(cudaMemsetAsync(c->lb.v, 0, kNParams * sizeof(float), c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->lb.step = 0;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -455,6 +563,9 @@ void ipm_default_options(ipm_options *o) {
   o->accept_tol = 1e-6;
   o->verbose = 0;
   o->warm_start = 0;
+  o->learned = 0;
+  o->learned_probes = 0;
+  o->learned_pcg_max = 30;
 }
 
 ipm_status ipm_create(int32_t n, int32_t m, const int64_t *jp, const int32_t *ji,
@@ -589,6 +700,10 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     }
     layout(c, base);
     CK(cudaStreamSynchronize(c->st));
+    if (c->fwd_graph) { CK(cudaGraphExecDestroy(c->fwd_graph)); c->fwd_graph = nullptr; }
+    if (c->bwd_graph) { CK(cudaGraphExecDestroy(c->bwd_graph)); c->bwd_graph = nullptr; }
+    c->have_stale = false;
+    if (c->opts.learned != 0 || c->opts.learned_probes > 0) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
       c->tcp.encode(c->plan, (float *)c->L, c->st);
     } catch (const std::exception &e) {
@@ -709,25 +824,75 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       CK(cudaEventRecord(ev[0], c->st));
       V.scaling(s, lam, o.delta_d, c->vD);
       CK(cudaEventRecord(ev[1], c->st));
-      stt = factor_with_retry(c, wv, jv, o.precision, delta_p, &res);
-      CK(cudaEventRecord(ev[2], c->st));
-      if (stt != IPM_OK) { res.status = stt; break; }
-      // predictor (w = 0)
+      // Learned skip: keep the held (stale) factor, correct it with the
+      // network's Delta + U U^T and solve both directions by PCG; any solve
+      // that misses ir_tol within learned_pcg_max iterations falls back to
+      // the exact refactorisation.
+      const bool try_skip = o.learned != 0 && c->have_stale && c->factor_prec != IPM_FP64 &&
+                            c->tcp.ready();
+      bool factored = false;
+      auto refactor = [&]() -> ipm_status {
+        c->learned_active = false;
+        c->refine_override = c->pcg_override = -1;
+        ipm_status f = factor_with_retry(c, wv, jv, o.precision, delta_p, &res);
+        if (f == IPM_OK) {
+          factored = true;
+          save_stale(c, jv);
+        }
+        return f;
+      };
       ipm_solve_info si{};
-      stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
+      if (try_skip) {
+        learned_prepare(c, jv, x, delta_p, o.learned == 2);
+        c->cur_jvals = jv;
+        c->cur_D = c->vD;
+        c->cur_wvals = wv;
+        c->cur_delta_p = delta_p;
+        c->learned_active = true;
+        c->refine_override = IPM_REFINE_PCG;
+        c->pcg_override = o.learned_pcg_max;
+        const int64_t pcg0 = c->pcg_steps;
+        stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
+        res.learned_pcg_steps += (int32_t)(c->pcg_steps - pcg0);
+        if (stt != IPM_OK || !(c->last_rel <= o.ir_tol)) {
+          stt = refactor();
+          if (stt == IPM_OK)
+            stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
+        }
+      } else {
+        stt = refactor();
+        if (stt == IPM_OK)
+          stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
+      }
+      CK(cudaEventRecord(ev[2], c->st));
       res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
       if (stt != IPM_OK && o.fallback_fp64 && o.precision != IPM_FP64 && c->storage_bytes == 8) {
         res.fp64_fallbacks++;
+        c->learned_active = false;
+        c->refine_override = c->pcg_override = -1;
         stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
         if (stt == IPM_OK)
           stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
       }
-      if (stt != IPM_OK) { res.status = stt; break; }
+      if (stt != IPM_OK) { res.status = stt; c->learned_active = false; break; }
       V.ftb(s, c->vds, lam, c->vdl, c->scal + 32, c->sc, true);
       V.muaff(s, c->vds, lam, c->vdl, c->scal + 34, c->sc);
       // corrector: w = sigma mu - ds_aff .* dl_aff
       V.corrector_target(c->vds, c->vdl, c->sc, c->vw);
-      stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+      {
+        const int64_t pcg0 = c->pcg_steps;
+        const bool with_stale = c->learned_active;
+        stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+        if (with_stale) res.learned_pcg_steps += (int32_t)(c->pcg_steps - pcg0);
+        if (with_stale && (stt != IPM_OK || !(c->last_rel <= o.ir_tol))) {
+          stt = refactor();
+          if (stt == IPM_OK)
+            stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+        }
+      }
+      c->learned_active = false;
+      c->refine_override = c->pcg_override = -1;
+      if (try_skip && !factored) res.learned_skips++;
       res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
       if (stt != IPM_OK) { res.status = stt; break; }
       CK(cudaEventRecord(ev[3], c->st));
@@ -816,12 +981,100 @@ ipm_status kkt_factor_entries(ipm_ctx *c, int64_t count, const int32_t *rows, co
 
 int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0; }
 
+int32_t ipm_learned_param_count(void) { return kNParams; }
+
+static bool learned_on(const ipm_ctx *c) { return c->opts.learned != 0 || c->opts.learned_probes > 0; }
+
+ipm_status ipm_learned_weights(ipm_ctx *c, float *h_get, const float *h_set) {
+  if (!c) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (c->state < 2 || !learned_on(c)) throw Fail{IPM_ERR_STATE, "learned buffers not set up"};
+    if (h_get) CK(cudaMemcpyAsync(h_get, c->lb.w, kNParams * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    if (h_set) {
+      CK(cudaMemcpyAsync(c->lb.w, h_set, kNParams * sizeof(float), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemsetAsync(c->lb.m, 0, kNParams * sizeof(float), c->st));
+      CK(cudaMemsetAsync(c->lb.v, 0, kNParams * sizeof(float), c->st));
+      c->lb.step = 0;
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return IPM_OK;
+  });
+}
+
+ipm_status ipm_learned_sample(ipm_ctx *c, const double *jv, const double *x, const double *s,
+                              const double *lam, const float *z, float *feat, float *w) {
+  if (!c || !s || !lam || !z || !feat || !w) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (!learned_on(c) || !c->have_stale || c->factor_prec == IPM_FP64 || c->state < 4)
+      throw Fail{IPM_ERR_STATE, "needs a held FP32-storage factor and learned buffers"};
+    LearnedBufs &B = c->lb;
+    VecOps V = c->vec();
+    const int64_t n = c->P.n, mt = c->P.mt;
+    V.scaling(s, lam, c->opts.delta_d, c->vD);
+    V.dot(mt, s, lam, c->scal + 40);
+    const double mu = d2h_scalar(c, c->scal + 40) / (double)std::max<int64_t>(mt, 1);
+    CK(cudaMemcpyAsync(B.mu + 1, &mu, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    learned_diag(c->dp, jv, c->vD, c->cur_delta_p, B.diag_new, c->st);
+    learned_features(c->dp, B, jv, c->vD, x, c->st);
+    CK(cudaMemcpyAsync(feat, B.feat, n * kNF * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemsetAsync(c->vc, 0, n * sizeof(double), c->st));
+    for (int p = 0; p < B.P; p++) {  // w_p = L^{-1} P K P^T L^{-T} z_p
+      CK(cudaMemcpyAsync(c->fsb, z + (int64_t)p * n, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+      launch_fused_graph(c, 2);
+      V.permute_out<float>(c->fsx, nullptr, c->vz, false);
+      V.residual(jv, c->vD, c->cur_wvals, c->cur_delta_p, c->vz, c->vc, c->vq, c->vtA);
+      V.negate(n, c->vq);
+      V.permute_in<float>(c->vq, nullptr, c->fsa);
+      launch_fused_graph(c, 1);
+      CK(cudaMemcpyAsync(w + (int64_t)p * n, c->fsb, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return IPM_OK;
+  });
+}
+
+ipm_status ipm_learned_loss_grad(ipm_ctx *c, const float *feat, const float *z, const float *w,
+                                 double *h_loss, float *h_grad) {
+  if (!c || !feat || !z || !w) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (!learned_on(c) || c->state < 2) throw Fail{IPM_ERR_STATE, "learned buffers not set up"};
+    LearnedBufs &B = c->lb;
+    CK(cudaMemcpyAsync(B.feat, feat, c->P.n * kNF * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    learned_forward(B, false, c->st);
+    learned_loss_grad(B, z, w, c->lb_loss, c->st);
+    if (h_loss) CK(cudaMemcpyAsync(h_loss, c->lb_loss, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (h_grad) CK(cudaMemcpyAsync(h_grad, B.grad, kNParams * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return IPM_OK;
+  });
+}
+
+ipm_status ipm_learned_train(ipm_ctx *c, const float *feat, const float *z, const float *w,
+                             float lr, int32_t steps, double *h_loss) {
+  if (!c || !feat || !z || !w || steps < 0) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (!learned_on(c) || c->state < 2) throw Fail{IPM_ERR_STATE, "learned buffers not set up"};
+    LearnedBufs &B = c->lb;
+    CK(cudaMemcpyAsync(B.feat, feat, c->P.n * kNF * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    for (int k = 0; k < steps; k++) {
+      learned_forward(B, false, c->st);
+      learned_loss_grad(B, z, w, c->lb_loss, c->st);
+      learned_adam(B, lr, c->st);
+    }
+    if (h_loss) CK(cudaMemcpyAsync(h_loss, c->lb_loss, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return IPM_OK;
+  });
+}
+
 int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }
 
 const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 void ipm_destroy(ipm_ctx *c) {
   if (c && c->solve_graph) cudaGraphExecDestroy(c->solve_graph);
+  if (c && c->fwd_graph) cudaGraphExecDestroy(c->fwd_graph);
+  if (c && c->bwd_graph) cudaGraphExecDestroy(c->bwd_graph);
   delete c;
 }
 

@@ -178,10 +178,11 @@ void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Din
 }
 
 int launch_solve_fused(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv,
-                       float *a, float *b, float *x, float *t, cudaStream_t st) {
+                       float *a, float *b, float *x, float *t, cudaStream_t st, bool fwd,
+                       bool bwd) {
   int launches = 0;
   const int nlev = (int)plan.levels.size();
-  for (int li = 0; li < nlev; li++) {
+  for (int li = 0; li < nlev && fwd; li++) {
     const LevelPlan &LP = plan.levels[li];
     if (LP.gath_e > LP.gath_b) {
       note_launch(); launches++;
@@ -195,7 +196,7 @@ int launch_solve_fused(const DevPlan &dp, const Plan &plan, const float *L, cons
       }
     }
   }
-  for (int li = nlev - 1; li >= 0; li--) {
+  for (int li = nlev - 1; li >= 0 && bwd; li--) {
     const LevelPlan &LP = plan.levels[li];
     if (LP.rg_e > LP.rg_b) {
       note_launch(); launches++;

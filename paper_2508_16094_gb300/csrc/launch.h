@@ -38,8 +38,11 @@ void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, c
 // the update vectors (all fixed buffers, so the launch sequence can be captured
 // in a CUDA graph). Returns the number of kernels launched.
 void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Dinv, cudaStream_t st);
+// fwd/bwd select the sweeps: forward only maps a to b = L^{-1} a; backward only
+// maps b to x = L^{-T} b (b is overwritten).
 int launch_solve_fused(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv,
-                       float *a, float *b, float *x, float *t, cudaStream_t st);
+                       float *a, float *b, float *x, float *t, cudaStream_t st, bool fwd = true,
+                       bool bwd = true);
 
 // Sampled entries of L (final numbering).
 template <typename T>
