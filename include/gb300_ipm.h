@@ -286,29 +286,50 @@ IPM_API ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t
                                     ipm_mpc_config *best, float *h_ms);
 
 /* --- learned correction of a stale factor --------------------------------
- * Not in the paper. A per-variable network (8 features -> 32 -> 32 -> 17, tanh)
- * maps the change between the matrix a held factor L_s was computed from and
- * the current K to Delta = diag(exp(o_0)) and U (n x 16, rank 16) so that
- * M^{-1} = P^T L_s^{-T} (Delta + U U^T)^{-1} L_s^{-1} P preconditions PCG on K
- * (Woodbury identity with a 16 x 16 capacitance). Training minimises
- * sum_z ||w_z - Delta z - U (U^T z)||^2 / (probes n) with w_z = L_s^{-1} P K P^T
- * L_s^{-T} z on iterates of the method itself. Features, targets, loss,
- * gradients and Adam run in this library's kernels. Requires learned_probes > 0
- * (or learned != 0) at kkt_analyze and an FP32-storage factor. */
+ * Not in the paper (its iterative-solver discussion in Sec. 1 is the nearest
+ * passage). A per-variable network (8 features -> 32 -> 32 -> 17, tanh; 1905
+ * FP32 weights W1[32x8], b1, W2[32x32], b2, W3[17x32], b3, row-major) maps the
+ * change between the matrix a held factor L_s was computed from and the current
+ * K of Eq. (5) to Delta = diag(exp(o_0)) and U = 0.1 o_{1..16} (n x 16) so that
+ *   M^{-1} = P^T L_s^{-T} (Delta + U U^T)^{-1} L_s^{-1} P
+ * preconditions PCG on K (Woodbury identity, 16 x 16 capacitance in FP64).
+ * ipm_solve with options.learned = 1 then skips the refactorisation of an
+ * iteration whenever both PCG solves reach ir_tol within learned_pcg_max
+ * iterations, and refactors otherwise; learned = 2 is the ablation Delta = 1,
+ * U = 0 (plain stale factor). Training minimises the relative probe loss
+ *   sum_z ||Delta^{-1} (w_z - Delta z - U (U^T z))||^2 / (probes n),
+ *   w_z = L_s^{-1} P K P^T L_s^{-T} z,
+ * on iterates of the method itself; features, targets, loss, gradients and
+ * Adam run in this library's kernels, with fixed-order reductions (the same
+ * call gives the same bits). The learned buffers are sized at kkt_analyze:
+ * options.learned != 0 or learned_probes > 0 must be set before it (else
+ * ipm_set_options returns IPM_ERR_STATE), and the factor must be stored in
+ * FP32 (precision TF32, TF32X3 or FP32). Features of variable i (stored at its
+ * permuted index): log(K_ii / K_s,ii); log of the ratio of its bound-row
+ * weights / 10; asinh of the signed and absolute change of sum_r J_ri^2 D_r,
+ * relative to K_s,ii; log10(mu) / 10; log(mu / mu_s) / 10; log(bound weight /
+ * K_ii) / 10; x_i / 10 (clamped as documented in the kernels). */
 IPM_API int32_t ipm_learned_param_count(void);
-/* Copy the weights out (h_get, may be NULL) and/or in (h_set, may be NULL). */
+/* Copy the weights out (h_get, may be NULL) and/or in (h_set, may be NULL;
+ * setting resets the Adam moments). Host arrays of ipm_learned_param_count()
+ * floats. IPM_ERR_STATE before ipm_set_workspace or without learned buffers. */
 IPM_API ipm_status ipm_learned_weights(ipm_ctx *ctx, float *h_get, const float *h_set);
-/* One training sample for the held factor and the current iterate: features
- * (d_feat, n x 8, permuted index) and targets d_w (probes x n) for the probes
- * d_z (probes x n, permuted index). All device memory. */
+/* One training sample against the factor the last ipm_solve iteration left
+ * held (its iterate recorded by ipm_solve) at the iterate (d_x, d_s,
+ * d_lambda): features d_feat (n x 8, permuted index) and targets d_w
+ * (probes x n) for the probes d_z (probes x n, permuted index), probes =
+ * min(8, max(1, learned_probes)). All device memory owned by the caller.
+ * IPM_ERR_STATE without a held FP32 factor recorded by ipm_solve (a direct
+ * kkt_factor call, or a cold-started ipm_solve, drops it). */
 IPM_API ipm_status ipm_learned_sample(ipm_ctx *ctx, const double *d_jvals, const double *d_x,
                                       const double *d_s, const double *d_lambda,
                                       const float *d_z, float *d_feat, float *d_w);
-/* Loss and its gradient w.r.t. the weights for one sample (no update). */
+/* Loss and its gradient w.r.t. the weights for one sample (no update); h_loss,
+ * h_grad (param_count floats) are host pointers and may be NULL. */
 IPM_API ipm_status ipm_learned_loss_grad(ipm_ctx *ctx, const float *d_feat, const float *d_z,
                                          const float *d_w, double *h_loss, float *h_grad);
-/* steps Adam updates (learning rate lr) on one sample; h_loss: loss before
- * the last update. */
+/* steps Adam updates (learning rate lr, beta 0.9 / 0.999) on one sample;
+ * h_loss (host, may be NULL): loss before the last update. */
 IPM_API ipm_status ipm_learned_train(ipm_ctx *ctx, const float *d_feat, const float *d_z,
                                      const float *d_w, float lr, int32_t steps, double *h_loss);
 

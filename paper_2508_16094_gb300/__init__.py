@@ -202,11 +202,12 @@ class IpmContext:
     # --- C entry points -----------------------------------------------------
     def ipm_set_options(self, options: Options | None = None, **kw):
         """Push options to the library (the context keeps its own copy)."""
-        if options is not None:
-            self.options = options
+        o = Options()
+        C.pointer(o)[0] = options if options is not None else self.options
         for k, v in kw.items():
-            setattr(self.options, k, v)
-        self._check(self._lib.ipm_set_options(self.handle, C.byref(self.options)))
+            setattr(o, k, v)
+        self._check(self._lib.ipm_set_options(self.handle, C.byref(o)))
+        self.options = o
 
     def kkt_analyze(self, perm=None) -> SymbolicInfo:
         info = SymbolicInfo()

@@ -49,6 +49,7 @@ struct ipm_ctx {
   // learned correction of a stale factor
   LearnedBufs lb;
   bool learned_active = false;  // PCG preconditioner = corrected stale factor
+  bool lb_on = false;           // learned buffers sized for n (fixed by the layout)
   bool have_stale = false;      // lb.D_old / diag_old / mu[0] describe the held factor
   int refine_override = -1, pcg_override = -1;
   double *lb_loss = nullptr;
@@ -224,6 +225,7 @@ void layout(ipm_ctx *c, char *base) {
   {  // learned-correction buffers (only when enabled)
     LearnedBufs &B = c->lb;
     const bool on = c->opts.learned != 0 || c->opts.learned_probes > 0;
+    c->lb_on = on;
     B.n = P.n;
     B.mt = P.mt;
     B.P = std::min(8, std::max(1, c->opts.learned_probes));
@@ -295,6 +297,7 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   CK(cudaStreamSynchronize(c->st));
   c->last_perturbed = out[ST_PERTURBED];
   c->factor_prec = prec;
+  c->have_stale = false;  // ipm_solve re-records what a new factor was computed from
   c->state = 4;
   if (out[ST_TIMEOUT]) {
     c->state = 3;
@@ -412,6 +415,7 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
     apply_factor(c, r, z, false);
     CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     V.dot(n, r, z, sN + 2);
+    const double rel0 = rel;
     int k = 0;
     for (; k < pcg_max && rel > o.ir_tol; k++) {
       // q = K p  (residual of b = 0 gives -K p)
@@ -423,6 +427,15 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
       V.absmax(n, r, sN + 1);
       rel = d2h_scalar(c, sN + 1) / bn;
       if (rel <= o.ir_tol || !std::isfinite(rel)) { k++; break; }
+      // a corrected stale factor is only worth keeping if PCG converges
+      // within the budget: from the fifth iteration on, give up once the mean
+      // contraction so far projects past pcg_max
+      if (c->learned_active && k + 1 >= 5) {
+        if (!(rel < rel0)) { k++; break; }
+        const double rate = std::log(rel / rel0) / (k + 1);  // < 0
+        const double need = (k + 1) + std::log(o.ir_tol / rel) / rate;
+        if (need > pcg_max) { k++; break; }
+      }
       apply_factor(c, r, z, false);
       V.dot(n, r, z, sN + 4);
       V.xpby_ratio(n, sN + 4, sN + 2, z, p);
@@ -500,7 +513,7 @@ ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jval
 // later iterations compare against it).
 void save_stale(ipm_ctx *c, const double *jv) {
   LearnedBufs &B = c->lb;
-  if (!(c->opts.learned != 0 || c->opts.learned_probes > 0)) return;
+  if (!c->lb_on || !(c->opts.learned != 0 || c->opts.learned_probes > 0)) return;
   CK(cudaMemcpyAsync(B.D_old, c->cur_D, c->P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   learned_diag(c->dp, jv, c->cur_D, c->cur_delta_p, B.diag_old, c->st);
   CK(cudaMemcpyAsync(B.mu, &c->sc->mu, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -641,6 +654,12 @@ ipm_status ipm_create(int32_t n, int32_t m, const int64_t *jp, const int32_t *ji
 
 ipm_status ipm_set_options(ipm_ctx *c, const ipm_options *o) {
   if (!c || !o) return IPM_ERR_ARG;
+  // the learned buffers are sized when the workspace is laid out: they cannot
+  // be switched on afterwards
+  if (c->state >= 1 && !c->lb_on && (o->learned != 0 || o->learned_probes > 0)) {
+    c->err = "learned options must be set before kkt_analyze";
+    return IPM_ERR_STATE;
+  }
   c->opts = *o;
   return IPM_OK;
 }
@@ -703,7 +722,7 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     if (c->fwd_graph) { CK(cudaGraphExecDestroy(c->fwd_graph)); c->fwd_graph = nullptr; }
     if (c->bwd_graph) { CK(cudaGraphExecDestroy(c->bwd_graph)); c->bwd_graph = nullptr; }
     c->have_stale = false;
-    if (c->opts.learned != 0 || c->opts.learned_probes > 0) learned_init_weights(c);
+    if (c->lb_on) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
       c->tcp.encode(c->plan, (float *)c->L, c->st);
     } catch (const std::exception &e) {
@@ -771,6 +790,7 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
     c->refine_steps = c->pcg_steps = 0;
     // starting point (unless warm-started from the caller's x, s, lambda)
     if (!o.warm_start) {
+      c->have_stale = false;  // a held factor belongs to another run
       std::vector<double> x0(P.n);
       for (int32_t i = 0; i < P.n; i++) {
         const bool fl = std::isfinite(P.l[i]), fu = std::isfinite(P.u[i]);
@@ -828,7 +848,7 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       // network's Delta + U U^T and solve both directions by PCG; any solve
       // that misses ir_tol within learned_pcg_max iterations falls back to
       // the exact refactorisation.
-      const bool try_skip = o.learned != 0 && c->have_stale && c->factor_prec != IPM_FP64 &&
+      const bool try_skip = o.learned != 0 && c->lb_on && c->have_stale && c->factor_prec != IPM_FP64 &&
                             c->tcp.ready();
       bool factored = false;
       auto refactor = [&]() -> ipm_status {
@@ -854,6 +874,10 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
         const int64_t pcg0 = c->pcg_steps;
         stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
         res.learned_pcg_steps += (int32_t)(c->pcg_steps - pcg0);
+        if (o.verbose)
+          std::fprintf(stderr, "ipm it %3d stale-factor PCG: %d iterations, residual %.2e -> %s\n",
+                       it, (int)(c->pcg_steps - pcg0), c->last_rel,
+                       c->last_rel <= o.ir_tol ? "kept" : "refactor");
         if (stt != IPM_OK || !(c->last_rel <= o.ir_tol)) {
           stt = refactor();
           if (stt == IPM_OK)
@@ -983,7 +1007,9 @@ int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0;
 
 int32_t ipm_learned_param_count(void) { return kNParams; }
 
-static bool learned_on(const ipm_ctx *c) { return c->opts.learned != 0 || c->opts.learned_probes > 0; }
+static bool learned_on(const ipm_ctx *c) {
+  return c->lb_on && (c->opts.learned != 0 || c->opts.learned_probes > 0);
+}
 
 ipm_status ipm_learned_weights(ipm_ctx *c, float *h_get, const float *h_set) {
   if (!c) return IPM_ERR_ARG;

@@ -227,14 +227,15 @@ __global__ void __launch_bounds__(256) probe_t_kernel(LearnedBufs B, const float
 
 __global__ void sum_partials_kernel(const float *partial, int nblocks, int width, int stride,
                                     float *out) {
-  for (int a = threadIdx.x; a < width; a += blockDim.x) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < width; a += blockDim.x * gridDim.x) {
     float s = 0.f;
     for (int k = 0; k < nblocks; k++) s += partial[k * stride + a];
     out[a] = s;
   }
 }
 
-// residual r_p = w_p - Delta z_p - U t_p: loss partials (FP64) and partials of q_p = U^T r_p
+// relative residual r_p = Delta^{-1} (w_p - Delta z_p - U t_p): loss partials (FP64)
+// and partials of q_p = U^T Delta^{-1} r_p
 __global__ void __launch_bounds__(256) resid_kernel(LearnedBufs B, const float *z, const float *wt) {
   __shared__ float red[256 / 32][kMaxP * kNR];
   __shared__ double lred[256 / 32];
@@ -246,9 +247,11 @@ __global__ void __launch_bounds__(256) resid_kernel(LearnedBufs B, const float *
       const float zv = z[(int64_t)p * B.n + j];
       float ut = 0.f;
       for (int a = 0; a < kNR; a++) ut = fmaf(B.U[j * kNR + a], B.probe_t[p * kNR + a], ut);
-      const float r = wt[(int64_t)p * B.n + j] - B.delta[j] * zv - ut;
+      const float dj = B.delta[j];
+      const float r = (wt[(int64_t)p * B.n + j] - dj * zv - ut) / dj;
       loss += (double)r * (double)r;
-      for (int a = 0; a < kNR; a++) acc[p * kNR + a] = fmaf(B.U[j * kNR + a], r, acc[p * kNR + a]);
+      const float rd = r / dj;
+      for (int a = 0; a < kNR; a++) acc[p * kNR + a] = fmaf(B.U[j * kNR + a], rd, acc[p * kNR + a]);
     }
   }
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
@@ -290,17 +293,20 @@ __global__ void __launch_bounds__(256) outgrad_bwd_kernel(LearnedBufs B, const f
     float go[kNO];
     float gd = 0.f, gu[kNR];
     for (int a = 0; a < kNR; a++) gu[a] = 0.f;
+    const float dj = B.delta[j];
     for (int p = 0; p < B.P; p++) {
       const float zv = z[(int64_t)p * B.n + j];
       float ut = 0.f;
       for (int a = 0; a < kNR; a++) ut = fmaf(B.U[j * kNR + a], B.probe_t[p * kNR + a], ut);
-      const float r = wt[(int64_t)p * B.n + j] - B.delta[j] * zv - ut;
-      gd += -2.f * r * zv;
+      const float r = (wt[(int64_t)p * B.n + j] - dj * zv - ut) / dj;
+      // d r / d Delta_j = -(r + z_j) / Delta_j; d loss / d log Delta_j = Delta_j d loss / d Delta_j
+      gd += -2.f * r * (r + zv);
+      const float rd = r / dj;
       for (int a = 0; a < kNR; a++)
-        gu[a] += -2.f * (r * B.probe_t[p * kNR + a] + zv * B.probe_q[p * kNR + a]);
+        gu[a] += -2.f * (rd * B.probe_t[p * kNR + a] + zv * B.probe_q[p * kNR + a]);
     }
     const float o0 = B.out[j * kNO];
-    go[0] = (o0 > -20.f && o0 < 20.f) ? gd * B.delta[j] * scale : 0.f;
+    go[0] = (o0 > -20.f && o0 < 20.f) ? gd * scale : 0.f;
     for (int a = 0; a < kNR; a++) go[1 + a] = gu[a] * kUScale * scale;
     float *g = B.gout + j * (kNO + 2 * kNH);
     for (int a = 0; a < kNO; a++) g[a] = go[a];

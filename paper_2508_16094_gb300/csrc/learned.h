@@ -46,8 +46,8 @@ void learned_forward(const LearnedBufs &B, bool ablate, cudaStream_t st);
 void learned_capacitance(const LearnedBufs &B, cudaStream_t st);
 // v <- (Delta + U U^T)^{-1} v (permuted index, FP32) by the Woodbury identity
 void learned_apply(const LearnedBufs &B, float *v, cudaStream_t st);
-// loss sum_z ||w_z - Delta z - U U^T z||^2 / (P n) and its gradient w.r.t. the
-// weights (into B.grad); h_loss receives the loss (synchronises)
+// loss sum_z ||Delta^{-1} (w_z - Delta z - U U^T z)||^2 / (P n) and its gradient
+// w.r.t. the weights (into B.grad); the loss goes to d_loss (device)
 void learned_loss_grad(const LearnedBufs &B, const float *z, const float *wt, double *d_loss,
                        cudaStream_t st);
 void learned_adam(LearnedBufs &B, float lr, cudaStream_t st);

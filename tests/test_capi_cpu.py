@@ -95,3 +95,12 @@ def test_argument_errors(lib):
     # workspace size is reported and covers the FP64 factor
     info = ctx.kkt_analyze(None)
     assert info.workspace_bytes >= 8 * info.factor_entries
+
+
+def test_options_cannot_enable_learned_after_analysis():
+    lp = gen.grid_lp(6, seed=24)
+    o = gb.default_options(precision=4, storage_fp64=0)
+    ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u, options=o)
+    ctx.kkt_analyze(gen.nd_order_grid3d(6))
+    with pytest.raises(gb.IpmError):
+        ctx.ipm_set_options(learned=1)
