@@ -154,6 +154,72 @@ def mpc_measure(steps: int = 3):
     return out
 
 
+def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
+    """Time to a 1e-6 KKT residual from the cold start on the G^3 member of the
+    grid-LP family for every form of the path: the FP64 factor, the split-TF32
+    factor with FP64 refinement, and the latter with stale-factor skipping
+    corrected by the trained network (learned = 1) or uncorrected (learned = 2,
+    the E = 0 ablation). The network is first trained on the iterates of the
+    method itself on other seeds of the same family."""
+    import torch
+    import paper_2508_16094_gb300 as gb
+    from paper_2508_16094_gb300 import learned as GL
+    perm = gen.nd_order_grid3d(G)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    lp = gen.grid_lp(G, seed=seed)
+    jv, b, c = dev(lp.val), dev(lp.b), dev(lp.c)
+
+    def mk(**kw):
+        ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u,
+                            options=gb.default_options(tol=1e-6, max_iter=200, **kw))
+        ctx.kkt_analyze(perm)
+        ctx.ipm_set_workspace()
+        return ctx
+
+    def run(ctx, **kw):
+        ctx.ipm_set_options(warm_start=0, **kw)
+        x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+        s = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        lam = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.ipm_solve(jv, b, c, x, s, lam)
+        torch.cuda.synchronize()
+        return {"seconds": time.perf_counter() - t0, "status": int(r.status),
+                "iterations": int(r.iterations), "factorizations": int(r.factorizations),
+                "learned_skips": int(r.learned_skips), "pcg_steps": int(r.pcg_steps),
+                "refine_steps": int(r.refine_steps), "kkt": r.kkt, "objective": r.objective,
+                "time_factor_s": r.time_factor_ms / 1e3, "time_solve_s": r.time_solve_ms / 1e3}
+
+    out = {"workload": f"grid LP {G}^3 (n={lp.n}), seed {seed}; network trained on seeds "
+                       f"{list(train_seeds)} of the same family"}
+    c64 = mk(precision=gb.IPM_FP64, storage_fp64=1)
+    run(c64, max_iter=1)  # first-touch of the workspace and graphs
+    out["fp64"] = run(c64, max_iter=200)
+    c64.close()
+    ctx = mk(precision=gb.IPM_TF32X3, storage_fp64=0, learned_probes=4)
+    run(ctx, max_iter=1, learned=0)
+    out["tf32x3"] = run(ctx, max_iter=200, learned=0)
+    t0 = time.perf_counter()
+    samples = []
+    for sd in train_seeds:
+        lpt = gen.grid_lp(G, seed=sd)
+        jt, bt, ct = dev(lpt.val), dev(lpt.b), dev(lpt.c)
+        traj = GL.trajectory(ctx, jt, bt, ct, 60)
+        samples += GL.collect(ctx, jt, bt, ct, traj, staleness=(1, 2, 3), seed=sd)
+    hist = GL.train(ctx, samples, epochs=30, lr=3e-3)
+    torch.cuda.synchronize()
+    out["training"] = {"samples": len(samples), "seconds": time.perf_counter() - t0,
+                       "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]}
+    out["tf32x3_learned"] = run(ctx, max_iter=200, learned=1)
+    out["tf32x3_stale_E0"] = run(ctx, max_iter=200, learned=2)
+    ctx.close()
+    ref = out["fp64"]["objective"]
+    for k in ("tf32x3", "tf32x3_learned", "tf32x3_stale_E0"):
+        out[k]["objective_rel_diff_vs_fp64"] = abs(out[k]["objective"] - ref) / max(1.0, abs(ref))
+    return out
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,6 +393,9 @@ def run_ours(args, ws, rank, local):
     mpc = None
     if rank == 0 and not args.no_mpc:
         mpc = mpc_measure()
+    forms = None
+    if rank == 0 and args.forms_grid > 0:
+        forms = forms_measure(args.forms_grid)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -360,6 +429,7 @@ def run_ours(args, ws, rank, local):
             "clocks": clk.summary(),
             "time_to_kkt_1e-6": tti,
             "mpc_batch": mpc,
+            "time_to_kkt_1e-6_forms": forms,
             "ipm_step": {"refine_steps": int(res.refine_steps), "pcg_steps": int(res.pcg_steps),
                          "factor_ms": res.time_factor_ms / steps_done,
                          "solve_ms": res.time_solve_ms / steps_done},
@@ -380,6 +450,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vary-seed", action="store_true")
     ap.add_argument("--no-mpc", action="store_true")
+    ap.add_argument("--forms-grid", type=int, default=48,
+                    help="grid of the FP64 / split-TF32 / learned time-to-1e-6 comparison (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank, local = dist_init()

@@ -41,11 +41,9 @@ struct ipm_ctx {
          *vt = nullptr, *vjd = nullptr, *vjx = nullptr, *vtA = nullptr;
   double *dl_ = nullptr, *du_ = nullptr;
   double *jv_copy = nullptr, *D_copy = nullptr, *wv_copy = nullptr;  // inputs kept for refinement
-  float *dinv = nullptr, *fsa = nullptr, *fsb = nullptr, *fsx = nullptr;  // fused FP32 solve
-  cudaGraphExec_t solve_graph = nullptr;  // captured fused solve (fixed buffers)
-  int solve_graph_launches = 0;
-  cudaGraphExec_t fwd_graph = nullptr, bwd_graph = nullptr;  // its two sweeps alone
-  int fwd_graph_launches = 0, bwd_graph_launches = 0;
+  float *dinv = nullptr, *fsa = nullptr, *fsb = nullptr, *fsx = nullptr;  // persistent FP32 solve
+  unsigned *psbar = nullptr;  // its grid-barrier state
+  float *pspart = nullptr;    // its partial sums
   // learned correction of a stale factor
   LearnedBufs lb;
   bool learned_active = false;  // PCG preconditioner = corrected stale factor
@@ -158,9 +156,9 @@ void layout(ipm_ctx *c, char *base) {
   d.sgemv = upload(cv, pl.sgemv_tasks, st);
   d.rgemv = upload(cv, pl.rgemv_tasks, st);
   d.toff = upload(cv, pl.toff, st);
-  d.fs_fwd = upload(cv, pl.fs_fwd, st);
-  d.fs_bwd = upload(cv, pl.fs_bwd, st);
   d.fs_inv = upload(cv, pl.fs_inv, st);
+  d.ps_tasks = upload(cv, pl.ps_tasks, st);
+  d.ps_phases = upload(cv, pl.ps_phases, st);
   d.fs_dinv_off = upload(cv, pl.fs_dinv_off, st);
   d.k_slot = upload(cv, pl.k_slot, st);
   d.k_poff = upload(cv, pl.k_poff, st);
@@ -222,6 +220,9 @@ void layout(ipm_ctx *c, char *base) {
   c->fsa = cv.take<float>(n);
   c->fsb = cv.take<float>(n);
   c->fsx = cv.take<float>(n);
+  c->psbar = cv.take<unsigned>(kPsBarrierWords);
+  c->pspart = cv.take<float>(pl.ps_part_entries);
+  if (base) CK(cudaMemsetAsync(c->psbar, 0, kPsBarrierWords * sizeof(unsigned), st));
   {  // learned-correction buffers (only when enabled)
     LearnedBufs &B = c->lb;
     const bool on = c->opts.learned != 0 || c->opts.learned_probes > 0;
@@ -311,30 +312,15 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   return IPM_OK;
 }
 
-// out = M^{-1} b with the current factor (b, out: original numbering, device)
-// capture (once) and launch one of the fused-solve graphs: which = 0 both
-// sweeps, 1 forward only, 2 backward only
-void launch_fused_graph(ipm_ctx *c, int which) {
-  cudaGraphExec_t *g = which == 0 ? &c->solve_graph : which == 1 ? &c->fwd_graph : &c->bwd_graph;
-  int *nl = which == 0 ? &c->solve_graph_launches
-                       : which == 1 ? &c->fwd_graph_launches : &c->bwd_graph_launches;
-  if (!*g) {
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t gr;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    *nl = launch_solve_fused(c->dp, c->plan, (const float *)c->L, c->dinv, c->fsa, c->fsb, c->fsx,
-                             reinterpret_cast<float *>(c->tv), cs, which != 2, which != 1);
-    CK(cudaStreamEndCapture(cs, &gr));
-    CK(cudaGraphInstantiate(g, gr, 0));
-    CK(cudaGraphDestroy(gr));
-    CK(cudaStreamDestroy(cs));
-  } else {
-    for (int k = 0; k < *nl; k++) note_launch();
-  }
-  CK(cudaGraphLaunch(*g, c->st));
+// One persistent FP32 solve launch over the workspace vectors: which = 0 both
+// sweeps (fsa -> fsx), 1 forward only (fsa -> fsb), 2 backward only (fsb -> fsx)
+void launch_fp32_solve(ipm_ctx *c, int which) {
+  launch_psolve(c->dp, c->plan, (const float *)c->L, c->dinv, c->fsa, c->fsb, c->fsx,
+                reinterpret_cast<float *>(c->tv), c->pspart, c->psbar, c->status, which != 2, which != 1,
+                c->st);
 }
 
+// out = M^{-1} b with the current factor (b, out: original numbering, device)
 void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
   VecOps V = c->vec();
   if (c->learned_active) {  // P^T L_s^{-T} (Delta + U U^T)^{-1} L_s^{-1} P b
@@ -342,9 +328,9 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
     V.absmax(c->P.n, b, amax);
     V.inv_scale(amax, scale);
     V.permute_in<float>(b, scale, c->fsa);
-    launch_fused_graph(c, 1);
+    launch_fp32_solve(c, 1);
     learned_apply(c->lb, c->fsb, c->st);
-    launch_fused_graph(c, 2);
+    launch_fp32_solve(c, 2);
     V.permute_out<float>(c->fsx, scale, out, accumulate);
     return;
   }
@@ -359,8 +345,21 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
     float *t = reinterpret_cast<float *>(c->tv);
     (void)t;
     V.permute_in<float>(b, scale, c->fsa);
-    launch_fused_graph(c, 0);
+    launch_fp32_solve(c, 0);
     V.permute_out<float>(c->fsx, scale, out, accumulate);
+  }
+}
+
+// A grid barrier of the persistent solve that ran out of time leaves its state
+// inconsistent: reset it and report the timeout.
+void check_solve_barrier(ipm_ctx *c) {
+  int32_t flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->status + ST_SOLVE_TIMEOUT, sizeof(flag), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (flag) {
+    CK(cudaMemsetAsync(c->status + ST_SOLVE_TIMEOUT, 0, sizeof(int32_t), c->st));
+    CK(cudaMemsetAsync(c->psbar, 0, kPsBarrierWords * sizeof(unsigned), c->st));
+    throw Fail{IPM_ERR_TIMEOUT, "a grid barrier of the persistent solve ran out of time"};
   }
 }
 
@@ -447,6 +446,7 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
   }
   CK(cudaMemcpyAsync(x, xx, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   CK(cudaGetLastError());
+  if (c->factor_prec != IPM_FP64) check_solve_barrier(c);
   c->last_rel = rel;
   if (info) *info = ipm_solve_info{iters, used_pcg, rel};
   if (!(rel <= o.accept_tol)) {
@@ -713,14 +713,8 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     if ((size_t)(base - (char *)buf) + c->ws_need - 256 > bytes) throw Fail{IPM_ERR_NOMEM, "workspace misaligned"};
     c->ws = base;
     c->ws_bytes = bytes;
-    if (c->solve_graph) {  // captured against the previous buffers
-      CK(cudaGraphExecDestroy(c->solve_graph));
-      c->solve_graph = nullptr;
-    }
     layout(c, base);
     CK(cudaStreamSynchronize(c->st));
-    if (c->fwd_graph) { CK(cudaGraphExecDestroy(c->fwd_graph)); c->fwd_graph = nullptr; }
-    if (c->bwd_graph) { CK(cudaGraphExecDestroy(c->bwd_graph)); c->bwd_graph = nullptr; }
     c->have_stale = false;
     if (c->lb_on) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
@@ -1046,15 +1040,15 @@ ipm_status ipm_learned_sample(ipm_ctx *c, const double *jv, const double *x, con
     CK(cudaMemsetAsync(c->vc, 0, n * sizeof(double), c->st));
     for (int p = 0; p < B.P; p++) {  // w_p = L^{-1} P K P^T L^{-T} z_p
       CK(cudaMemcpyAsync(c->fsb, z + (int64_t)p * n, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
-      launch_fused_graph(c, 2);
+      launch_fp32_solve(c, 2);
       V.permute_out<float>(c->fsx, nullptr, c->vz, false);
       V.residual(jv, c->vD, c->cur_wvals, c->cur_delta_p, c->vz, c->vc, c->vq, c->vtA);
       V.negate(n, c->vq);
       V.permute_in<float>(c->vq, nullptr, c->fsa);
-      launch_fused_graph(c, 1);
+      launch_fp32_solve(c, 1);
       CK(cudaMemcpyAsync(w + (int64_t)p * n, c->fsb, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
     }
-    CK(cudaStreamSynchronize(c->st));
+    check_solve_barrier(c);
     return IPM_OK;
   });
 }
@@ -1098,9 +1092,6 @@ int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }
 const char *ipm_last_error(const ipm_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 void ipm_destroy(ipm_ctx *c) {
-  if (c && c->solve_graph) cudaGraphExecDestroy(c->solve_graph);
-  if (c && c->fwd_graph) cudaGraphExecDestroy(c->fwd_graph);
-  if (c && c->bwd_graph) cudaGraphExecDestroy(c->bwd_graph);
   delete c;
 }
 

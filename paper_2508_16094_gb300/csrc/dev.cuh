@@ -15,7 +15,8 @@ struct DevPlan {
   const int32_t *children, *inv, *relpos, *sri;
   const Task *build, *gemm, *potrf, *trsm, *syrk, *gath, *sdiag, *sgemv, *rgemv;
   const int64_t *toff;
-  const Task *fs_fwd, *fs_bwd, *fs_inv;  // fused FP32 solve
+  const Task *fs_inv, *ps_tasks;  // persistent FP32 solve
+  const SolvePhase *ps_phases;
   const int64_t *fs_dinv_off;
   const int64_t *k_slot, *k_poff, *k_w, *k_orig;
   const int32_t *k_pa, *k_pb, *k_diag;
@@ -36,7 +37,8 @@ struct DevPlan {
 enum StatusWord : int {
   ST_FAIL_COL = 0,   // smallest column with a non-positive pivot (INT32_MAX if none)
   ST_PERTURBED = 1,  // pivots replaced by the low-precision factorisation
-  ST_TIMEOUT = 2,    // a bounded device-side wait ran out
+  ST_TIMEOUT = 2,    // a bounded device-side wait of the factorisation ran out
+  ST_SOLVE_TIMEOUT = 3,  // a grid barrier of the persistent solve ran out
   ST_COUNT = 8
 };
 

@@ -48,6 +48,20 @@ struct Task {
   int32_t front, a, b, c;
 };
 
+// One phase of the persistent solve: tasks [begin, end) of one kind.
+enum SolvePhaseKind : int32_t {
+  PS_FWD_GATHER = 0,  // (front, first row of a 256-row chunk, slot of block 0 or -1)
+  PS_FWD_STEP = 1,    // (front, first row of a 128-row chunk, block column j, slot of block j+128 or -1)
+  PS_BWD_PART = 2,    // (front, first column of a 128-column block, first row below the front
+                      //  of a 128-row chunk, partial-sum slot)
+  PS_BWD_ROWS = 3,    // (front, first column of a 128-column block, slot if it is the last block
+                      //  or -1, first partial-sum slot of the block)
+  PS_BWD_STEP = 4     // (front, first column of a 128-column chunk, block row j, slot of block j-128 or -1)
+};
+struct SolvePhase {
+  int32_t begin, end, kind, pad;
+};
+
 // Work of one level of the supernodal tree, as ranges into the task arrays.
 struct StepRange {
   int32_t gemm_b, gemm_e, potrf_b, potrf_e, trsm_b, trsm_e;
@@ -63,7 +77,6 @@ struct LevelPlan {
   std::vector<StepRange> steps;      // factor steps (block columns)
   std::vector<int32_t> sstep_b;      // solve steps: [sstep_b[j], sstep_b[j+1]) in stasks
   std::vector<int32_t> sgemv_b;      // solve update tasks per step
-  std::vector<int32_t> ffwd_b, fbwd_b;  // fused FP32 solve: task ranges per 128-wide step
   int32_t max_ncol = 0;
 };
 
@@ -83,9 +96,17 @@ struct Plan {
   std::vector<int64_t> toff;         // per front: offset of its solve update vector (length nrow)
   int64_t t_entries = 0;
   // fused FP32 solve: explicit inverses of the 128-wide diagonal blocks
-  std::vector<Task> fs_fwd, fs_bwd, fs_inv;  // c = block slot
-  std::vector<int64_t> fs_dinv_off;          // per block slot: offset of its jb x jb inverse
+  // persistent FP32 solve: inverses of the 128-wide diagonal blocks (slot s:
+  // jb rows of round_up(jb, 4) floats at fs_dinv_off[s]) and the phases of the
+  // two sweeps, each a range of ps_tasks separated by a grid barrier
+  std::vector<Task> fs_inv;                  // (front, first column, slot)
+  std::vector<int64_t> fs_dinv_off;
   int64_t fs_dinv_entries = 0;
+  std::vector<Task> ps_tasks;
+  std::vector<SolvePhase> ps_phases;         // forward phases, then backward ones
+  int32_t ps_fwd_phases = 0;
+  int32_t ps_max_tasks = 0;                  // largest phase
+  int64_t ps_part_entries = 0;               // partial sums of the backward row phases (floats)
   // K entries in level-major order
   std::vector<int64_t> k_slot;   // element offset of L(i, j) in the factor storage
   std::vector<int64_t> k_poff;   // products [k_poff[q], k_poff[q+1])

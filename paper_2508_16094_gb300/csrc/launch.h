@@ -33,16 +33,18 @@ void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L,
 template <typename T, typename V>
 void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st);
 
-// Fused FP32 solve: inverses of the 128-wide diagonal blocks (after each FP32
-// factorisation), then x = L^{-T} L^{-1} a with b as the forward result and t
-// the update vectors (all fixed buffers, so the launch sequence can be captured
-// in a CUDA graph). Returns the number of kernels launched.
+// Persistent FP32 solve: inverses of the 128-wide diagonal blocks (after each
+// FP32 factorisation), then x = L^{-T} L^{-1} a in one cooperative launch, with
+// b the forward result and t the update vectors. fwd/bwd select the sweeps:
+// forward only maps a to b = L^{-1} a; backward only maps b to x = L^{-T} b
+// (b is overwritten). part: plan.ps_part_entries floats of scratch. bar:
+// kPsBarrierWords zeroed words of grid-barrier state; a barrier that waits too
+// long sets status[ST_SOLVE_TIMEOUT] and the launch returns.
+constexpr int kPsBarrierWords = 32 + 1024;
 void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Dinv, cudaStream_t st);
-// fwd/bwd select the sweeps: forward only maps a to b = L^{-1} a; backward only
-// maps b to x = L^{-T} b (b is overwritten).
-int launch_solve_fused(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv,
-                       float *a, float *b, float *x, float *t, cudaStream_t st, bool fwd = true,
-                       bool bwd = true);
+void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv, float *a,
+                   float *b, float *x, float *t, float *part, unsigned *bar, int32_t *status, bool fwd,
+                   bool bwd, cudaStream_t st);
 
 // Sampled entries of L (final numbering).
 template <typename T>
