@@ -41,6 +41,7 @@ struct ipm_ctx {
          *vt = nullptr, *vjd = nullptr, *vjx = nullptr, *vtA = nullptr;
   double *dl_ = nullptr, *du_ = nullptr;
   double *jv_copy = nullptr, *D_copy = nullptr, *wv_copy = nullptr;  // inputs kept for refinement
+  float *Llo = nullptr;  // low parts of the split-TF32 factor
   float *dinv = nullptr, *fsa = nullptr, *fsb = nullptr, *fsx = nullptr;  // persistent FP32 solve
   unsigned *psbar = nullptr;  // its grid-barrier state
   float *pspart = nullptr;    // its partial sums
@@ -157,6 +158,7 @@ void layout(ipm_ctx *c, char *base) {
   d.rgemv = upload(cv, pl.rgemv_tasks, st);
   d.toff = upload(cv, pl.toff, st);
   d.fs_inv = upload(cv, pl.fs_inv, st);
+  d.fs_first_slot = upload(cv, pl.fs_first_slot, st);
   d.ps_tasks = upload(cv, pl.ps_tasks, st);
   d.ps_phases = upload(cv, pl.ps_phases, st);
   d.fs_dinv_off = upload(cv, pl.fs_dinv_off, st);
@@ -259,6 +261,10 @@ void layout(ipm_ctx *c, char *base) {
   c->sc = cv.take<IpmScalars>(1);
   c->status = cv.take<int32_t>(ST_COUNT);
   c->L = cv.take<char>((size_t)pl.l_entries * c->storage_bytes);
+  // low parts of the split-TF32 factor: the second half of an FP64-sized
+  // buffer, else their own array
+  c->Llo = c->storage_bytes == 8 ? (c->L ? reinterpret_cast<float *>(c->L) + pl.l_entries : nullptr)
+                                 : cv.take<float>((size_t)pl.l_entries);
   c->U = cv.take<char>((size_t)pl.u_entries * c->storage_bytes);
   c->ws_need = cv.off + 256;
 }
@@ -287,11 +293,11 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
                               true, c->st);
   } else {
     if (!c->tcp.ready()) throw Fail{IPM_ERR_UNSUPPORTED, "tensor-core factor not prepared"};
-    c->tcp.factor(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->status,
+    c->tcp.factor(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->dinv, c->status,
                   prec == IPM_TF32X3 ? 3 : 1, c->st);
   }
-  if (prec != IPM_FP64)  // explicit inverses of the diagonal blocks for the fused solve
-    launch_dinv(c->dp, c->plan, (const float *)c->L, c->dinv, c->st);
+  if (prec == IPM_FP32)  // explicit inverses of the diagonal blocks for the persistent solve
+    launch_dinv(c->dp, c->plan, (const float *)c->L, c->dinv, c->st);  // (the TF32 paths write them)
   CK(cudaGetLastError());
   int32_t out[ST_COUNT];
   CK(cudaMemcpyAsync(out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
@@ -718,7 +724,7 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     c->have_stale = false;
     if (c->lb_on) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
-      c->tcp.encode(c->plan, (float *)c->L, c->st);
+      c->tcp.encode(c->plan, (float *)c->L, c->Llo, c->st);
     } catch (const std::exception &e) {
       c->err = std::string("tensor-core path unavailable: ") + e.what();
     }

@@ -18,6 +18,7 @@ struct DevPlan {
   const Task *fs_inv, *ps_tasks;  // persistent FP32 solve
   const SolvePhase *ps_phases;
   const int64_t *fs_dinv_off;
+  const int32_t *fs_first_slot;  // per front: slot of its first diagonal block
   const int64_t *k_slot, *k_poff, *k_w, *k_orig;
   const int32_t *k_pa, *k_pb, *k_diag;
   const int32_t *perm;  // final new -> old

@@ -100,6 +100,7 @@ struct Plan {
   // jb rows of round_up(jb, 4) floats at fs_dinv_off[s]) and the phases of the
   // two sweeps, each a range of ps_tasks separated by a grid barrier
   std::vector<Task> fs_inv;                  // (front, first column, slot)
+  std::vector<int32_t> fs_first_slot;        // per front: slot of block 0 (consecutive after it)
   std::vector<int64_t> fs_dinv_off;
   int64_t fs_dinv_entries = 0;
   std::vector<Task> ps_tasks;

@@ -725,8 +725,10 @@ void build_fused_solve(Plan &pl) {
   pl.ps_tasks.clear();
   pl.ps_phases.clear();
   std::vector<std::vector<int32_t>> slot_of(pl.fronts.size());
+  pl.fs_first_slot.assign(pl.fronts.size(), 0);
   for (size_t s = 0; s < pl.fronts.size(); s++) {
     const FrontInfo &F = pl.fronts[s];
+    pl.fs_first_slot[s] = (int32_t)pl.fs_dinv_off.size();
     for (int32_t j = 0; j < F.ncol; j += B) {
       const int32_t jb = std::min(B, F.ncol - j);
       const int32_t slot = (int32_t)pl.fs_dinv_off.size();

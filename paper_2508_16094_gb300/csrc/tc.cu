@@ -13,6 +13,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <stdexcept>
 #include <string>
 
@@ -23,15 +24,19 @@ namespace gipm {
 
 namespace {
 
-constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kStages = 4;
-constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per operand tile
+constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kSyrkN = 256;
+constexpr int kSuper = 512;  // columns per super-step of the left-looking panel updates
+constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per 128-row operand tile
 constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
-template <int SPLIT> struct StagesOf { static constexpr int value = SPLIT == 3 ? 3 : kStages; };
-template <int SPLIT>
-constexpr int smem_bytes() {
-  return (SPLIT == 3 ? 4 : 2) * StagesOf<SPLIT>::value * kTileBytes + 1024 /*barriers*/ +
-         1024 /*alignment*/;
-}
+// Ring depth: as many stages as fit in ~200 KB (each stage: A and B tiles, and
+// their low parts when SPLIT == 3). BN = 256 tiles (SYRK) halve the operand
+// bytes per product of the B side.
+template <int SPLIT, int BN> struct Cfg {
+  static constexpr int kB = BN / 128;                            // 128-row B tiles per stage
+  static constexpr int kStage = (SPLIT == 3 ? 2 : 1) * (1 + kB) * kTileBytes;
+  static constexpr int S = (200 * 1024) / kStage > 4 ? 4 : (200 * 1024) / kStage;
+  static constexpr int smem = S * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -106,8 +111,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 
 // Instruction descriptor of tcgen05.mma kind::tf32: FP32 accumulator, TF32 A
 // and B, both K-major, N = 128, M = 128.
+template <int BN>
 __host__ __device__ constexpr uint32_t tf32_idesc() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
          ((uint32_t)(kTileM >> 4) << 24);
 }
 
@@ -154,64 +160,92 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 //    with its inverse): C = panel[a:a+128, k:k+kb] = A B^T with A = the same
 //    panel rows and columns, B = L_kk^{-1} from scratch slot `slot`, K = kb.
 //    The tile's rows are read completely before its epilogue overwrites them.
-template <int SPLIT>
+//
+// SPLIT == 3: modes 0 and 1 read finished panel entries, whose low parts the
+// mode-2 epilogue stored in Llo: all four tiles (A, A_lo, B, B_lo) arrive by
+// TMA. Mode 2 reads entries that are still being updated and the inverse, so
+// warps 2-5 form their low parts in shared memory.
+// Geometry of one task (see the task encoding above).
+struct Geo {
+  int mode, arow, brow, K, M, N, ax0, bx0, nk;
+  float *C;
+  int64_t ldc;
+  const CUtensorMap *amap, *bmap, *lomap;
+};
+
+template <int BN>
+__device__ __forceinline__ Geo task_geo(const DevPlan &dp, const Task &tk, const CUtensorMap *maps,
+                                        const CUtensorMap *maps_lo, const CUtensorMap *inv_map,
+                                        float *L, float *U, int nb) {
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow;
+  Geo g;
+  g.mode = tk.c & 3;
+  g.amap = maps + tk.front;
+  g.bmap = g.amap;
+  g.lomap = maps_lo + tk.front;
+  g.ax0 = g.bx0 = 0;
+  if (g.mode == 0) {  // K range [kbeg, kend) of the update of block column k
+    const int k = tk.b, kbeg = ((tk.c >> 2) & 0x7FFF) * kTileN, kend = ((tk.c >> 17) & 0x7FFF) * kTileN;
+    g.arow = tk.a;
+    g.brow = k;
+    g.ax0 = g.bx0 = kbeg;
+    g.K = kend - kbeg;
+    g.M = min(kTileM, nf - tk.a);
+    g.N = min(nb, F.ncol - k);
+    g.C = L + F.loff + (int64_t)tk.a * F.ld + k;
+    g.ldc = F.ld;
+  } else if (g.mode == 2) {
+    const int k = tk.b;
+    g.arow = tk.a;
+    g.ax0 = k;
+    g.brow = (tk.c >> 2) * kTileN;
+    g.bmap = inv_map;
+    g.N = min(nb, F.ncol - k);
+    g.K = g.N;
+    g.M = min(kTileM, nf - tk.a);
+    g.C = L + F.loff + (int64_t)tk.a * F.ld + k;
+    g.ldc = F.ld;
+  } else {
+    g.arow = F.ncol + tk.a;
+    g.brow = F.ncol + tk.b;
+    g.K = F.ncol;
+    g.M = min(kTileM, F.nrow - tk.a);
+    g.N = min(BN, F.nrow - tk.b);
+    g.C = U + F.uoff + (int64_t)tk.a * F.uld + tk.b;
+    g.ldc = F.uld;
+  }
+  g.nk = (g.K + kTileK - 1) / kTileK;
+  return g;
+}
+
+// Persistent: each CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ...
+// The k-steps of all its tasks flow through one ring of shared-memory stages;
+// two accumulators in tensor memory let the epilogue of one tile overlap the
+// main loop of the next.
+template <int SPLIT, int BN>
 __global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, const CUtensorMap *__restrict__ maps,
+    tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, int ntask,
+                   const CUtensorMap *__restrict__ maps, const CUtensorMap *__restrict__ maps_lo,
                    const CUtensorMap *__restrict__ inv_map, float *__restrict__ L,
-                   float *__restrict__ U, int nb, int32_t *status) {
+                   float *__restrict__ Llo, float *__restrict__ U, int nb, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  constexpr int S = StagesOf<SPLIT>::value;
-  uint8_t *sA = base;
-  uint8_t *sB = base + S * kTileBytes;
-  uint8_t *sAl = base + 2 * S * kTileBytes;  // low parts (SPLIT == 3 only)
-  uint8_t *sBl = base + 3 * S * kTileBytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + (SPLIT == 3 ? 4 : 2) * S * kTileBytes);
+  using CF = Cfg<SPLIT, BN>;
+  constexpr int S = CF::S, kBB = CF::kB * kTileBytes;  // bytes of a B tile
+  uint8_t *sA = base;                          // S x A tiles
+  uint8_t *sB = sA + S * kTileBytes;           // S x B tiles
+  uint8_t *sAl = sB + S * kBB;                 // low parts (SPLIT == 3 only)
+  uint8_t *sBl = sAl + (SPLIT == 3 ? S * kTileBytes : 0);
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + S * CF::kStage);
   uint64_t *empty = full + S;
   uint64_t *lofull = empty + S;
-  uint64_t *accum = lofull + S;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+  uint64_t *accfull = lofull + S;   // [2] accumulator ready for the epilogue
+  uint64_t *accempty = accfull + 2; // [2] accumulator free for the next tile
+  uint64_t *drain = accempty + 2;   // all products issued by this CTA complete
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-
-  const Task tk = tasks[blockIdx.x];
-  const FrontInfo F = dp.fronts[tk.front];
-  const int nf = F.ncol + F.nrow;
-  const int mode = tk.c & 3;
-  int arow, brow, K, M, N, ax0 = 0;
-  float *C;
-  int64_t ldc;
-  const CUtensorMap *amap = maps + tk.front, *bmap = amap;
-  if (mode == 0) {
-    const int k = tk.b;
-    arow = tk.a;
-    brow = k;
-    K = k;
-    M = min(kTileM, nf - tk.a);
-    N = min(nb, F.ncol - k);
-    C = L + F.loff + (int64_t)tk.a * F.ld + k;
-    ldc = F.ld;
-  } else if (mode == 2) {
-    const int k = tk.b;
-    arow = tk.a;
-    ax0 = k;
-    brow = (tk.c >> 2) * kTileN;
-    bmap = inv_map;
-    N = min(nb, F.ncol - k);
-    K = N;
-    M = min(kTileM, nf - tk.a);
-    C = L + F.loff + (int64_t)tk.a * F.ld + k;
-    ldc = F.ld;
-  } else {
-    arow = F.ncol + tk.a;
-    brow = F.ncol + tk.b;
-    K = F.ncol;
-    M = min(kTileM, F.nrow - tk.a);
-    N = min(kTileN, F.nrow - tk.b);
-    C = U + F.uoff + (int64_t)tk.a * F.uld + tk.b;
-    ldc = F.uld;
-  }
-  const int nk = (K + kTileK - 1) / kTileK;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   if (threadIdx.x == 0) {
@@ -220,7 +254,11 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&empty[s], 1);
       mbar_init(&lofull[s], 4);  // one arrival per converting warp
     }
-    mbar_init(accum, 1);
+    for (int a = 0; a < 2; a++) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -228,7 +266,7 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(kTileN));
+                 "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -237,76 +275,117 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
-      for (int kt = 0; kt < nk; kt++) {
-        const int s = kt % S, round = kt / S;
-        if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
-        mbar_arrive_expect_tx(&full[s], 2 * kTileBytes);
-        tma_load_2d(sA + s * kTileBytes, amap, &full[s], ax0 + kt * kTileK, arow);
-        tma_load_2d(sB + s * kTileBytes, bmap, &full[s], kt * kTileK, brow);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = tf32_idesc();
-      for (int kt = 0; kt < nk; kt++) {
-        const int s = kt % S, round = kt / S;
-        if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
-        if (SPLIT == 3 && !mbar_wait(&lofull[s], round & 1, status)) { *abort_flag = 1; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ad = sw128_desc(smem_u32(sA + s * kTileBytes));
-        const uint64_t bd = sw128_desc(smem_u32(sB + s * kTileBytes));
-        const uint64_t ald = sw128_desc(smem_u32(sAl + s * kTileBytes));
-        const uint64_t bld = sw128_desc(smem_u32(sBl + s * kTileBytes));
-#pragma unroll
-        for (int k4 = 0; k4 < kTileK / 8; k4++) {  // 8 TF32 = 32 bytes per MMA along K
-          if (SPLIT == 3) {  // small terms first: A_lo B + A B_lo, then A B
-            mma_tf32(tmem, ald + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
-            mma_tf32(tmem, ad + 2 * k4, bld + 2 * k4, idesc, 1);
-            mma_tf32(tmem, ad + 2 * k4, bd + 2 * k4, idesc, 1);
-          } else {
-            mma_tf32(tmem, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+    if (lane == 0) {  // TMA producer
+      uint32_t g = 0;
+      for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x) {
+        const Geo G = task_geo<BN>(dp, tasks[t], maps, maps_lo, inv_map, L, U, nb);
+        const bool pre = SPLIT == 3 && G.mode != 2;  // low parts loaded with the tiles
+        for (int kt = 0; kt < G.nk; kt++, g++) {
+          const int s = g % S;
+          const uint32_t round = g / S;
+          if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
+          mbar_arrive_expect_tx(&full[s], (pre ? 2 : 1) * (kTileBytes + kBB));
+          tma_load_2d(sA + s * kTileBytes, G.amap, &full[s], G.ax0 + kt * kTileK, G.arow);
+          for (int h = 0; h < CF::kB; h++)  // a 256-row B tile is two 128-row boxes
+            tma_load_2d(sB + s * kBB + h * kTileBytes, G.bmap, &full[s], G.bx0 + kt * kTileK,
+                        G.brow + 128 * h);
+          if (pre) {
+            tma_load_2d(sAl + s * kTileBytes, G.lomap, &full[s], G.ax0 + kt * kTileK, G.arow);
+            for (int h = 0; h < CF::kB; h++)
+              tma_load_2d(sBl + s * kBB + h * kTileBytes, G.lomap, &full[s], G.bx0 + kt * kTileK,
+                          G.brow + 128 * h);
           }
         }
-        mma_commit(&empty[s]);
       }
-      mma_commit(accum);
+      if (*abort_flag)  // let the copies already issued land before the CTA exits
+        for (uint32_t q = g > (uint32_t)S ? g - S : 0; q < g; q++)
+          mbar_wait(&full[q % S], (q / S) & 1, status);
     }
-  } else {
-    if (SPLIT == 3) {
-      // low parts x - tf32(x) of both operand tiles (tf32 keeps the top 19 bits)
-      const int t = threadIdx.x - 64;
-      for (int kt = 0; kt < nk && !*abort_flag; kt++) {
-        const int s = kt % S, round = kt / S;
-        if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
-        const float4 *a = reinterpret_cast<const float4 *>(sA + s * kTileBytes);
-        const float4 *b = reinterpret_cast<const float4 *>(sB + s * kTileBytes);
-        float4 *al = reinterpret_cast<float4 *>(sAl + s * kTileBytes);
-        float4 *bl = reinterpret_cast<float4 *>(sBl + s * kTileBytes);
-        for (int i = t; i < kTileBytes / 16; i += 128) {
-          al[i] = lo_part(a[i]);
-          bl[i] = lo_part(b[i]);
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = tf32_idesc<BN>();
+      uint32_t g = 0;
+      int i = 0;
+      for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
+        const Geo G = task_geo<BN>(dp, tasks[t], maps, maps_lo, inv_map, L, U, nb);
+        const bool conv = SPLIT == 3 && G.mode == 2;
+        const int a = i & 1;
+        if (!mbar_wait(&accempty[a], ((i >> 1) & 1) ^ 1, status)) { *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        for (int kt = 0; kt < G.nk; kt++, g++) {
+          const int s = g % S;
+          const uint32_t round = g / S;
+          if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
+          if (conv && !mbar_wait(&lofull[s], round & 1, status)) { *abort_flag = 1; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ad = sw128_desc(smem_u32(sA + s * kTileBytes));
+          const uint64_t bd = sw128_desc(smem_u32(sB + s * kBB));
+          const uint64_t ald = sw128_desc(smem_u32(sAl + s * kTileBytes));
+          const uint64_t bld = sw128_desc(smem_u32(sBl + s * kBB));
+#pragma unroll
+          for (int k4 = 0; k4 < kTileK / 8; k4++) {  // 8 TF32 = 32 bytes per MMA along K
+            if (SPLIT == 3) {  // small terms first: A_lo B + A B_lo, then A B
+              mma_tf32(acc, ald + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+              mma_tf32(acc, ad + 2 * k4, bld + 2 * k4, idesc, 1);
+              mma_tf32(acc, ad + 2 * k4, bd + 2 * k4, idesc, 1);
+            } else {
+              mma_tf32(acc, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+            }
+          }
+          mma_commit(&empty[s]);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&lofull[s]);
+        if (*abort_flag) break;
+        mma_commit(&accfull[a]);
       }
+      mma_commit(drain);  // tensor memory is released only after every product landed
+      mbar_wait(drain, 0, status);
     }
-    const bool ok = mbar_wait(accum, 0, status);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  } else {  // warps 2-5: low parts (mode 2) and the epilogue
     const int q = warp % 4;  // tensor-memory lane quarter this warp may access
     const int row = q * 32 + lane;
-    if (ok && !*abort_flag) {
-      for (int cb = 0; cb < (N + 31) / 32; cb++) {
+    uint32_t g = 0;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
+      const Geo G = task_geo<BN>(dp, tasks[t], maps, maps_lo, inv_map, L, U, nb);
+      if (SPLIT == 3 && G.mode == 2) {
+        // low parts x - tf32(x) of both operand tiles (tf32 keeps the top 19 bits)
+        const int tt = threadIdx.x - 64;
+        for (int kt = 0; kt < G.nk; kt++, g++) {
+          const int s = g % S;
+          const uint32_t round = g / S;
+          if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; break; }
+          const float4 *av = reinterpret_cast<const float4 *>(sA + s * kTileBytes);
+          const float4 *bv = reinterpret_cast<const float4 *>(sB + s * kBB);
+          float4 *al = reinterpret_cast<float4 *>(sAl + s * kTileBytes);
+          float4 *bl = reinterpret_cast<float4 *>(sBl + s * kBB);
+          for (int e = tt; e < kTileBytes / 16; e += 128) al[e] = lo_part(av[e]);
+          for (int e = tt; e < kBB / 16; e += 128) bl[e] = lo_part(bv[e]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&lofull[s]);
+        }
+        if (*abort_flag) break;
+      } else {
+        g += G.nk;
+      }
+      const int a = i & 1;
+      if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int cb = 0; cb < (G.N + 31) / 32; cb++) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), v);
-        if (row < M) {
-          float *crow = C + (int64_t)row * ldc + cb * 32;
-          const int nc = min(32, N - cb * 32);
-          if (mode == 2) {
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
+        if (row < G.M) {
+          float *crow = G.C + (int64_t)row * G.ldc + cb * 32;
+          const int nc = min(32, G.N - cb * 32);
+          if (G.mode == 2) {
+            float *lrow = Llo + (crow - L);
 #pragma unroll
             for (int c = 0; c < 32; c++)
-              if (c < nc) crow[c] = v[c];
+              if (c < nc) {
+                crow[c] = v[c];
+                if (SPLIT == 3) lrow[c] = lo1(v[c]);
+              }
           } else {
 #pragma unroll
             for (int c = 0; c < 32; c++)
@@ -314,78 +393,225 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[a]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTileN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
 }
 
 // Cholesky of one diagonal block (kb <= 128) in FP32 and the explicit inverse
 // of its factor, written row-major (128 x 128, zero outside the lower kb x kb
 // triangle) to scratch slot `b` for the triangular solve of the rows below as
-// a tensor-core product. Division-free 2D thread mapping for the trailing
-// update; a non-positive pivot is replaced by a large value (static pivoting)
-// and counted.
+// a tensor-core product, and (when Dinv is given) in the layout of the
+// persistent solve. Both are blocked in 32-column panels: warp 0 factors the
+// 32 x 32 diagonal block, one thread per row solves the rows below it, all
+// threads update the trailing block; the inverse takes the four 32 x 32
+// diagonal blocks in four warps, then the off-diagonal blocks by their
+// distance from the diagonal (X_ij = -X_ii sum_k L_ik X_kj). A non-positive
+// pivot is replaced by a large value (static pivoting) and counted.
+constexpr int kLS = 129;  // padded row of the shared-memory blocks
 __global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *__restrict__ tasks,
                                                         float *__restrict__ L,
                                                         float *__restrict__ Linv,
-                                                        int32_t *status) {
-  constexpr int LS = 129;
+                                                        float *__restrict__ Dinv, int32_t *status) {
   const Task tk = tasks[blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
   const int k = tk.a, slot = tk.b, kb = min(TcPlan::kNb, F.ncol - k);
   extern __shared__ float smf[];
-  float *A = smf;            // [128][129]
-  float *X = smf + 128 * LS;  // [128][129]
+  float *A = smf;                  // [128][129] factor
+  float *X = A + 128 * kLS;        // [128][129] inverse
+  float *T = X + 128 * kLS;        // [3][32][33] products of the off-diagonal step
+  float *rd = T + 3 * 32 * 33;     // [128] reciprocals of the diagonal of the factor
+  float *col = rd + 128;           // [32] column broadcast of the diagonal-block step
   float *g = L + F.loff + (int64_t)k * F.ld + k;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   for (int e = tid; e < 128 * 128; e += 256) {
     const int r = e >> 7, c = e & 127;
-    A[r * LS + c] = (r < kb && c <= r) ? g[(int64_t)r * F.ld + c] : 0.f;
+    A[r * kLS + c] = (r < kb && c <= r) ? g[(int64_t)r * F.ld + c] : 0.f;
+    X[r * kLS + c] = 0.f;
   }
   __syncthreads();
-  for (int j = 0; j < kb; j++) {
-    if (tid == 0) {
-      float d = A[j * LS + j];
-      if (!(d > 0.f) || !(d < 3.0e38f)) {
-        d = 1e30f;
-        atomicAdd(&status[ST_PERTURBED], 1);
+  for (int c0 = 0; c0 < kb; c0 += 32) {
+    const int pb = min(32, kb - c0);
+    if (warp == 0) {  // 32 x 32 diagonal block: lane i holds row i in registers;
+                      // each column is broadcast through shared memory (right-looking)
+      float rw[32];
+      const int i = c0 + lane;
+#pragma unroll
+      for (int m = 0; m < 32; m++) rw[m] = (lane < pb && m <= lane) ? A[i * kLS + c0 + m] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; j++) {
+        if (j < pb) {
+          if (lane == j) {
+            float d = rw[j];
+            if (!(d > 0.f) || !(d < 3.0e38f)) {
+              d = 1e30f;
+              atomicAdd(&status[ST_PERTURBED], 1);
+            }
+            rw[j] = sqrtf(d);
+            rd[c0 + j] = 1.f / rw[j];
+          }
+          __syncwarp();
+          if (lane > j) rw[j] *= rd[c0 + j];
+          col[lane] = rw[j];  // L[c0 + lane][c0 + j] (0 above the diagonal)
+          __syncwarp();
+#pragma unroll
+          for (int m = j + 1; m < 32; m++)
+            if (lane >= m) rw[m] = fmaf(-rw[j], col[m], rw[m]);
+          __syncwarp();
+        }
       }
-      A[j * LS + j] = sqrtf(d);
+#pragma unroll
+      for (int m = 0; m < 32; m++)
+        if (lane < pb && m <= lane) A[i * kLS + c0 + m] = rw[m];
     }
     __syncthreads();
-    const float ljj = A[j * LS + j];
-    if (tid > j && tid < kb) A[tid * LS + j] /= ljj;
+    {  // rows below the diagonal block: x L11^T = a, one thread per row, the
+       // row held in registers and updated column by column (independent FMAs)
+      const int r = c0 + pb + tid;
+      if (r < kb) {
+        float *ar = A + r * kLS + c0;
+        float x[32];
+#pragma unroll
+        for (int m = 0; m < 32; m++) x[m] = m < pb ? ar[m] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          if (j < pb) {
+            x[j] *= rd[c0 + j];
+#pragma unroll
+            for (int m = j + 1; m < 32; m++)
+              if (m < pb) x[m] = fmaf(-x[j], A[(c0 + m) * kLS + c0 + j], x[m]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < 32; m++)
+          if (m < pb) ar[m] = x[m];
+      }
+    }
     __syncthreads();
-    for (int r = j + 1 + ty; r < kb; r += 16) {
-      const float arj = A[r * LS + j];
-      for (int c = j + 1 + tx; c <= r; c += 16) A[r * LS + c] = fmaf(-arj, A[c * LS + j], A[r * LS + c]);
+    // trailing block [t0, kb)^2, lower part: thread (ty, tx) owns rows
+    // t0 + ty + 16a and columns t0 + tx + 16b (6 x 6 independent sums)
+    const int t0 = c0 + pb;
+    if (t0 < kb) {
+      const int ty = tid / 16, tx = tid % 16;
+      float acc[6][6];
+#pragma unroll
+      for (int a2 = 0; a2 < 6; a2++)
+#pragma unroll
+        for (int b2 = 0; b2 < 6; b2++) acc[a2][b2] = 0.f;
+#pragma unroll 4
+      for (int m = 0; m < pb; m++) {
+        float ra[6], cb[6];
+#pragma unroll
+        for (int a2 = 0; a2 < 6; a2++) {
+          const int r = min(t0 + ty + 16 * a2, 127), c = min(t0 + tx + 16 * a2, 127);
+          ra[a2] = A[r * kLS + c0 + m];
+          cb[a2] = A[c * kLS + c0 + m];
+        }
+#pragma unroll
+        for (int a2 = 0; a2 < 6; a2++)
+#pragma unroll
+          for (int b2 = 0; b2 < 6; b2++) acc[a2][b2] = fmaf(ra[a2], cb[b2], acc[a2][b2]);
+      }
+#pragma unroll
+      for (int a2 = 0; a2 < 6; a2++)
+#pragma unroll
+        for (int b2 = 0; b2 < 6; b2++) {
+          const int r = t0 + ty + 16 * a2, c = t0 + tx + 16 * b2;
+          if (r < kb && c <= r) A[r * kLS + c] -= acc[a2][b2];
+        }
     }
     __syncthreads();
   }
   for (int e = tid; e < kb * kb; e += 256) {
     const int r = e / kb, c = e % kb;
-    if (c <= r) g[(int64_t)r * F.ld + c] = A[r * LS + c];
+    if (c <= r) g[(int64_t)r * F.ld + c] = A[r * kLS + c];
   }
-  if (tid < 128) {  // column c of the inverse by forward substitution
-    const int c = tid;
-    for (int i = 0; i < 128; i++) X[i * LS + c] = 0.f;
-    if (c < kb)
-      for (int i = c; i < kb; i++) {
-        float s = (i == c) ? 1.f : 0.f;
-        for (int m = c; m < i; m++) s = fmaf(-A[i * LS + m], X[m * LS + c], s);
-        X[i * LS + c] = s / A[i * LS + i];
+  // inverse: diagonal 32 x 32 blocks, one warp each, lane = column (held in
+  // registers, updated row by row with independent FMAs)
+  if (warp < 4) {
+    const int b0 = 32 * warp, bb = min(32, kb - b0);
+    if (lane < bb) {
+      const int c = b0 + lane;
+      float x[32];
+#pragma unroll
+      for (int r = 0; r < 32; r++) x[r] = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int r = 0; r < 32; r++) {
+        if (r < bb && r >= lane) {
+          x[r] *= rd[b0 + r];
+#pragma unroll
+          for (int m = r + 1; m < 32; m++)
+            if (m < bb) x[m] = fmaf(-A[(b0 + m) * kLS + b0 + r], x[r], x[m]);
+        }
       }
+#pragma unroll
+      for (int r = 0; r < 32; r++)
+        if (r < bb && r >= lane) X[(b0 + r) * kLS + c] = x[r];
+    }
   }
   __syncthreads();
+  // off-diagonal blocks (i, j), i = j + d: T = sum_{m in blocks j..i-1} L[R][m] X[m][C],
+  // then X[R][C] = -sum_{m in block i, m <= R} X[R][m] T[m][C]; each thread
+  // takes four consecutive columns C
+  for (int d = 1; d < 4; d++) {
+    const int np = 4 - d;
+    for (int e = tid; e < np * 256; e += 256) {
+      const int j = e / 256, i = j + d, rr = (e % 256) / 8, cq = e % 8;
+      const int R = 32 * i + rr, C = 32 * j + 4 * cq;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      if (R < kb)
+#pragma unroll 4
+        for (int m = 32 * j; m < 32 * i; m++) {
+          const float a = A[R * kLS + m];
+          const float *xm = X + m * kLS + C;
+          s0 = fmaf(a, xm[0], s0);
+          s1 = fmaf(a, xm[1], s1);
+          s2 = fmaf(a, xm[2], s2);
+          s3 = fmaf(a, xm[3], s3);
+        }
+      float *t = T + (j * 32 + rr) * 33 + 4 * cq;
+      t[0] = s0; t[1] = s1; t[2] = s2; t[3] = s3;
+    }
+    __syncthreads();
+    for (int e = tid; e < np * 256; e += 256) {
+      const int j = e / 256, i = j + d, rr = (e % 256) / 8, cq = e % 8;
+      const int R = 32 * i + rr, C = 32 * j + 4 * cq;
+      if (R < kb) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+        for (int mm = 0; mm <= rr; mm++) {
+          const float xv = X[R * kLS + 32 * i + mm];
+          const float *t = T + (j * 32 + mm) * 33 + 4 * cq;
+          s0 = fmaf(xv, t[0], s0);
+          s1 = fmaf(xv, t[1], s1);
+          s2 = fmaf(xv, t[2], s2);
+          s3 = fmaf(xv, t[3], s3);
+        }
+        float *xr = X + R * kLS + C;
+        xr[0] = -s0; xr[1] = -s1; xr[2] = -s2; xr[3] = -s3;
+      }
+    }
+    __syncthreads();
+  }
   float *out = Linv + (int64_t)slot * 128 * 128;
-  for (int e = tid; e < 128 * 128; e += 256) out[e] = X[(e >> 7) * LS + (e & 127)];
+  for (int e = tid; e < 128 * 128; e += 256) out[e] = X[(e >> 7) * kLS + (e & 127)];
+  if (Dinv) {  // persistent-solve copy: kb rows of round_up(kb, 4) floats
+    const int ldi = (kb + 3) & ~3;
+    float *o2 = Dinv + dp.fs_dinv_off[dp.fs_first_slot[tk.front] + k / TcPlan::kNb];
+    for (int e = tid; e < kb * ldi; e += 256) {
+      const int r = e / ldi, c = e % ldi;
+      o2[e] = (c <= r && c < kb) ? X[r * kLS + c] : 0.f;
+    }
+  }
 }
 
-constexpr int kPotrfInvSmem = 2 * 128 * 129 * 4;
+constexpr int kPotrfInvSmem = (2 * 128 * kLS + 3 * 32 * 33 + 128 + 32) * 4;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -414,14 +640,34 @@ void TcPlan::build(const Plan &plan) {
   for (size_t li = 0; li < plan.levels.size(); li++) {
     const LevelPlan &LP = plan.levels[li];
     Level &lv = levels_[li];
+    // Left-looking in super-steps of kSuper columns: one launch updates all
+    // block columns of a super-step with the columns before it (many tiles, the
+    // long K), then each 128-wide block column takes the columns of its own
+    // super-step before it (short K), is factored and solved below.
+    auto enc = [](int32_t kbeg, int32_t kend) { return 0 | (kbeg / kNb) << 2 | (kend / kNb) << 17; };
     for (int32_t k = 0; k < LP.max_ncol; k += kNb) {
+      const int32_t K0 = k - k % kSuper;
+      if (k == K0 && K0 > 0) {
+        Step out{};
+        out.gemm_b = (int)gemm_.size();
+        for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+          const int32_t s = plan.level_fronts[t];
+          const FrontInfo &F = plan.fronts[s];
+          for (int32_t c = K0; c < std::min(F.ncol, K0 + kSuper); c += kNb)
+            for (int32_t i0 = c; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, c, enc(0, K0)});
+        }
+        out.gemm_e = (int)gemm_.size();
+        out.potrf_b = out.potrf_e = (int)potrf_.size();
+        out.trsm_b = out.trsm_e = (int)trsm_.size();
+        if (out.gemm_e > out.gemm_b) lv.steps.push_back(out);
+      }
       Step st{};
       st.gemm_b = (int)gemm_.size();
-      for (int32_t t = LP.front_b; t < LP.front_e && k > 0; t++) {
+      for (int32_t t = LP.front_b; t < LP.front_e && k > K0; t++) {
         const int32_t s = plan.level_fronts[t];
         const FrontInfo &F = plan.fronts[s];
         if (F.ncol <= k) continue;
-        for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, k, 0});
+        for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, k, enc(K0, k)});
       }
       st.gemm_e = (int)gemm_.size();
       st.potrf_b = (int)potrf_.size();
@@ -449,8 +695,8 @@ void TcPlan::build(const Plan &plan) {
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = plan.level_fronts[t];
       const FrontInfo &F = plan.fronts[s];
-      for (int32_t i0 = 0; i0 < F.nrow; i0 += kTileM)
-        for (int32_t j0 = 0; j0 <= i0; j0 += kTileN) syrk_.push_back({s, i0, j0, 1});
+      for (int32_t i0 = 0; i0 < F.nrow; i0 += kTileM)  // 128 x 256 tiles touching the lower triangle
+        for (int32_t j0 = 0; j0 <= i0; j0 += kSyrkN) syrk_.push_back({s, i0, j0, 1});
     }
     lv.syrk_e = (int)syrk_.size();
   }
@@ -458,7 +704,10 @@ void TcPlan::build(const Plan &plan) {
   auto fail = [](const char *w) { throw std::runtime_error(std::string("tc plan check: ") + w); };
   for (const Task &t : gemm_) {
     const FrontInfo &F = plan.fronts[t.front];
-    if (!(t.b > 0 && t.b < F.ncol && t.a >= t.b && t.a < F.ncol + F.nrow && t.c == 0)) fail("gemm");
+    const int32_t kbeg = ((t.c >> 2) & 0x7FFF) * kNb, kend = ((t.c >> 17) & 0x7FFF) * kNb;
+    if (!(t.b > 0 && t.b < F.ncol && t.b % kNb == 0 && t.a >= t.b && t.a < F.ncol + F.nrow &&
+          (t.c & 3) == 0 && kbeg >= 0 && kbeg < kend && kend <= t.b))
+      fail("gemm");
   }
   for (const Task &t : syrk_) {
     const FrontInfo &F = plan.fronts[t.front];
@@ -487,26 +736,29 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_potrf_ = up(potrf_);
   d_trsm_ = up(trsm_);
   d_syrk_ = up(syrk_);
-  d_maps_ = cv.take<CUtensorMap>(std::max(nfronts_, 1) + 1);  // + the inverse-scratch map
+  d_maps_ = cv.take<CUtensorMap>(2 * std::max(nfronts_, 1) + 1);  // L, Llo, the inverse scratch
   d_inv_ = cv.take<float>((size_t)max_slots_ * kTileM * kTileN);
   ready_ = false;
 }
 
-void TcPlan::encode(const Plan &plan, float *L, cudaStream_t st) {
+void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  std::vector<CUtensorMap> maps(plan.fronts.size());
-  for (size_t s = 0; s < plan.fronts.size(); s++) {
-    const FrontInfo &F = plan.fronts[s];
+  L_ = L;
+  Llo_ = Llo;
+  const size_t nfr = plan.fronts.size();
+  std::vector<CUtensorMap> maps(2 * nfr);  // panels of L, then of Llo
+  for (size_t s = 0; s < 2 * nfr; s++) {
+    const FrontInfo &F = plan.fronts[s % nfr];
+    float *base = (s < nfr ? L : Llo) + F.loff;
     cuuint64_t dims[2] = {(cuuint64_t)F.ncol, (cuuint64_t)(F.ncol + F.nrow)};
     cuuint64_t strides[1] = {(cuuint64_t)F.ld * sizeof(float)};
     cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)kTileM};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(L + F.loff), dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
-      throw std::runtime_error("cuTensorMapEncodeTiled failed for front " + std::to_string(s));
+      throw std::runtime_error("cuTensorMapEncodeTiled failed for front " + std::to_string(s % nfr));
   }
   {
     CUtensorMap im;
@@ -525,39 +777,57 @@ void TcPlan::encode(const Plan &plan, float *L, cudaStream_t st) {
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
       throw std::runtime_error("tensor map upload failed");
   if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("tensor map upload failed");
-  cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
-  cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<3>());
+  cudaFuncSetAttribute(tc_gemm_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, 128>::smem);
+  cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, 128>::smem);
+  cudaFuncSetAttribute(tc_gemm_kernel<1, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
+  cudaFuncSetAttribute(tc_gemm_kernel<3, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
   cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfInvSmem);
   ready_ = true;
 }
 
-template <int SPLIT>
+template <int SPLIT, int BN>
 static void gemm_launch(int ntask, const DevPlan &dp, const Task *tasks, const CUtensorMap *maps,
-                        const CUtensorMap *inv_map, float *L, float *U, int32_t *status,
-                        cudaStream_t st) {
+                        const CUtensorMap *maps_lo, const CUtensorMap *inv_map, float *L,
+                        float *Llo, float *U, int32_t *status, cudaStream_t st) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
   note_launch();
-  tc_gemm_kernel<SPLIT><<<ntask, 192, smem_bytes<SPLIT>(), st>>>(dp, tasks, maps, inv_map, L, U,
-                                                                 TcPlan::kNb, status);
+  tc_gemm_kernel<SPLIT, BN><<<std::min(ntask, sms), 192, Cfg<SPLIT, BN>::smem, st>>>(
+      dp, tasks, ntask, maps, maps_lo, inv_map, L, Llo, U, TcPlan::kNb, status);
 }
 
 void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
-                    int32_t *status, int split, cudaStream_t st) {
-  auto gemm = split == 3 ? gemm_launch<3> : gemm_launch<1>;
+                    float *Dinv, int32_t *status, int split, cudaStream_t st) {
+  auto gemm3 = split == 3 ? gemm_launch<3, 128> : gemm_launch<1, 128>;
+  auto syrk3 = split == 3 ? gemm_launch<3, kSyrkN> : gemm_launch<1, kSyrkN>;
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
-  const CUtensorMap *inv_map = maps + nfronts_;
+  const CUtensorMap *maps_lo = maps + nfronts_;
+  const CUtensorMap *inv_map = maps + 2 * nfronts_;
+  if (L != L_) throw std::runtime_error("tensor maps were encoded for another factor buffer");
+  float *Llo = Llo_;
+  auto gemm = [&](int n, const DevPlan &d, const Task *t, const CUtensorMap *m, const CUtensorMap *im,
+                  float *l, float *u, int32_t *stt, cudaStream_t s) {
+    gemm3(n, d, t, m, maps_lo, im, l, Llo, u, stt, s);
+  };
   for (size_t li = 0; li < levels_.size(); li++) {
     launch_build_level<float>(dp, plan.levels[li], kval, L, U, st);
     for (const Step &s : levels_[li].steps) {
       if (s.gemm_e > s.gemm_b)
         gemm(s.gemm_e - s.gemm_b, dp, d_gemm_ + s.gemm_b, maps, inv_map, L, U, status, st);
       if (s.potrf_e > s.potrf_b)
-        { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, kPotrfInvSmem, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, status); }
+        { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, kPotrfInvSmem, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, Dinv, status); }
       if (s.trsm_e > s.trsm_b)
         gemm(s.trsm_e - s.trsm_b, dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, status, st);
     }
     const Level &lv = levels_[li];
     if (lv.syrk_e > lv.syrk_b)
-      gemm(lv.syrk_e - lv.syrk_b, dp, d_syrk_ + lv.syrk_b, maps, inv_map, L, U, status, st);
+      syrk3(lv.syrk_e - lv.syrk_b, dp, d_syrk_ + lv.syrk_b, maps, maps_lo, inv_map, L, Llo, U, status,
+            st);
   }
 }
 

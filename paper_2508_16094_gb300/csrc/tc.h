@@ -18,13 +18,16 @@ class TcPlan {
   void build(const Plan &plan);
   // Carve device memory for tasks and tensor maps (cv.base == nullptr: size only).
   void layout(Carve &cv, cudaStream_t st);
-  // Encode one TMA tensor map per front panel of the FP32 factor storage L.
-  void encode(const Plan &plan, float *L, cudaStream_t st);
+  // Encode one TMA tensor map per front panel of the FP32 factor storage L and
+  // of Llo (low parts x - tf32(x) of the finished entries, same layout).
+  void encode(const Plan &plan, float *L, float *Llo, cudaStream_t st);
   bool ready() const { return ready_; }
-  // split = 1: plain TF32 products; split = 3: A_lo B + A B_lo + A B with the
-  // low parts formed in shared memory (FP32-accurate products on tensor cores)
+  // split = 1: plain TF32 products; split = 3: A_lo B + A B_lo + A B
+  // (FP32-accurate products on tensor cores; L must be the encoded buffer)
+  // Dinv (may be null): also write the diagonal-block inverses in the layout of
+  // the persistent solve.
   void factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
-              int32_t *status, int split, cudaStream_t st);
+              float *Dinv, int32_t *status, int split, cudaStream_t st);
 
  private:
   struct Step { int gemm_b, gemm_e, potrf_b, potrf_e, trsm_b, trsm_e; };
@@ -34,7 +37,8 @@ class TcPlan {
   int nfronts_ = 0, max_slots_ = 1;
   float *d_inv_ = nullptr;  // inverses of the diagonal blocks of one step (max_slots_ x 128 x 128)
   Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_syrk_ = nullptr;
-  void *d_maps_ = nullptr;  // nfronts_ CUtensorMap (128 bytes each)
+  void *d_maps_ = nullptr;  // 2 nfronts_ + 1 CUtensorMap (128 bytes each)
+  float *L_ = nullptr, *Llo_ = nullptr;
   bool ready_ = false;
 };
 
