@@ -380,3 +380,86 @@ def mpc_instance_qp(A, B, Q, R, x0, u_max=1.0, x_max=5.0):
     wp = np.arange(n + 1, dtype=np.int64)
     wi = np.arange(n, dtype=np.int32)
     return lp, (wp, wi, wdiag)
+
+
+# ---------------------------------------------------------------------------
+# Grid NLP: min 1/2 ||u - u_t||^2 + alpha/2 ||v||^2  s.t.  -Lap u + c3 u^3 - v = 0
+# (as the pair of rows h >= 0, -h >= 0), v_lo <= v <= v_hi, on an N x N grid
+# of interior points (spacing 1/(N+1), u = 0 on the boundary).
+# ---------------------------------------------------------------------------
+@dataclass
+class GridNLP:
+    N: int
+    alpha: float
+    v_lo: float
+    v_hi: float
+    cubic: int           # 1: the u^3 term is present
+    v_bounded: int       # 1: v_lo <= v <= v_hi
+    ut: np.ndarray       # target, N*N, index ix + N*iy
+    rowptr: np.ndarray   # J pattern (2 N^2 rows, CSR, ascending columns)
+    col: np.ndarray
+    l: np.ndarray
+    u: np.ndarray
+    wp: np.ndarray       # W pattern: lower CSC, diagonal only
+    wi: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return 2 * self.N * self.N
+
+    @property
+    def m(self) -> int:
+        return 2 * self.N * self.N
+
+
+def grid_nlp_pattern(N: int):
+    """CSR pattern of the Jacobian of [h; -h]: row of grid point (ix, iy) holds
+    u at (iy-1), (ix-1), centre, (ix+1), (iy+1) (those inside the grid, in this
+    order = ascending index) and then v of the point; rows N^2.. repeat it."""
+    NN = N * N
+    rows = []
+    for idx in range(NN):
+        ix, iy = idx % N, idx // N
+        c = []
+        if iy > 0: c.append(idx - N)
+        if ix > 0: c.append(idx - 1)
+        c.append(idx)
+        if ix < N - 1: c.append(idx + 1)
+        if iy < N - 1: c.append(idx + N)
+        c.append(NN + idx)
+        rows.append(c)
+    rows = rows + rows
+    rowptr = np.zeros(len(rows) + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.asarray(r, np.int32) for r in rows])
+    return rowptr, col
+
+
+def grid_nlp(N: int = 512, seed: int = 5, alpha: float = 5e-3, v_lo: float = -1.0,
+             v_hi: float = 1.0, cubic: int = 1, v_bounded: int = 1) -> GridNLP:
+    """Target u_t = sin(pi x) sin(pi y) + N(0, 0.01) (standard deviation 0.1)
+    at x = (ix + 1) h, y = (iy + 1) h, h = 1 / (N + 1)."""
+    NN = N * N
+    h = 1.0 / (N + 1)
+    ix = np.arange(NN) % N
+    iy = np.arange(NN) // N
+    ut = np.sin(np.pi * (ix + 1) * h) * np.sin(np.pi * (iy + 1) * h) + normal(seed, NN, 0.0, 0.1)
+    rowptr, col = grid_nlp_pattern(N)
+    l = np.full(2 * NN, -np.inf)
+    u = np.full(2 * NN, np.inf)
+    if v_bounded:
+        l[NN:] = v_lo
+        u[NN:] = v_hi
+    wp = np.arange(2 * NN + 1, dtype=np.int64)
+    wi = np.arange(2 * NN, dtype=np.int32)
+    return GridNLP(N, alpha, v_lo, v_hi, cubic, v_bounded, ut, rowptr, col, l, u, wp, wi)
+
+
+def nd_order_grid_nlp(N: int, leaf: int = 64) -> np.ndarray:
+    """Nested dissection of the N x N grid (coupling reach two steps, as for the
+    squared Laplacian), each point contributing u then v."""
+    pts = nd_order_grid3d(N, N, 1, leaf=leaf).astype(np.int64)
+    out = np.empty(2 * pts.size, np.int32)
+    out[0::2] = pts
+    out[1::2] = pts + N * N
+    return out

@@ -285,6 +285,54 @@ IPM_API ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t
                                     double *d_kkt, int32_t *d_iters, int32_t *d_status,
                                     ipm_mpc_config *best, float *h_ms);
 
+/* --- grid NLP (the nonlinear problem class of Sec. 2, equalities as pairs) ---
+ * min 1/2 ||u - u_t||^2 + alpha/2 ||v||^2 over u, v on an nx x nx grid of
+ * interior points (spacing h = 1/(nx+1), u = 0 on the boundary) subject to
+ * h(x) = -Lap_h u + c3 u^3 - v = 0, written as the rows h >= 0 and -h >= 0, and
+ * v_lo <= v <= v_hi when v_bounded. Variables x = [u; v] (index ix + nx iy),
+ * n = m = 2 nx^2. The library evaluates f, h, J (6 entries per row: u at the
+ * five-point stencil in ascending column order, then v) and the diagonal
+ * Hessian of the Lagrangian W = diag(1 - 6 c3 u (lambda^+ - lambda^-), alpha)
+ * in its own kernels. */
+typedef struct {
+  int32_t nx;          /* grid points per side */
+  double alpha;        /* weight of ||v||^2 */
+  double v_lo, v_hi;   /* bounds of v (used when v_bounded) */
+  int32_t cubic;       /* 1: the u^3 term is present */
+  int32_t v_bounded;   /* 1: v_lo <= v <= v_hi */
+} ipm_grid_nlp;
+
+/* n, m and nnz(J) of the problem. */
+IPM_API ipm_status ipm_grid_nlp_sizes(const ipm_grid_nlp *p, int32_t *n, int32_t *m,
+                                      int64_t *nnz_j);
+/* Host arrays of the patterns the context must be created with: J (CSR,
+ * m + 1 and nnz_j entries), W (lower CSC, diagonal: n + 1 and n entries) and
+ * the bounds l, u (n each, +-INFINITY where absent). Any may be NULL. */
+IPM_API ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *p, int64_t *h_jrowptr,
+                                        int32_t *h_jcol, int64_t *h_wcolptr, int32_t *h_wrow,
+                                        double *h_l, double *h_u);
+/* Interior-point method on the grid NLP (Sec. 2: Newton system (3) condensed
+ * to Eq. (5) at every iterate, W the Hessian of L = f - lambda^T (g - s)).
+ * The context must have been created with the patterns above. Rules: start
+ * x = 0, s = max(g, 1), lambda = 1, mu = 0.1; monotone barrier update
+ * mu <- max(tol/10, min(0.2 mu, mu^1.5)) once the scaled barrier error is at
+ * most 10 mu; complementarity target mu (no corrector); one common step from
+ * the fraction to the boundary (tau = max(0.99, 1 - mu)) shortened by halving
+ * (at most 10 times) until the merit f - mu sum ln s + nu ||g - s||_1 decreases
+ * by 1e-4 alpha times its directional derivative (up to 10 eps |merit|). A
+ * non-positive pivot raises delta_p 100-fold and refactors; an FP32 factor
+ * that had to perturb a pivot is redone in FP64 when fallback_fp64 is set and
+ * the storage holds FP64 (else delta_p is raised). The pair formulation makes
+ * the interior degenerate (both slacks of a pair vanish): on fine grids the
+ * dual residual can stall above tol while the objective has converged.
+ * d_ut: target (nx^2, device); d_x (n), d_s, d_lambda (m_tot): outputs (device).
+ * Allocates 4 n + 5 m_tot + nnz(J) doubles of scratch on the context's stream
+ * for the call. res: as for ipm_solve. Errors: IPM_ERR_ARG if the context's
+ * pattern is not the grid NLP's; otherwise as ipm_solve. */
+IPM_API ipm_status ipm_solve_grid_nlp(ipm_ctx *ctx, const ipm_grid_nlp *p, const double *d_ut,
+                                      double *d_x, double *d_s, double *d_lambda,
+                                      ipm_result *res);
+
 /* --- learned correction of a stale factor --------------------------------
  * Not in the paper (its iterative-solver discussion in Sec. 1 is the nearest
  * passage). A per-variable network (8 features -> 32 -> 32 -> 17, tanh; 1905

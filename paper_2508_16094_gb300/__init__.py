@@ -31,7 +31,8 @@ EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze
             "kkt_solve_noalloc_capacity", "ipm_mpc_workspace_bytes", "ipm_mpc_prepare",
             "ipm_solve_batched", "ipm_mpc_autotune", "ipm_learned_param_count",
             "ipm_learned_weights", "ipm_learned_sample", "ipm_learned_loss_grad",
-            "ipm_learned_train", "ipm_last_error", "ipm_destroy"]
+            "ipm_learned_train", "ipm_grid_nlp_sizes", "ipm_grid_nlp_pattern",
+            "ipm_solve_grid_nlp", "ipm_last_error", "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -126,6 +127,9 @@ def load() -> C.CDLL:
         "ipm_mpc_prepare": (I32, [P, P, C.c_size_t, P]),
         "ipm_solve_batched": (I32, [P, P, P, C.c_size_t, D, I32, P, P, P, P, P, P]),
         "ipm_mpc_autotune": (I32, [P, P, C.c_size_t, D, I32, P, P, P, P, P, P, P, P]),
+        "ipm_grid_nlp_sizes": (I32, [P, P, P, P]),
+        "ipm_grid_nlp_pattern": (I32, [P] * 7),
+        "ipm_solve_grid_nlp": (I32, [P] * 7),
         "ipm_last_error": (C.c_char_p, [P]),
         "ipm_destroy": (None, [P]),
     }
@@ -393,3 +397,50 @@ class BatchedMPC:
             C.c_void_p(self.stream) if self.stream else None, _dp(self.z), _dp(self.obj),
             _dp(self.kkt), _dp(self.iters), _dp(self.status), C.byref(cfg), ms))
         return cfg, list(ms)
+
+
+# --- grid NLP -----------------------------------------------------------------
+class GridNlpParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("alpha", C.c_double), ("v_lo", C.c_double),
+                ("v_hi", C.c_double), ("cubic", C.c_int32), ("v_bounded", C.c_int32)]
+
+
+def ipm_grid_nlp_pattern(nx, alpha=5e-3, v_lo=-1.0, v_hi=1.0, cubic=1, v_bounded=1) -> dict:
+    """Patterns (J CSR, W lower CSC), bounds and sizes of the grid NLP as the
+    library evaluates it."""
+    lib = load()
+    prm = GridNlpParams(int(nx), float(alpha), float(v_lo), float(v_hi), int(cubic), int(v_bounded))
+    n, m, nnz = C.c_int32(), C.c_int32(), C.c_int64()
+    st = lib.ipm_grid_nlp_sizes(C.byref(prm), C.byref(n), C.byref(m), C.byref(nnz))
+    if st != 0:
+        raise IpmError(st, "invalid grid NLP parameters")
+    out = dict(params=prm, n=n.value, m=m.value, rowptr=np.empty(m.value + 1, np.int64),
+               col=np.empty(nnz.value, np.int32), wp=np.empty(n.value + 1, np.int64),
+               wi=np.empty(n.value, np.int32), l=np.empty(n.value), u=np.empty(n.value))
+    st = lib.ipm_grid_nlp_pattern(C.byref(prm), *[_hp(out[k]) for k in
+                                                  ("rowptr", "col", "wp", "wi", "l", "u")])
+    if st != 0:
+        raise IpmError(st, "grid NLP pattern")
+    return out
+
+
+class GridNLP:
+    """Context for the grid NLP: created with the library's patterns, analysed
+    with the given ordering; ipm_solve_grid_nlp runs the method."""
+
+    def __init__(self, nx, perm=None, alpha=5e-3, v_lo=-1.0, v_hi=1.0, cubic=1, v_bounded=1,
+                 options: Options | None = None):
+        self.pat = ipm_grid_nlp_pattern(nx, alpha, v_lo, v_hi, cubic, v_bounded)
+        pt = self.pat
+        self.ctx = IpmContext(pt["n"], pt["m"], pt["rowptr"], pt["col"], pt["l"], pt["u"],
+                              pt["wp"], pt["wi"], options=options)
+        self.info = self.ctx.kkt_analyze(perm)
+        self.ctx.ipm_set_workspace()
+
+    def ipm_solve_grid_nlp(self, ut, x, s, lam, raise_on_error=False) -> Result:
+        res = Result()
+        st = self.ctx._lib.ipm_solve_grid_nlp(self.ctx.handle, C.byref(self.pat["params"]), _dp(ut),
+                                              _dp(x), _dp(s), _dp(lam), C.byref(res))
+        if raise_on_error:
+            self.ctx._check(st)
+        return res

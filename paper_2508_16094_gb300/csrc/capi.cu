@@ -3,8 +3,10 @@
 // interior-point iteration.
 #include <algorithm>
 #include <chrono>
+#include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -15,6 +17,7 @@
 #include "ipm_kernels.h"
 #include "launch.h"
 #include "learned.h"
+#include "nlp.h"
 #include "tc.h"
 
 using namespace gipm;
@@ -49,6 +52,9 @@ struct ipm_ctx {
   LearnedBufs lb;
   bool learned_active = false;  // PCG preconditioner = corrected stale factor
   bool lb_on = false;           // learned buffers sized for n (fixed by the layout)
+  bool nlp_grad = false;        // direction(): cc is the whole gradient (no W x term)
+  bool bwd_measure = false;     // do_solve: normwise backward error instead of ||r|| / ||b||
+  double knorm = 0.0;           // ||K||_inf of the assembled matrix (when bwd_measure)
   bool have_stale = false;      // lb.D_old / diag_old / mu[0] describe the held factor
   int refine_override = -1, pcg_override = -1;
   double *lb_loss = nullptr;
@@ -387,10 +393,21 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
     c->last_rel = 0.0;
     return IPM_OK;
   }
+  // ||b - K x|| / ||b|| drives refinement. For a badly scaled matrix (the grid
+  // NLP: entries up to (nx+1)^4 times D) its floor is about eps ||K|| ||x|| / ||b||,
+  // so with bwd_measure the solve is accepted on the normwise backward error
+  // ||b - K x|| / (||K|| ||x|| + ||b||) instead (refinement still runs until it stalls).
+  double bwd = 0.0;
   auto residual = [&](const double *xv) {
     V.residual(c->cur_jvals, c->cur_D, c->cur_wvals, c->cur_delta_p, xv, bb, r, c->vtA);
     V.absmax(n, r, sN + 1);
-    return d2h_scalar(c, sN + 1) / bn;
+    if (!c->bwd_measure) return d2h_scalar(c, sN + 1) / bn;
+    V.absmax(n, xv, sN + 5);
+    double h2[5];
+    CK(cudaMemcpyAsync(h2, sN + 1, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    bwd = h2[0] / (c->knorm * h2[4] + bn);
+    return h2[0] / bn;
   };
   apply_factor(c, bb, xx, false);
   double rel = residual(xx);
@@ -409,7 +426,8 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
     }
     c->refine_steps += iters;
   }
-  if ((refine == IPM_REFINE_PCG || refine == IPM_REFINE_IR) && (rel > o.ir_tol || !std::isfinite(rel))) {
+  if ((refine == IPM_REFINE_PCG || refine == IPM_REFINE_IR) && (rel > o.ir_tol || !std::isfinite(rel)) &&
+      !(c->bwd_measure && bwd <= o.ir_tol && std::isfinite(rel))) {
     // PCG on K x = b preconditioned by the factor, from the current x
     if (!std::isfinite(rel)) {
       CK(cudaMemsetAsync(xx, 0, n * sizeof(double), c->st));
@@ -453,6 +471,7 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
   CK(cudaMemcpyAsync(x, xx, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   CK(cudaGetLastError());
   if (c->factor_prec != IPM_FP64) check_solve_barrier(c);
+  if (c->bwd_measure) rel = bwd;
   c->last_rel = rel;
   if (info) *info = ipm_solve_info{iters, used_pcg, rel};
   if (!(rel <= o.accept_tol)) {
@@ -469,6 +488,12 @@ void set_assembly(ipm_ctx *c, const double *wv, const double *jv, const double *
   c->cur_delta_p = dp;
   launch_assemble(c->dp, jv, D, wv, dp, c->kval, c->st);
   CK(cudaGetLastError());
+  if (c->bwd_measure) {  // ||K||_inf for the backward error of the solves
+    VecOps V = c->vec();
+    V.abs_rowsum(jv, D, wv, dp, c->vz, c->vtA);
+    V.absmax(c->P.n, c->vz, c->scal + 7);
+    c->knorm = d2h_scalar(c, c->scal + 7);
+  }
   if (c->state < 3) c->state = 3;
 }
 
@@ -479,7 +504,8 @@ ipm_status direction(ipm_ctx *c, const double *jvals, const double *b, const dou
                      const double *w, double *dx, double *ds, double *dl, ipm_solve_info *si) {
   VecOps V = c->vec();
   V.rhs_rows(c->vD, c->vg, w, lam, c->vt);
-  V.jtv(jvals, c->vt, 1.0, wvals, x, cc, c->vrd);  // r_p = c + W x + J^T (D (g - w/lam) - lam)
+  // r_p = c + W x + J^T (D (g - w/lam) - lam); for the NLP, cc is grad f itself
+  V.jtv(jvals, c->vt, 1.0, wvals, c->nlp_grad ? nullptr : x, cc, c->vrd);
   V.negate(c->P.n, c->vrd);
   ipm_status stt = do_solve(c, c->vrd, dx,
                             c->refine_override >= 0 ? c->refine_override : c->opts.refine, si);
@@ -1091,6 +1117,226 @@ ipm_status ipm_learned_train(ipm_ctx *c, const float *feat, const float *z, cons
     CK(cudaStreamSynchronize(c->st));
     return IPM_OK;
   });
+}
+
+static bool grid_from(const ipm_grid_nlp *pp, GridNlp &p) {
+  if (!pp || pp->nx < 2 || pp->nx > 16384 || !(pp->alpha >= 0.0)) return false;
+  if (pp->v_bounded && !(pp->v_lo < pp->v_hi)) return false;
+  p.N = pp->nx;
+  p.alpha = pp->alpha;
+  p.v_lo = pp->v_lo;
+  p.v_hi = pp->v_hi;
+  p.cubic = pp->cubic ? 1 : 0;
+  p.v_bounded = pp->v_bounded ? 1 : 0;
+  return true;
+}
+
+ipm_status ipm_grid_nlp_sizes(const ipm_grid_nlp *pp, int32_t *n, int32_t *m, int64_t *nnz_j) {
+  GridNlp p;
+  if (!grid_from(pp, p)) return IPM_ERR_ARG;
+  const int64_t NN = p.NN();
+  if (n) *n = (int32_t)(2 * NN);
+  if (m) *m = (int32_t)(2 * NN);
+  if (nnz_j) *nnz_j = 2 * (5 * NN - 4 * (int64_t)p.N + NN);
+  return IPM_OK;
+}
+
+ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *pp, int64_t *h_jrowptr, int32_t *h_jcol,
+                                int64_t *h_wcolptr, int32_t *h_wrow, double *h_l, double *h_u) {
+  GridNlp p;
+  if (!grid_from(pp, p)) return IPM_ERR_ARG;
+  try {
+    std::vector<int64_t> rp;
+    std::vector<int32_t> cl;
+    grid_nlp_pattern(p, rp, cl);
+    const int64_t NN = p.NN(), n = 2 * NN;
+    if (h_jrowptr) std::memcpy(h_jrowptr, rp.data(), rp.size() * sizeof(int64_t));
+    if (h_jcol) std::memcpy(h_jcol, cl.data(), cl.size() * sizeof(int32_t));
+    for (int64_t j = 0; j <= n && h_wcolptr; j++) h_wcolptr[j] = j;
+    for (int64_t j = 0; j < n && h_wrow; j++) h_wrow[j] = (int32_t)j;
+    for (int64_t j = 0; j < n; j++) {
+      const bool bv = p.v_bounded && j >= NN;
+      if (h_l) h_l[j] = bv ? p.v_lo : -INFINITY;
+      if (h_u) h_u[j] = bv ? p.v_hi : INFINITY;
+    }
+  } catch (const std::bad_alloc &) {
+    return IPM_ERR_NOMEM;
+  }
+  return IPM_OK;
+}
+
+ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *ut, double *x,
+                              double *s, double *lam, ipm_result *res_out) {
+  if (!c || !pp || !ut || !x || !s || !lam) return IPM_ERR_ARG;
+  ipm_result res{};
+  double *scratch = nullptr;
+  ipm_status rs = guarded(c, [&]() -> ipm_status {
+    if (c->state < 2) throw Fail{IPM_ERR_STATE, "ipm_solve_grid_nlp before ipm_set_workspace"};
+    GridNlp p;
+    if (!grid_from(pp, p)) throw Fail{IPM_ERR_ARG, "invalid grid NLP parameters"};
+    const Problem &P = c->P;
+    const int64_t NN = p.NN(), n = P.n, m = P.m, mt = P.mt;
+    {  // the context must carry this problem's patterns
+      std::vector<int64_t> rp;
+      std::vector<int32_t> cl;
+      grid_nlp_pattern(p, rp, cl);
+      bool ok = n == 2 * NN && m == 2 * NN && P.jp.size() == rp.size() && P.ji.size() == cl.size() &&
+                std::equal(rp.begin(), rp.end(), P.jp.begin()) &&
+                std::equal(cl.begin(), cl.end(), P.ji.begin()) && (int64_t)P.wp.size() == n + 1;
+      for (int64_t j = 0; ok && j < n; j++)
+        ok = P.wp[j] == j && P.wi[j] == (int32_t)j &&
+             std::isfinite(P.l[j]) == (p.v_bounded && j >= NN) &&
+             std::isfinite(P.u[j]) == (p.v_bounded && j >= NN);
+      if (!ok) throw Fail{IPM_ERR_ARG, "context pattern is not the grid NLP's"};
+    }
+    const auto t_start = std::chrono::steady_clock::now();
+    const ipm_options &o = c->opts;
+    VecOps V = c->vec();
+    c->refine_steps = c->pcg_steps = 0;
+    const int64_t nnz = (int64_t)P.ji.size();
+    c->bwd_measure = true;
+    const size_t words = (size_t)(4 * n + 5 * mt + nnz);
+    CK(cudaMallocAsync(&scratch, words * sizeof(double), c->st));
+    double *jv = scratch, *hrows = jv + nnz, *grad = hrows + mt, *wv = grad + n, *zero = wv + n,
+           *xt = zero + mt, *stv = xt + n, *gt = stv + mt, *gcur = gt + mt;
+    CK(cudaMemsetAsync(zero, 0, mt * sizeof(double), c->st));
+    double *d_f = c->scal + 44, *terms = c->scal + 48;
+    auto d2h = [&](const double *d, double *h, int cnt) {
+      CK(cudaMemcpyAsync(h, d, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    };
+    auto eval_at = [&](const double *xx, double *gout) {  // f (returned), h, J, grad, g
+      nlp_eval(p, c->dp.jp, xx, ut, hrows, jv, grad, d_f, c->partial, c->st);
+      V.g(hrows, xx, zero, c->dl_, c->du_, gout);
+      double f;
+      d2h(d_f, &f, 1);
+      return f;
+    };
+    auto set_sc = [&](size_t off, double v) {
+      CK(cudaMemcpyAsync(reinterpret_cast<char *>(c->sc) + off, &v, sizeof(double),
+                         cudaMemcpyHostToDevice, c->st));
+    };
+    // starting point
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->st));
+    eval_at(x, c->vg);
+    V.init_slack(c->vg, s, lam);
+    double mu = 0.1, nu = 0.0;
+    const double bscale = p.v_bounded ? std::max(1.0, std::max(std::fabs(p.v_lo), std::fabs(p.v_hi))) : 1.0;
+    V.absmax(n, grad, c->scal + 20);
+    const double cscale = std::max(1.0, d2h_scalar(c, c->scal + 20));
+    res.status = IPM_ERR_MAXITER;
+    ipm_status stt = IPM_OK;
+    int it = 0;
+    for (it = 0; it <= o.max_iter; it++) {
+      const double f = eval_at(x, c->vg);
+      V.jtv(jv, lam, -1.0, nullptr, nullptr, grad, c->vrd);  // grad f - J^T lambda
+      V.kkt(c->vg, s, lam, c->vrd, zero, nullptr, x, c->scal + 24, c->sc);
+      IpmScalars h;
+      CK(cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      const double fs = std::max(1.0, std::fabs(f));
+      res.primal_res = h.primal_inf / bscale;
+      res.dual_res = h.dual_inf / cscale;
+      res.compl_res = h.compl_inf / fs;
+      res.kkt = std::max(res.primal_res, std::max(res.dual_res, res.compl_res));
+      res.objective = f;
+      res.mu = mu;
+      if (o.verbose)
+        std::fprintf(stderr, "nlp it %3d f % .10e kkt %.3e (p %.2e d %.2e c %.2e) mu %.2e\n", it, f,
+                     res.kkt, res.primal_res, res.dual_res, res.compl_res, mu);
+      if (!std::isfinite(res.kkt)) { res.status = IPM_ERR_NUMERIC; break; }
+      if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
+      if (it == o.max_iter) break;
+      // monotone barrier update once the barrier problem is solved to 10 mu
+      nlp_barrier_err(mt, s, lam, mu, terms, c->partial, c->st);
+      double berr;
+      d2h(terms, &berr, 1);
+      if (std::max(res.primal_res, std::max(res.dual_res, berr / fs)) <= 10.0 * mu)
+        mu = std::max(o.tol / 10.0, std::min(0.2 * mu, std::pow(mu, 1.5)));
+      // Newton direction with target mu; inertia by regularisation
+      nlp_hess(p, x, lam, wv, c->st);
+      V.scaling(s, lam, o.delta_d, c->vD);
+      double delta_p = o.delta_p;
+      for (int tries = 0; tries < 12; tries++) {
+        stt = factor_with_retry(c, wv, jv, o.precision, delta_p, &res);
+        if (stt != IPM_OK || c->factor_prec == IPM_FP64 || c->last_perturbed == 0) break;
+        // the FP32 factor met a non-positive pivot: an FP64 factor tells a
+        // rounding breakdown from true indefiniteness (which it regularises)
+        if (o.fallback_fp64 && c->storage_bytes == 8) {
+          res.fp64_fallbacks++;
+          stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
+          break;
+        }
+        delta_p = delta_p > 0 ? delta_p * 100.0 : 1e-8;
+        res.regularizations++;
+      }
+      ipm_solve_info si{};
+      if (stt == IPM_OK) {
+        nlp_fill(mt, mu, c->vw, c->st);
+        c->nlp_grad = true;
+        stt = direction(c, jv, nullptr, grad, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+        c->nlp_grad = false;
+        if (stt != IPM_OK && o.fallback_fp64 && o.precision != IPM_FP64 && c->storage_bytes == 8) {
+          res.fp64_fallbacks++;
+          stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
+          if (stt == IPM_OK) {
+            c->nlp_grad = true;
+            stt = direction(c, jv, nullptr, grad, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+            c->nlp_grad = false;
+          }
+        }
+      }
+      res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
+      if (stt != IPM_OK) { res.status = stt; break; }
+      // common step from the fraction to the boundary, then backtracking on the merit
+      set_sc(offsetof(IpmScalars, mu), mu);
+      V.ftb(s, c->vds, lam, c->vdl, c->scal + 32, c->sc, false);
+      CK(cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      double alpha = std::min(h.alpha_p, h.alpha_d);
+      double dt[3], mt2[2];
+      nlp_dir_terms(n, mt, grad, c->vdx, s, c->vds, lam, c->vdl, terms, c->partial, c->st);
+      d2h(terms, dt, 3);
+      nu = std::max(nu, dt[2] + 1.0);
+      nlp_merit_terms(mt, s, c->vg, terms, c->partial, c->st);
+      d2h(terms, mt2, 2);
+      const double phi0 = f - mu * mt2[0] + nu * mt2[1];
+      const double dphi = dt[0] - mu * dt[1] - nu * mt2[1];
+      if (dphi < 0.0) {
+        for (int hv = 0; hv < 10; hv++) {
+          nlp_trial(n, mt, x, c->vdx, s, c->vds, alpha, xt, stv, c->st);
+          const double ft = eval_at(xt, gt);
+          nlp_merit_terms(mt, stv, gt, terms, c->partial, c->st);
+          d2h(terms, mt2, 2);
+          // Armijo, allowing for the rounding of phi (10 eps |phi|)
+          if (ft - mu * mt2[0] + nu * mt2[1] <= phi0 + 1e-4 * alpha * dphi + 10.0 * DBL_EPSILON * std::fabs(phi0))
+            break;
+          alpha *= 0.5;
+        }
+      }
+      set_sc(offsetof(IpmScalars, alpha_p), alpha);
+      set_sc(offsetof(IpmScalars, alpha_d), alpha);
+      V.update(c->sc, x, c->vdx, s, c->vds, lam, c->vdl);
+    }
+    (void)gcur;
+    res.iterations = it;
+    CK(cudaStreamSynchronize(c->st));
+    res.time_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    res.refine_steps = (int32_t)c->refine_steps;
+    res.pcg_steps = (int32_t)c->pcg_steps;
+    return (ipm_status)res.status;
+  });
+  c->nlp_grad = false;
+  c->bwd_measure = false;
+  if (scratch) {
+    cudaFreeAsync(scratch, c->st);
+    cudaStreamSynchronize(c->st);
+  }
+  if (res_out) {
+    res.status = rs;
+    *res_out = res;
+  }
+  return rs;
 }
 
 int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }

@@ -40,6 +40,9 @@ struct VecOps {
   // r = b - K x (matrix-free); tA: scratch of length m
   void residual(const double *jvals, const double *D, const double *wv, double delta_p,
                 const double *x, const double *b, double *r, double *tA) const;
+  // out_j = sum_i |K_ji| (matrix-free, D >= 0); tA: scratch of length m
+  void abs_rowsum(const double *jvals, const double *D, const double *wv, double delta_p,
+                  double *out, double *tA) const;
   template <typename V> void permute_in(const double *b, const double *scale, V *y) const;
   template <typename V>
   void permute_out(const V *y, const double *scale, double *x, bool accumulate) const;

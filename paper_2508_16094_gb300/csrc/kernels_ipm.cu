@@ -153,6 +153,34 @@ __global__ void resid_cols_kernel(DevPlan dp, const double *__restrict__ jv,
   }
 }
 
+// row sums of |K|: |W| 1 + |J_A|^T D_A |J_A| 1 + D_l + D_u + delta_p (D >= 0)
+__global__ void absk_rows_kernel(DevPlan dp, const double *__restrict__ jv,
+                                 const double *__restrict__ D, double *__restrict__ tA) {
+  GRID_STRIDE(r, dp.m) {
+    double a = 0.0;
+    for (int64_t e = dp.jp[r]; e < dp.jp[r + 1]; e++) a += fabs(jv[e]);
+    tA[r] = D[r] * a;
+  }
+}
+__global__ void absk_cols_kernel(DevPlan dp, const double *__restrict__ jv,
+                                 const double *__restrict__ D, const double *__restrict__ wv,
+                                 double delta_p, const double *__restrict__ tA,
+                                 double *__restrict__ out) {
+  GRID_STRIDE(j, dp.n) {
+    double a = 0.0;
+    for (int64_t t = dp.jtp[j]; t < dp.jtp[j + 1]; t++) {
+      const int32_t e = dp.jtpos[t];
+      a = fma(fabs(jv[e]), tA[dp.jrow[e]], a);
+    }
+    double d = fabs(delta_p);
+    if (dp.lpos[j] >= 0) d += D[dp.lpos[j]];
+    if (dp.upos[j] >= 0) d += D[dp.upos[j]];
+    a += d;
+    if (wv)
+      for (int64_t e = dp.wfp[j]; e < dp.wfp[j + 1]; e++) a += fabs(wv[dp.wfsrc[e]]);
+    out[j] = a;
+  }
+}
 template <typename V>
 __global__ void permute_in_kernel(int32_t n, const int32_t *__restrict__ perm,
                                   const double *__restrict__ b, const double *__restrict__ scale,
@@ -376,6 +404,11 @@ void VecOps::residual(const double *jvals, const double *D, const double *wv, do
                       const double *x, const double *b, double *r, double *tA) const {
   if (dp.m > 0) { note_launch(); resid_rows_kernel<<<grid_of(dp.m), 256, 0, st>>>(dp, jvals, D, x, tA); }
   { note_launch(); resid_cols_kernel<<<grid_of(dp.n), 256, 0, st>>>(dp, jvals, D, wv, delta_p, tA, x, b, r); }
+}
+void VecOps::abs_rowsum(const double *jvals, const double *D, const double *wv, double delta_p,
+                        double *out, double *tA) const {
+  if (dp.m > 0) { note_launch(); absk_rows_kernel<<<grid_of(dp.m), 256, 0, st>>>(dp, jvals, D, tA); }
+  { note_launch(); absk_cols_kernel<<<grid_of(dp.n), 256, 0, st>>>(dp, jvals, D, wv, delta_p, tA, out); }
 }
 template <typename V>
 void VecOps::permute_in(const double *b, const double *scale, V *y) const {

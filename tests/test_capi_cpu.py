@@ -104,3 +104,17 @@ def test_options_cannot_enable_learned_after_analysis():
     ctx.kkt_analyze(gen.nd_order_grid3d(6))
     with pytest.raises(gb.IpmError):
         ctx.ipm_set_options(learned=1)
+
+
+def test_grid_nlp_pattern_matches_generator():
+    """The library's grid-NLP patterns and bounds are the generator's (the
+    oracle evaluates on the generator's)."""
+    for N, vb in ((5, 1), (12, 1), (7, 0)):
+        pt = gb.ipm_grid_nlp_pattern(N, v_bounded=vb)
+        P = gen.grid_nlp(N, v_bounded=vb)
+        assert pt["n"] == P.n and pt["m"] == P.m
+        for a, b in (("rowptr", P.rowptr), ("col", P.col), ("wp", P.wp), ("wi", P.wi),
+                     ("l", P.l), ("u", P.u)):
+            assert np.array_equal(pt[a], b), a
+    with pytest.raises(gb.IpmError):
+        gb.ipm_grid_nlp_pattern(1)
