@@ -220,6 +220,39 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
     return out
 
 
+def nlp_measure(N: int, max_iter: int = 60):
+    """Grid NLP (512^2 grid, cubic PDE constraint as inequality pairs, -1 <= v <= 1):
+    the FP64 factor against the split-TF32 factor with FP64 fallback, from the
+    cold start, at most max_iter iterations towards a 1e-6 KKT residual."""
+    import torch
+    import paper_2508_16094_gb300 as gb
+    P = gen.grid_nlp(N, seed=5)
+    perm = gen.nd_order_grid_nlp(N)
+    ut = torch.as_tensor(P.ut, dtype=torch.float64, device="cuda")
+    out = {"workload": f"grid NLP {N}^2 (n = m = {P.n}), alpha 5e-3, |v| <= 1, seed 5",
+           "max_iter": max_iter}
+    for name, prec in (("fp64", gb.IPM_FP64), ("tf32x3", gb.IPM_TF32X3)):
+        o = gb.default_options(precision=prec, tol=1e-6, max_iter=max_iter, storage_fp64=1,
+                               fallback_fp64=1)
+        G = gb.GridNLP(N, perm=perm, options=o)
+        n, mt = G.pat["n"], G.ctx.m_tot
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        s = torch.empty(mt, dtype=torch.float64, device="cuda")
+        lam = torch.empty(mt, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = G.ipm_solve_grid_nlp(ut, x, s, lam)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "status": int(r.status),
+                     "iterations": int(r.iterations), "objective": r.objective, "kkt": r.kkt,
+                     "primal": r.primal_res, "dual": r.dual_res, "fp64_fallbacks": int(r.fp64_fallbacks),
+                     "regularizations": int(r.regularizations), "refine_steps": int(r.refine_steps),
+                     "factor_flops": G.info.flops}
+        G.ctx.close()
+    out["objective_rel_diff_tf32x3_vs_fp64"] = abs(out["tf32x3"]["objective"] - out["fp64"]["objective"]) / max(1.0, abs(out["fp64"]["objective"]))
+    return out
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -396,6 +429,9 @@ def run_ours(args, ws, rank, local):
     forms = None
     if rank == 0 and args.forms_grid > 0:
         forms = forms_measure(args.forms_grid)
+    nlp = None
+    if rank == 0 and args.nlp_grid > 0:
+        nlp = nlp_measure(args.nlp_grid)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -430,6 +466,7 @@ def run_ours(args, ws, rank, local):
             "time_to_kkt_1e-6": tti,
             "mpc_batch": mpc,
             "time_to_kkt_1e-6_forms": forms,
+            "grid_nlp": nlp,
             "ipm_step": {"refine_steps": int(res.refine_steps), "pcg_steps": int(res.pcg_steps),
                          "factor_ms": res.time_factor_ms / steps_done,
                          "solve_ms": res.time_solve_ms / steps_done},
@@ -450,6 +487,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vary-seed", action="store_true")
     ap.add_argument("--no-mpc", action="store_true")
+    ap.add_argument("--nlp-grid", type=int, default=512,
+                    help="grid of the NLP comparison (0: skip)")
     ap.add_argument("--forms-grid", type=int, default=48,
                     help="grid of the FP64 / split-TF32 / learned time-to-1e-6 comparison (0: skip)")
     args = ap.parse_args()
