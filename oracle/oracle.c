@@ -604,7 +604,7 @@ typedef struct {
 } orc_ipm_opts;
 
 typedef struct {
-  int32_t status;      /* 0 converged, 1 iteration limit, 2 factorisation failure */
+  int32_t status;      /* 0 converged, 1 iteration limit, 2 factorisation failure, 3 non-finite iterate */
   int32_t iterations;
   int32_t refactorizations;
   double objective;
@@ -849,6 +849,9 @@ ORC_EXPORT int orc_ipm_lp(const orc_sym *S, int32_t m, const int64_t *ap, const 
     res->primal_res = pr / bscale; res->dual_res = dr / cscale; res->compl_res = cr / fs;
     if (log_mu) log_mu[it] = mu;
     if (log_kkt) log_kkt[it] = kkt;
+    /* the maxima above skip NaN, the sums do not: a non-finite iterate cannot
+       satisfy the KKT conditions (2) */
+    if (!isfinite(fx) || !isfinite(mu)) { res->status = 3; break; }
     if (kkt <= o->tol) { res->status = 0; break; }
     if (it == o->max_iter) break;
 

@@ -864,7 +864,11 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       if (o.verbose)
         std::fprintf(stderr, "ipm it %3d f % .10e kkt %.3e (p %.2e d %.2e c %.2e) mu %.2e\n", it,
                      h.fx, res.kkt, res.primal_res, res.dual_res, res.compl_res, h.mu);
-      if (!std::isfinite(res.kkt)) { res.status = IPM_ERR_NUMERIC; break; }
+      // the maxima skip NaN, the sums (mu, f) do not
+      if (!std::isfinite(res.kkt) || !std::isfinite(h.mu) || !std::isfinite(h.fx)) {
+        res.status = IPM_ERR_NUMERIC;
+        break;
+      }
       if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
       if (it == o.max_iter) break;
       CK(cudaEventRecord(ev[0], c->st));
@@ -1244,7 +1248,10 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       if (o.verbose)
         std::fprintf(stderr, "nlp it %3d f % .10e kkt %.3e (p %.2e d %.2e c %.2e) mu %.2e\n", it, f,
                      res.kkt, res.primal_res, res.dual_res, res.compl_res, mu);
-      if (!std::isfinite(res.kkt)) { res.status = IPM_ERR_NUMERIC; break; }
+      if (!std::isfinite(res.kkt) || !std::isfinite(h.mu) || !std::isfinite(f)) {
+        res.status = IPM_ERR_NUMERIC;
+        break;
+      }
       if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
       if (it == o.max_iter) break;
       // monotone barrier update once the barrier problem is solved to 10 mu
