@@ -326,7 +326,7 @@ IPM_API ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *p, int64_t *h_jrowpt
  * the interior degenerate (both slacks of a pair vanish): on fine grids the
  * dual residual can stall above tol while the objective has converged.
  * d_ut: target (nx^2, device); d_x (n), d_s, d_lambda (m_tot): outputs (device).
- * Allocates 4 n + 5 m_tot + nnz(J) doubles of scratch on the context's stream
+ * Allocates 3 n + 4 m_tot + nnz(J) doubles of scratch on the context's stream
  * for the call. res: as for ipm_solve. Errors: IPM_ERR_ARG if the context's
  * pattern is not the grid NLP's; otherwise as ipm_solve. */
 IPM_API ipm_status ipm_solve_grid_nlp(ipm_ctx *ctx, const ipm_grid_nlp *p, const double *d_ut,

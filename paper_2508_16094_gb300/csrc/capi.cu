@@ -1199,10 +1199,10 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
     c->refine_steps = c->pcg_steps = 0;
     const int64_t nnz = (int64_t)P.ji.size();
     c->bwd_measure = true;
-    const size_t words = (size_t)(4 * n + 5 * mt + nnz);
+    const size_t words = (size_t)(3 * n + 4 * mt + nnz);
     CK(cudaMallocAsync(&scratch, words * sizeof(double), c->st));
     double *jv = scratch, *hrows = jv + nnz, *grad = hrows + mt, *wv = grad + n, *zero = wv + n,
-           *xt = zero + mt, *stv = xt + n, *gt = stv + mt, *gcur = gt + mt;
+           *xt = zero + mt, *stv = xt + n, *gt = stv + mt;
     CK(cudaMemsetAsync(zero, 0, mt * sizeof(double), c->st));
     double *d_f = c->scal + 44, *terms = c->scal + 48;
     auto d2h = [&](const double *d, double *h, int cnt) {
@@ -1325,7 +1325,6 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       set_sc(offsetof(IpmScalars, alpha_d), alpha);
       V.update(c->sc, x, c->vdx, s, c->vds, lam, c->vdl);
     }
-    (void)gcur;
     res.iterations = it;
     CK(cudaStreamSynchronize(c->st));
     res.time_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
