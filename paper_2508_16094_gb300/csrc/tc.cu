@@ -25,6 +25,7 @@ namespace gipm {
 namespace {
 
 constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kSyrkN = 256;
+constexpr int kMaxClusters = 76;  // CTA pairs of the persistent SYRK (152 SMs)
 constexpr int kSuper = 512;  // columns per super-step of the left-looking panel updates
 constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per 128-row operand tile
 constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
@@ -97,6 +98,28 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_
       : "memory");
 }
 
+// The same box written to this CTA's and its cluster peer's shared memory at
+// the same offset; each destination's mbarrier at the same offset receives its bytes.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const void *tmap, uint64_t *bar, int x,
+                                               int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart (stride byte offset).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -124,6 +147,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Completion of this CTA's issued products, signalled to the mbarrier at the
+// same offset in every CTA of the mask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -404,6 +437,173 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
 }
 
+// Update-matrix SYRK in clusters of two CTAs: a task is the pair of 128 x 256
+// tiles (i0, j0) and (i0 + 128, j0) of one front, which share their B operand
+// (256 rows of the panel). CTA r loads its own A rows and the r-th 128-row half
+// of B with TMA multicast into both CTAs' shared memory, so each CTA reads 2/3
+// of the operand bytes of an unpaired tile. A stage is free again when the
+// products of both CTAs have read it (each MMA commit is multicast to both
+// CTAs' empty barriers, which count two arrivals). The second tile of a pair
+// at the edge of the front (i0 + 128 >= nrow) reads zeros and stores nothing.
+template <int SPLIT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    tc_syrk_pair_kernel(DevPlan dp, const Task *__restrict__ pairs, int npair,
+                        const CUtensorMap *__restrict__ maps,
+                        const CUtensorMap *__restrict__ maps_lo, float *__restrict__ U,
+                        int32_t *status) {
+  constexpr int BN = 256;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  using CF = Cfg<SPLIT, BN>;
+  constexpr int S = CF::S, kBB = CF::kB * kTileBytes;
+  uint8_t *sA = base;
+  uint8_t *sB = sA + S * kTileBytes;
+  uint8_t *sAl = sB + S * kBB;
+  uint8_t *sBl = sAl + (SPLIT == 3 ? S * kTileBytes : 0);
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + S * CF::kStage);
+  uint64_t *empty = full + S;
+  uint64_t *accfull = empty + S;
+  uint64_t *accempty = accfull + 2;
+  uint64_t *drain = accempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = cluster_rank();
+  const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
+  constexpr uint16_t kBoth = 0x3;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; st++) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 2);  // the products of both CTAs
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // the peer's barriers exist before anything is multicast to them
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer: own A rows, this CTA's half of B for both CTAs
+      uint32_t g = 0;
+      for (int p = cid; p < npair && !*abort_flag; p += ncl) {
+        const Task tk = pairs[p];
+        const FrontInfo F = dp.fronts[tk.front];
+        const CUtensorMap *amap = maps + tk.front, *lomap = maps_lo + tk.front;
+        const int arow = F.ncol + tk.a + 128 * (int)rank, brow = F.ncol + tk.b + 128 * (int)rank;
+        const int nk = (F.ncol + kTileK - 1) / kTileK;
+        for (int kt = 0; kt < nk; kt++, g++) {
+          const int st = g % S;
+          const uint32_t round = g / S;
+          if (!mbar_wait(&empty[st], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
+          mbar_arrive_expect_tx(&full[st], (SPLIT == 3 ? 2 : 1) * (kTileBytes + kBB));
+          tma_load_2d(sA + st * kTileBytes, amap, &full[st], kt * kTileK, arow);
+          tma_load_2d_mc(sB + st * kBB + rank * kTileBytes, amap, &full[st], kt * kTileK, brow, kBoth);
+          if (SPLIT == 3) {
+            tma_load_2d(sAl + st * kTileBytes, lomap, &full[st], kt * kTileK, arow);
+            tma_load_2d_mc(sBl + st * kBB + rank * kTileBytes, lomap, &full[st], kt * kTileK, brow,
+                           kBoth);
+          }
+        }
+      }
+      if (*abort_flag)
+        for (uint32_t q = g > (uint32_t)S ? g - S : 0; q < g; q++)
+          mbar_wait(&full[q % S], (q / S) & 1, status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = tf32_idesc<BN>();
+      uint32_t g = 0;
+      int i = 0;
+      for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
+        const Task tk = pairs[p];
+        const FrontInfo F = dp.fronts[tk.front];
+        const int nk = (F.ncol + kTileK - 1) / kTileK;
+        const int a = i & 1;
+        if (!mbar_wait(&accempty[a], ((i >> 1) & 1) ^ 1, status)) { *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        for (int kt = 0; kt < nk; kt++, g++) {
+          const int st = g % S;
+          const uint32_t round = g / S;
+          if (!mbar_wait(&full[st], round & 1, status)) { *abort_flag = 1; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ad = sw128_desc(smem_u32(sA + st * kTileBytes));
+          const uint64_t bd = sw128_desc(smem_u32(sB + st * kBB));
+          const uint64_t ald = sw128_desc(smem_u32(sAl + st * kTileBytes));
+          const uint64_t bld = sw128_desc(smem_u32(sBl + st * kBB));
+#pragma unroll
+          for (int k4 = 0; k4 < kTileK / 8; k4++) {
+            if (SPLIT == 3) {
+              mma_tf32(acc, ald + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+              mma_tf32(acc, ad + 2 * k4, bld + 2 * k4, idesc, 1);
+              mma_tf32(acc, ad + 2 * k4, bd + 2 * k4, idesc, 1);
+            } else {
+              mma_tf32(acc, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+            }
+          }
+          mma_commit_mc(&empty[st], kBoth);
+        }
+        if (*abort_flag) break;
+        mma_commit(&accfull[a]);
+      }
+      mma_commit(drain);
+      mbar_wait(drain, 0, status);
+    }
+  } else {  // warps 2-5: epilogue of this CTA's tile
+    const int q = warp % 4;
+    const int row = q * 32 + lane;
+    int i = 0;
+    for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
+      const Task tk = pairs[p];
+      const FrontInfo F = dp.fronts[tk.front];
+      const int r0 = tk.a + 128 * (int)rank;
+      const int M = min(kTileM, F.nrow - r0), N = min(BN, F.nrow - tk.b);
+      const int a = i & 1;
+      if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (M > 0) {
+        float *C = U + F.uoff + (int64_t)r0 * F.uld + tk.b;
+        for (int cb = 0; cb < (N + 31) / 32; cb++) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
+          if (row < M) {
+            float *crow = C + (int64_t)row * F.uld + cb * 32;
+            const int nc = min(32, N - cb * 32);
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+              if (c < nc) crow[c] -= v[c];
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[a]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // no multicast can still target this CTA's shared memory
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+}
+
 // Cholesky of one diagonal block (kb <= 128) in FP32 and the explicit inverse
 // of its factor, written row-major (128 x 128, zero outside the lower kb x kb
 // triangle) to scratch slot `b` for the triangular solve of the rows below as
@@ -634,6 +834,7 @@ void TcPlan::build(const Plan &plan) {
   potrf_.clear();
   trsm_.clear();
   syrk_.clear();
+  pairs_.clear();
   levels_.assign(plan.levels.size(), Level{});
   nfronts_ = (int)plan.fronts.size();
   max_slots_ = 1;
@@ -699,6 +900,14 @@ void TcPlan::build(const Plan &plan) {
         for (int32_t j0 = 0; j0 <= i0; j0 += kSyrkN) syrk_.push_back({s, i0, j0, 1});
     }
     lv.syrk_e = (int)syrk_.size();
+    lv.pair_b = (int)pairs_.size();  // the same tiles as pairs (i0, j0), (i0 + 128, j0)
+    for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+      const int32_t s = plan.level_fronts[t];
+      const FrontInfo &F = plan.fronts[s];
+      for (int32_t i0 = 0; i0 < F.nrow; i0 += 2 * kTileM)
+        for (int32_t j0 = 0; j0 <= i0; j0 += kSyrkN) pairs_.push_back({s, i0, j0, 1});
+    }
+    lv.pair_e = (int)pairs_.size();
   }
   // range checks of the tasks against the fronts (the kernel masks only the tile edges)
   auto fail = [](const char *w) { throw std::runtime_error(std::string("tc plan check: ") + w); };
@@ -712,6 +921,12 @@ void TcPlan::build(const Plan &plan) {
   for (const Task &t : syrk_) {
     const FrontInfo &F = plan.fronts[t.front];
     if (!(t.a >= 0 && t.a < F.nrow && t.b >= 0 && t.b <= t.a && t.c == 1)) fail("syrk");
+  }
+  for (const Task &t : pairs_) {
+    const FrontInfo &F = plan.fronts[t.front];
+    if (!(t.a >= 0 && t.a < F.nrow && t.a % (2 * kTileM) == 0 && t.b >= 0 && t.b <= t.a &&
+          t.b % kSyrkN == 0 && t.c == 1))
+      fail("syrk pair");
   }
   for (const Task &t : trsm_) {
     const FrontInfo &F = plan.fronts[t.front];
@@ -736,6 +951,7 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_potrf_ = up(potrf_);
   d_trsm_ = up(trsm_);
   d_syrk_ = up(syrk_);
+  d_pairs_ = up(pairs_);
   d_maps_ = cv.take<CUtensorMap>(2 * std::max(nfronts_, 1) + 1);  // L, Llo, the inverse scratch
   d_inv_ = cv.take<float>((size_t)max_slots_ * kTileM * kTileN);
   ready_ = false;
@@ -781,6 +997,7 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, 128>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<1, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<3, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
+  cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
   cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfInvSmem);
   ready_ = true;
 }
@@ -825,9 +1042,15 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
         gemm(s.trsm_e - s.trsm_b, dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, status, st);
     }
     const Level &lv = levels_[li];
-    if (lv.syrk_e > lv.syrk_b)
+    if (split == 3 && lv.pair_e > lv.pair_b) {  // cluster pairs sharing B by multicast
+      const int np = lv.pair_e - lv.pair_b;
+      note_launch();
+      tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, Cfg<3, kSyrkN>::smem, st>>>(
+          dp, d_pairs_ + lv.pair_b, np, maps, maps_lo, U, status);
+    } else if (lv.syrk_e > lv.syrk_b) {
       syrk3(lv.syrk_e - lv.syrk_b, dp, d_syrk_ + lv.syrk_b, maps, maps_lo, inv_map, L, Llo, U, status,
             st);
+    }
   }
 }
 
