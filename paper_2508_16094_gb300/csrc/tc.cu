@@ -608,13 +608,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 // of its factor, written row-major (128 x 128, zero outside the lower kb x kb
 // triangle) to scratch slot `b` for the triangular solve of the rows below as
 // a tensor-core product, and (when Dinv is given) in the layout of the
-// persistent solve. Both are blocked in 32-column panels: warp 0 factors the
-// 32 x 32 diagonal block, one thread per row solves the rows below it, all
-// threads update the trailing block; the inverse takes the four 32 x 32
-// diagonal blocks in four warps, then the off-diagonal blocks by their
-// distance from the diagonal (X_ij = -X_ii sum_k L_ik X_kj). A non-positive
-// pivot is replaced by a large value (static pivoting) and counted.
-constexpr int kLS = 129;  // padded row of the shared-memory blocks
+// persistent solve. Both run right-looking, one column of the factor (one row
+// of the inverse) per step, on register tiles: thread (ty, tx) of a 16 x 16
+// grid owns rows ty + 16a and columns tx + 16b of the lower tiles a >= b (36
+// entries). The column (row) a step needs is published in shared memory,
+// double-buffered, so a step costs one barrier; the loop over the 16 columns
+// of a tile column stays rolled, which keeps the code that runs once per
+// launch small. A non-positive pivot is replaced by a large value (static
+// pivoting) and counted.
+constexpr int kLS = 129;  // padded row of the shared-memory copy of the factor
 __global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *__restrict__ tasks,
                                                         float *__restrict__ L,
                                                         float *__restrict__ Linv,
@@ -623,195 +625,145 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *
   const FrontInfo F = dp.fronts[tk.front];
   const int k = tk.a, slot = tk.b, kb = min(TcPlan::kNb, F.ncol - k);
   extern __shared__ float smf[];
-  float *A = smf;                  // [128][129] factor
-  float *X = A + 128 * kLS;        // [128][129] inverse
-  float *T = X + 128 * kLS;        // [3][32][33] products of the off-diagonal step
-  float *rd = T + 3 * 32 * 33;     // [128] reciprocals of the diagonal of the factor
-  float *col = rd + 128;           // [32] column broadcast of the diagonal-block step
+  float *Ls = smf;              // [128][129] the factor, read by the inverse
+  float *buf = Ls + 128 * kLS;  // [2][128] published column of the factor / row of the inverse
+  float *rdv = buf + 2 * 128;   // [128] 1 / L_jj
+  float *sqv = rdv + 128;       // [128] L_jj
   float *g = L + F.loff + (int64_t)k * F.ld + k;
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  for (int e = tid; e < 128 * 128; e += 256) {
-    const int r = e >> 7, c = e & 127;
-    A[r * kLS + c] = (r < kb && c <= r) ? g[(int64_t)r * F.ld + c] : 0.f;
-    X[r * kLS + c] = 0.f;
-  }
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  float acc[8][8];  // entries a >= b only
+#pragma unroll
+  for (int a = 0; a < 8; a++)
+#pragma unroll
+    for (int b = 0; b <= a; b++) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      acc[a][b] = (r < kb && c <= r) ? g[(int64_t)r * F.ld + c] : 0.f;
+    }
+  if (tx == 0)
+#pragma unroll
+    for (int a = 0; a < 8; a++) buf[ty + 16 * a] = acc[a][0];
   __syncthreads();
-  for (int c0 = 0; c0 < kb; c0 += 32) {
-    const int pb = min(32, kb - c0);
-    if (warp == 0) {  // 32 x 32 diagonal block: lane i holds row i in registers;
-                      // each column is broadcast through shared memory (right-looking)
-      float rw[32];
-      const int i = c0 + lane;
+  // Cholesky: step j reads column j (updated through step j - 1), applies the
+  // rank-1 update of the trailing entries and publishes column j + 1.
 #pragma unroll
-      for (int m = 0; m < 32; m++) rw[m] = (lane < pb && m <= lane) ? A[i * kLS + c0 + m] : 0.f;
+  for (int jb = 0; jb < 8; jb++) {
+    if (16 * jb < kb) {
+#pragma unroll 1
+      for (int jj = 0; jj < 16; jj++) {
+        const int j = 16 * jb + jj;
+        if (j >= kb) break;
+        const float *cb = buf + (j & 1) * 128;
+        float d = cb[j];
+        const bool bad = !(d > 0.f) || !(d < 3.0e38f);
+        if (bad) d = 1e30f;
+        const float sq = sqrtf(d), rs = 1.f / sq;
+        if (tid == 0) {
+          rdv[j] = rs;
+          sqv[j] = sq;
+          if (bad) atomicAdd(&status[ST_PERTURBED], 1);
+        }
+        float u[8], v[8];
 #pragma unroll
-      for (int j = 0; j < 32; j++) {
-        if (j < pb) {
-          if (lane == j) {
-            float d = rw[j];
-            if (!(d > 0.f) || !(d < 3.0e38f)) {
-              d = 1e30f;
-              atomicAdd(&status[ST_PERTURBED], 1);
+        for (int a = jb; a < 8; a++) {
+          const int r = ty + 16 * a, c = tx + 16 * a;
+          u[a] = r > j ? cb[r] * rs : 0.f;
+          v[a] = c > j ? cb[c] * rs : 0.f;
+        }
+#pragma unroll
+        for (int a = jb; a < 8; a++)
+#pragma unroll
+          for (int b = jb; b <= a; b++) acc[a][b] = fmaf(-u[a], v[b], acc[a][b]);
+        float *nb = buf + ((j + 1) & 1) * 128;
+        if (jj < 15) {
+          if (tx == jj + 1)
+#pragma unroll
+            for (int a = jb; a < 8; a++) nb[ty + 16 * a] = acc[a][jb];
+        } else if (jb < 7) {
+          if (tx == 0)
+#pragma unroll
+            for (int a = jb + 1; a < 8; a++) nb[ty + 16 * a] = acc[a][jb + 1];
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // the factor: column c scaled by 1 / L_cc below the diagonal, L_cc on it
+#pragma unroll
+  for (int a = 0; a < 8; a++)
+#pragma unroll
+    for (int b = 0; b <= a; b++) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      float x = 0.f;
+      if (r < kb && c < r) x = acc[a][b] * rdv[c];
+      if (r < kb && c == r) x = sqv[c];
+      Ls[r * kLS + c] = x;
+      if (r < kb && c <= r) g[(int64_t)r * F.ld + c] = x;
+    }
+  // inverse X = L^{-1}: Y starts as I; step j takes row j of X = Y_j / L_jj
+  // (published) and subtracts L_ij times it from the rows i > j of Y.
+#pragma unroll
+  for (int a = 0; a < 8; a++)
+#pragma unroll
+    for (int b = 0; b <= a; b++) acc[a][b] = (a == b && tx == ty) ? 1.f : 0.f;
+  if (ty == 0) buf[tx] = acc[0][0] * rdv[0];
+  __syncthreads();
+#pragma unroll
+  for (int jb = 0; jb < 8; jb++) {
+    if (16 * jb < kb) {
+#pragma unroll 1
+      for (int jj = 0; jj < 16; jj++) {
+        const int j = 16 * jb + jj;
+        if (j >= kb) break;
+        const float *xr = buf + (j & 1) * 128;
+        float l[8], x[8];
+#pragma unroll
+        for (int a = jb; a < 8; a++) {
+          const int r = ty + 16 * a;
+          l[a] = r > j ? Ls[r * kLS + j] : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b <= jb; b++) x[b] = xr[tx + 16 * b];
+#pragma unroll
+        for (int a = jb; a < 8; a++)
+#pragma unroll
+          for (int b = 0; b <= jb && b <= a; b++) acc[a][b] = fmaf(-l[a], x[b], acc[a][b]);
+        const int jn = j + 1;
+        float *nb = buf + (jn & 1) * 128;
+        if (jn < kb) {
+          if (jj < 15) {
+            if (ty == jj + 1) {
+              const float s = rdv[jn];
+#pragma unroll
+              for (int b = 0; b <= jb; b++) nb[tx + 16 * b] = acc[jb][b] * s;
             }
-            rw[j] = sqrtf(d);
-            rd[c0 + j] = 1.f / rw[j];
-          }
-          __syncwarp();
-          if (lane > j) rw[j] *= rd[c0 + j];
-          col[lane] = rw[j];  // L[c0 + lane][c0 + j] (0 above the diagonal)
-          __syncwarp();
+          } else if (jb < 7) {
+            if (ty == 0) {
+              const float s = rdv[jn];
 #pragma unroll
-          for (int m = j + 1; m < 32; m++)
-            if (lane >= m) rw[m] = fmaf(-rw[j], col[m], rw[m]);
-          __syncwarp();
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < 32; m++)
-        if (lane < pb && m <= lane) A[i * kLS + c0 + m] = rw[m];
-    }
-    __syncthreads();
-    {  // rows below the diagonal block: x L11^T = a, one thread per row, the
-       // row held in registers and updated column by column (independent FMAs)
-      const int r = c0 + pb + tid;
-      if (r < kb) {
-        float *ar = A + r * kLS + c0;
-        float x[32];
-#pragma unroll
-        for (int m = 0; m < 32; m++) x[m] = m < pb ? ar[m] : 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; j++) {
-          if (j < pb) {
-            x[j] *= rd[c0 + j];
-#pragma unroll
-            for (int m = j + 1; m < 32; m++)
-              if (m < pb) x[m] = fmaf(-x[j], A[(c0 + m) * kLS + c0 + j], x[m]);
+              for (int b = 0; b <= jb + 1; b++) nb[tx + 16 * b] = acc[jb + 1][b] * s;
+            }
           }
         }
-#pragma unroll
-        for (int m = 0; m < 32; m++)
-          if (m < pb) ar[m] = x[m];
+        __syncthreads();
       }
     }
-    __syncthreads();
-    // trailing block [t0, kb)^2, lower part: thread (ty, tx) owns rows
-    // t0 + ty + 16a and columns t0 + tx + 16b (6 x 6 independent sums)
-    const int t0 = c0 + pb;
-    if (t0 < kb) {
-      const int ty = tid / 16, tx = tid % 16;
-      float acc[6][6];
-#pragma unroll
-      for (int a2 = 0; a2 < 6; a2++)
-#pragma unroll
-        for (int b2 = 0; b2 < 6; b2++) acc[a2][b2] = 0.f;
-#pragma unroll 4
-      for (int m = 0; m < pb; m++) {
-        float ra[6], cb[6];
-#pragma unroll
-        for (int a2 = 0; a2 < 6; a2++) {
-          const int r = min(t0 + ty + 16 * a2, 127), c = min(t0 + tx + 16 * a2, 127);
-          ra[a2] = A[r * kLS + c0 + m];
-          cb[a2] = A[c * kLS + c0 + m];
-        }
-#pragma unroll
-        for (int a2 = 0; a2 < 6; a2++)
-#pragma unroll
-          for (int b2 = 0; b2 < 6; b2++) acc[a2][b2] = fmaf(ra[a2], cb[b2], acc[a2][b2]);
-      }
-#pragma unroll
-      for (int a2 = 0; a2 < 6; a2++)
-#pragma unroll
-        for (int b2 = 0; b2 < 6; b2++) {
-          const int r = t0 + ty + 16 * a2, c = t0 + tx + 16 * b2;
-          if (r < kb && c <= r) A[r * kLS + c] -= acc[a2][b2];
-        }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < kb * kb; e += 256) {
-    const int r = e / kb, c = e % kb;
-    if (c <= r) g[(int64_t)r * F.ld + c] = A[r * kLS + c];
-  }
-  // inverse: diagonal 32 x 32 blocks, one warp each, lane = column (held in
-  // registers, updated row by row with independent FMAs)
-  if (warp < 4) {
-    const int b0 = 32 * warp, bb = min(32, kb - b0);
-    if (lane < bb) {
-      const int c = b0 + lane;
-      float x[32];
-#pragma unroll
-      for (int r = 0; r < 32; r++) x[r] = (r == lane) ? 1.f : 0.f;
-#pragma unroll
-      for (int r = 0; r < 32; r++) {
-        if (r < bb && r >= lane) {
-          x[r] *= rd[b0 + r];
-#pragma unroll
-          for (int m = r + 1; m < 32; m++)
-            if (m < bb) x[m] = fmaf(-A[(b0 + m) * kLS + b0 + r], x[r], x[m]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < 32; r++)
-        if (r < bb && r >= lane) X[(b0 + r) * kLS + c] = x[r];
-    }
-  }
-  __syncthreads();
-  // off-diagonal blocks (i, j), i = j + d: T = sum_{m in blocks j..i-1} L[R][m] X[m][C],
-  // then X[R][C] = -sum_{m in block i, m <= R} X[R][m] T[m][C]; each thread
-  // takes four consecutive columns C
-  for (int d = 1; d < 4; d++) {
-    const int np = 4 - d;
-    for (int e = tid; e < np * 256; e += 256) {
-      const int j = e / 256, i = j + d, rr = (e % 256) / 8, cq = e % 8;
-      const int R = 32 * i + rr, C = 32 * j + 4 * cq;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      if (R < kb)
-#pragma unroll 4
-        for (int m = 32 * j; m < 32 * i; m++) {
-          const float a = A[R * kLS + m];
-          const float *xm = X + m * kLS + C;
-          s0 = fmaf(a, xm[0], s0);
-          s1 = fmaf(a, xm[1], s1);
-          s2 = fmaf(a, xm[2], s2);
-          s3 = fmaf(a, xm[3], s3);
-        }
-      float *t = T + (j * 32 + rr) * 33 + 4 * cq;
-      t[0] = s0; t[1] = s1; t[2] = s2; t[3] = s3;
-    }
-    __syncthreads();
-    for (int e = tid; e < np * 256; e += 256) {
-      const int j = e / 256, i = j + d, rr = (e % 256) / 8, cq = e % 8;
-      const int R = 32 * i + rr, C = 32 * j + 4 * cq;
-      if (R < kb) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll 4
-        for (int mm = 0; mm <= rr; mm++) {
-          const float xv = X[R * kLS + 32 * i + mm];
-          const float *t = T + (j * 32 + mm) * 33 + 4 * cq;
-          s0 = fmaf(xv, t[0], s0);
-          s1 = fmaf(xv, t[1], s1);
-          s2 = fmaf(xv, t[2], s2);
-          s3 = fmaf(xv, t[3], s3);
-        }
-        float *xr = X + R * kLS + C;
-        xr[0] = -s0; xr[1] = -s1; xr[2] = -s2; xr[3] = -s3;
-      }
-    }
-    __syncthreads();
   }
   float *out = Linv + (int64_t)slot * 128 * 128;
-  for (int e = tid; e < 128 * 128; e += 256) out[e] = X[(e >> 7) * kLS + (e & 127)];
-  if (Dinv) {  // persistent-solve copy: kb rows of round_up(kb, 4) floats
-    const int ldi = (kb + 3) & ~3;
-    float *o2 = Dinv + dp.fs_dinv_off[dp.fs_first_slot[tk.front] + k / TcPlan::kNb];
-    for (int e = tid; e < kb * ldi; e += 256) {
-      const int r = e / ldi, c = e % ldi;
-      o2[e] = (c <= r && c < kb) ? X[r * kLS + c] : 0.f;
+  const int ldi = (kb + 3) & ~3;
+  float *o2 = Dinv ? Dinv + dp.fs_dinv_off[dp.fs_first_slot[tk.front] + k / TcPlan::kNb] : nullptr;
+#pragma unroll
+  for (int a = 0; a < 8; a++)
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      float x = 0.f;
+      if (b <= a) x = (r < kb && c <= r) ? acc[a][b] * rdv[r] : 0.f;
+      out[r * 128 + c] = x;
+      if (o2 && r < kb && c < ldi) o2[r * ldi + c] = x;
     }
-  }
 }
 
-constexpr int kPotrfInvSmem = (2 * 128 * kLS + 3 * 32 * 33 + 128 + 32) * 4;
+constexpr int kPotrfInvSmem = (128 * kLS + 4 * 128) * 4;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
