@@ -41,44 +41,71 @@ __global__ void assemble_kernel(DevPlan dp, const double *__restrict__ jv,
   }
 }
 
-// Front assembly: one 32x32 tile of a front's lower triangle per block. Each
-// entry is the sum, over the children in ascending order, of the matching
-// entry of the child's update matrix (through the child->front inverse map).
+// Front assembly: one 32x32 tile of a front's lower triangle per block of 128
+// threads (eight entries each). Each entry is the sum, over the children in
+// ascending order, of the matching entry of the child's update matrix (through
+// the child->front inverse map). The maps of up to four children are staged
+// together (one memory round trip), and a child none of whose rows or none of
+// whose columns fall in the tile is skipped by the whole block.
+constexpr int kBuildThreads = 128, kBuildGroup = 4;
 template <typename T>
-__global__ void __launch_bounds__(256) build_front_kernel(DevPlan dp, int32_t task0,
-                                                          T *__restrict__ L, T *__restrict__ U) {
+__global__ void __launch_bounds__(kBuildThreads) build_front_kernel(DevPlan dp, int32_t task0,
+                                                                    T *__restrict__ L,
+                                                                    T *__restrict__ U) {
   const Task tk = dp.build[task0 + blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
   const int nf = F.ncol + F.nrow;
   const int r0 = tk.a, c0 = tk.b;
-  __shared__ int32_t rinv[kBuildTile], cinv[kBuildTile];
-  T acc[4] = {0, 0, 0, 0};
-  const int tid = threadIdx.x;
-  for (int ci = F.child_begin; ci < F.child_end; ci++) {
-    const FrontInfo C = dp.fronts[dp.children[ci]];
+  __shared__ int32_t map[kBuildGroup][2 * kBuildTile];  // row maps, then column maps
+  __shared__ int32_t hit[kBuildGroup][2];               // some row / some column maps into the child
+  __shared__ int64_t uoff[kBuildGroup];
+  __shared__ int32_t uld[kBuildGroup];
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  T acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) acc[i] = T(0);
+  for (int cg = F.child_begin; cg < F.child_end; cg += kBuildGroup) {
+    const int nc = min(kBuildGroup, F.child_end - cg);
     __syncthreads();
-    if (tid < kBuildTile) {
-      rinv[tid] = (r0 + tid < nf) ? dp.inv[C.inv_off + r0 + tid] : -1;
-    } else if (tid < 2 * kBuildTile) {
-      const int c = c0 + tid - kBuildTile;
-      cinv[tid - kBuildTile] = (c < nf) ? dp.inv[C.inv_off + c] : -1;
+    // a warp's 32 entries are one child's row maps or column maps
+    for (int e = tid; e < nc * 2 * kBuildTile; e += kBuildThreads) {
+      const int q = e / (2 * kBuildTile), m = e % (2 * kBuildTile);
+      const FrontInfo C = dp.fronts[dp.children[cg + q]];
+      const int idx = m < kBuildTile ? r0 + m : c0 + m - kBuildTile;
+      const int32_t t = idx < nf ? dp.inv[C.inv_off + idx] : -1;
+      map[q][m] = t;
+      const unsigned any = __ballot_sync(0xffffffffu, t >= 0);
+      if (lane == 0) hit[q][m / kBuildTile] = any != 0u;
+      if (m == 0) {
+        uoff[q] = C.uoff;
+        uld[q] = C.uld;
+      }
     }
     __syncthreads();
+    for (int q = 0; q < nc; q++) {
+      if (!hit[q][0] || !hit[q][1]) continue;
+      const int b = map[q][kBuildTile + lane];
+      const T *Uc = U + uoff[q];
+      const int64_t ldq = uld[q];
+      T v[8];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int e = tid + 256 * q, rr = e / kBuildTile, cc = e % kBuildTile;
-      const int a = rinv[rr], b = cinv[cc];
-      if (a >= 0 && b >= 0 && r0 + rr >= c0 + cc) acc[q] += U[C.uoff + (int64_t)a * C.uld + b];
+      for (int i = 0; i < 8; i++) {
+        const int rr = w + 4 * i;
+        const int a = map[q][rr];
+        v[i] = (a >= 0 && b >= 0 && r0 + rr >= c0 + lane) ? Uc[a * ldq + b] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i++) acc[i] += v[i];
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int e = tid + 256 * q, r = r0 + e / kBuildTile, c = c0 + e % kBuildTile;
+  for (int i = 0; i < 8; i++) {
+    const int r = r0 + w + 4 * i, c = c0 + lane;
     if (r >= nf || c >= nf) continue;
     if (c < F.ncol) {
-      L[F.loff + (int64_t)r * F.ld + c] = (r >= c) ? acc[q] : T(0);
+      L[F.loff + (int64_t)r * F.ld + c] = (r >= c) ? acc[i] : T(0);
     } else if (r >= c) {
-      U[F.uoff + (int64_t)(r - F.ncol) * F.uld + (c - F.ncol)] = acc[q];
+      U[F.uoff + (int64_t)(r - F.ncol) * F.uld + (c - F.ncol)] = acc[i];
     }
   }
 }
@@ -305,7 +332,7 @@ template <typename T>
 void launch_build_level(const DevPlan &dp, const LevelPlan &LP, const double *kval, T *L, T *U,
                         cudaStream_t st) {
   if (LP.build_e > LP.build_b)
-    { note_launch(); build_front_kernel<T><<<LP.build_e - LP.build_b, 256, 0, st>>>(dp, LP.build_b, L, U); }
+    { note_launch(); build_front_kernel<T><<<LP.build_e - LP.build_b, kBuildThreads, 0, st>>>(dp, LP.build_b, L, U); }
   if (LP.k_e > LP.k_b)
     { note_launch(); kadd_kernel<T><<<grid_for(LP.k_e - LP.k_b, 256), 256, 0, st>>>(dp, LP.k_b, LP.k_e, kval, L); }
 }

@@ -608,43 +608,56 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 // of its factor, written row-major (128 x 128, zero outside the lower kb x kb
 // triangle) to scratch slot `b` for the triangular solve of the rows below as
 // a tensor-core product, and (when Dinv is given) in the layout of the
-// persistent solve. Both run right-looking, one column of the factor (one row
-// of the inverse) per step, on register tiles: thread (ty, tx) of a 16 x 16
-// grid owns rows ty + 16a and columns tx + 16b of the lower tiles a >= b (36
-// entries). The column (row) a step needs is published in shared memory,
-// double-buffered, so a step costs one barrier; the loop over the 16 columns
-// of a tile column stays rolled, which keeps the code that runs once per
-// launch small. A non-positive pivot is replaced by a large value (static
-// pivoting) and counted.
-constexpr int kLS = 129;  // padded row of the shared-memory copy of the factor
-__global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *__restrict__ tasks,
+// persistent solve. One right-looking step per column j does both: the rank-1
+// update of the trailing block with column j of the factor, and the update of
+// Y (which starts as I and ends as L^{-1} up to row scaling) with the same
+// column and row j of the inverse, Y_j / L_jj. Thread (ty, tx) of a 16 x 16
+// grid holds rows ty + 16a and columns tx + 16b of the lower tiles a >= b of
+// both matrices in registers; the column of the factor, the row of Y and the
+// next pivot's 1 / L_jj (computed by its owner before the barrier) are
+// published in shared memory, double-buffered, so a step costs one barrier.
+// The loop over the 16 columns of a tile column stays rolled, which keeps the
+// code that runs once per launch small. A non-positive pivot is replaced by a
+// large value (static pivoting) and counted.
+__global__ void __launch_bounds__(256, 1) potrf_inv_kernel(DevPlan dp, const Task *__restrict__ tasks,
                                                         float *__restrict__ L,
                                                         float *__restrict__ Linv,
                                                         float *__restrict__ Dinv, int32_t *status) {
   const Task tk = tasks[blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
   const int k = tk.a, slot = tk.b, kb = min(TcPlan::kNb, F.ncol - k);
-  extern __shared__ float smf[];
-  float *Ls = smf;              // [128][129] the factor, read by the inverse
-  float *buf = Ls + 128 * kLS;  // [2][128] published column of the factor / row of the inverse
-  float *rdv = buf + 2 * 128;   // [128] 1 / L_jj
-  float *sqv = rdv + 128;       // [128] L_jj
+  __shared__ float cbuf[2][128];  // column j of the factor (unscaled, updated through step j - 1)
+  __shared__ float ybuf[2][128];  // row j of Y
+  __shared__ float rdv[128];      // 1 / L_jj
+  __shared__ float sqv[128];      // L_jj
   float *g = L + F.loff + (int64_t)k * F.ld + k;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  float acc[8][8];  // entries a >= b only
+  // the pivot of column j, owned by the thread holding entry (j, j)
+  auto pivot = [&](int j, float d) {
+    const bool bad = !(d > 0.f) || !(d < 3.0e38f);
+    if (bad) {
+      d = 1e30f;
+      atomicAdd(&status[ST_PERTURBED], 1);
+    }
+    const float sq = sqrtf(d);
+    sqv[j] = sq;
+    rdv[j] = 1.f / sq;
+  };
+  float acc[8][8], y[8][8];  // entries a >= b only
 #pragma unroll
   for (int a = 0; a < 8; a++)
 #pragma unroll
     for (int b = 0; b <= a; b++) {
       const int r = ty + 16 * a, c = tx + 16 * b;
       acc[a][b] = (r < kb && c <= r) ? g[(int64_t)r * F.ld + c] : 0.f;
+      y[a][b] = (a == b && tx == ty) ? 1.f : 0.f;
     }
   if (tx == 0)
 #pragma unroll
-    for (int a = 0; a < 8; a++) buf[ty + 16 * a] = acc[a][0];
+    for (int a = 0; a < 8; a++) cbuf[0][ty + 16 * a] = acc[a][0];
+  if (ty == 0) ybuf[0][tx] = y[0][0];
+  if (tid == 0) pivot(0, acc[0][0]);
   __syncthreads();
-  // Cholesky: step j reads column j (updated through step j - 1), applies the
-  // rank-1 update of the trailing entries and publishes column j + 1.
 #pragma unroll
   for (int jb = 0; jb < 8; jb++) {
     if (16 * jb < kb) {
@@ -652,96 +665,46 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *
       for (int jj = 0; jj < 16; jj++) {
         const int j = 16 * jb + jj;
         if (j >= kb) break;
-        const float *cb = buf + (j & 1) * 128;
-        float d = cb[j];
-        const bool bad = !(d > 0.f) || !(d < 3.0e38f);
-        if (bad) d = 1e30f;
-        const float sq = sqrtf(d), rs = 1.f / sq;
-        if (tid == 0) {
-          rdv[j] = rs;
-          sqv[j] = sq;
-          if (bad) atomicAdd(&status[ST_PERTURBED], 1);
-        }
-        float u[8], v[8];
+        const float *cb = cbuf[j & 1], *yb = ybuf[j & 1];
+        const float rs = rdv[j];
+        float u[8], v[8], x[8];
 #pragma unroll
         for (int a = jb; a < 8; a++) {
           const int r = ty + 16 * a, c = tx + 16 * a;
-          u[a] = r > j ? cb[r] * rs : 0.f;
+          u[a] = r > j ? cb[r] * rs : 0.f;  // L_rj below the diagonal
           v[a] = c > j ? cb[c] * rs : 0.f;
         }
+#pragma unroll
+        for (int b = 0; b <= jb; b++) x[b] = yb[tx + 16 * b] * rs;  // row j of L^{-1}
 #pragma unroll
         for (int a = jb; a < 8; a++)
 #pragma unroll
           for (int b = jb; b <= a; b++) acc[a][b] = fmaf(-u[a], v[b], acc[a][b]);
-        float *nb = buf + ((j + 1) & 1) * 128;
-        if (jj < 15) {
-          if (tx == jj + 1)
-#pragma unroll
-            for (int a = jb; a < 8; a++) nb[ty + 16 * a] = acc[a][jb];
-        } else if (jb < 7) {
-          if (tx == 0)
-#pragma unroll
-            for (int a = jb + 1; a < 8; a++) nb[ty + 16 * a] = acc[a][jb + 1];
-        }
-        __syncthreads();
-      }
-    }
-  }
-  // the factor: column c scaled by 1 / L_cc below the diagonal, L_cc on it
-#pragma unroll
-  for (int a = 0; a < 8; a++)
-#pragma unroll
-    for (int b = 0; b <= a; b++) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      float x = 0.f;
-      if (r < kb && c < r) x = acc[a][b] * rdv[c];
-      if (r < kb && c == r) x = sqv[c];
-      Ls[r * kLS + c] = x;
-      if (r < kb && c <= r) g[(int64_t)r * F.ld + c] = x;
-    }
-  // inverse X = L^{-1}: Y starts as I; step j takes row j of X = Y_j / L_jj
-  // (published) and subtracts L_ij times it from the rows i > j of Y.
-#pragma unroll
-  for (int a = 0; a < 8; a++)
-#pragma unroll
-    for (int b = 0; b <= a; b++) acc[a][b] = (a == b && tx == ty) ? 1.f : 0.f;
-  if (ty == 0) buf[tx] = acc[0][0] * rdv[0];
-  __syncthreads();
-#pragma unroll
-  for (int jb = 0; jb < 8; jb++) {
-    if (16 * jb < kb) {
-#pragma unroll 1
-      for (int jj = 0; jj < 16; jj++) {
-        const int j = 16 * jb + jj;
-        if (j >= kb) break;
-        const float *xr = buf + (j & 1) * 128;
-        float l[8], x[8];
-#pragma unroll
-        for (int a = jb; a < 8; a++) {
-          const int r = ty + 16 * a;
-          l[a] = r > j ? Ls[r * kLS + j] : 0.f;
-        }
-#pragma unroll
-        for (int b = 0; b <= jb; b++) x[b] = xr[tx + 16 * b];
 #pragma unroll
         for (int a = jb; a < 8; a++)
 #pragma unroll
-          for (int b = 0; b <= jb && b <= a; b++) acc[a][b] = fmaf(-l[a], x[b], acc[a][b]);
+          for (int b = 0; b <= jb && b <= a; b++) y[a][b] = fmaf(-u[a], x[b], y[a][b]);
         const int jn = j + 1;
-        float *nb = buf + (jn & 1) * 128;
         if (jn < kb) {
+          float *nc = cbuf[jn & 1], *ny = ybuf[jn & 1];
           if (jj < 15) {
-            if (ty == jj + 1) {
-              const float s = rdv[jn];
+            if (tx == jj + 1) {
 #pragma unroll
-              for (int b = 0; b <= jb; b++) nb[tx + 16 * b] = acc[jb][b] * s;
+              for (int a = jb; a < 8; a++) nc[ty + 16 * a] = acc[a][jb];
+              if (ty == jj + 1) pivot(jn, acc[jb][jb]);
             }
+            if (ty == jj + 1)
+#pragma unroll
+              for (int b = 0; b <= jb; b++) ny[tx + 16 * b] = y[jb][b];
           } else if (jb < 7) {
-            if (ty == 0) {
-              const float s = rdv[jn];
+            if (tx == 0) {
 #pragma unroll
-              for (int b = 0; b <= jb + 1; b++) nb[tx + 16 * b] = acc[jb + 1][b] * s;
+              for (int a = jb + 1; a < 8; a++) nc[ty + 16 * a] = acc[a][jb + 1];
+              if (ty == 0) pivot(jn, acc[jb + 1][jb + 1]);
             }
+            if (ty == 0)
+#pragma unroll
+              for (int b = 0; b <= jb + 1; b++) ny[tx + 16 * b] = y[jb + 1][b];
           }
         }
         __syncthreads();
@@ -756,14 +719,16 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(DevPlan dp, const Task *
 #pragma unroll
     for (int b = 0; b < 8; b++) {
       const int r = ty + 16 * a, c = tx + 16 * b;
-      float x = 0.f;
-      if (b <= a) x = (r < kb && c <= r) ? acc[a][b] * rdv[r] : 0.f;
-      out[r * 128 + c] = x;
-      if (o2 && r < kb && c < ldi) o2[r * ldi + c] = x;
+      float xv = 0.f;
+      if (b <= a) {
+        if (r < kb && c < r) g[(int64_t)r * F.ld + c] = acc[a][b] * rdv[c];
+        if (r < kb && c == r) g[(int64_t)r * F.ld + c] = sqv[c];
+        if (r < kb && c <= r) xv = y[a][b] * rdv[r];
+      }
+      out[r * 128 + c] = xv;
+      if (o2 && r < kb && c < ldi) o2[r * ldi + c] = xv;
     }
 }
-
-constexpr int kPotrfInvSmem = (128 * kLS + 4 * 128) * 4;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -950,7 +915,6 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   cudaFuncSetAttribute(tc_gemm_kernel<1, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<3, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
   cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
-  cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfInvSmem);
   ready_ = true;
 }
 
@@ -989,7 +953,7 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
       if (s.gemm_e > s.gemm_b)
         gemm(s.gemm_e - s.gemm_b, dp, d_gemm_ + s.gemm_b, maps, inv_map, L, U, status, st);
       if (s.potrf_e > s.potrf_b)
-        { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, kPotrfInvSmem, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, Dinv, status); }
+        { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, 0, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, Dinv, status); }
       if (s.trsm_e > s.trsm_b)
         gemm(s.trsm_e - s.trsm_b, dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, status, st);
     }
