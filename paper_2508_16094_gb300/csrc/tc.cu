@@ -27,6 +27,7 @@ namespace {
 constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kSyrkN = 256;
 constexpr int kMaxClusters = 76;  // CTA pairs of the persistent SYRK (152 SMs)
 constexpr int kSuper = 512;  // columns per super-step of the left-looking panel updates
+constexpr int kAheadFronts = 2;  // levels with at most this many fronts run the look-ahead
 constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per 128-row operand tile
 constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
 // Ring depth: as many stages as fit in ~200 KB (each stage: A and B tiles, and
@@ -758,56 +759,68 @@ void TcPlan::build(const Plan &plan) {
   for (size_t li = 0; li < plan.levels.size(); li++) {
     const LevelPlan &LP = plan.levels[li];
     Level &lv = levels_[li];
-    // Left-looking in super-steps of kSuper columns: one launch updates all
-    // block columns of a super-step with the columns before it (many tiles, the
-    // long K), then each 128-wide block column takes the columns of its own
-    // super-step before it (short K), is factored and solved below.
+    // Left-looking in super-steps of kSuper columns. Super-step s (columns
+    // [K0, K0 + kSuper)) starts with the update of its columns by the columns
+    // before it; then each 128-wide block column takes the columns of its own
+    // super-step before it (short K), is factored and solved below. On a level
+    // of at most kAheadFronts fronts that chain of block steps is latency-bound,
+    // so the update of super-step s + 1 by the columns before K0 runs ahead on
+    // the side stream meanwhile, and super-step s + 1 starts with the update by
+    // super-step s's columns only (K in [K0, K0 + kSuper)).
     auto enc = [](int32_t kbeg, int32_t kend) { return 0 | (kbeg / kNb) << 2 | (kend / kNb) << 17; };
-    for (int32_t k = 0; k < LP.max_ncol; k += kNb) {
-      const int32_t K0 = k - k % kSuper;
-      if (k == K0 && K0 > 0) {
-        Step out{};
-        out.gemm_b = (int)gemm_.size();
+    auto span = [&](int32_t c0, int32_t kbeg, int32_t kend) {  // columns [c0, c0 + kSuper), all fronts
+      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+        const int32_t s = plan.level_fronts[t];
+        const FrontInfo &F = plan.fronts[s];
+        for (int32_t c = c0; c < std::min(F.ncol, c0 + kSuper); c += kNb)
+          for (int32_t i0 = c; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, c, enc(kbeg, kend)});
+      }
+    };
+    bool ahead_done = false;  // the previous super-step ran this one's update ahead
+    for (int32_t K0 = 0; K0 < LP.max_ncol; K0 += kSuper) {
+      Super sp{};
+      sp.now_b = (int)gemm_.size();
+      if (K0 > 0) span(K0, ahead_done ? K0 - kSuper : 0, K0);
+      sp.now_e = (int)gemm_.size();
+      sp.ahead_b = (int)gemm_.size();
+      if (K0 > 0 && K0 + kSuper < LP.max_ncol && LP.front_e - LP.front_b <= kAheadFronts)
+        span(K0 + kSuper, 0, K0);
+      sp.ahead_e = (int)gemm_.size();
+      ahead_done = sp.ahead_e > sp.ahead_b;
+      sp.step_b = (int)lv.steps.size();
+      for (int32_t k = K0; k < std::min(LP.max_ncol, K0 + kSuper); k += kNb) {
+        Step st{};
+        st.gemm_b = (int)gemm_.size();
+        for (int32_t t = LP.front_b; t < LP.front_e && k > K0; t++) {
+          const int32_t s = plan.level_fronts[t];
+          const FrontInfo &F = plan.fronts[s];
+          if (F.ncol <= k) continue;
+          for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, k, enc(K0, k)});
+        }
+        st.gemm_e = (int)gemm_.size();
+        st.potrf_b = (int)potrf_.size();
+        int32_t slot = 0;
+        for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+          const int32_t s = plan.level_fronts[t];
+          if (plan.fronts[s].ncol > k) potrf_.push_back({s, k, slot++, 0});
+        }
+        st.potrf_e = (int)potrf_.size();
+        max_slots_ = std::max(max_slots_, slot);
+        st.trsm_b = (int)trsm_.size();
+        slot = 0;
         for (int32_t t = LP.front_b; t < LP.front_e; t++) {
           const int32_t s = plan.level_fronts[t];
           const FrontInfo &F = plan.fronts[s];
-          for (int32_t c = K0; c < std::min(F.ncol, K0 + kSuper); c += kNb)
-            for (int32_t i0 = c; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, c, enc(0, K0)});
+          if (F.ncol <= k) continue;
+          const int32_t kb = std::min(kNb, F.ncol - k);
+          for (int32_t i0 = k + kb; i0 < F.ncol + F.nrow; i0 += kTileM) trsm_.push_back({s, i0, k, 2 | (slot << 2)});
+          slot++;
         }
-        out.gemm_e = (int)gemm_.size();
-        out.potrf_b = out.potrf_e = (int)potrf_.size();
-        out.trsm_b = out.trsm_e = (int)trsm_.size();
-        if (out.gemm_e > out.gemm_b) lv.steps.push_back(out);
+        st.trsm_e = (int)trsm_.size();
+        lv.steps.push_back(st);
       }
-      Step st{};
-      st.gemm_b = (int)gemm_.size();
-      for (int32_t t = LP.front_b; t < LP.front_e && k > K0; t++) {
-        const int32_t s = plan.level_fronts[t];
-        const FrontInfo &F = plan.fronts[s];
-        if (F.ncol <= k) continue;
-        for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, k, enc(K0, k)});
-      }
-      st.gemm_e = (int)gemm_.size();
-      st.potrf_b = (int)potrf_.size();
-      int32_t slot = 0;
-      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
-        const int32_t s = plan.level_fronts[t];
-        if (plan.fronts[s].ncol > k) potrf_.push_back({s, k, slot++, 0});
-      }
-      st.potrf_e = (int)potrf_.size();
-      max_slots_ = std::max(max_slots_, slot);
-      st.trsm_b = (int)trsm_.size();
-      slot = 0;
-      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
-        const int32_t s = plan.level_fronts[t];
-        const FrontInfo &F = plan.fronts[s];
-        if (F.ncol <= k) continue;
-        const int32_t kb = std::min(kNb, F.ncol - k);
-        for (int32_t i0 = k + kb; i0 < F.ncol + F.nrow; i0 += kTileM) trsm_.push_back({s, i0, k, 2 | (slot << 2)});
-        slot++;
-      }
-      st.trsm_e = (int)trsm_.size();
-      lv.steps.push_back(st);
+      sp.step_e = (int)lv.steps.size();
+      lv.supers.push_back(sp);
     }
     lv.syrk_b = (int)syrk_.size();
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
@@ -876,6 +889,14 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
 
 void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!side_) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&side_, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_main_, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_side_, cudaEventDisableTiming) != cudaSuccess)
+      throw std::runtime_error("cannot create the look-ahead stream");
+  }
   L_ = L;
   Llo_ = Llo;
   const size_t nfr = plan.fronts.size();
@@ -918,10 +939,7 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   ready_ = true;
 }
 
-template <int SPLIT, int BN>
-static void gemm_launch(int ntask, const DevPlan &dp, const Task *tasks, const CUtensorMap *maps,
-                        const CUtensorMap *maps_lo, const CUtensorMap *inv_map, float *L,
-                        float *Llo, float *U, int32_t *status, cudaStream_t st) {
+static int sm_count() {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -929,9 +947,24 @@ static void gemm_launch(int ntask, const DevPlan &dp, const Task *tasks, const C
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
+  return sms;
+}
+
+// Persistent launch: at most ctas CTAs (one per SM), each taking tiles ctas apart.
+template <int SPLIT, int BN>
+static void gemm_launch(int ntask, int ctas, const DevPlan &dp, const Task *tasks,
+                        const CUtensorMap *maps, const CUtensorMap *maps_lo,
+                        const CUtensorMap *inv_map, float *L, float *Llo, float *U,
+                        int32_t *status, cudaStream_t st) {
   note_launch();
-  tc_gemm_kernel<SPLIT, BN><<<std::min(ntask, sms), 192, Cfg<SPLIT, BN>::smem, st>>>(
+  tc_gemm_kernel<SPLIT, BN><<<std::min(ntask, std::max(ctas, 1)), 192, Cfg<SPLIT, BN>::smem, st>>>(
       dp, tasks, ntask, maps, maps_lo, inv_map, L, Llo, U, TcPlan::kNb, status);
+}
+
+TcPlan::~TcPlan() {
+  if (ev_main_) cudaEventDestroy(ev_main_);
+  if (ev_side_) cudaEventDestroy(ev_side_);
+  if (side_) cudaStreamDestroy(side_);
 }
 
 void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
@@ -942,30 +975,54 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
   const CUtensorMap *maps_lo = maps + nfronts_;
   const CUtensorMap *inv_map = maps + 2 * nfronts_;
   if (L != L_) throw std::runtime_error("tensor maps were encoded for another factor buffer");
+  if (!side_) throw std::runtime_error("tensor-core factor streams not created");
   float *Llo = Llo_;
-  auto gemm = [&](int n, const DevPlan &d, const Task *t, const CUtensorMap *m, const CUtensorMap *im,
-                  float *l, float *u, int32_t *stt, cudaStream_t s) {
-    gemm3(n, d, t, m, maps_lo, im, l, Llo, u, stt, s);
+  const int sms = sm_count();
+  const int main_ctas = std::min(kMainCtas, sms / 2), side_ctas = sms - main_ctas;
+  auto gemm = [&](const Task *t, int n, int ctas, cudaStream_t s) {
+    gemm3(n, ctas, dp, t, maps, maps_lo, inv_map, L, Llo, U, status, s);
   };
+  bool pending = false;  // look-ahead work on the side stream not yet joined
   for (size_t li = 0; li < levels_.size(); li++) {
-    launch_build_level<float>(dp, plan.levels[li], kval, L, U, st);
-    for (const Step &s : levels_[li].steps) {
-      if (s.gemm_e > s.gemm_b)
-        gemm(s.gemm_e - s.gemm_b, dp, d_gemm_ + s.gemm_b, maps, inv_map, L, U, status, st);
-      if (s.potrf_e > s.potrf_b)
-        { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, 0, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, Dinv, status); }
-      if (s.trsm_e > s.trsm_b)
-        gemm(s.trsm_e - s.trsm_b, dp, d_trsm_ + s.trsm_b, maps, inv_map, L, U, status, st);
-    }
     const Level &lv = levels_[li];
+    launch_build_level<float>(dp, plan.levels[li], kval, L, U, st);
+    for (const Super &sp : lv.supers) {
+      if (pending) {  // this super-step's columns took the look-ahead update
+        cudaStreamWaitEvent(st, ev_side_, 0);
+        pending = false;
+      }
+      const bool ahead = sp.ahead_e > sp.ahead_b;
+      if (ahead) {  // the columns before this super-step are final: fork
+        cudaEventRecord(ev_main_, st);
+        cudaStreamWaitEvent(side_, ev_main_, 0);
+      }
+      if (sp.now_e > sp.now_b) gemm(d_gemm_ + sp.now_b, sp.now_e - sp.now_b, sms, st);
+      const int ctas = ahead ? main_ctas : sms;
+      if (ahead) {
+        gemm(d_gemm_ + sp.ahead_b, sp.ahead_e - sp.ahead_b, side_ctas, side_);
+        cudaEventRecord(ev_side_, side_);
+        pending = true;
+      }
+      for (int i = sp.step_b; i < sp.step_e; i++) {
+        const Step &s = lv.steps[i];
+        if (s.gemm_e > s.gemm_b) gemm(d_gemm_ + s.gemm_b, s.gemm_e - s.gemm_b, ctas, st);
+        if (s.potrf_e > s.potrf_b)
+          { note_launch(); potrf_inv_kernel<<<s.potrf_e - s.potrf_b, 256, 0, st>>>(dp, d_potrf_ + s.potrf_b, L, d_inv_, Dinv, status); }
+        if (s.trsm_e > s.trsm_b) gemm(d_trsm_ + s.trsm_b, s.trsm_e - s.trsm_b, ctas, st);
+      }
+    }
+    if (pending) {
+      cudaStreamWaitEvent(st, ev_side_, 0);
+      pending = false;
+    }
     if (split == 3 && lv.pair_e > lv.pair_b) {  // cluster pairs sharing B by multicast
       const int np = lv.pair_e - lv.pair_b;
       note_launch();
       tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, Cfg<3, kSyrkN>::smem, st>>>(
           dp, d_pairs_ + lv.pair_b, np, maps, maps_lo, U, status);
     } else if (lv.syrk_e > lv.syrk_b) {
-      syrk3(lv.syrk_e - lv.syrk_b, dp, d_syrk_ + lv.syrk_b, maps, maps_lo, inv_map, L, Llo, U, status,
-            st);
+      syrk3(lv.syrk_e - lv.syrk_b, sms, dp, d_syrk_ + lv.syrk_b, maps, maps_lo, inv_map, L, Llo, U,
+            status, st);
     }
   }
 }
