@@ -750,7 +750,7 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     c->have_stale = false;
     if (c->lb_on) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
-      c->tcp.encode(c->plan, (float *)c->L, c->Llo, c->st);
+      c->tcp.encode(c->plan, (float *)c->L, c->Llo, (float *)c->U, c->st);
     } catch (const std::exception &e) {
       c->err = std::string("tensor-core path unavailable: ") + e.what();
     }

@@ -20,6 +20,8 @@
 #include "launch.h"
 #include "tc.h"
 
+#include <cstring>
+
 namespace gipm {
 
 namespace {
@@ -39,6 +41,11 @@ template <int SPLIT, int BN> struct Cfg {
   static constexpr int S = (200 * 1024) / kStage > 4 ? 4 : (200 * 1024) / kStage;
   static constexpr int smem = S * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
 };
+// The SYRK pair kernel adds 4 epilogue warps x 2 x 4 KB of staging after the
+// ring and its barriers (1024-byte aligned for the 128-byte swizzle).
+constexpr int kPairStageOff = Cfg<3, kSyrkN>::S * Cfg<3, kSyrkN>::kStage + 1024;
+constexpr int kPairSmem = kPairStageOff + 4 * 8192 + 1024;
+static_assert(kPairSmem <= 227 * 1024, "SYRK pair kernel shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -108,6 +115,24 @@ __device__ __forceinline__ void tma_load_2d_mc(void *dst, const void *tmap, uint
       " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
       : "memory");
+}
+
+// C[box at (x, y)] += the box in shared memory (128-byte swizzled rows), done
+// in L2 by the TMA unit; the issuing thread tracks it as a bulk group.
+__device__ __forceinline__ void tma_reduce_add_2d(const void *tmap, const void *src, int x, int y) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3}], [%1];"
+      ::"l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until at most N of this thread's bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -450,8 +475,8 @@ template <int SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     tc_syrk_pair_kernel(DevPlan dp, const Task *__restrict__ pairs, int npair,
                         const CUtensorMap *__restrict__ maps,
-                        const CUtensorMap *__restrict__ maps_lo, float *__restrict__ U,
-                        int32_t *status) {
+                        const CUtensorMap *__restrict__ maps_lo,
+                        const CUtensorMap *__restrict__ umaps, int32_t *status) {
   constexpr int BN = 256;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -567,36 +592,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
       mma_commit(drain);
       mbar_wait(drain, 0, status);
     }
-  } else {  // warps 2-5: epilogue of this CTA's tile
+  } else {  // warps 2-5: epilogue of this CTA's tile, 32 rows per warp
+    // Each 32 x 32 block of the accumulator goes (negated) through this warp's
+    // two 4 KB staging buffers in the 128-byte swizzled layout of the U tensor
+    // maps, and is added to U by a TMA reduction in L2: U -= A B^T without
+    // reading U into the SM and with whole 128-byte rows per transfer.
     const int q = warp % 4;
-    const int row = q * 32 + lane;
+    uint8_t *stg = base + kPairStageOff + q * 8192;
+    uint32_t nissued = 0;
     int i = 0;
     for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
       const Task tk = pairs[p];
       const FrontInfo F = dp.fronts[tk.front];
       const int r0 = tk.a + 128 * (int)rank;
-      const int M = min(kTileM, F.nrow - r0), N = min(BN, F.nrow - tk.b);
+      const int N = min(BN, F.nrow - tk.b);
       const int a = i & 1;
       if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (M > 0) {
-        float *C = U + F.uoff + (int64_t)r0 * F.uld + tk.b;
+      if (r0 + 32 * q < F.nrow) {
+        const CUtensorMap *um = umaps + tk.front;
         for (int cb = 0; cb < (N + 31) / 32; cb++) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
-          if (row < M) {
-            float *crow = C + (int64_t)row * F.uld + cb * 32;
-            const int nc = min(32, N - cb * 32);
+          uint8_t *buf = stg + (nissued & 1) * 4096;
+          if (lane == 0) bulk_wait_read<1>();  // the reduction that last read buf is done
+          __syncwarp();
+          uint8_t *rowp = buf + lane * 128;
 #pragma unroll
-            for (int c = 0; c < 32; c++)
-              if (c < nc) crow[c] -= v[c];
-          }
+          for (int j = 0; j < 8; j++)
+            *reinterpret_cast<float4 *>(rowp + ((j ^ (lane & 7)) << 4)) =
+                make_float4(-v[4 * j], -v[4 * j + 1], -v[4 * j + 2], -v[4 * j + 3]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) tma_reduce_add_2d(um, buf, tk.b + 32 * cb, r0 + 32 * q);
+          nissued++;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty[a]);
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -882,12 +919,12 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_trsm_ = up(trsm_);
   d_syrk_ = up(syrk_);
   d_pairs_ = up(pairs_);
-  d_maps_ = cv.take<CUtensorMap>(2 * std::max(nfronts_, 1) + 1);  // L, Llo, the inverse scratch
+  d_maps_ = cv.take<CUtensorMap>(3 * std::max(nfronts_, 1) + 1);  // L, Llo, the inverse scratch, U
   d_inv_ = cv.take<float>((size_t)max_slots_ * kTileM * kTileN);
   ready_ = false;
 }
 
-void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
+void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream_t st) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!side_) {
     int lo = 0, hi = 0;
@@ -899,6 +936,7 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   }
   L_ = L;
   Llo_ = Llo;
+  U_ = U;
   const size_t nfr = plan.fronts.size();
   std::vector<CUtensorMap> maps(2 * nfr);  // panels of L, then of Llo
   for (size_t s = 0; s < 2 * nfr; s++) {
@@ -926,6 +964,23 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
     if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed for the inverse scratch");
     maps.push_back(im);
   }
+  for (size_t s = 0; s < nfr; s++) {  // update matrices, 32 x 32 boxes for the SYRK's reductions
+    const FrontInfo &F = plan.fronts[s];
+    CUtensorMap um;
+    std::memset(&um, 0, sizeof(um));
+    if (F.nrow > 0) {
+      cuuint64_t dims[2] = {(cuuint64_t)F.nrow, (cuuint64_t)F.nrow};
+      cuuint64_t strides[1] = {(cuuint64_t)F.uld * sizeof(float)};
+      cuuint32_t box[2] = {32, 32};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult r = enc(&um, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(U + F.uoff), dims, strides,
+                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        throw std::runtime_error("cuTensorMapEncodeTiled failed for update matrix " + std::to_string(s));
+    }
+    maps.push_back(um);
+  }
   if (!maps.empty())
     if (cudaMemcpyAsync(d_maps_, maps.data(), maps.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -935,7 +990,7 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, cudaStream_t st) {
   cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, 128>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<1, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<3, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
-  cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
+  cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmem);
   ready_ = true;
 }
 
@@ -974,7 +1029,8 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
   const CUtensorMap *maps_lo = maps + nfronts_;
   const CUtensorMap *inv_map = maps + 2 * nfronts_;
-  if (L != L_) throw std::runtime_error("tensor maps were encoded for another factor buffer");
+  const CUtensorMap *umaps = maps + 2 * nfronts_ + 1;
+  if (L != L_ || U != U_) throw std::runtime_error("tensor maps were encoded for other factor buffers");
   if (!side_) throw std::runtime_error("tensor-core factor streams not created");
   float *Llo = Llo_;
   const int sms = sm_count();
@@ -1018,8 +1074,8 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
     if (split == 3 && lv.pair_e > lv.pair_b) {  // cluster pairs sharing B by multicast
       const int np = lv.pair_e - lv.pair_b;
       note_launch();
-      tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, Cfg<3, kSyrkN>::smem, st>>>(
-          dp, d_pairs_ + lv.pair_b, np, maps, maps_lo, U, status);
+      tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, kPairSmem, st>>>(
+          dp, d_pairs_ + lv.pair_b, np, maps, maps_lo, umaps, status);
     } else if (lv.syrk_e > lv.syrk_b) {
       syrk3(lv.syrk_e - lv.syrk_b, sms, dp, d_syrk_ + lv.syrk_b, maps, maps_lo, inv_map, L, Llo, U,
             status, st);

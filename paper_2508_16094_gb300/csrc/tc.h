@@ -26,9 +26,10 @@ class TcPlan {
   // Carve device memory for tasks and tensor maps (cv.base == nullptr: size only).
   void layout(Carve &cv, cudaStream_t st);
   // Encode one TMA tensor map per front panel of the FP32 factor storage L and
-  // of Llo (low parts x - tf32(x) of the finished entries, same layout); also
-  // creates the side stream and events of the look-ahead (once).
-  void encode(const Plan &plan, float *L, float *Llo, cudaStream_t st);
+  // of Llo (low parts x - tf32(x) of the finished entries, same layout), and
+  // one per update matrix in U; also creates the side stream and events of
+  // the look-ahead (once).
+  void encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream_t st);
   bool ready() const { return ready_; }
   // split = 1: plain TF32 products; split = 3: A_lo B + A B_lo + A B
   // (FP32-accurate products on tensor cores; L must be the encoded buffer)
@@ -55,8 +56,8 @@ class TcPlan {
   float *d_inv_ = nullptr;  // inverses of the diagonal blocks of one step (max_slots_ x 128 x 128)
   Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_syrk_ = nullptr,
        *d_pairs_ = nullptr;
-  void *d_maps_ = nullptr;  // 2 nfronts_ + 1 CUtensorMap (128 bytes each)
-  float *L_ = nullptr, *Llo_ = nullptr;
+  void *d_maps_ = nullptr;  // 3 nfronts_ + 1 CUtensorMap (128 bytes each)
+  float *L_ = nullptr, *Llo_ = nullptr, *U_ = nullptr;
   cudaStream_t side_ = nullptr;                              // look-ahead stream (low priority)
   cudaEvent_t ev_main_ = nullptr, ev_side_ = nullptr;        // fork / join
   bool ready_ = false;
