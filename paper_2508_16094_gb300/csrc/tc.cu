@@ -35,17 +35,16 @@ constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
 // Ring depth: as many stages as fit in ~200 KB (each stage: A and B tiles, and
 // their low parts when SPLIT == 3). BN = 256 tiles (SYRK) halve the operand
 // bytes per product of the B side.
+// After the ring and its barriers: the epilogue's staging, 4 warps x 2 x 4 KB
+// (1024-byte aligned for the 128-byte swizzle).
 template <int SPLIT, int BN> struct Cfg {
   static constexpr int kB = BN / 128;                            // 128-row B tiles per stage
   static constexpr int kStage = (SPLIT == 3 ? 2 : 1) * (1 + kB) * kTileBytes;
   static constexpr int S = (200 * 1024) / kStage > 4 ? 4 : (200 * 1024) / kStage;
-  static constexpr int smem = S * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
+  static constexpr int stage_off = S * kStage + 1024 /*barriers*/;
+  static constexpr int smem = stage_off + 4 * 8192 + 1024 /*alignment*/;
+  static_assert(smem <= 227 * 1024, "tensor-core kernel shared memory");
 };
-// The SYRK pair kernel adds 4 epilogue warps x 2 x 4 KB of staging after the
-// ring and its barriers (1024-byte aligned for the 128-byte swizzle).
-constexpr int kPairStageOff = Cfg<3, kSyrkN>::S * Cfg<3, kSyrkN>::kStage + 1024;
-constexpr int kPairSmem = kPairStageOff + 4 * 8192 + 1024;
-static_assert(kPairSmem <= 227 * 1024, "SYRK pair kernel shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -125,6 +124,23 @@ __device__ __forceinline__ void tma_reduce_add_2d(const void *tmap, const void *
       ::"l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(src)), "r"(x), "r"(y)
       : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// C[box at (x, y)] = the box in shared memory (128-byte swizzled rows).
+__device__ __forceinline__ void tma_store_2d(const void *tmap, const void *src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];"
+               ::"l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Writes 32 floats (one row of a 32 x 32 box, `row` = lane) in the 128-byte
+// swizzled layout: 16-byte chunk j of row r sits at chunk j ^ (r % 8).
+template <typename F>
+__device__ __forceinline__ void stage_row(uint8_t *buf, int row, const float (&v)[32], F f) {
+  uint8_t *rowp = buf + row * 128;
+#pragma unroll
+  for (int j = 0; j < 8; j++)
+    *reinterpret_cast<float4 *>(rowp + ((j ^ (row & 7)) << 4)) =
+        make_float4(f(v[4 * j]), f(v[4 * j + 1]), f(v[4 * j + 2]), f(v[4 * j + 3]));
 }
 // Wait until at most N of this thread's bulk groups still read shared memory.
 template <int N>
@@ -286,8 +302,9 @@ template <int SPLIT, int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, int ntask,
                    const CUtensorMap *__restrict__ maps, const CUtensorMap *__restrict__ maps_lo,
-                   const CUtensorMap *__restrict__ inv_map, float *__restrict__ L,
-                   float *__restrict__ Llo, float *__restrict__ U, int nb, int32_t *status) {
+                   const CUtensorMap *__restrict__ inv_map, const CUtensorMap *__restrict__ umaps,
+                   const CUtensorMap *__restrict__ lmaps, const CUtensorMap *__restrict__ llomaps,
+                   float *__restrict__ L, float *__restrict__ U, int nb, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -402,7 +419,8 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else {  // warps 2-5: low parts (mode 2) and the epilogue
     const int q = warp % 4;  // tensor-memory lane quarter this warp may access
-    const int row = q * 32 + lane;
+    uint8_t *stg = base + CF::stage_off + q * 8192;  // this warp's two 4 KB staging buffers
+    uint32_t nissued = 0;
     uint32_t g = 0;
     int i = 0;
     for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
@@ -431,24 +449,36 @@ __global__ void __launch_bounds__(192, 1)
       const int a = i & 1;
       if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int cb = 0; cb < (G.N + 31) / 32; cb++) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
-        if (row < G.M) {
-          float *crow = G.C + (int64_t)row * G.ldc + cb * 32;
-          const int nc = min(32, G.N - cb * 32);
+      // 32 x 32 blocks through shared memory to TMA: modes 0 and 1 add the
+      // negated block in L2 (C -= A B^T), mode 2 stores it and its low parts.
+      if (32 * q < G.M) {
+        const Task tk = tasks[t];
+        const int y = tk.a + 32 * q, x0 = tk.b;  // panel (modes 0, 2) or update-matrix rows
+        const CUtensorMap *cm = G.mode == 1 ? umaps + tk.front : lmaps + tk.front;
+        for (int cb = 0; cb < (G.N + 31) / 32; cb++) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
           if (G.mode == 2) {
-            float *lrow = Llo + (crow - L);
-#pragma unroll
-            for (int c = 0; c < 32; c++)
-              if (c < nc) {
-                crow[c] = v[c];
-                if (SPLIT == 3) lrow[c] = lo1(v[c]);
-              }
+            if (lane == 0) bulk_wait_read<0>();
+            __syncwarp();
+            stage_row(stg, lane, v, [](float x) { return x; });
+            if (SPLIT == 3) stage_row(stg + 4096, lane, v, [](float x) { return lo1(x); });
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(cm, stg, x0 + 32 * cb, y);
+              if (SPLIT == 3) tma_store_2d(llomaps + tk.front, stg + 4096, x0 + 32 * cb, y);
+            }
+            nissued = 0;  // a later reduction stages into the buffer read first
           } else {
-#pragma unroll
-            for (int c = 0; c < 32; c++)
-              if (c < nc) crow[c] -= v[c];
+            uint8_t *buf = stg + (nissued & 1) * 4096;
+            if (lane == 0) bulk_wait_read<1>();
+            __syncwarp();
+            stage_row(buf, lane, v, [](float x) { return -x; });
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tma_reduce_add_2d(cm, buf, x0 + 32 * cb, y);
+            nissued++;
           }
         }
       }
@@ -456,6 +486,8 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty[a]);
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -598,7 +630,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     // maps, and is added to U by a TMA reduction in L2: U -= A B^T without
     // reading U into the SM and with whole 128-byte rows per transfer.
     const int q = warp % 4;
-    uint8_t *stg = base + kPairStageOff + q * 8192;
+    uint8_t *stg = base + CF::stage_off + q * 8192;
     uint32_t nissued = 0;
     int i = 0;
     for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
@@ -617,11 +649,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
           uint8_t *buf = stg + (nissued & 1) * 4096;
           if (lane == 0) bulk_wait_read<1>();  // the reduction that last read buf is done
           __syncwarp();
-          uint8_t *rowp = buf + lane * 128;
-#pragma unroll
-          for (int j = 0; j < 8; j++)
-            *reinterpret_cast<float4 *>(rowp + ((j ^ (lane & 7)) << 4)) =
-                make_float4(-v[4 * j], -v[4 * j + 1], -v[4 * j + 2], -v[4 * j + 3]);
+          stage_row(buf, lane, v, [](float x) { return -x; });
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) tma_reduce_add_2d(um, buf, tk.b + 32 * cb, r0 + 32 * q);
@@ -919,7 +947,8 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_trsm_ = up(trsm_);
   d_syrk_ = up(syrk_);
   d_pairs_ = up(pairs_);
-  d_maps_ = cv.take<CUtensorMap>(3 * std::max(nfronts_, 1) + 1);  // L, Llo, the inverse scratch, U
+  // L, Llo (32 x 128 boxes), the inverse scratch, U, L, Llo (32 x 32 boxes)
+  d_maps_ = cv.take<CUtensorMap>(5 * std::max(nfronts_, 1) + 1);
   d_inv_ = cv.take<float>((size_t)max_slots_ * kTileM * kTileN);
   ready_ = false;
 }
@@ -964,22 +993,36 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream
     if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed for the inverse scratch");
     maps.push_back(im);
   }
-  for (size_t s = 0; s < nfr; s++) {  // update matrices, 32 x 32 boxes for the SYRK's reductions
-    const FrontInfo &F = plan.fronts[s];
-    CUtensorMap um;
-    std::memset(&um, 0, sizeof(um));
-    if (F.nrow > 0) {
-      cuuint64_t dims[2] = {(cuuint64_t)F.nrow, (cuuint64_t)F.nrow};
-      cuuint64_t strides[1] = {(cuuint64_t)F.uld * sizeof(float)};
+  auto box32 = [&](float *ptr, const char *what, size_t s, uint64_t cols, uint64_t rows, int64_t ld) {
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    if (cols > 0 && rows > 0) {
+      cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+      cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
       cuuint32_t box[2] = {32, 32};
       cuuint32_t estr[2] = {1, 1};
-      CUresult r = enc(&um, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(U + F.uoff), dims, strides,
-                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+      CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS)
-        throw std::runtime_error("cuTensorMapEncodeTiled failed for update matrix " + std::to_string(s));
+        throw std::runtime_error(std::string("cuTensorMapEncodeTiled failed for ") + what + " " +
+                                 std::to_string(s));
     }
-    maps.push_back(um);
+    maps.push_back(m);
+  };
+  // 32 x 32 boxes for the epilogues' stores and reductions: update matrices,
+  // then panels of L and of Llo
+  for (size_t s = 0; s < nfr; s++) {
+    const FrontInfo &F = plan.fronts[s];
+    box32(U + F.uoff, "update matrix", s, F.nrow, F.nrow, F.uld);
+  }
+  for (size_t s = 0; s < nfr; s++) {
+    const FrontInfo &F = plan.fronts[s];
+    box32(L + F.loff, "panel", s, F.ncol, F.ncol + F.nrow, F.ld);
+  }
+  for (size_t s = 0; s < nfr; s++) {
+    const FrontInfo &F = plan.fronts[s];
+    box32(Llo + F.loff, "low-part panel", s, F.ncol, F.ncol + F.nrow, F.ld);
   }
   if (!maps.empty())
     if (cudaMemcpyAsync(d_maps_, maps.data(), maps.size() * sizeof(CUtensorMap),
@@ -990,7 +1033,7 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream
   cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, 128>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<1, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<3, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
-  cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmem);
+  cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
   ready_ = true;
 }
 
@@ -1008,12 +1051,13 @@ static int sm_count() {
 // Persistent launch: at most ctas CTAs (one per SM), each taking tiles ctas apart.
 template <int SPLIT, int BN>
 static void gemm_launch(int ntask, int ctas, const DevPlan &dp, const Task *tasks,
-                        const CUtensorMap *maps, const CUtensorMap *maps_lo,
-                        const CUtensorMap *inv_map, float *L, float *Llo, float *U,
-                        int32_t *status, cudaStream_t st) {
+                        const CUtensorMap *maps, int nfronts, float *L, float *U, int32_t *status,
+                        cudaStream_t st) {
+  const CUtensorMap *maps_lo = maps + nfronts, *inv_map = maps + 2 * nfronts;
+  const CUtensorMap *umaps = inv_map + 1, *lmaps = umaps + nfronts, *llomaps = lmaps + nfronts;
   note_launch();
   tc_gemm_kernel<SPLIT, BN><<<std::min(ntask, std::max(ctas, 1)), 192, Cfg<SPLIT, BN>::smem, st>>>(
-      dp, tasks, ntask, maps, maps_lo, inv_map, L, Llo, U, TcPlan::kNb, status);
+      dp, tasks, ntask, maps, maps_lo, inv_map, umaps, lmaps, llomaps, L, U, TcPlan::kNb, status);
 }
 
 TcPlan::~TcPlan() {
@@ -1028,15 +1072,13 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
   auto syrk3 = split == 3 ? gemm_launch<3, kSyrkN> : gemm_launch<1, kSyrkN>;
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
   const CUtensorMap *maps_lo = maps + nfronts_;
-  const CUtensorMap *inv_map = maps + 2 * nfronts_;
   const CUtensorMap *umaps = maps + 2 * nfronts_ + 1;
   if (L != L_ || U != U_) throw std::runtime_error("tensor maps were encoded for other factor buffers");
   if (!side_) throw std::runtime_error("tensor-core factor streams not created");
-  float *Llo = Llo_;
   const int sms = sm_count();
   const int main_ctas = std::min(kMainCtas, sms / 2), side_ctas = sms - main_ctas;
   auto gemm = [&](const Task *t, int n, int ctas, cudaStream_t s) {
-    gemm3(n, ctas, dp, t, maps, maps_lo, inv_map, L, Llo, U, status, s);
+    gemm3(n, ctas, dp, t, maps, nfronts_, L, U, status, s);
   };
   bool pending = false;  // look-ahead work on the side stream not yet joined
   for (size_t li = 0; li < levels_.size(); li++) {
@@ -1074,11 +1116,10 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
     if (split == 3 && lv.pair_e > lv.pair_b) {  // cluster pairs sharing B by multicast
       const int np = lv.pair_e - lv.pair_b;
       note_launch();
-      tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, kPairSmem, st>>>(
+      tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, Cfg<3, kSyrkN>::smem, st>>>(
           dp, d_pairs_ + lv.pair_b, np, maps, maps_lo, umaps, status);
     } else if (lv.syrk_e > lv.syrk_b) {
-      syrk3(lv.syrk_e - lv.syrk_b, sms, dp, d_syrk_ + lv.syrk_b, maps, maps_lo, inv_map, L, Llo, U,
-            status, st);
+      syrk3(lv.syrk_e - lv.syrk_b, sms, dp, d_syrk_ + lv.syrk_b, maps, nfronts_, L, U, status, st);
     }
   }
 }
