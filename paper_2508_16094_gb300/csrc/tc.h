@@ -16,7 +16,7 @@ class TcPlan {
   static constexpr int kNb = 128;  // block-column width of the tensor-core path
   // CTAs left to the main stream's panel steps while the side stream runs the
   // look-ahead update of the next super-step on the other SMs.
-  static constexpr int kMainCtas = 48;
+  static constexpr int kMainCtas = 24;
   TcPlan() = default;
   TcPlan(const TcPlan &) = delete;
   TcPlan &operator=(const TcPlan &) = delete;
