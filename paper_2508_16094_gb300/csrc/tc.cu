@@ -495,20 +495,62 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
 }
 
-// Update-matrix SYRK in clusters of two CTAs: a task is the pair of 128 x 256
-// tiles (i0, j0) and (i0 + 128, j0) of one front, which share their B operand
-// (256 rows of the panel). CTA r loads its own A rows and the r-th 128-row half
-// of B with TMA multicast into both CTAs' shared memory, so each CTA reads 2/3
-// of the operand bytes of an unpaired tile. A stage is free again when the
-// products of both CTAs have read it (each MMA commit is multicast to both
-// CTAs' empty barriers, which count two arrivals). The second tile of a pair
-// at the edge of the front (i0 + 128 >= nrow) reads zeros and stores nothing.
+// Geometry of a pair task {front, a = i0, b = j0 or c, mode}: CTA `rank` of the
+// pair computes the 128 x 256 tile whose rows start 128 * rank below i0.
+//  Mode 1 (update-matrix SYRK): U[i0.., j0..j0+256) -= A B^T, A = panel rows
+//    ncol + i0 + 128 rank.., B = panel rows ncol + j0.., K = ncol.
+//  Mode 0 (super-step update): panel[i0.., c..c+256) -= A B^T over the columns
+//    [kbeg, kend) (encoded as in the 128 x 128 tasks), A = panel rows
+//    i0 + 128 rank.., B = panel rows c.., i0 >= c.
+// Rows and columns past the target matrix are cut off by the stores' tensor
+// maps (and read as zeros by the loads).
+struct PairGeo {
+  int arow, brow, x0, nk;  // operand rows (this CTA's A, this CTA's half of B), first column, k-steps
+  int cy, cx, rows, N;     // target origin (rows, columns), its row count, columns of the tile
+  bool panel;              // target is the panel (mode 0), else the update matrix
+};
+__device__ __forceinline__ PairGeo pair_geo(const FrontInfo &F, const Task &tk, int rank) {
+  PairGeo g;
+  int K;
+  if ((tk.c & 3) == 1) {
+    g.arow = F.ncol + tk.a + 128 * rank;
+    g.brow = F.ncol + tk.b + 128 * rank;
+    g.x0 = 0;
+    K = F.ncol;
+    g.cy = tk.a + 128 * rank;
+    g.rows = F.nrow;
+    g.N = min(256, F.nrow - tk.b);
+    g.panel = false;
+  } else {
+    const int kbeg = ((tk.c >> 2) & 0x7FFF) * kTileN, kend = ((tk.c >> 17) & 0x7FFF) * kTileN;
+    g.arow = tk.a + 128 * rank;
+    g.brow = tk.b + 128 * rank;
+    g.x0 = kbeg;
+    K = kend - kbeg;
+    g.cy = g.arow;
+    g.rows = F.ncol + F.nrow;
+    g.N = min(256, F.ncol - tk.b);
+    g.panel = true;
+  }
+  g.cx = tk.b;
+  g.nk = (K + kTileK - 1) / kTileK;
+  return g;
+}
+
+// 128 x 256 tiles in clusters of two CTAs: a task is the pair of tiles whose
+// rows start at i0 and i0 + 128 and which share their B operand (256 rows of
+// the panel). CTA r loads its own A rows and the r-th 128-row half of B with
+// TMA multicast into both CTAs' shared memory, so each CTA reads 2/3 of the
+// operand bytes of an unpaired tile. A stage is free again when the products
+// of both CTAs have read it (each MMA commit is multicast to both CTAs' empty
+// barriers, which count two arrivals). The second tile of a pair past the end
+// of the target reads zeros and stores nothing.
 template <int SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
-    tc_syrk_pair_kernel(DevPlan dp, const Task *__restrict__ pairs, int npair,
-                        const CUtensorMap *__restrict__ maps,
-                        const CUtensorMap *__restrict__ maps_lo,
-                        const CUtensorMap *__restrict__ umaps, int32_t *status) {
+    tc_pair_kernel(DevPlan dp, const Task *__restrict__ pairs, int npair,
+                   const CUtensorMap *__restrict__ maps, const CUtensorMap *__restrict__ maps_lo,
+                   const CUtensorMap *__restrict__ umaps, const CUtensorMap *__restrict__ lmaps,
+                   int32_t *status) {
   constexpr int BN = 256;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -564,19 +606,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         const Task tk = pairs[p];
         const FrontInfo F = dp.fronts[tk.front];
         const CUtensorMap *amap = maps + tk.front, *lomap = maps_lo + tk.front;
-        const int arow = F.ncol + tk.a + 128 * (int)rank, brow = F.ncol + tk.b + 128 * (int)rank;
-        const int nk = (F.ncol + kTileK - 1) / kTileK;
-        for (int kt = 0; kt < nk; kt++, g++) {
+        const PairGeo G = pair_geo(F, tk, (int)rank);
+        for (int kt = 0; kt < G.nk; kt++, g++) {
           const int st = g % S;
           const uint32_t round = g / S;
+          const int x = G.x0 + kt * kTileK;
           if (!mbar_wait(&empty[st], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
           mbar_arrive_expect_tx(&full[st], (SPLIT == 3 ? 2 : 1) * (kTileBytes + kBB));
-          tma_load_2d(sA + st * kTileBytes, amap, &full[st], kt * kTileK, arow);
-          tma_load_2d_mc(sB + st * kBB + rank * kTileBytes, amap, &full[st], kt * kTileK, brow, kBoth);
+          tma_load_2d(sA + st * kTileBytes, amap, &full[st], x, G.arow);
+          tma_load_2d_mc(sB + st * kBB + rank * kTileBytes, amap, &full[st], x, G.brow, kBoth);
           if (SPLIT == 3) {
-            tma_load_2d(sAl + st * kTileBytes, lomap, &full[st], kt * kTileK, arow);
-            tma_load_2d_mc(sBl + st * kBB + rank * kTileBytes, lomap, &full[st], kt * kTileK, brow,
-                           kBoth);
+            tma_load_2d(sAl + st * kTileBytes, lomap, &full[st], x, G.arow);
+            tma_load_2d_mc(sBl + st * kBB + rank * kTileBytes, lomap, &full[st], x, G.brow, kBoth);
           }
         }
       }
@@ -592,7 +633,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
       for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
         const Task tk = pairs[p];
         const FrontInfo F = dp.fronts[tk.front];
-        const int nk = (F.ncol + kTileK - 1) / kTileK;
+        const int nk = pair_geo(F, tk, (int)rank).nk;
         const int a = i & 1;
         if (!mbar_wait(&accempty[a], ((i >> 1) & 1) ^ 1, status)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -626,9 +667,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     }
   } else {  // warps 2-5: epilogue of this CTA's tile, 32 rows per warp
     // Each 32 x 32 block of the accumulator goes (negated) through this warp's
-    // two 4 KB staging buffers in the 128-byte swizzled layout of the U tensor
-    // maps, and is added to U by a TMA reduction in L2: U -= A B^T without
-    // reading U into the SM and with whole 128-byte rows per transfer.
+    // two 4 KB staging buffers in the 128-byte swizzled layout of the 32 x 32
+    // tensor maps, and is added to the target by a TMA reduction in L2:
+    // C -= A B^T without reading C into the SM, whole 128-byte rows per transfer.
     const int q = warp % 4;
     uint8_t *stg = base + CF::stage_off + q * 8192;
     uint32_t nissued = 0;
@@ -636,14 +677,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
       const Task tk = pairs[p];
       const FrontInfo F = dp.fronts[tk.front];
-      const int r0 = tk.a + 128 * (int)rank;
-      const int N = min(BN, F.nrow - tk.b);
+      const PairGeo G = pair_geo(F, tk, (int)rank);
       const int a = i & 1;
       if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (r0 + 32 * q < F.nrow) {
-        const CUtensorMap *um = umaps + tk.front;
-        for (int cb = 0; cb < (N + 31) / 32; cb++) {
+      if (G.cy + 32 * q < G.rows) {
+        const CUtensorMap *um = (G.panel ? lmaps : umaps) + tk.front;
+        for (int cb = 0; cb < (G.N + 31) / 32; cb++) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
           uint8_t *buf = stg + (nissued & 1) * 4096;
@@ -652,7 +692,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
           stage_row(buf, lane, v, [](float x) { return -x; });
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
-          if (lane == 0) tma_reduce_add_2d(um, buf, tk.b + 32 * cb, r0 + 32 * q);
+          if (lane == 0) tma_reduce_add_2d(um, buf, G.cx + 32 * cb, G.cy + 32 * q);
           nissued++;
         }
       }
@@ -816,7 +856,6 @@ void TcPlan::build(const Plan &plan) {
   gemm_.clear();
   potrf_.clear();
   trsm_.clear();
-  syrk_.clear();
   pairs_.clear();
   levels_.assign(plan.levels.size(), Level{});
   nfronts_ = (int)plan.fronts.size();
@@ -833,24 +872,26 @@ void TcPlan::build(const Plan &plan) {
     // the side stream meanwhile, and super-step s + 1 starts with the update by
     // super-step s's columns only (K in [K0, K0 + kSuper)).
     auto enc = [](int32_t kbeg, int32_t kend) { return 0 | (kbeg / kNb) << 2 | (kend / kNb) << 17; };
-    auto span = [&](int32_t c0, int32_t kbeg, int32_t kend) {  // columns [c0, c0 + kSuper), all fronts
+    // columns [c0, c0 + kSuper) of all fronts: 256-wide tiles in row pairs
+    auto span = [&](int32_t c0, int32_t kbeg, int32_t kend) {
       for (int32_t t = LP.front_b; t < LP.front_e; t++) {
         const int32_t s = plan.level_fronts[t];
         const FrontInfo &F = plan.fronts[s];
-        for (int32_t c = c0; c < std::min(F.ncol, c0 + kSuper); c += kNb)
-          for (int32_t i0 = c; i0 < F.ncol + F.nrow; i0 += kTileM) gemm_.push_back({s, i0, c, enc(kbeg, kend)});
+        for (int32_t c = c0; c < std::min(F.ncol, c0 + kSuper); c += kSyrkN)
+          for (int32_t i0 = c; i0 < F.ncol + F.nrow; i0 += 2 * kTileM)
+            pairs_.push_back({s, i0, c, enc(kbeg, kend)});
       }
     };
     bool ahead_done = false;  // the previous super-step ran this one's update ahead
     for (int32_t K0 = 0; K0 < LP.max_ncol; K0 += kSuper) {
       Super sp{};
-      sp.now_b = (int)gemm_.size();
+      sp.now_b = (int)pairs_.size();
       if (K0 > 0) span(K0, ahead_done ? K0 - kSuper : 0, K0);
-      sp.now_e = (int)gemm_.size();
-      sp.ahead_b = (int)gemm_.size();
+      sp.now_e = (int)pairs_.size();
+      sp.ahead_b = (int)pairs_.size();
       if (K0 > 0 && K0 + kSuper < LP.max_ncol && LP.front_e - LP.front_b <= kAheadFronts)
         span(K0 + kSuper, 0, K0);
-      sp.ahead_e = (int)gemm_.size();
+      sp.ahead_e = (int)pairs_.size();
       ahead_done = sp.ahead_e > sp.ahead_b;
       sp.step_b = (int)lv.steps.size();
       for (int32_t k = K0; k < std::min(LP.max_ncol, K0 + kSuper); k += kNb) {
@@ -887,15 +928,7 @@ void TcPlan::build(const Plan &plan) {
       sp.step_e = (int)lv.steps.size();
       lv.supers.push_back(sp);
     }
-    lv.syrk_b = (int)syrk_.size();
-    for (int32_t t = LP.front_b; t < LP.front_e; t++) {
-      const int32_t s = plan.level_fronts[t];
-      const FrontInfo &F = plan.fronts[s];
-      for (int32_t i0 = 0; i0 < F.nrow; i0 += kTileM)  // 128 x 256 tiles touching the lower triangle
-        for (int32_t j0 = 0; j0 <= i0; j0 += kSyrkN) syrk_.push_back({s, i0, j0, 1});
-    }
-    lv.syrk_e = (int)syrk_.size();
-    lv.pair_b = (int)pairs_.size();  // the same tiles as pairs (i0, j0), (i0 + 128, j0)
+    lv.pair_b = (int)pairs_.size();  // SYRK: 128 x 256 tiles (i0, j0), (i0 + 128, j0) of the lower triangle
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = plan.level_fronts[t];
       const FrontInfo &F = plan.fronts[s];
@@ -913,15 +946,18 @@ void TcPlan::build(const Plan &plan) {
           (t.c & 3) == 0 && kbeg >= 0 && kbeg < kend && kend <= t.b))
       fail("gemm");
   }
-  for (const Task &t : syrk_) {
-    const FrontInfo &F = plan.fronts[t.front];
-    if (!(t.a >= 0 && t.a < F.nrow && t.b >= 0 && t.b <= t.a && t.c == 1)) fail("syrk");
-  }
   for (const Task &t : pairs_) {
     const FrontInfo &F = plan.fronts[t.front];
-    if (!(t.a >= 0 && t.a < F.nrow && t.a % (2 * kTileM) == 0 && t.b >= 0 && t.b <= t.a &&
-          t.b % kSyrkN == 0 && t.c == 1))
-      fail("syrk pair");
+    if ((t.c & 3) == 1) {
+      if (!(t.a >= 0 && t.a < F.nrow && t.a % (2 * kTileM) == 0 && t.b >= 0 && t.b <= t.a &&
+            t.b % kSyrkN == 0 && t.c == 1))
+        fail("syrk pair");
+    } else {
+      const int32_t kbeg = ((t.c >> 2) & 0x7FFF) * kNb, kend = ((t.c >> 17) & 0x7FFF) * kNb;
+      if (!(t.b > 0 && t.b < F.ncol && t.b % kSyrkN == 0 && t.a >= t.b && t.a < F.ncol + F.nrow &&
+            (t.c & 3) == 0 && kbeg >= 0 && kbeg < kend && kend <= t.b))
+        fail("update pair");
+    }
   }
   for (const Task &t : trsm_) {
     const FrontInfo &F = plan.fronts[t.front];
@@ -945,7 +981,6 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_gemm_ = up(gemm_);
   d_potrf_ = up(potrf_);
   d_trsm_ = up(trsm_);
-  d_syrk_ = up(syrk_);
   d_pairs_ = up(pairs_);
   // L, Llo (32 x 128 boxes), the inverse scratch, U, L, Llo (32 x 32 boxes)
   d_maps_ = cv.take<CUtensorMap>(5 * std::max(nfronts_, 1) + 1);
@@ -1031,9 +1066,8 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream
   if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("tensor map upload failed");
   cudaFuncSetAttribute(tc_gemm_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, 128>::smem);
   cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, 128>::smem);
-  cudaFuncSetAttribute(tc_gemm_kernel<1, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
-  cudaFuncSetAttribute(tc_gemm_kernel<3, kSyrkN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
-  cudaFuncSetAttribute(tc_syrk_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
+  cudaFuncSetAttribute(tc_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
+  cudaFuncSetAttribute(tc_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
   ready_ = true;
 }
 
@@ -1060,6 +1094,18 @@ static void gemm_launch(int ntask, int ctas, const DevPlan &dp, const Task *task
       dp, tasks, ntask, maps, maps_lo, inv_map, umaps, lmaps, llomaps, L, U, TcPlan::kNb, status);
 }
 
+// Pair kernel on at most ctas CTAs (clusters of two, each pair of tiles ncl apart).
+template <int SPLIT>
+static void pair_launch(int npair, int ctas, const DevPlan &dp, const Task *pairs,
+                        const CUtensorMap *maps, int nfronts, int32_t *status, cudaStream_t st) {
+  const CUtensorMap *maps_lo = maps + nfronts, *umaps = maps + 2 * nfronts + 1;
+  const CUtensorMap *lmaps = umaps + nfronts;
+  const int ncl = std::max(1, std::min({npair, ctas / 2, kMaxClusters}));
+  note_launch();
+  tc_pair_kernel<SPLIT><<<2 * ncl, 192, Cfg<SPLIT, kSyrkN>::smem, st>>>(dp, pairs, npair, maps,
+                                                                      maps_lo, umaps, lmaps, status);
+}
+
 TcPlan::~TcPlan() {
   if (ev_main_) cudaEventDestroy(ev_main_);
   if (ev_side_) cudaEventDestroy(ev_side_);
@@ -1069,16 +1115,17 @@ TcPlan::~TcPlan() {
 void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
                     float *Dinv, int32_t *status, int split, cudaStream_t st) {
   auto gemm3 = split == 3 ? gemm_launch<3, 128> : gemm_launch<1, 128>;
-  auto syrk3 = split == 3 ? gemm_launch<3, kSyrkN> : gemm_launch<1, kSyrkN>;
+  auto pair3 = split == 3 ? pair_launch<3> : pair_launch<1>;
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
-  const CUtensorMap *maps_lo = maps + nfronts_;
-  const CUtensorMap *umaps = maps + 2 * nfronts_ + 1;
   if (L != L_ || U != U_) throw std::runtime_error("tensor maps were encoded for other factor buffers");
   if (!side_) throw std::runtime_error("tensor-core factor streams not created");
   const int sms = sm_count();
   const int main_ctas = std::min(kMainCtas, sms / 2), side_ctas = sms - main_ctas;
   auto gemm = [&](const Task *t, int n, int ctas, cudaStream_t s) {
     gemm3(n, ctas, dp, t, maps, nfronts_, L, U, status, s);
+  };
+  auto pair = [&](int b, int e, int ctas, cudaStream_t s) {
+    if (e > b) pair3(e - b, ctas, dp, d_pairs_ + b, maps, nfronts_, status, s);
   };
   bool pending = false;  // look-ahead work on the side stream not yet joined
   for (size_t li = 0; li < levels_.size(); li++) {
@@ -1094,10 +1141,10 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
         cudaEventRecord(ev_main_, st);
         cudaStreamWaitEvent(side_, ev_main_, 0);
       }
-      if (sp.now_e > sp.now_b) gemm(d_gemm_ + sp.now_b, sp.now_e - sp.now_b, sms, st);
+      pair(sp.now_b, sp.now_e, sms, st);
       const int ctas = ahead ? main_ctas : sms;
       if (ahead) {
-        gemm(d_gemm_ + sp.ahead_b, sp.ahead_e - sp.ahead_b, side_ctas, side_);
+        pair(sp.ahead_b, sp.ahead_e, side_ctas, side_);
         cudaEventRecord(ev_side_, side_);
         pending = true;
       }
@@ -1113,14 +1160,7 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
       cudaStreamWaitEvent(st, ev_side_, 0);
       pending = false;
     }
-    if (split == 3 && lv.pair_e > lv.pair_b) {  // cluster pairs sharing B by multicast
-      const int np = lv.pair_e - lv.pair_b;
-      note_launch();
-      tc_syrk_pair_kernel<3><<<2 * std::min(np, kMaxClusters), 192, Cfg<3, kSyrkN>::smem, st>>>(
-          dp, d_pairs_ + lv.pair_b, np, maps, maps_lo, umaps, status);
-    } else if (lv.syrk_e > lv.syrk_b) {
-      syrk3(lv.syrk_e - lv.syrk_b, sms, dp, d_syrk_ + lv.syrk_b, maps, nfronts_, L, U, status, st);
-    }
+    pair(lv.pair_b, lv.pair_e, sms, st);  // the level's update matrices
   }
 }
 

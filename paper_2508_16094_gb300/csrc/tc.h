@@ -48,14 +48,13 @@ class TcPlan {
   struct Level {
     std::vector<Step> steps;
     std::vector<Super> supers;
-    int syrk_b = 0, syrk_e = 0, pair_b = 0, pair_e = 0;
+    int pair_b = 0, pair_e = 0;  // the level's update-matrix SYRK
   };
-  std::vector<Task> gemm_, potrf_, trsm_, syrk_, pairs_;
+  std::vector<Task> gemm_, potrf_, trsm_, pairs_;
   std::vector<Level> levels_;
   int nfronts_ = 0, max_slots_ = 1;
   float *d_inv_ = nullptr;  // inverses of the diagonal blocks of one step (max_slots_ x 128 x 128)
-  Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_syrk_ = nullptr,
-       *d_pairs_ = nullptr;
+  Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_pairs_ = nullptr;
   void *d_maps_ = nullptr;  // 3 nfronts_ + 1 CUtensorMap (128 bytes each)
   float *L_ = nullptr, *Llo_ = nullptr, *U_ = nullptr;
   cudaStream_t side_ = nullptr;                              // look-ahead stream (low priority)
