@@ -92,7 +92,10 @@ typedef struct {
   int32_t precision;     /* ipm_precision of kkt_factor inside ipm_solve (IPM_FP64) */
   int32_t storage_fp64;  /* 1: size the factor storage for FP64 values (needed by IPM_FP64
                             and by fallback_fp64); 0: FP32 storage only. -1: automatic */
-  int32_t refine;        /* ipm_refine used inside ipm_solve (IPM_REFINE_IR) */
+  int32_t refine;        /* ipm_refine used inside ipm_solve (IPM_REFINE_PCG: the condensed
+                            matrix of an LP/QP is SPD, and CG preconditioned by the factor
+                            needs fewer solves than refinement; the grid NLP, whose matrix
+                            may be indefinite, refines with IPM_REFINE_IR instead) */
   int32_t ir_max;        /* refinement steps per solve (10) */
   double ir_tol;         /* stop once ||b - K x||_inf <= ir_tol ||b||_inf (1e-10) */
   int32_t pcg_max;       /* PCG iterations per solve (100) */

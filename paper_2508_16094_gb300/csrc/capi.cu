@@ -354,8 +354,6 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
     double *scale = c->scal + 8, *amax = c->scal + 9;
     V.absmax(c->P.n, b, amax);
     V.inv_scale(amax, scale);
-    float *t = reinterpret_cast<float *>(c->tv);
-    (void)t;
     V.permute_in<float>(b, scale, c->fsa);
     launch_fp32_solve(c, 0);
     V.permute_out<float>(c->fsx, scale, out, accumulate);
@@ -600,7 +598,7 @@ void ipm_default_options(ipm_options *o) {
   o->delta_d = 1e-8;
   o->precision = IPM_FP64;
   o->storage_fp64 = -1;
-  o->refine = IPM_REFINE_IR;
+  o->refine = IPM_REFINE_PCG;
   o->ir_max = 10;
   o->ir_tol = 1e-10;
   o->pcg_max = 100;
@@ -1281,6 +1279,9 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       if (stt == IPM_OK) {
         nlp_fill(mt, mu, c->vw, c->st);
         c->nlp_grad = true;
+        // K may be indefinite away from a local minimum (W is the Hessian of
+        // the Lagrangian): refine without conjugate gradients
+        if (o.refine == IPM_REFINE_PCG) c->refine_override = IPM_REFINE_IR;
         stt = direction(c, jv, nullptr, grad, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
         c->nlp_grad = false;
         if (stt != IPM_OK && o.fallback_fp64 && o.precision != IPM_FP64 && c->storage_bytes == 8) {
@@ -1292,6 +1293,7 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
             c->nlp_grad = false;
           }
         }
+        c->refine_override = -1;
       }
       res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
       if (stt != IPM_OK) { res.status = stt; break; }

@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kB = 128;                     // block width of the solve
 constexpr int kT = 256;                     // threads per CTA
-constexpr unsigned kBarrierSpins = 1u << 24;  // x ~64 ns sleep: > 1 s before giving up
+constexpr unsigned kBarrierSpins = 1u << 24;  // polls of >= 0.3 us each: seconds before giving up
 
 void ck(cudaError_t e, const char *what) {
   if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -69,12 +69,11 @@ struct PsArgs {
   const float *L, *Dinv;
   float *a, *b, *x, *t, *part;
   int32_t p0, p1;   // phases [p0, p1)
-  unsigned *bar;    // [0] generation, [kFlagOff + b] arrival epoch of CTA b
+  unsigned *bar;    // [2..3] 64-bit arrival counter of the grid barrier
   int32_t *status;  // ST_SOLVE_TIMEOUT
 };
 
-constexpr int kFlagOff = 32;
-constexpr int kMaxGrid = kPsBarrierWords - kFlagOff;
+constexpr int kMaxGrid = 1024;  // CTAs of one cooperative solve launch
 constexpr int kRC = 128;  // rows below a front per partial-sum task
 constexpr long long kCopySpinCycles = 2000000000ll;  // bounded wait on a staging copy (~1 s)
 
@@ -92,46 +91,35 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident): every CTA
-// publishes its arrival epoch in its own word, CTA 0 waits for all of them and
-// releases the generation word. Every wait is bounded; on a timeout the status
-// word is set (the release still happens) and all CTAs return false.
-__device__ bool grid_barrier(unsigned *bar, int32_t *status, unsigned &epoch) {
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident): one
+// 64-bit arrival counter (words 2-3 of the barrier state) that only grows. A
+// CTA adds 1 (release) and waits (acquire) until the counter reaches the next
+// multiple of the grid size above the value it found, so launches need no
+// reset as long as every barrier of the previous one completed (after a
+// timeout the host zeroes the state). Every wait is bounded; on a timeout the
+// status word is set and all CTAs return false.
+__device__ bool grid_barrier(unsigned *bar, int32_t *status) {
   __shared__ int ok;
-  const unsigned target = epoch + 1;
-  epoch = target;
   __syncthreads();
   if (threadIdx.x == 0) {
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(bar + 2);
+    unsigned long long old, v;
     __threadfence();
-    *(volatile unsigned *)(bar + kFlagOff + blockIdx.x) = target;
-  }
-  int good = 1;
-  if (blockIdx.x == 0) {
-    for (int cta = threadIdx.x; cta < (int)gridDim.x; cta += blockDim.x) {
-      unsigned spins = 0;
-      while ((int)(*(volatile unsigned *)(bar + kFlagOff + cta) - target) < 0) {
-        if (++spins > kBarrierSpins) { good = 0; break; }
-        __nanosleep(32);
-      }
-    }
-    good = __syncthreads_and(good);
-    if (threadIdx.x == 0) {
-      if (!good) atomicExch(status + ST_SOLVE_TIMEOUT, 1);
-      __threadfence();
-      *(volatile unsigned *)bar = target;
-    }
-  } else if (threadIdx.x == 0) {
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(ctr) : "memory");
+    const unsigned long long G = gridDim.x, target = (old / G + 1) * G;
     unsigned spins = 0;
-    while ((int)(*(volatile unsigned *)bar - target) < 0) {
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
       if (++spins > kBarrierSpins) {
         atomicExch(status + ST_SOLVE_TIMEOUT, 1);
         break;
       }
-      __nanosleep(32);
+      __nanosleep(16);
     }
     __threadfence();
+    ok = *(volatile int32_t *)(status + ST_SOLVE_TIMEOUT) == 0;
   }
-  if (threadIdx.x == 0) ok = *(volatile int32_t *)(status + ST_SOLVE_TIMEOUT) == 0;
   __syncthreads();
   return ok != 0;
 }
@@ -446,7 +434,6 @@ __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
     S.parity = 0;
   }
   __syncthreads();
-  unsigned epoch = *(volatile unsigned *)A.bar;
   for (int p = A.p0; p < A.p1; p++) {
     const SolvePhase ph = A.dp.ps_phases[p];
     int q = ph.begin + blockIdx.x;
@@ -476,7 +463,7 @@ __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
       F = Fn;
       q = qn;
     }
-    if (p + 1 < A.p1 && !grid_barrier(A.bar, A.status, epoch)) return;
+    if (p + 1 < A.p1 && !grid_barrier(A.bar, A.status)) return;
   }
 }
 
