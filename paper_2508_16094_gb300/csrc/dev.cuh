@@ -56,7 +56,6 @@ struct Carve {
   }
 };
 
-constexpr int kBuildTile = 32;
 constexpr int kGemmTile = 64;
 constexpr int kTrsmRows = 128;
 constexpr int kGathPos = 256;

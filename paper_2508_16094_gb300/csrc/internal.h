@@ -33,6 +33,9 @@ struct Symbolic {
 // first + p, p >= ncol is row sri[rows_off + p - ncol]. The first ncol columns
 // live in the panel (row-major, nf rows x ld), the trailing nrow x nrow block
 // (the update matrix handed to the parent) lives in U storage (row-major, uld).
+// Front assembly tiles: kBuildTile rows x at most kBuildTile columns.
+constexpr int kBuildTile = 64;
+
 struct FrontInfo {
   int64_t loff;      // panel offset in the factor storage (elements)
   int64_t uoff;      // update matrix offset in the update storage (elements)

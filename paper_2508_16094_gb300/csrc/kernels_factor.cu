@@ -41,41 +41,61 @@ __global__ void assemble_kernel(DevPlan dp, const double *__restrict__ jv,
   }
 }
 
-// Front assembly: one 32x32 tile of a front's lower triangle per block of 128
-// threads (eight entries each). Each entry is the sum, over the children in
-// ascending order, of the matching entry of the child's update matrix (through
-// the child->front inverse map). The maps of up to four children are staged
-// together (one memory round trip), and a child none of whose rows or none of
-// whose columns fall in the tile is skipped by the whole block.
+// Four consecutive entries at a 16-byte aligned address.
+__device__ __forceinline__ void store4(float *p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double *p, double a, double b, double c, double d) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
+
+// Front assembly: one tile of 64 rows x (at most) 64 columns of a front's
+// lower triangle per block of 128 threads; thread (row group g, column group
+// q) owns rows r0 + g + 8i (i < 8) and columns c0 + 4q .. c0 + 4q + 3. Each
+// entry is the sum, over the children in ascending order, of the matching
+// entry of the child's update matrix (through the child->front inverse map).
+// The maps of up to four children are staged together (one memory round
+// trip), and a child none of whose rows or none of whose columns fall in the
+// tile is skipped by the whole block. Panel tiles start at multiples of 64
+// columns and update-matrix tiles at ncol + multiples of 64, so every
+// 4-column group is one aligned vector store (entries above the diagonal and
+// padding past ncol or nf are written as zeros). 32 entries per thread keep
+// enough bytes in flight per block for the chain of dependent loads
+// (task, front, children, maps) a tile starts with.
 constexpr int kBuildThreads = 128, kBuildGroup = 4;
 template <typename T>
 __global__ void __launch_bounds__(kBuildThreads) build_front_kernel(DevPlan dp, int32_t task0,
                                                                     T *__restrict__ L,
                                                                     T *__restrict__ U) {
+  constexpr int BT = kBuildTile, RS = kBuildThreads / (BT / 4), NR = BT / RS;  // 8 row groups, 8 rows each
   const Task tk = dp.build[task0 + blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
   const int nf = F.ncol + F.nrow;
-  const int r0 = tk.a, c0 = tk.b;
-  __shared__ int32_t map[kBuildGroup][2 * kBuildTile];  // row maps, then column maps
-  __shared__ int32_t hit[kBuildGroup][2];               // some row / some column maps into the child
+  const int r0 = tk.a, c0 = tk.b, w = tk.c;
+  __shared__ __align__(16) int32_t map[kBuildGroup][2 * BT];  // row maps, then column maps
+  __shared__ int32_t hit[kBuildGroup][2 * BT / 32];  // per 32 maps: some entry maps into the child
   __shared__ int64_t uoff[kBuildGroup];
   __shared__ int32_t uld[kBuildGroup];
-  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
-  T acc[8];
+  const int tid = threadIdx.x, lane = tid % 32, g = tid / (BT / 4), q4 = 4 * (tid % (BT / 4));
+  T acc[NR][4];
 #pragma unroll
-  for (int i = 0; i < 8; i++) acc[i] = T(0);
+  for (int i = 0; i < NR; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = T(0);
   for (int cg = F.child_begin; cg < F.child_end; cg += kBuildGroup) {
     const int nc = min(kBuildGroup, F.child_end - cg);
     __syncthreads();
-    // a warp's 32 entries are one child's row maps or column maps
-    for (int e = tid; e < nc * 2 * kBuildTile; e += kBuildThreads) {
-      const int q = e / (2 * kBuildTile), m = e % (2 * kBuildTile);
+    // a warp's 32 entries are half of one child's row maps or column maps
+    for (int e = tid; e < nc * 2 * BT; e += kBuildThreads) {
+      const int q = e / (2 * BT), m = e % (2 * BT);
       const FrontInfo C = dp.fronts[dp.children[cg + q]];
-      const int idx = m < kBuildTile ? r0 + m : c0 + m - kBuildTile;
-      const int32_t t = idx < nf ? dp.inv[C.inv_off + idx] : -1;
+      const int idx = m < BT ? r0 + m : c0 + m - BT;
+      const bool inside = m < BT ? idx < nf : m - BT < w;
+      const int32_t t = inside ? dp.inv[C.inv_off + idx] : -1;
       map[q][m] = t;
       const unsigned any = __ballot_sync(0xffffffffu, t >= 0);
-      if (lane == 0) hit[q][m / kBuildTile] = any != 0u;
+      if (lane == 0) hit[q][m / 32] = any != 0u;
       if (m == 0) {
         uoff[q] = C.uoff;
         uld[q] = C.uld;
@@ -83,30 +103,39 @@ __global__ void __launch_bounds__(kBuildThreads) build_front_kernel(DevPlan dp, 
     }
     __syncthreads();
     for (int q = 0; q < nc; q++) {
-      if (!hit[q][0] || !hit[q][1]) continue;
-      const int b = map[q][kBuildTile + lane];
+      if (!(hit[q][0] | hit[q][1]) || !(hit[q][2] | hit[q][3])) continue;
+      const int4 b = *reinterpret_cast<const int4 *>(&map[q][BT + q4]);
+      const int bb[4] = {b.x, b.y, b.z, b.w};
       const T *Uc = U + uoff[q];
       const int64_t ldq = uld[q];
-      T v[8];
 #pragma unroll
-      for (int i = 0; i < 8; i++) {
-        const int rr = w + 4 * i;
+      for (int i = 0; i < NR; i++) {
+        const int rr = g + RS * i;
         const int a = map[q][rr];
-        v[i] = (a >= 0 && b >= 0 && r0 + rr >= c0 + lane) ? Uc[a * ldq + b] : T(0);
-      }
+        const T *row = Uc + a * ldq;
+        T v[4];
 #pragma unroll
-      for (int i = 0; i < 8; i++) acc[i] += v[i];
+        for (int j = 0; j < 4; j++)
+          v[j] = (a >= 0 && bb[j] >= 0 && r0 + rr >= c0 + q4 + j) ? row[bb[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] += v[j];
+      }
     }
   }
+  if (q4 >= w) return;
+  const int c = c0 + q4;
+  const bool panel = c0 < F.ncol;
+  const int lim = panel ? F.ncol : nf;  // columns past lim are padding
 #pragma unroll
-  for (int i = 0; i < 8; i++) {
-    const int r = r0 + w + 4 * i, c = c0 + lane;
-    if (r >= nf || c >= nf) continue;
-    if (c < F.ncol) {
-      L[F.loff + (int64_t)r * F.ld + c] = (r >= c) ? acc[i] : T(0);
-    } else if (r >= c) {
-      U[F.uoff + (int64_t)(r - F.ncol) * F.uld + (c - F.ncol)] = acc[i];
-    }
+  for (int i = 0; i < NR; i++) {
+    const int r = r0 + g + RS * i;
+    if (r >= nf) continue;
+    T o[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) o[j] = (c + j <= r && c + j < lim) ? acc[i][j] : T(0);
+    T *dst = panel ? L + F.loff + (int64_t)r * F.ld + c
+                   : U + F.uoff + (int64_t)(r - F.ncol) * F.uld + (c - F.ncol);
+    if (panel || r >= F.ncol) store4(dst, o[0], o[1], o[2], o[3]);
   }
 }
 

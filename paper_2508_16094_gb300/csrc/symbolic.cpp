@@ -494,7 +494,7 @@ void build_plan(const Problem &P, const Symbolic &S, Plan &plan, int nb, int nbs
       }
 
   // ---- task lists of every level -----------------------------------------
-  const int BT = 32;        // front-assembly tile
+  const int BT = kBuildTile;  // front-assembly tile
   const int GM = 64;        // GEMM / SYRK tile rows
   const int TR = 128;       // TRSM rows per task
   const int GR = 256;       // solve gather positions per task
@@ -519,8 +519,16 @@ void build_plan(const Problem &P, const Symbolic &S, Plan &plan, int nb, int nbs
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = plan.level_fronts[t];
       const int32_t nfr = plan.fronts[s].ncol + plan.fronts[s].nrow;
-      for (int32_t r0 = 0; r0 < nfr; r0 += BT)
-        for (int32_t c0 = 0; c0 <= r0; c0 += BT) plan.build_tasks.push_back({s, r0, c0, 0});
+      const int32_t ncol = plan.fronts[s].ncol;
+      // BT x BT tiles of the lower triangle; column tiles start at multiples
+      // of BT in the panel and at ncol + multiples of BT in the update matrix,
+      // so both take aligned 4-wide stores (c = tile width)
+      for (int32_t r0 = 0; r0 < nfr; r0 += BT) {
+        for (int32_t c0 = 0; c0 < ncol && c0 <= r0 + BT - 1; c0 += BT)
+          plan.build_tasks.push_back({s, r0, c0, std::min(BT, ncol - c0)});
+        for (int32_t c0 = ncol; c0 < nfr && c0 <= r0 + BT - 1; c0 += BT)
+          plan.build_tasks.push_back({s, r0, c0, std::min(BT, nfr - c0)});
+      }
     }
     LP.build_e = (int32_t)plan.build_tasks.size();
     LP.steps.clear();
@@ -663,8 +671,14 @@ void validate_plan(const Problem &P, const Symbolic &S, const Plan &pl) {
     for (size_t i = 1; i < iv.size(); i++) need(iv[i].first >= iv[i - 1].second, "update overlap");
   }
   auto in_front = [&](const Task &t) { return t.front >= 0 && t.front < ns; };
-  for (const Task &t : pl.build_tasks)
-    need(in_front(t) && t.a >= 0 && t.a < nf(t.front) && t.b >= 0 && t.b <= t.a, "build task");
+  for (const Task &t : pl.build_tasks) {
+    need(in_front(t), "build task");
+    const int32_t nc = pl.fronts[t.front].ncol, lim = t.b < nc ? nc : nf(t.front);
+    need(t.a >= 0 && t.a < nf(t.front) && t.a % kBuildTile == 0 && t.b >= 0 &&
+             t.b <= t.a + kBuildTile - 1 && t.c >= 1 && t.c <= kBuildTile && t.b + t.c <= lim &&
+             (t.b < nc ? t.b : t.b - nc) % kBuildTile == 0,
+         "build task");
+  }
   for (const Task &t : pl.gemm_tasks)
     need(in_front(t) && t.b > 0 && t.b < pl.fronts[t.front].ncol && t.a >= t.b &&
              t.a < nf(t.front), "gemm task");
