@@ -671,13 +671,42 @@ void validate_plan(const Problem &P, const Symbolic &S, const Plan &pl) {
     for (size_t i = 1; i < iv.size(); i++) need(iv[i].first >= iv[i - 1].second, "update overlap");
   }
   auto in_front = [&](const Task &t) { return t.front >= 0 && t.front < ns; };
-  for (const Task &t : pl.build_tasks) {
-    need(in_front(t), "build task");
-    const int32_t nc = pl.fronts[t.front].ncol, lim = t.b < nc ? nc : nf(t.front);
-    need(t.a >= 0 && t.a < nf(t.front) && t.a % kBuildTile == 0 && t.b >= 0 &&
-             t.b <= t.a + kBuildTile - 1 && t.c >= 1 && t.c <= kBuildTile && t.b + t.c <= lim &&
-             (t.b < nc ? t.b : t.b - nc) % kBuildTile == 0,
-         "build task");
+  // build tiles: in range, and together covering every lower-triangle entry of
+  // each front exactly once (tiles of a front in strictly increasing (row,
+  // column) order, entry counts adding up to nf (nf + 1) / 2)
+  {
+    int32_t cur = -1, pa = -1, pb = -1;
+    int64_t covered = 0;
+    auto close_front = [&]() {
+      if (cur >= 0) need(covered == (int64_t)nf(cur) * (nf(cur) + 1) / 2, "build tiles cover the front");
+    };
+    for (const Task &t : pl.build_tasks) {
+      need(in_front(t), "build task");
+      const int32_t nc = pl.fronts[t.front].ncol, n = nf(t.front), lim = t.b < nc ? nc : n;
+      need(t.a >= 0 && t.a < n && t.a % kBuildTile == 0 && t.b >= 0 &&
+               t.b <= t.a + kBuildTile - 1 && t.c >= 1 && t.c <= kBuildTile && t.b + t.c <= lim &&
+               (t.b < nc ? t.b : t.b - nc) % kBuildTile == 0,
+           "build task");
+      if (t.front != cur) {
+        close_front();
+        cur = t.front;
+        covered = 0;
+        pa = pb = -1;
+      } else {
+        need(t.a > pa || (t.a == pa && t.b > pb), "build tiles in order");
+      }
+      pa = t.a;
+      pb = t.b;
+      // entries (r, c) with c <= r, r in [a, min(a + tile, n)), c in [b, b + w)
+      const int64_t lo = t.a, hi = std::min<int64_t>(t.a + kBuildTile, n) - 1, b = t.b, w = t.c;
+      const int64_t s0 = std::max(lo, b), s1 = std::min(hi, b + w - 2);
+      if (s1 >= s0) {
+        const int64_t u0 = s0 - b + 1, u1 = s1 - b + 1;
+        covered += (u0 + u1) * (u1 - u0 + 1) / 2;
+      }
+      covered += w * std::max<int64_t>(0, hi - std::max(lo, b + w - 1) + 1);
+    }
+    close_front();
   }
   for (const Task &t : pl.gemm_tasks)
     need(in_front(t) && t.b > 0 && t.b < pl.fronts[t.front].ncol && t.a >= t.b &&
