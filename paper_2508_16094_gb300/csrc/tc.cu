@@ -30,6 +30,7 @@ constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kSyrkN = 256;
 constexpr int kMaxClusters = 76;  // CTA pairs of the persistent SYRK (152 SMs)
 constexpr int kSuper = 512;  // columns per super-step of the left-looking panel updates
 constexpr int kAheadFronts = 2;  // levels with at most this many fronts run the look-ahead
+constexpr int kBandGroup = 16;   // row bands per group of the SYRK's tile order
 constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per 128-row operand tile
 constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
 // Ring depth: as many stages as fit in ~200 KB (each stage: A and B tiles, and
@@ -872,13 +873,15 @@ void TcPlan::build(const Plan &plan) {
     // the side stream meanwhile, and super-step s + 1 starts with the update by
     // super-step s's columns only (K in [K0, K0 + kSuper)).
     auto enc = [](int32_t kbeg, int32_t kend) { return 0 | (kbeg / kNb) << 2 | (kend / kNb) << 17; };
-    // columns [c0, c0 + kSuper) of all fronts: 256-wide tiles in row pairs
+    // columns [c0, c0 + kSuper) of all fronts: 256-wide tiles in row pairs,
+    // rows outermost so that the column tiles of a row band run back to back
+    // (one read of the band's A rows serves both)
     auto span = [&](int32_t c0, int32_t kbeg, int32_t kend) {
       for (int32_t t = LP.front_b; t < LP.front_e; t++) {
         const int32_t s = plan.level_fronts[t];
         const FrontInfo &F = plan.fronts[s];
-        for (int32_t c = c0; c < std::min(F.ncol, c0 + kSuper); c += kSyrkN)
-          for (int32_t i0 = c; i0 < F.ncol + F.nrow; i0 += 2 * kTileM)
+        for (int32_t i0 = c0; i0 < F.ncol + F.nrow; i0 += 2 * kTileM)
+          for (int32_t c = c0; c < std::min(F.ncol, c0 + kSuper) && c <= i0; c += kSyrkN)
             pairs_.push_back({s, i0, c, enc(kbeg, kend)});
       }
     };
@@ -928,12 +931,20 @@ void TcPlan::build(const Plan &plan) {
       sp.step_e = (int)lv.steps.size();
       lv.supers.push_back(sp);
     }
-    lv.pair_b = (int)pairs_.size();  // SYRK: 128 x 256 tiles (i0, j0), (i0 + 128, j0) of the lower triangle
+    // SYRK: 128 x 256 tiles (i0, j0), (i0 + 128, j0) of the lower triangle,
+    // ordered in groups of kBandGroup row bands with the column outermost, so
+    // that the pairs running at the same time share a few A bands and B panels
+    lv.pair_b = (int)pairs_.size();
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = plan.level_fronts[t];
       const FrontInfo &F = plan.fronts[s];
-      for (int32_t i0 = 0; i0 < F.nrow; i0 += 2 * kTileM)
-        for (int32_t j0 = 0; j0 <= i0; j0 += kSyrkN) pairs_.push_back({s, i0, j0, 1});
+      constexpr int32_t band = 2 * kTileM;
+      for (int32_t g0 = 0; g0 < F.nrow; g0 += kBandGroup * band) {
+        const int32_t g1 = std::min(F.nrow, g0 + kBandGroup * band);
+        for (int32_t j0 = 0; j0 < g1; j0 += kSyrkN)
+          for (int32_t i0 = g0; i0 < g1; i0 += band)
+            if (j0 <= i0) pairs_.push_back({s, i0, j0, 1});
+      }
     }
     lv.pair_e = (int)pairs_.size();
   }
