@@ -1,15 +1,22 @@
-// Tensor-core GEMM for the supernodal factorisation on sm_103a (tcgen05 + TMA).
+// Tensor-core kernels of the supernodal factorisation on sm_103a (tcgen05,
+// TMA, thread-block clusters).
 //
-// One CTA computes one 128 x 128 tile of C -= A B^T, where A and B are row
-// blocks of a front's panel (row-major, K contiguous: "K-major") and C is
-// either the panel itself (left-looking update of a block column) or the
-// front's update matrix (SYRK). Warp 0 streams 128 x 32 FP32 tiles of A and B
-// through a 4-stage ring of 128B-swizzled shared memory with TMA, warp 1
-// issues tcgen05.mma kind::tf32 (M=128, N=128, K=8) into a 128-column FP32
-// accumulator in tensor memory, warps 2-5 read the accumulator back with
-// tcgen05.ld and subtract it from C. Every wait on an mbarrier is bounded by a
-// clock limit; on expiry the CTA records ST_TIMEOUT, skips the epilogue and
-// still releases its tensor memory.
+// Two persistent GEMM kernels compute C -= A B^T (or C = A B^T) where A and B
+// are row blocks of a front's panel (row-major, K contiguous: "K-major"):
+//  - tc_pair_kernel: 128 x 256 tiles in clusters of two CTAs that share their
+//    B rows by TMA multicast; the update-matrix SYRK and the left-looking
+//    super-step updates of the panel;
+//  - tc_gemm_kernel: 128 x 128 tiles; the short per-block-step updates and the
+//    triangular solve of the rows below a diagonal block as a product with its
+//    inverse.
+// In both, warp 0 streams 128 x 32 FP32 tiles (and, for the 3-term split, their
+// low parts) through a ring of 128B-swizzled shared memory with TMA, warp 1
+// issues tcgen05.mma kind::tf32 into one of two FP32 accumulators in tensor
+// memory, and warps 2-5 read the other accumulator back with tcgen05.ld and
+// hand it to TMA through shared memory (reduce-add or store). potrf_inv_kernel
+// factors and inverts the 128 x 128 diagonal blocks on the FMA pipe. Every wait
+// on an mbarrier is bounded by a clock limit; on expiry the CTA records
+// ST_TIMEOUT, skips the rest of its work and still releases its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -226,33 +233,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// Task: front, a = first row of the A tile (front-local), b = k (modes 0, 2) or
-// j0 (mode 1), c = mode | slot << 2.
-//  Mode 0 (left-looking update): C = panel[a:a+128, k:k+kb] -= A B^T with
-//    A = panel rows a.., B = panel rows k.., K = k.
-//  Mode 1 (update matrix): C = U[a:a+128, b:b+128] -= A B^T with
-//    A = panel rows ncol+a.., B = panel rows ncol+b.., K = ncol.
+// Task of the 128 x 128 kernel: front, a = first row of the A tile
+// (front-local), b = k, c = mode | slot << 2 (mode 2) or mode | kbeg / 128 << 2
+// | kend / 128 << 17 (mode 0).
+//  Mode 0 (left-looking update of block column k by the columns [kbeg, kend)):
+//    C = panel[a:a+128, k:k+kb] -= A B^T with A = panel rows a.., B = panel
+//    rows k.., K = kend - kbeg.
 //  Mode 2 (triangular solve of the rows below a diagonal block, as a product
 //    with its inverse): C = panel[a:a+128, k:k+kb] = A B^T with A = the same
 //    panel rows and columns, B = L_kk^{-1} from scratch slot `slot`, K = kb.
 //    The tile's rows are read completely before its epilogue overwrites them.
+// (The update-matrix SYRK and the super-step updates run in the pair kernel.)
 //
-// SPLIT == 3: modes 0 and 1 read finished panel entries, whose low parts the
-// mode-2 epilogue stored in Llo: all four tiles (A, A_lo, B, B_lo) arrive by
-// TMA. Mode 2 reads entries that are still being updated and the inverse, so
-// warps 2-5 form their low parts in shared memory.
+// SPLIT == 3: mode 0 reads finished panel entries, whose low parts the mode-2
+// epilogue stored in Llo: all four tiles (A, A_lo, B, B_lo) arrive by TMA.
+// Mode 2 reads entries that are still being updated and the inverse, so warps
+// 2-5 form their low parts in shared memory.
 // Geometry of one task (see the task encoding above).
 struct Geo {
   int mode, arow, brow, K, M, N, ax0, bx0, nk;
-  float *C;
-  int64_t ldc;
   const CUtensorMap *amap, *bmap, *lomap;
 };
 
-template <int BN>
 __device__ __forceinline__ Geo task_geo(const DevPlan &dp, const Task &tk, const CUtensorMap *maps,
                                         const CUtensorMap *maps_lo, const CUtensorMap *inv_map,
-                                        float *L, float *U, int nb) {
+                                        int nb) {
   const FrontInfo F = dp.fronts[tk.front];
   const int nf = F.ncol + F.nrow;
   Geo g;
@@ -260,36 +265,21 @@ __device__ __forceinline__ Geo task_geo(const DevPlan &dp, const Task &tk, const
   g.amap = maps + tk.front;
   g.bmap = g.amap;
   g.lomap = maps_lo + tk.front;
-  g.ax0 = g.bx0 = 0;
+  const int k = tk.b;
+  g.arow = tk.a;
+  g.M = min(kTileM, nf - tk.a);
+  g.N = min(nb, F.ncol - k);
   if (g.mode == 0) {  // K range [kbeg, kend) of the update of block column k
-    const int k = tk.b, kbeg = ((tk.c >> 2) & 0x7FFF) * kTileN, kend = ((tk.c >> 17) & 0x7FFF) * kTileN;
-    g.arow = tk.a;
+    const int kbeg = ((tk.c >> 2) & 0x7FFF) * kTileN, kend = ((tk.c >> 17) & 0x7FFF) * kTileN;
     g.brow = k;
     g.ax0 = g.bx0 = kbeg;
     g.K = kend - kbeg;
-    g.M = min(kTileM, nf - tk.a);
-    g.N = min(nb, F.ncol - k);
-    g.C = L + F.loff + (int64_t)tk.a * F.ld + k;
-    g.ldc = F.ld;
-  } else if (g.mode == 2) {
-    const int k = tk.b;
-    g.arow = tk.a;
+  } else {
     g.ax0 = k;
+    g.bx0 = 0;
     g.brow = (tk.c >> 2) * kTileN;
     g.bmap = inv_map;
-    g.N = min(nb, F.ncol - k);
     g.K = g.N;
-    g.M = min(kTileM, nf - tk.a);
-    g.C = L + F.loff + (int64_t)tk.a * F.ld + k;
-    g.ldc = F.ld;
-  } else {
-    g.arow = F.ncol + tk.a;
-    g.brow = F.ncol + tk.b;
-    g.K = F.ncol;
-    g.M = min(kTileM, F.nrow - tk.a);
-    g.N = min(BN, F.nrow - tk.b);
-    g.C = U + F.uoff + (int64_t)tk.a * F.uld + tk.b;
-    g.ldc = F.uld;
   }
   g.nk = (g.K + kTileK - 1) / kTileK;
   return g;
@@ -303,9 +293,8 @@ template <int SPLIT, int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, int ntask,
                    const CUtensorMap *__restrict__ maps, const CUtensorMap *__restrict__ maps_lo,
-                   const CUtensorMap *__restrict__ inv_map, const CUtensorMap *__restrict__ umaps,
-                   const CUtensorMap *__restrict__ lmaps, const CUtensorMap *__restrict__ llomaps,
-                   float *__restrict__ L, float *__restrict__ U, int nb, int32_t *status) {
+                   const CUtensorMap *__restrict__ inv_map, const CUtensorMap *__restrict__ lmaps,
+                   const CUtensorMap *__restrict__ llomaps, int nb, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -355,7 +344,7 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {  // TMA producer
       uint32_t g = 0;
       for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x) {
-        const Geo G = task_geo<BN>(dp, tasks[t], maps, maps_lo, inv_map, L, U, nb);
+        const Geo G = task_geo(dp, tasks[t], maps, maps_lo, inv_map, nb);
         const bool pre = SPLIT == 3 && G.mode != 2;  // low parts loaded with the tiles
         for (int kt = 0; kt < G.nk; kt++, g++) {
           const int s = g % S;
@@ -384,7 +373,7 @@ __global__ void __launch_bounds__(192, 1)
       uint32_t g = 0;
       int i = 0;
       for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
-        const Geo G = task_geo<BN>(dp, tasks[t], maps, maps_lo, inv_map, L, U, nb);
+        const Geo G = task_geo(dp, tasks[t], maps, maps_lo, inv_map, nb);
         const bool conv = SPLIT == 3 && G.mode == 2;
         const int a = i & 1;
         if (!mbar_wait(&accempty[a], ((i >> 1) & 1) ^ 1, status)) { *abort_flag = 1; break; }
@@ -425,7 +414,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t g = 0;
     int i = 0;
     for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
-      const Geo G = task_geo<BN>(dp, tasks[t], maps, maps_lo, inv_map, L, U, nb);
+      const Geo G = task_geo(dp, tasks[t], maps, maps_lo, inv_map, nb);
       if (SPLIT == 3 && G.mode == 2) {
         // low parts x - tf32(x) of both operand tiles (tf32 keeps the top 19 bits)
         const int tt = threadIdx.x - 64;
@@ -450,12 +439,12 @@ __global__ void __launch_bounds__(192, 1)
       const int a = i & 1;
       if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // 32 x 32 blocks through shared memory to TMA: modes 0 and 1 add the
-      // negated block in L2 (C -= A B^T), mode 2 stores it and its low parts.
+      // 32 x 32 blocks through shared memory to TMA: mode 0 adds the negated
+      // block in L2 (C -= A B^T), mode 2 stores it and its low parts.
       if (32 * q < G.M) {
         const Task tk = tasks[t];
-        const int y = tk.a + 32 * q, x0 = tk.b;  // panel (modes 0, 2) or update-matrix rows
-        const CUtensorMap *cm = G.mode == 1 ? umaps + tk.front : lmaps + tk.front;
+        const int y = tk.a + 32 * q, x0 = tk.b;  // panel rows and columns
+        const CUtensorMap *cm = lmaps + tk.front;
         for (int cb = 0; cb < (G.N + 31) / 32; cb++) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + cb * 32), v);
@@ -1096,13 +1085,12 @@ static int sm_count() {
 // Persistent launch: at most ctas CTAs (one per SM), each taking tiles ctas apart.
 template <int SPLIT, int BN>
 static void gemm_launch(int ntask, int ctas, const DevPlan &dp, const Task *tasks,
-                        const CUtensorMap *maps, int nfronts, float *L, float *U, int32_t *status,
-                        cudaStream_t st) {
+                        const CUtensorMap *maps, int nfronts, int32_t *status, cudaStream_t st) {
   const CUtensorMap *maps_lo = maps + nfronts, *inv_map = maps + 2 * nfronts;
-  const CUtensorMap *umaps = inv_map + 1, *lmaps = umaps + nfronts, *llomaps = lmaps + nfronts;
+  const CUtensorMap *lmaps = inv_map + 1 + nfronts, *llomaps = lmaps + nfronts;
   note_launch();
   tc_gemm_kernel<SPLIT, BN><<<std::min(ntask, std::max(ctas, 1)), 192, Cfg<SPLIT, BN>::smem, st>>>(
-      dp, tasks, ntask, maps, maps_lo, inv_map, umaps, lmaps, llomaps, L, U, TcPlan::kNb, status);
+      dp, tasks, ntask, maps, maps_lo, inv_map, lmaps, llomaps, TcPlan::kNb, status);
 }
 
 // Pair kernel on at most ctas CTAs (clusters of two, each pair of tiles ncl apart).
@@ -1133,7 +1121,7 @@ void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, flo
   const int sms = sm_count();
   const int main_ctas = std::min(kMainCtas, sms / 2), side_ctas = sms - main_ctas;
   auto gemm = [&](const Task *t, int n, int ctas, cudaStream_t s) {
-    gemm3(n, ctas, dp, t, maps, nfronts_, L, U, status, s);
+    gemm3(n, ctas, dp, t, maps, nfronts_, status, s);
   };
   auto pair = [&](int b, int e, int ctas, cudaStream_t s) {
     if (e > b) pair3(e - b, ctas, dp, d_pairs_ + b, maps, nfronts_, status, s);

@@ -1,8 +1,9 @@
 // Tensor-core (tcgen05) factorisation path: TF32 operands staged by TMA into
 // 128B-swizzled shared memory, FP32 accumulators in tensor memory. The GEMM-
-// shaped work of the factorisation (left-looking panel updates and the
-// update-matrix SYRK) runs here; the diagonal-block Cholesky and the
-// triangular solve of the rows below stay on the FP32 FMA pipe.
+// shaped work of the factorisation (left-looking panel updates, the triangular
+// solve of the rows below a diagonal block as a product with its inverse, and
+// the update-matrix SYRK) runs on the tensor cores; the diagonal-block
+// Cholesky and its inverse run on the FP32 FMA pipe.
 #pragma once
 
 #include <vector>
