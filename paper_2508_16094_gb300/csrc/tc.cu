@@ -877,6 +877,7 @@ void TcPlan::build(const Plan &plan) {
     bool ahead_done = false;  // the previous super-step ran this one's update ahead
     for (int32_t K0 = 0; K0 < LP.max_ncol; K0 += kSuper) {
       Super sp{};
+      sp.k0 = K0;
       sp.now_b = (int)pairs_.size();
       if (K0 > 0) span(K0, ahead_done ? K0 - kSuper : 0, K0);
       sp.now_e = (int)pairs_.size();
@@ -968,6 +969,28 @@ void TcPlan::build(const Plan &plan) {
   }
   for (const Task &t : potrf_)
     if (!(t.a >= 0 && t.a < plan.fronts[t.front].ncol && t.b >= 0 && t.b < max_slots_)) fail("potrf");
+  // The look-ahead runs concurrently with the block steps of its super-step:
+  // it may only read columns before k0 and write columns from k0 + kSuper on,
+  // while everything on the main stream stays inside [k0, k0 + kSuper).
+  auto kend_of = [](const Task &t) { return ((t.c >> 17) & 0x7FFF) * kNb; };
+  auto kbeg_of = [](const Task &t) { return ((t.c >> 2) & 0x7FFF) * kNb; };
+  for (const Level &lv : levels_)
+    for (const Super &sp : lv.supers) {
+      const int32_t lo = sp.k0, hi = sp.k0 + kSuper;
+      for (int i = sp.ahead_b; i < sp.ahead_e; i++)
+        if (!(kend_of(pairs_[i]) <= lo && pairs_[i].b >= hi)) fail("look-ahead columns");
+      for (int i = sp.now_b; i < sp.now_e; i++)
+        if (!(pairs_[i].b >= lo && pairs_[i].b < hi && kend_of(pairs_[i]) <= lo)) fail("super-step update");
+      for (int i = sp.step_b; i < sp.step_e; i++) {
+        const Step &st = lv.steps[i];
+        for (int q = st.gemm_b; q < st.gemm_e; q++)
+          if (!(gemm_[q].b >= lo && gemm_[q].b < hi && kbeg_of(gemm_[q]) >= lo)) fail("block-step update");
+        for (int q = st.potrf_b; q < st.potrf_e; q++)
+          if (!(potrf_[q].a >= lo && potrf_[q].a < hi)) fail("block-step factor");
+        for (int q = st.trsm_b; q < st.trsm_e; q++)
+          if (!(trsm_[q].b >= lo && trsm_[q].b < hi)) fail("block-step solve");
+      }
+    }
   ready_ = false;
 }
 

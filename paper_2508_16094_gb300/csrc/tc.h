@@ -45,7 +45,7 @@ class TcPlan {
   // A super-step: the update of its columns by the previous super-step's
   // (now_*), the look-ahead update of the next super-step's columns by all
   // columns before this one (ahead_*, side stream), and its block steps.
-  struct Super { int now_b, now_e, ahead_b, ahead_e, step_b, step_e; };
+  struct Super { int k0, now_b, now_e, ahead_b, ahead_e, step_b, step_e; };  // k0: first column
   struct Level {
     std::vector<Step> steps;
     std::vector<Super> supers;
