@@ -448,7 +448,7 @@ def run_ours(args, ws, rank, local):
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": f"grid LP {G}^3 (n=m={lp.n}, 7-point rows, N(0,1)+8 diagonal, "
                                    f"bounds [0,10], ND ordering), one IPM iteration per step",
-                       "precision": args.precision, "global_batch": ws, "seq_len": None,
+                       "precision": args.precision, "replicas": ws,
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (factor storage "
                              f"{info.factor_entries * (8 if prec == 0 else 4) / 1e9:.1f} GB)",
