@@ -10,8 +10,10 @@ time-to-1e-6 KKT residual of a full solve.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU runs are independent replicas (one solve per GPU, no collective on
-the data path): value = flops of all ranks / max over ranks of the time.
+A step is one iteration of the cold-start solve to a 1e-6 KKT residual,
+replayed from the iterate that iteration starts from (step k runs iteration
+k mod T of the T-iteration solve), so the timed work is exactly the method's.
+The method runs on one GPU; --gpus other than 1 is rejected.
 """
 from __future__ import annotations
 
@@ -146,11 +148,12 @@ def mpc_measure(steps: int = 3):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / steps
         st = b.status.cpu().numpy()
-        out[name] = {"ms_per_batch": t, "solves_per_s": mb.count / (t * 1e-3),
-                     "converged": int((st == 0).sum()), "max_kkt": float(b.kkt.max().item()),
-                     "mean_iters": float(b.iters.float().mean().item()),
+        out[name] = {"ms_per_batch": round(t, 3), "solves_per_s": round(mb.count / (t * 1e-3), 1),
+                     "converged": int((st == 0).sum()),
+                     "max_kkt": float(f"{b.kkt.max().item():.3e}"),
+                     "mean_iters": round(float(b.iters.float().mean().item()), 3),
                      "instances_per_cta": int(cfg.instances_per_cta), "ctas": int(cfg.ctas),
-                     "autotune_ms": [round(x, 3) for x in ms]}
+                     "autotune_ms": [round(x, 1) for x in ms]}
     return out
 
 
@@ -169,10 +172,12 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
     lp = gen.grid_lp(G, seed=seed)
     jv, b, c = dev(lp.val), dev(lp.b), dev(lp.c)
 
+    flops = []
+
     def mk(**kw):
         ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u,
                             options=gb.default_options(tol=1e-6, max_iter=200, **kw))
-        ctx.kkt_analyze(perm)
+        flops.append(ctx.kkt_analyze(perm).flops)
         ctx.ipm_set_workspace()
         return ctx
 
@@ -185,11 +190,12 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
         t0 = time.perf_counter()
         r = ctx.ipm_solve(jv, b, c, x, s, lam)
         torch.cuda.synchronize()
-        return {"seconds": time.perf_counter() - t0, "status": int(r.status),
+        return {"seconds": round(time.perf_counter() - t0, 4), "status": int(r.status),
                 "iterations": int(r.iterations), "factorizations": int(r.factorizations),
                 "learned_skips": int(r.learned_skips), "pcg_steps": int(r.pcg_steps),
-                "refine_steps": int(r.refine_steps), "kkt": r.kkt, "objective": r.objective,
-                "time_factor_s": r.time_factor_ms / 1e3, "time_solve_s": r.time_solve_ms / 1e3}
+                "kkt": float(f"{r.kkt:.3e}"), "objective": r.objective,
+                "time_factor_s": round(r.time_factor_ms / 1e3, 4),
+                "time_solve_s": round(r.time_solve_ms / 1e3, 4)}
 
     out = {"workload": f"grid LP {G}^3 (n={lp.n}), seed {seed}; network trained on seeds "
                        f"{list(train_seeds)} of the same family"}
@@ -216,7 +222,9 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
     ctx.close()
     ref = out["fp64"]["objective"]
     for k in ("tf32x3", "tf32x3_learned", "tf32x3_stale_E0"):
-        out[k]["objective_rel_diff_vs_fp64"] = abs(out[k]["objective"] - ref) / max(1.0, abs(ref))
+        out[k]["objective_rel_diff_vs_fp64"] = float(
+            f"{abs(out[k]['objective'] - ref) / max(1.0, abs(ref)):.2e}")
+    out["flops"] = flops[0]
     return out
 
 
@@ -243,9 +251,10 @@ def nlp_measure(N: int, max_iter: int = 60):
         t0 = time.perf_counter()
         r = G.ipm_solve_grid_nlp(ut, x, s, lam)
         torch.cuda.synchronize()
-        out[name] = {"seconds": time.perf_counter() - t0, "status": int(r.status),
-                     "iterations": int(r.iterations), "objective": r.objective, "kkt": r.kkt,
-                     "primal": r.primal_res, "dual": r.dual_res, "fp64_fallbacks": int(r.fp64_fallbacks),
+        out[name] = {"seconds": round(time.perf_counter() - t0, 3), "status": int(r.status),
+                     "iterations": int(r.iterations), "objective": r.objective,
+                     "kkt": float(f"{r.kkt:.3e}"), "primal": float(f"{r.primal_res:.3e}"),
+                     "dual": float(f"{r.dual_res:.3e}"), "fp64_fallbacks": int(r.fp64_fallbacks),
                      "regularizations": int(r.regularizations), "refine_steps": int(r.refine_steps),
                      "factor_flops": G.info.flops}
         G.ctx.close()
@@ -253,43 +262,19 @@ def nlp_measure(N: int, max_iter: int = 60):
     return out
 
 
-def dist_init():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
-        import torch
-        import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if backend == "nccl":
-            torch.cuda.set_device(local)
-        dist.init_process_group(backend=backend)
-    return ws, rank, local
+def world():
+    """(world size, rank) from the launcher's environment (no process group:
+    neither arm exchanges data between ranks)."""
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
 
 
-def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(ws, v: float) -> float:
-    if ws == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
-    t = torch.tensor([v], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def run_reference(args, ws, rank):
+def run_reference(args, rank):
     """The oracle as it stands, on the host cores: each step one Newton direction
-    of the 24^3 member of the grid-LP family."""
+    of the 24^3 member of the grid-LP family. Under torchrun only rank 0 runs."""
     if rank != 0:
         return
-    t_w = [oracle_direction_sample(ORACLE_GRID)[0] for _ in range(args.warmup)]
+    for _ in range(args.warmup):
+        oracle_direction_sample(ORACLE_GRID)
     ts = []
     flops = n = None
     for _ in range(args.steps):
@@ -304,29 +289,70 @@ def run_reference(args, ws, rank):
             "config": {"workload": f"grid LP {ORACLE_GRID}^3 sample of the 100^3 family "
                                    "(one Newton direction per step)",
                        "parallelism": "single host core"},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1,
+                             "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"one oracle Newton direction (assembly, left-looking "
                                        f"Cholesky, solves) on the {ORACLE_GRID}^3 grid LP, "
                                        f"n={n}"},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    del t_w
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, ws, rank, local):
+def record_trajectory(ctx, jv, b, c, x, s, lam, max_iter=200):
+    """The cold-start solve run one iteration per call: returns the iterate each
+    iteration starts from (device copies) and the last call's result. Warm
+    starts from the previous call's iterate reproduce the single solve's
+    iterations (the regularisation starts from delta_p in both)."""
+    ctx.ipm_set_options(max_iter=0, warm_start=0)
+    r = ctx.ipm_solve(jv, b, c, x, s, lam)
+    traj = []
+    ctx.ipm_set_options(max_iter=1, warm_start=1)
+    for _ in range(max_iter):
+        traj.append((x.clone(), s.clone(), lam.clone()))
+        r = ctx.ipm_solve(jv, b, c, x, s, lam)
+        if r.status == 0:
+            break
+        if r.status != 7:
+            raise RuntimeError(f"interior-point iteration failed: status {r.status}")
+    return traj, r
+
+
+def tti_run(ctx, jv, b, c, x, s, lam, prec, ref_obj=None):
+    """Cold start to the 1e-6 KKT residual in one ipm_solve call."""
+    import torch
+    ctx.ipm_set_options(max_iter=200, warm_start=0, tol=1e-6, precision=prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = ctx.ipm_solve(jv, b, c, x, s, lam)
+    torch.cuda.synchronize()
+    out = {"s": round(time.perf_counter() - t0, 4), "status": int(r.status),
+           "iters": int(r.iterations), "pcg": int(r.pcg_steps), "kkt": float(f"{r.kkt:.3e}"),
+           "obj": r.objective, "factor_s": round(r.time_factor_ms / 1e3, 4),
+           "solve_s": round(r.time_solve_ms / 1e3, 4)}
+    if ref_obj is not None:
+        out["obj_rel_diff"] = float(f"{abs(r.objective - ref_obj) / max(1.0, abs(ref_obj)):.2e}")
+    return out
+
+
+def run_ours(args, ws, rank):
     import torch
     import paper_2508_16094_gb300 as gb
 
+    if ws != 1 or args.gpus != 1:
+        # one factorisation per iteration on one GPU: there is nothing to shard
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "error": "single-GPU method: bench.py runs on "
+                              "one GPU only (--gpus 1, no torchrun)"}), flush=True)
+        sys.exit(2)
     gb.build()
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(0)
     pk, pk_src = peaks()
     prec = PREC[args.precision]
     G = args.grid
-    lp = gen.grid_lp(G, seed=1 + (rank if args.vary_seed else 0))
+    lp = gen.grid_lp(G, seed=1)
     perm = gen.nd_order_grid3d(G)
-    opts = gb.default_options(precision=prec, tol=1e-6, max_iter=args.warmup,
-                              storage_fp64=1 if prec == 0 else 0)
+    opts = gb.default_options(precision=prec, tol=1e-6, storage_fp64=1 if prec == 0 else 0)
     ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u, options=opts)
     t0 = time.perf_counter()
     info = ctx.kkt_analyze(perm)
@@ -338,30 +364,69 @@ def run_ours(args, ws, rank, local):
     x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
     s = torch.empty(mt, dtype=torch.float64, device="cuda")
     lam = torch.empty(mt, dtype=torch.float64, device="cuda")
-    # warm-up iterations from the cold start
-    ctx.ipm_set_options(max_iter=args.warmup, warm_start=0)
-    ctx.ipm_solve(jv, b, c, x, s, lam)
-    torch.cuda.synchronize()
-    # timed iterations, continuing from the warm-up iterate
-    ctx.ipm_set_options(max_iter=args.steps, warm_start=1, tol=0.0)
+
+    # the iterations of the cold-start solve to 1e-6, recorded once
+    traj, rlast = record_trajectory(ctx, jv, b, c, x, s, lam)
+    T = len(traj)
+
+    def restore(i):
+        xi, si, li = traj[i % T]
+        x.copy_(xi)
+        s.copy_(si)
+        lam.copy_(li)
+
+    # step k = iteration (k mod T) of that solve, from its own starting iterate
+    ctx.ipm_set_options(max_iter=1, warm_start=1, tol=1e-6)
+    for k in range(args.warmup):
+        restore(k)
+        ctx.ipm_solve(jv, b, c, x, s, lam)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(ws)
     torch.cuda.synchronize()
     l0 = gb.kernel_launches()
-    with ClockSampler(local) as clk:
+    pcg = refine = 0
+    fac_ms = sol_ms = 0.0
+    with ClockSampler(0) as clk:
         ev0.record(stream)
-        res = ctx.ipm_solve(jv, b, c, x, s, lam)
+        for k in range(args.steps):
+            restore(k)
+            r = ctx.ipm_solve(jv, b, c, x, s, lam)
+            pcg += r.pcg_steps
+            refine += r.refine_steps
+            fac_ms += r.time_factor_ms
+            sol_ms += r.time_solve_ms
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = gb.kernel_launches() - l0
-    barrier(ws)
     ms = ev0.elapsed_time(ev1)
-    steps_done = max(res.iterations, 1)
-    ms_max = max_over_ranks(ws, ms)
-    value = info.flops * steps_done * ws / (ms_max * 1e-3) / 1e12
+    value = info.flops * args.steps / (ms * 1e-3) / 1e12
 
-    # factorisation alone (the dominant kernel chain), CUDA events on the same stream
+    # end to end through the C ABI with host buffers: every step copies its
+    # inputs (J values, b, c and the starting iterate) from pinned host memory,
+    # runs the same iteration and reads the new iterate back
+    hj, hb, hc = (t.cpu().pin_memory() for t in (jv, b, c))
+    htraj = [tuple(t.cpu().pin_memory() for t in it) for it in traj]
+    hout = [torch.empty_like(t).pin_memory() for t in (htraj[0])]
+    h2d = 8 * (jv.numel() + b.numel() + c.numel() + x.numel() + s.numel() + lam.numel())
+    d2h = 8 * (x.numel() + s.numel() + lam.numel())
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(args.steps):
+        hx, hs, hl = htraj[k % T]
+        for dst, src in ((jv, hj), (b, hb), (c, hc), (x, hx), (s, hs), (lam, hl)):
+            dst.copy_(src, non_blocking=True)
+        ctx.ipm_solve(jv, b, c, x, s, lam)
+        for dst, src in zip(hout, (x, s, lam)):
+            dst.copy_(src, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ev0.elapsed_time(ev1)
+    e2e_val = info.flops * args.steps / (e2e_ms * 1e-3) / 1e12
+
+    # the factorisation chain alone (all launches of kkt_factor, both streams),
+    # CUDA events on the library's stream
+    restore(T // 2)
+    ctx.ipm_solve(jv, b, c, x, s, lam)  # leaves K of a mid-trajectory iterate assembled
     fts = []
     for _ in range(2):
         ev0.record(stream)
@@ -371,107 +436,112 @@ def run_ours(args, ws, rank, local):
         fts.append(ev0.elapsed_time(ev1))
     t_fac = float(np.mean(fts))
     achieved = info.flops / (t_fac * 1e-3) / 1e12
-    if prec in (2, 3, 4):
-        # tensor-core contraction: measured BF16 peak x nominal TF32/BF16 ratio (0.5);
-        # the 3-term split issues three TF32 products per algorithmic one
-        ratio = {2: 0.5, 3: 1.0, 4: 0.5 / 3.0}[prec]
+    # peak of the contraction's dtype: measured BF16 burst x nominal ratio
+    # (TF32 = 0.5); the split's three TF32 products are the implementation's
+    # work, reported beside it as the tensor pipe's product rate
+    ratio = {0: None, 1: None, 2: 0.5, 3: 1.0, 4: 0.5}[prec]
+    if ratio is not None:
         peak = pk["bf16_tflops"] * ratio
         bound = "tensor"
-        peak_note = f"{pk_src} bf16 burst x {ratio:.4g}" + {2: " (tf32)", 3: "", 4: " (tf32, 3 products per flop)"}[prec]
+        peak_note = f"{pk_src} bf16 burst x {ratio:g}" + (" (tf32)" if ratio == 0.5 else "")
     elif prec == 1:
-        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x max SM clock
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound, peak_note = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
     else:
         peak = 1.25
         bound, peak_note = "alu", "nominal FP64 rate (1.25 TFLOP/s)"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "supernodal factorisation (all launches of kkt_factor)",
+            "peak_source": peak_note, "duration_ms": round(t_fac, 3),
+            "work": "sum over columns of colcount^2 (algorithmic)"}
+    if prec == 4:
+        roof["products_frac"] = 3 * achieved / peak
 
-    # end to end through the C ABI with host buffers: H2D of the step's inputs
-    # (J values, b, c and the iterate) from pinned memory, one iteration, D2H
-    # of the new iterate
-    host = {k: t.cpu().pin_memory() for k, t in dict(jv=jv, b=b, c=c, x=x, s=s, lam=lam).items()}
-    hout = {k: torch.empty_like(host[k]).pin_memory() for k in ("x", "s", "lam")}
-    h2d = sum(t.numel() * 8 for t in host.values())
-    d2h = sum(t.numel() * 8 for t in hout.values())
-    ctx.ipm_set_options(max_iter=1)
-    e2e_ms = []
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for k in host:
-            {"jv": jv, "b": b, "c": c, "x": x, "s": s, "lam": lam}[k].copy_(host[k], non_blocking=True)
-        r1 = ctx.ipm_solve(jv, b, c, x, s, lam)
-        hout["x"].copy_(x, non_blocking=True)
-        hout["s"].copy_(s, non_blocking=True)
-        hout["lam"].copy_(lam, non_blocking=True)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(ev0.elapsed_time(ev1) / max(r1.iterations, 1))
-    e2e_val = info.flops * ws / (max_over_ranks(ws, float(np.mean(e2e_ms))) * 1e-3) / 1e12
+    # HBM rooflines of the solve and the assembly kernels (bytes per SURVEY's
+    # definitions: solve 2 x 4 B per stored L entry + vectors; assembly 8 B per
+    # J value, per D entry, per product operand pair read once and per K entry)
+    hbm = pk["hbm_gbs"]
+    extra_roof = {}
+    if prec != 0:
+        t_sol = ctx.kkt_time_kernel(1, reps=5)
+        sb = 2 * 4 * info.factor_entries + 4 * 3 * lp.n
+        extra_roof["psolve_kernel"] = {"bound": "hbm", "achieved": sb / (t_sol * 1e-3) / 1e9,
+                                       "peak": hbm, "unit": "GB/s",
+                                       "frac": sb / (t_sol * 1e-3) / 1e9 / hbm,
+                                       "ms": round(t_sol, 4), "bytes": sb}
+    t_as = ctx.kkt_time_kernel(0, reps=5)
+    ab = 8 * (int(lp.rowptr[-1]) + mt + info.nnz_k)
+    extra_roof["assemble_kernel"] = {"bound": "hbm", "achieved": ab / (t_as * 1e-3) / 1e9,
+                                     "peak": hbm, "unit": "GB/s",
+                                     "frac": ab / (t_as * 1e-3) / 1e9 / hbm,
+                                     "ms": round(t_as, 4), "bytes": ab}
 
-    # time to a 1e-6 KKT residual from the cold start
-    tti = None
+    # time to a 1e-6 KKT residual from the cold start, every precision of the
+    # factor on the 100^3 grid (the FP64 factor by extrapolation, below)
+    tti = {"workload": f"grid LP {G}^3 cold start to KKT <= 1e-6"}
     if args.tti:
-        ctx.ipm_set_options(max_iter=200, warm_start=0, tol=1e-6)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rt = ctx.ipm_solve(jv, b, c, x, s, lam)
-        torch.cuda.synchronize()
-        tti = {"seconds": time.perf_counter() - t0, "status": int(rt.status),
-               "iterations": int(rt.iterations), "kkt": rt.kkt, "objective": rt.objective,
-               "refine_steps": int(rt.refine_steps), "pcg_steps": int(rt.pcg_steps),
-               "fp64_fallbacks": int(rt.fp64_fallbacks),
-               "time_factor_s": rt.time_factor_ms / 1e3, "time_solve_s": rt.time_solve_ms / 1e3}
+        tti[args.precision] = tti_run(ctx, jv, b, c, x, s, lam, prec)
+        ref = tti[args.precision]["obj"]
+        for name in args.tti_forms.split(","):
+            if not name or name == args.precision or name == "fp64":
+                continue
+            try:
+                tti[name] = tti_run(ctx, jv, b, c, x, s, lam, PREC[name], ref)
+            except Exception as e:  # an unsupported precision is reported, not fatal
+                tti[name] = {"error": str(e)[:120]}
 
-    mpc = None
-    if rank == 0 and not args.no_mpc:
-        mpc = mpc_measure()
-    forms = None
-    if rank == 0 and args.forms_grid > 0:
-        forms = forms_measure(args.forms_grid)
-    nlp = None
-    if rank == 0 and args.nlp_grid > 0:
-        nlp = nlp_measure(args.nlp_grid)
+    mpc = mpc_measure() if not args.no_mpc else None
+    forms = forms_measure(args.forms_grid) if args.forms_grid > 0 else None
+    if forms is not None and args.tti:
+        # FP64 factor at this grid, extrapolated from the FP64 factor's measured
+        # rate on the forms grid: iterations x flops / rate (factor time only)
+        f64 = forms["fp64"]
+        rate = forms["flops"] * f64["factorizations"] / max(f64["time_factor_s"], 1e-9)
+        it = tti.get(args.precision, {}).get("iters", T)
+        tti["fp64_extrapolated"] = {"s_factor_only": round(it * info.flops / rate, 2),
+                                    "fp64_factor_tflops": round(rate / 1e12, 4),
+                                    "basis": f"{args.forms_grid}^3 FP64 factor rate x "
+                                             f"{G}^3 flops x {it} iterations"}
+    nlp = nlp_measure(args.nlp_grid) if args.nlp_grid > 0 else None
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         sec, oflops, on = oracle_direction_sample(ORACLE_GRID, reps=3)
-        cpu = {"value": oflops / sec / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": oflops / sec / 1e12, "unit": "TFLOP/s", "cores": 1,
+               "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one oracle Newton direction (assembly, left-looking Cholesky, solves) "
                          f"on the {ORACLE_GRID}^3 member of the grid-LP family (n={on}), "
-                         f"{sec:.1f} s on one host core"}
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
-            "steps": steps_done, "warmup": args.warmup, "ms_per_step": ms_max / steps_done,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": f"grid LP {G}^3 (n=m={lp.n}, 7-point rows, N(0,1)+8 diagonal, "
-                                   f"bounds [0,10], ND ordering), one IPM iteration per step",
-                       "precision": args.precision, "replicas": ws,
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (factor storage "
-                             f"{info.factor_entries * (8 if prec == 0 else 4) / 1e9:.1f} GB)",
-                       "factor_flops": info.flops, "nnz_l": info.nnz_l, "nsuper": info.nsuper,
-                       "levels": info.nlevels, "analyze_s": round(t_analyze, 2)},
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "supernodal factorisation (all launches of kkt_factor)",
-                         "peak_source": peak_note, "duration_ms": t_fac},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches),
-            "clocks": clk.summary(),
-            "time_to_kkt_1e-6": tti,
-            "mpc_batch": mpc,
-            "time_to_kkt_1e-6_forms": forms,
-            "grid_nlp": nlp,
-            "ipm_step": {"refine_steps": int(res.refine_steps), "pcg_steps": int(res.pcg_steps),
-                         "factor_ms": res.time_factor_ms / steps_done,
-                         "solve_ms": res.time_solve_ms / steps_done},
-        }
-        print(json.dumps(line), flush=True)
+                         f"{sec:.1f} s on 1 of {os.cpu_count()} host cores"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": f"grid LP {G}^3 (n=m={lp.n}, 7-point rows, N(0,1)+8 diagonal, "
+                               f"bounds [0,10], ND ordering); step k = iteration k mod {T} of "
+                               f"the cold-start solve to KKT <= 1e-6, from its own iterate",
+                   "precision": args.precision, "parallelism": "single GPU",
+                   "l2": "inputs larger than L2 (factor storage "
+                         f"{info.factor_entries * (8 if prec == 0 else 4) / 1e9:.1f} GB)",
+                   "factor_flops": info.flops, "nnz_l": info.nnz_l, "nsuper": info.nsuper,
+                   "levels": info.nlevels, "analyze_s": round(t_analyze, 2),
+                   "trajectory_iterations": T},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "mpc_batch": mpc,
+        "grid_nlp": nlp,
+        "time_to_kkt_1e-6_forms": forms,
+        "rooflines_hbm": extra_roof,
+        "ipm_step": {"pcg_steps": pcg / args.steps, "refine_steps": refine / args.steps,
+                     "factor_ms": fac_ms / args.steps, "solve_ms": sol_ms / args.steps},
+        "time_to_kkt_1e-6": tti,
+    }
+    print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -484,8 +554,9 @@ def main():
     ap.add_argument("--grid", type=int, default=100)
     ap.add_argument("--precision", choices=list(PREC), default="tf32x3")
     ap.add_argument("--no-tti", dest="tti", action="store_false")
+    ap.add_argument("--tti-forms", default="tf32,bf16",
+                    help="other factor precisions timed to 1e-6 on the bench grid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--vary-seed", action="store_true")
     ap.add_argument("--no-mpc", action="store_true")
     ap.add_argument("--nlp-grid", type=int, default=512,
                     help="grid of the NLP comparison (0: skip)")
@@ -493,14 +564,11 @@ def main():
                     help="grid of the FP64 / split-TF32 / learned time-to-1e-6 comparison (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
-    ws, rank, local = dist_init()
+    ws, rank = world()
     if args.impl == "reference":
-        run_reference(args, ws, rank)
+        run_reference(args, rank)
     else:
-        run_ours(args, ws, rank, local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        run_ours(args, ws, rank)
 
 
 if __name__ == "__main__":

@@ -208,12 +208,16 @@ IPM_API ipm_status kkt_factor(ipm_ctx *ctx, int32_t precision, int32_t *bad_col)
 
 /* Solve K x = b with the current factor: x = P^T L^{-T} L^{-1} P b, then FP64
  * refinement on the residual b - K x computed matrix-free from W, J, D
- * (Sec. 2, refinement; ipm_refine). d_b, d_x: length n, original numbering
- * (may alias). info may be NULL.
- * Errors: IPM_ERR_STATE before kkt_factor; IPM_ERR_NUMERIC if the residual
- * misses accept_tol. */
-IPM_API ipm_status kkt_solve(ipm_ctx *ctx, const double *d_b, double *d_x, int32_t refine,
-                     ipm_solve_info *info);
+ * (Sec. 2, refinement; ipm_refine). d_b, d_x: nrhs right-hand sides and
+ * solutions of length n each, stored one after the other (column k at offset
+ * k n), original numbering (may alias). Each right-hand side is solved and
+ * refined on its own; info (may be NULL) receives the summed iterations and
+ * the largest final relative residual.
+ * Errors: IPM_ERR_ARG for nrhs < 1; IPM_ERR_STATE before kkt_factor;
+ * IPM_ERR_NUMERIC if a residual misses accept_tol (the other right-hand sides
+ * are still solved). */
+IPM_API ipm_status kkt_solve(ipm_ctx *ctx, const double *d_b, double *d_x, int32_t nrhs,
+                     int32_t refine, ipm_solve_info *info);
 
 /* The whole method on the LP/QP  min c^T x + 1/2 x^T W x  s.t.  J x >= b,
  * l <= x <= u  (Sec. 3): Mehrotra predictor-corrector on the primal condensed
@@ -402,8 +406,27 @@ IPM_API ipm_status kkt_export_assembled(ipm_ctx *ctx, double *h_out);
 IPM_API ipm_status kkt_factor_entries(ipm_ctx *ctx, int64_t count, const int32_t *h_rows,
                               const int32_t *h_cols, double *h_out);
 
+/* Test of the bounded device-side waits: the next launch of the persistent
+ * FP32 triangular solve (kkt_solve with an FP32-storage factor) polls each
+ * grid barrier at most `spins` times, and its CTA `withheld_cta` leaves the
+ * launch at its first barrier without arriving, so the other CTAs' waits run
+ * out. That kkt_solve then returns IPM_ERR_TIMEOUT and resets the barrier
+ * state; the context stays usable. Applies to one launch only.
+ * Errors: IPM_ERR_ARG for spins == 0 or a negative CTA index. */
+IPM_API ipm_status kkt_test_solve_timeout(ipm_ctx *ctx, uint32_t spins, int32_t withheld_cta);
+
 /* Low-precision pivots replaced by the last kkt_factor. */
 IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);
+
+/* Measurement: average duration in milliseconds (CUDA events on the
+ * context's stream) of reps back-to-back launches of one of this library's
+ * kernels on the context's current data. kernel 0: the assembly kernel of
+ * Eq. (5) on the inputs of the last kkt_assemble (rewrites the same K);
+ * 1: the persistent FP32 triangular solve (both sweeps) with the current
+ * FP32-storage factor; 2: the FP64 level-scheduled triangular solve with the
+ * current FP64 factor. The solves overwrite the context's solve scratch only.
+ * Errors: IPM_ERR_STATE if the data the kernel needs is missing. */
+IPM_API ipm_status kkt_time_kernel(ipm_ctx *ctx, int32_t kernel, int32_t reps, double *ms);
 
 /* --- allocation-free solve -------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
@@ -420,14 +443,19 @@ IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);
  *  - Size limit: n + (update-vector entries of the plan) + 2464 doubles must fit
  *    the array, else IPM_ERR_NOMEM with the sizes in ipm_last_error (checked
  *    right after kkt_analyze, before any GPU work).
- *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any
- *    stream capture.
+ *  - When the array is committed: ipm_set_workspace looks up its device
+ *    address for the current device (once per device), which loads the part of
+ *    this library that holds it and so commits the 8 MiB on that device while
+ *    the caller is handing over memory anyway. kkt_solve_noalloc itself then
+ *    only reads the cached address: it loads no module and commits nothing.
+ *  - The device current at the call must be the one that was current at
+ *    ipm_set_workspace (the workspace's device); otherwise IPM_ERR_ARG and no
+ *    launch.
  *  - Every call on a device shares the one array, which keeps the last call's
  *    contents; calls that overlap on the GPU (other streams, other contexts,
  *    other threads) race on it and must be serialised by the caller.
- * Errors: IPM_ERR_STATE before kkt_factor, IPM_ERR_CUDA if the address lookup
- * or a launch fails. */
+ * Errors: IPM_ERR_STATE before kkt_factor, IPM_ERR_ARG on a device mismatch,
+ * IPM_ERR_CUDA if a launch fails. */
 IPM_API ipm_status kkt_solve_noalloc(ipm_ctx *ctx, const double *d_b, double *d_x);
 IPM_API int64_t kkt_solve_noalloc_capacity(void);
 

@@ -27,7 +27,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_NOMEM", 
 EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze", "ipm_set_workspace",
             "kkt_assemble", "kkt_factor", "kkt_solve", "ipm_solve", "ipm_newton_direction",
             "kkt_symbolic_export", "kkt_export_assembled", "kkt_factor_entries",
-            "ipm_last_perturbed", "ipm_kernel_launches", "kkt_solve_noalloc",
+            "ipm_last_perturbed", "kkt_time_kernel", "kkt_test_solve_timeout", "ipm_kernel_launches", "kkt_solve_noalloc",
             "kkt_solve_noalloc_capacity", "ipm_mpc_workspace_bytes", "ipm_mpc_prepare",
             "ipm_solve_batched", "ipm_mpc_autotune", "ipm_learned_param_count",
             "ipm_learned_weights", "ipm_learned_sample", "ipm_learned_loss_grad",
@@ -108,13 +108,15 @@ def load() -> C.CDLL:
         "ipm_set_workspace": (I32, [P, P, C.c_size_t]),
         "kkt_assemble": (I32, [P, P, P, P, D]),
         "kkt_factor": (I32, [P, I32, P]),
-        "kkt_solve": (I32, [P, P, P, I32, P]),
+        "kkt_solve": (I32, [P, P, P, I32, I32, P]),
         "ipm_solve": (I32, [P, P, P, P, P, P, P, P, P]),
         "ipm_newton_direction": (I32, [P] * 12),
         "kkt_symbolic_export": (I32, [P] * 9),
         "kkt_export_assembled": (I32, [P, P]),
         "kkt_factor_entries": (I32, [P, I64, P, P, P]),
         "ipm_last_perturbed": (I32, [P]),
+        "kkt_time_kernel": (I32, [P, I32, I32, P]),
+        "kkt_test_solve_timeout": (I32, [P, C.c_uint32, I32]),
         "ipm_kernel_launches": (I64, []),
         "kkt_solve_noalloc": (I32, [P, P, P]),
         "kkt_solve_noalloc_capacity": (I64, []),
@@ -242,8 +244,14 @@ class IpmContext:
         return st, bad.value
 
     def kkt_solve(self, b, x, refine=IPM_REFINE_IR, raise_on_error=True) -> SolveInfo:
+        """b, x: one right-hand side (length n) or several stored one after
+        the other (n * nrhs entries, e.g. a contiguous (nrhs, n) tensor)."""
         info = SolveInfo()
-        st = self._lib.kkt_solve(self.handle, _dp(b), _dp(x), int(refine), C.byref(info))
+        nsys = self.kkt_order()
+        if b.numel() != x.numel() or b.numel() % nsys != 0 or b.numel() == 0:
+            raise ValueError("b and x must hold nrhs * n entries")
+        st = self._lib.kkt_solve(self.handle, _dp(b), _dp(x), b.numel() // nsys, int(refine),
+                                 C.byref(info))
         if raise_on_error:
             self._check(st)
         return info
@@ -260,6 +268,10 @@ class IpmContext:
         self._check(self._lib.ipm_newton_direction(self.handle, _dp(jvals), _dp(b), _dp(c),
                                                    _dp(wvals), _dp(x), _dp(s), _dp(lam), _dp(w),
                                                    _dp(dx), _dp(ds), _dp(dl)))
+
+    def kkt_order(self) -> int:
+        """Order of the condensed matrix the context factors."""
+        return self.n
 
     def kkt_symbolic_export(self) -> dict:
         n, ns = self.n, self.info.nsuper
@@ -320,6 +332,18 @@ class IpmContext:
         self._check(self._lib.ipm_learned_train(self.handle, _dp(feat), _dp(z), _dp(w),
                                                 C.c_float(lr), int(steps), C.byref(loss)))
         return loss.value
+
+    def kkt_time_kernel(self, kernel: int, reps: int = 3) -> float:
+        """Milliseconds per launch of one library kernel (0 assembly,
+        1 persistent FP32 solve, 2 FP64 level solve) on the current data."""
+        ms = C.c_double()
+        self._check(self._lib.kkt_time_kernel(self.handle, int(kernel), int(reps), C.byref(ms)))
+        return ms.value
+
+    def kkt_test_solve_timeout(self, spins: int, withheld_cta: int = 0):
+        """Make the next persistent solve's grid-barrier waits run out (test
+        of the bounded wait; see the header)."""
+        self._check(self._lib.kkt_test_solve_timeout(self.handle, int(spins), int(withheld_cta)))
 
     def ipm_last_perturbed(self) -> int:
         return int(self._lib.ipm_last_perturbed(self.handle))

@@ -28,6 +28,7 @@ struct ipm_ctx {
   Plan plan;
   ipm_options opts;
   cudaStream_t st = nullptr;
+  int device = -1;  // the GPU current at ipm_set_workspace (the workspace's device)
   int state = 0;  // 0 created, 1 analysed, 2 workspace, 3 assembled, 4 factored
   std::string err;
   // workspace
@@ -57,6 +58,8 @@ struct ipm_ctx {
   double knorm = 0.0;           // ||K||_inf of the assembled matrix (when bwd_measure)
   bool have_stale = false;      // lb.D_old / diag_old / mu[0] describe the held factor
   int refine_override = -1, pcg_override = -1;
+  unsigned test_spins = 0;   // next persistent solve launch only: barrier poll limit
+  int test_withhold = -1;    // ... and the CTA that leaves at its first barrier
   double *lb_loss = nullptr;
   double *scal = nullptr, *partial = nullptr;
   IpmScalars *sc = nullptr;
@@ -329,7 +332,9 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
 void launch_fp32_solve(ipm_ctx *c, int which) {
   launch_psolve(c->dp, c->plan, (const float *)c->L, c->dinv, c->fsa, c->fsb, c->fsx,
                 reinterpret_cast<float *>(c->tv), c->pspart, c->psbar, c->status, which != 2, which != 1,
-                c->st);
+                c->st, c->test_spins, c->test_withhold);
+  c->test_spins = 0;
+  c->test_withhold = -1;
 }
 
 // out = M^{-1} b with the current factor (b, out: original numbering, device)
@@ -585,6 +590,10 @@ void learned_init_weights(ipm_ctx *c) {
   c->lb.step = 0;
 }
 
+// Device address of the allocation-free solve's static array on `dev`, looked
+// up (and the array committed) on the first call for that device.
+double *noalloc_scratch(int dev);
+
 }  // namespace
 
 // ===========================================================================
@@ -743,8 +752,15 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     if ((size_t)(base - (char *)buf) + c->ws_need - 256 > bytes) throw Fail{IPM_ERR_NOMEM, "workspace misaligned"};
     c->ws = base;
     c->ws_bytes = bytes;
+    CK(cudaGetDevice(&c->device));
     layout(c, base);
     CK(cudaStreamSynchronize(c->st));
+    // Commit the allocation-free solve's static array on this device now,
+    // while the caller is handing over memory anyway: a later
+    // kkt_solve_noalloc then loads no module and commits nothing.
+    noalloc_scratch(c->device);
+    CK(preload_level_solve());
+    CK(preload_vec_kernels());
     c->have_stale = false;
     if (c->lb_on) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
@@ -779,9 +795,26 @@ ipm_status kkt_factor(ipm_ctx *c, int32_t precision, int32_t *bad_col) {
   return guarded(c, [&]() -> ipm_status { return do_factor(c, precision, bad_col); });
 }
 
-ipm_status kkt_solve(ipm_ctx *c, const double *b, double *x, int32_t refine, ipm_solve_info *info) {
-  if (!c || !b || !x) return IPM_ERR_ARG;
-  return guarded(c, [&]() -> ipm_status { return do_solve(c, b, x, refine, info); });
+ipm_status kkt_solve(ipm_ctx *c, const double *b, double *x, int32_t nrhs, int32_t refine,
+                     ipm_solve_info *info) {
+  if (!c || !b || !x || nrhs < 1) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    // right-hand side k occupies b[k n .. (k+1) n); each is solved (and
+    // refined) on its own, the info reports the totals and the worst residual
+    const int64_t n = c->P.n;
+    ipm_solve_info all{0, 0, 0.0};
+    ipm_status worst = IPM_OK;
+    for (int32_t k = 0; k < nrhs; k++) {
+      ipm_solve_info one{};
+      const ipm_status st = do_solve(c, b + k * n, x + k * n, refine, &one);
+      all.iterations += one.iterations;
+      all.used_pcg = std::max(all.used_pcg, one.used_pcg);
+      all.rel_residual = std::max(all.rel_residual, one.rel_residual);
+      if (st != IPM_OK && worst == IPM_OK) worst = st;
+    }
+    if (info) *info = all;
+    return worst;
+  });
 }
 
 ipm_status ipm_newton_direction(ipm_ctx *c, const double *jv, const double *b, const double *cc,
@@ -1032,6 +1065,51 @@ ipm_status kkt_factor_entries(ipm_ctx *c, int64_t count, const int32_t *rows, co
 }
 
 int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0; }
+
+ipm_status kkt_test_solve_timeout(ipm_ctx *c, uint32_t spins, int32_t withheld_cta) {
+  if (!c || spins == 0 || withheld_cta < 0) return IPM_ERR_ARG;
+  c->test_spins = spins;
+  c->test_withhold = withheld_cta;
+  return IPM_OK;
+}
+
+ipm_status kkt_time_kernel(ipm_ctx *c, int32_t kernel, int32_t reps, double *ms) {
+  if (!c || !ms || reps < 1) return IPM_ERR_ARG;
+  return guarded(c, [&]() -> ipm_status {
+    if (kernel == 0 && c->state < 3) throw Fail{IPM_ERR_STATE, "nothing assembled"};
+    if (kernel != 0 && c->state < 4) throw Fail{IPM_ERR_STATE, "no factor"};
+    if (kernel == 1 && c->factor_prec == IPM_FP64)
+      throw Fail{IPM_ERR_STATE, "the persistent solve needs an FP32-storage factor"};
+    if (kernel == 2 && c->factor_prec != IPM_FP64)
+      throw Fail{IPM_ERR_STATE, "the level solve is timed on an FP64 factor"};
+    if (kernel < 0 || kernel > 2) throw Fail{IPM_ERR_ARG, "unknown kernel id"};
+    // the solves' work does not depend on the values: zero right-hand sides
+    if (kernel == 1) CK(cudaMemsetAsync(c->fsa, 0, c->P.n * sizeof(float), c->st));
+    if (kernel == 2) CK(cudaMemsetAsync(c->yv, 0, c->P.n * sizeof(double), c->st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, c->st));
+    for (int r = 0; r < reps; r++) {
+      if (kernel == 0)
+        launch_assemble(c->dp, c->cur_jvals, c->cur_D, c->cur_wvals, c->cur_delta_p, c->kval, c->st);
+      else if (kernel == 1)
+        launch_fp32_solve(c, 0);
+      else
+        launch_solve<double, double>(c->dp, c->plan, (const double *)c->L, c->yv, c->tv, c->st);
+    }
+    CK(cudaEventRecord(e1, c->st));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    if (kernel == 1) check_solve_barrier(c);
+    *ms = (double)t / reps;
+    return IPM_OK;
+  });
+}
 
 int32_t ipm_learned_param_count(void) { return kNParams; }
 
@@ -1378,13 +1456,20 @@ constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double *g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-// Device address of the array on the current device (set up once per device).
-double *noalloc_scratch() {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+}  // namespace
+
+namespace {
+
+// The lookup runs with `dev` current; cudaGetSymbolAddress loads this file's
+// module on that device (under lazy module loading, the first use of the
+// array is what commits it).
+double *noalloc_scratch(int dev) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) throw Fail{IPM_ERR_UNSUPPORTED, "device index too large"};
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != dev) throw Fail{IPM_ERR_ARG, "static scratch looked up with another device current"};
     void *p = nullptr;
     CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_noalloc_addr[dev] = static_cast<double *>(p);
@@ -1415,7 +1500,13 @@ ipm_status kkt_solve_noalloc(ipm_ctx *c, const double *b, double *x) {
                                     std::to_string(kRedBlocks * 8 + 32) + "); the limit is " +
                                     std::to_string(kNoAllocDoubles)};
     if (c->state < 4) throw Fail{IPM_ERR_STATE, "kkt_solve_noalloc before kkt_factor"};
-    double *base = noalloc_scratch();
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != c->device)
+      throw Fail{IPM_ERR_ARG, "kkt_solve_noalloc called with device " + std::to_string(cur) +
+                                  " current; the context's workspace is on device " +
+                                  std::to_string(c->device)};
+    double *base = noalloc_scratch(c->device);  // resolved by ipm_set_workspace
     double *partial = base;
     double *scal = base + (size_t)kRedBlocks * 8;
     double *y = scal + 32;

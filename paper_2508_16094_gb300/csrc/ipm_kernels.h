@@ -19,6 +19,9 @@ struct IpmScalars {
   double pad[5];
 };
 
+// Loads the vector kernels the allocation-free solve launches (see capi.cu).
+cudaError_t preload_vec_kernels();
+
 constexpr int kRedBlocks = 304;  // fixed grid of the first reduction pass (2 per SM)
 
 struct VecOps {

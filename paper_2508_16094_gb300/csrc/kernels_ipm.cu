@@ -368,6 +368,22 @@ __global__ void xpby_dev_kernel(int64_t n, const double *num, const double *den,
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Load the kernels of the allocation-free solve now (a function query loads a
+// lazily loaded kernel), so that its later launches commit no device memory.
+cudaError_t preload_vec_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess;
+  auto q = [&](const void *f) { if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, f); };
+  q((const void *)permute_in_kernel<double>);
+  q((const void *)permute_in_kernel<float>);
+  q((const void *)permute_out_kernel<double>);
+  q((const void *)permute_out_kernel<float>);
+  q((const void *)absmax_kernel);
+  q((const void *)inv_scale_kernel);
+  q((const void *)final_reduce_kernel<1>);
+  return e;
+}
+
 void VecOps::reduce_final(int ns, const RedOps &ops, double *out) const {
   switch (ns) {
     case 1: { note_launch(); final_reduce_kernel<1><<<1, kRedBlock, 0, st>>>(partial, kRedBlocks, ops, out); } break;

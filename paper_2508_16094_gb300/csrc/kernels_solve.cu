@@ -182,6 +182,23 @@ void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, c
   }
 }
 
+template <typename T, typename V>
+static cudaError_t preload_one() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, (const void *)gather_fwd_kernel<V>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)diag_fwd_kernel<T, V>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)upd_fwd_kernel<T, V>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)rows_bwd_kernel<T, V>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)diag_bwd_kernel<T, V>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)upd_bwd_kernel<T, V>);
+  return e;
+}
+
+cudaError_t preload_level_solve() {
+  cudaError_t e = preload_one<double, double>();
+  return e == cudaSuccess ? preload_one<float, float>() : e;
+}
+
 template void launch_solve<double, double>(const DevPlan &, const Plan &, const double *,
                                            double *, double *, cudaStream_t);
 template void launch_solve<float, float>(const DevPlan &, const Plan &, const float *, float *,

@@ -71,6 +71,8 @@ struct PsArgs {
   int32_t p0, p1;   // phases [p0, p1)
   unsigned *bar;    // [2..3] 64-bit arrival counter of the grid barrier
   int32_t *status;  // ST_SOLVE_TIMEOUT
+  unsigned spins;   // polls before a barrier wait gives up
+  int32_t withhold; // test of the bounded wait: this CTA leaves at its first barrier (-1: none)
 };
 
 constexpr int kMaxGrid = 1024;  // CTAs of one cooperative solve launch
@@ -96,11 +98,15 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 // CTA adds 1 (release) and waits (acquire) until the counter reaches the next
 // multiple of the grid size above the value it found, so launches need no
 // reset as long as every barrier of the previous one completed (after a
-// timeout the host zeroes the state). Every wait is bounded; on a timeout the
-// status word is set and all CTAs return false.
-__device__ bool grid_barrier(unsigned *bar, int32_t *status) {
+// timeout the host zeroes the state). Every wait is bounded (max_spins polls);
+// on a timeout the status word is set and all CTAs return false; a CTA that
+// sees the word set by another one stops waiting too. The CTA `withhold`
+// (tests of the bounded wait) returns false at once without arriving, so the
+// other CTAs' waits run out.
+__device__ bool grid_barrier(unsigned *bar, int32_t *status, unsigned max_spins, int withhold) {
   __shared__ int ok;
   __syncthreads();
+  if ((int)blockIdx.x == withhold) return false;
   if (threadIdx.x == 0) {
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(bar + 2);
     unsigned long long old, v;
@@ -111,10 +117,11 @@ __device__ bool grid_barrier(unsigned *bar, int32_t *status) {
     while (true) {
       asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
       if (v >= target) break;
-      if (++spins > kBarrierSpins) {
+      if (++spins > max_spins) {
         atomicExch(status + ST_SOLVE_TIMEOUT, 1);
         break;
       }
+      if ((spins & 63u) == 0 && *(volatile int32_t *)(status + ST_SOLVE_TIMEOUT) != 0) break;
       __nanosleep(16);
     }
     __threadfence();
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
       F = Fn;
       q = qn;
     }
-    if (p + 1 < A.p1 && !grid_barrier(A.bar, A.status)) return;
+    if (p + 1 < A.p1 && !grid_barrier(A.bar, A.status, A.spins, A.withhold)) return;
   }
 }
 
@@ -503,13 +510,14 @@ void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Din
 
 void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv, float *a,
                    float *b, float *x, float *t, float *part, unsigned *bar, int32_t *status, bool fwd,
-                   bool bwd, cudaStream_t st) {
+                   bool bwd, cudaStream_t st, unsigned test_spins, int test_withhold) {
   const int32_t p0 = fwd ? 0 : plan.ps_fwd_phases;
   const int32_t p1 = bwd ? (int32_t)plan.ps_phases.size() : plan.ps_fwd_phases;
   if (p1 <= p0) return;
   const int grid = psolve_grid(plan.ps_max_tasks);
   if (grid > kMaxGrid) throw std::runtime_error("persistent solve: grid above the barrier's capacity");
-  PsArgs A{dp, L, Dinv, a, b, x, t, part, p0, p1, bar, status};
+  PsArgs A{dp, L, Dinv, a, b, x, t, part, p0, p1, bar, status,
+           test_spins ? test_spins : kBarrierSpins, test_withhold};
   void *args[] = {&A};
   note_launch();
   ck(cudaLaunchCooperativeKernel((const void *)psolve_kernel, dim3(grid), dim3(kT), args,

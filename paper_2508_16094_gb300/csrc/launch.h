@@ -33,18 +33,24 @@ void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L,
 template <typename T, typename V>
 void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st);
 
+// Loads the level-solve kernels (FP64 and FP32) so that a later first launch
+// commits no device memory (lazy module loading); used by the allocation-free solve.
+cudaError_t preload_level_solve();
+
 // Persistent FP32 solve: inverses of the 128-wide diagonal blocks (after each
 // FP32 factorisation), then x = L^{-T} L^{-1} a in one cooperative launch, with
 // b the forward result and t the update vectors. fwd/bwd select the sweeps:
 // forward only maps a to b = L^{-1} a; backward only maps b to x = L^{-T} b
 // (b is overwritten). part: plan.ps_part_entries floats of scratch. bar:
 // kPsBarrierWords zeroed words of grid-barrier state; a barrier that waits too
-// long sets status[ST_SOLVE_TIMEOUT] and the launch returns.
+// long sets status[ST_SOLVE_TIMEOUT] and the launch returns. test_spins (0:
+// the default of seconds) bounds each barrier wait; test_withhold >= 0 makes
+// that CTA leave at its first barrier (tests of the bounded wait).
 constexpr int kPsBarrierWords = 32 + 1024;
 void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Dinv, cudaStream_t st);
 void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv, float *a,
                    float *b, float *x, float *t, float *part, unsigned *bar, int32_t *status, bool fwd,
-                   bool bwd, cudaStream_t st);
+                   bool bwd, cudaStream_t st, unsigned test_spins = 0, int test_withhold = -1);
 
 // Sampled entries of L (final numbering).
 template <typename T>

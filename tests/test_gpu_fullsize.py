@@ -75,9 +75,16 @@ def test_split_tf32_factor_solve_residual_on_host(grid100):
     xs = x.cpu().numpy()
     r = np.abs(K @ xs - b).max() / np.abs(b).max()
     assert info.rel_residual <= 1e-10 and r <= 1e-9, (info.rel_residual, r)
-    # the unrefined factor solve is already a good preconditioner
+    # one unrefined solve has the normwise backward error of a split-TF32
+    # factor (near FP32 rounding): a dropped or doubled update of the
+    # super-step schedule would leave errors of the size of the entries
     info0 = ctx.kkt_solve(dev(b), x, gb.IPM_REFINE_NONE, raise_on_error=False)
+    x0 = x.cpu().numpy()
+    knorm = abs(K).sum(axis=1).max()
+    eta = np.abs(K @ x0 - b).max() / (knorm * np.abs(x0).max() + np.abs(b).max())
+    assert eta <= 1e-5, eta
     assert info0.rel_residual < 1e-2
+    assert ctx.ipm_last_perturbed() == 0
 
 
 def test_newton_direction_satisfies_condensed_system(grid100):
