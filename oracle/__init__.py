@@ -11,7 +11,10 @@ follows the paper's equations step by step:
   - ``factor`` / ``solve``: left-looking Cholesky without pivoting and
     forward/backward substitution (Sec. 2, "LDL^T Factorization"),
   - ``ipm_lp``: the interior-point method on the LP, KKT conditions (2),
-    Newton system (3) condensed to (5).
+    Newton system (3) condensed to (5),
+  - ``factor_ldlt`` / ``solve_ldlt``: LDL^T without pivoting of a
+    quasi-definite matrix, and ``forms``: the Newton direction through the
+    augmented system (4) and the dual condensed system (6).
 
 Pins (tests/test_oracle_*.py): numpy.linalg.cholesky on dense SPD matrices,
 brute-force symbolic factorisation, dense solves of the full Newton system (3),
@@ -23,6 +26,7 @@ from .oracle import (  # noqa: F401
     assemble,
     build,
     factor,
+    factor_ldlt,
     ipm_lp,
     k_dense,
     l_dense,
@@ -30,4 +34,5 @@ from .oracle import (  # noqa: F401
     lp_direction,
     lib_path,
     solve,
+    solve_ldlt,
 )

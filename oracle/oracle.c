@@ -558,6 +558,84 @@ ORC_EXPORT int32_t orc_factor(const orc_sym *S, const double *kval_orig, double 
   return bad;
 }
 
+/* Left-looking LDL^T factorisation K = L D L^T (L unit lower) without pivoting,
+ * for symmetric quasi-definite matrices such as the augmented system (4):
+ * a quasi-definite matrix has such a factorisation for every symmetric
+ * permutation, with the sign of each pivot fixed by the block its variable
+ * belongs to (strong factorizability, Sec. 2). sign_orig[i] (original
+ * numbering) is that expected sign (+1 or -1).
+ * For j = 0..n-1: w = K(j:, j); for every k < j with L(j, k) != 0:
+ * w -= L(j:, k) * L(j, k) * d_k; then d_j = w_j, L(i, j) = w_i / d_j.
+ * L is stored like the Cholesky factor (unit diagonal in the diagonal slot),
+ * d in dval (final numbering). Returns 0, or 1 + the first column whose pivot
+ * is zero, not finite or of the wrong sign. */
+ORC_EXPORT int32_t orc_factor_ldlt(const orc_sym *S, const double *kval_orig,
+                                   const int8_t *sign_orig, double *lval, double *dval) {
+  int32_t n = S->n;
+  double *kf = (double *)xmalloc(sizeof(double) * (S->kp[n] ? S->kp[n] : 1));
+  for (int64_t e = 0; e < S->kop[n]; e++) kf[S->kmap[e]] = kval_orig[e];
+  int64_t *rp = (int64_t *)xcalloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t e = 0; e < S->lp[n]; e++) rp[S->li[e] + 1]++;
+  for (int32_t i = 0; i < n; i++) rp[i + 1] += rp[i];
+  int32_t *rk = (int32_t *)xmalloc(sizeof(int32_t) * (S->lp[n] ? S->lp[n] : 1));
+  int64_t *fill = (int64_t *)xmalloc(sizeof(int64_t) * ((size_t)n + 1));
+  memcpy(fill, rp, sizeof(int64_t) * ((size_t)n + 1));
+  for (int32_t k = 0; k < n; k++)
+    for (int64_t e = S->lp[k]; e < S->lp[k + 1]; e++) rk[fill[S->li[e]]++] = k;
+  int64_t *next = (int64_t *)xmalloc(sizeof(int64_t) * ((size_t)(n > 0 ? n : 1)));
+  for (int32_t k = 0; k < n; k++) next[k] = S->lp[k];
+  double *w = (double *)xcalloc((size_t)n, sizeof(double));
+  int32_t bad = 0;
+  for (int32_t j = 0; j < n && !bad; j++) {
+    for (int64_t e = S->kp[j]; e < S->kp[j + 1]; e++) w[S->ki[e]] = kf[e];
+    for (int64_t t = rp[j]; t < rp[j + 1]; t++) {
+      int32_t k = rk[t];
+      int64_t pos = next[k]; /* li[pos] == j */
+      double ljk = lval[S->lp[k] + k + 1 + (pos - S->lp[k])];
+      double f = ljk * dval[k];
+      w[j] -= ljk * f;
+      for (int64_t e = pos + 1; e < S->lp[k + 1]; e++)
+        w[S->li[e]] -= lval[S->lp[k] + k + 1 + (e - S->lp[k])] * f;
+      next[k] = pos + 1;
+    }
+    double d = w[j];
+    int8_t sg = sign_orig[S->perm[j]];
+    if (!isfinite(d) || !(sg > 0 ? d > 0.0 : d < 0.0)) { bad = j + 1; break; }
+    dval[j] = d;
+    double *col = lval + S->lp[j] + j;
+    col[0] = 1.0;
+    w[j] = 0.0;
+    for (int64_t e = S->lp[j]; e < S->lp[j + 1]; e++) {
+      col[1 + (e - S->lp[j])] = w[S->li[e]] / d;
+      w[S->li[e]] = 0.0;
+    }
+  }
+  free(w); free(next); free(fill); free(rk); free(rp); free(kf);
+  return bad;
+}
+
+/* Solve K x = b with K = P^T L D L^T P: y = L^{-1} P b, y ./= d, z = L^{-T} y,
+ * x = P^T z (b, x in the ORIGINAL numbering). */
+ORC_EXPORT void orc_solve_ldlt(const orc_sym *S, const double *lval, const double *dval,
+                               const double *b, double *x) {
+  int32_t n = S->n;
+  double *y = (double *)xmalloc(sizeof(double) * ((size_t)(n > 0 ? n : 1)));
+  for (int32_t k = 0; k < n; k++) y[k] = b[S->perm[k]];
+  for (int32_t j = 0; j < n; j++) {
+    const double *col = lval + S->lp[j] + j;
+    for (int64_t e = S->lp[j]; e < S->lp[j + 1]; e++) y[S->li[e]] -= col[1 + (e - S->lp[j])] * y[j];
+  }
+  for (int32_t j = 0; j < n; j++) y[j] /= dval[j];
+  for (int32_t j = n - 1; j >= 0; j--) {
+    const double *col = lval + S->lp[j] + j;
+    double t = y[j];
+    for (int64_t e = S->lp[j]; e < S->lp[j + 1]; e++) t -= col[1 + (e - S->lp[j])] * y[S->li[e]];
+    y[j] = t;
+  }
+  for (int32_t k = 0; k < n; k++) x[S->perm[k]] = y[k];
+  free(y);
+}
+
 /* Solve K x = b with the factor: b, x in the ORIGINAL numbering.
  * y = L^{-1} P b (forward), z = L^{-T} y (backward), x = P^T z. */
 ORC_EXPORT void orc_solve(const orc_sym *S, const double *lval, const double *b, double *x) {

@@ -52,6 +52,9 @@ def _load():
         lib.orc_factor.restype = C.c_int32
         lib.orc_factor.argtypes = [P, P, P]
         lib.orc_solve.argtypes = [P, P, P, P]
+        lib.orc_factor_ldlt.restype = C.c_int32
+        lib.orc_factor_ldlt.argtypes = [P, P, P, P, P]
+        lib.orc_solve_ldlt.argtypes = [P, P, P, P, P]
         lib.orc_kmatvec.argtypes = [P, P, P, P]
         lib.orc_lp_direction.restype = C.c_int32
         lib.orc_lp_direction.argtypes = [P, C.c_int32] + [P] * 11 + [C.c_double, C.c_double,
@@ -154,6 +157,28 @@ def solve(S: OracleSymbolic, lval, b) -> np.ndarray:
     b = _c(b, np.float64)
     x = np.empty(S.n, np.float64)
     lib.orc_solve(C.c_void_p(S.handle), _p(_c(lval, np.float64)), _p(b), _p(x))
+    return x
+
+
+def factor_ldlt(S: OracleSymbolic, kval, sign) -> tuple[np.ndarray, np.ndarray, int]:
+    """Left-looking LDL^T without pivoting of a quasi-definite K; sign (original
+    numbering, +1/-1) is the pivot sign each variable's block prescribes.
+    Returns (unit-L values by column, d in the final numbering, bad) with bad
+    = 0 or 1 + the first column whose pivot is zero or of the wrong sign."""
+    lib = _load()
+    kval = _c(kval, np.float64)
+    sg = _c(sign, np.int8)
+    lval = np.zeros(S.nnz_l, np.float64)
+    dval = np.zeros(S.n, np.float64)
+    bad = lib.orc_factor_ldlt(C.c_void_p(S.handle), _p(kval), _p(sg), _p(lval), _p(dval))
+    return lval, dval, int(bad)
+
+
+def solve_ldlt(S: OracleSymbolic, lval, dval, b) -> np.ndarray:
+    lib = _load()
+    x = np.empty(S.n, np.float64)
+    lib.orc_solve_ldlt(C.c_void_p(S.handle), _p(_c(lval, np.float64)), _p(_c(dval, np.float64)),
+                       _p(_c(b, np.float64)), _p(x))
     return x
 
 
