@@ -321,13 +321,16 @@ def record_trajectory(ctx, jv, b, c, x, s, lam, max_iter=200):
 def tti_run(ctx, jv, b, c, x, s, lam, prec, ref_obj=None):
     """Cold start to the 1e-6 KKT residual in one ipm_solve call."""
     import torch
-    ctx.ipm_set_options(max_iter=200, warm_start=0, tol=1e-6, precision=prec)
+    # TF32/BF16 factors fall back to a split-TF32 refactorisation when their
+    # PCG misses the acceptance tolerance (counted in "fallbacks")
+    ctx.ipm_set_options(max_iter=200, warm_start=0, tol=1e-6, precision=prec, fallback_fp64=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = ctx.ipm_solve(jv, b, c, x, s, lam)
     torch.cuda.synchronize()
     out = {"s": round(time.perf_counter() - t0, 4), "status": int(r.status),
            "iters": int(r.iterations), "pcg": int(r.pcg_steps), "kkt": float(f"{r.kkt:.3e}"),
+           "fallbacks": int(r.fp64_fallbacks), "perturbed": int(r.perturbed_pivots),
            "obj": r.objective, "factor_s": round(r.time_factor_ms / 1e3, 4),
            "solve_s": round(r.time_solve_ms / 1e3, 4)}
     if ref_obj is not None:

@@ -99,7 +99,10 @@ typedef struct {
   int32_t ir_max;        /* refinement steps per solve (10) */
   double ir_tol;         /* stop once ||b - K x||_inf <= ir_tol ||b||_inf (1e-10) */
   int32_t pcg_max;       /* PCG iterations per solve (100) */
-  int32_t fallback_fp64; /* refactor in FP64 when refinement misses ir_tol (0) */
+  int32_t fallback_fp64; /* after a linear solve that misses accept_tol with a TF32/BF16/FP32
+                            factor, refactor in the most accurate arithmetic the storage
+                            allows (FP64 with FP64 storage, else the split TF32) and solve
+                            again; counted in ipm_result.fp64_fallbacks (0) */
   double accept_tol;     /* a solve that misses ir_tol but reaches accept_tol is used (1e-6) */
   int32_t verbose;       /* print one line per interior-point iteration to stderr */
   int32_t warm_start;    /* 1: ipm_solve starts from the x, s, lambda it is given (0) */
@@ -142,7 +145,8 @@ typedef struct {
   int32_t regularizations;  /* delta_p increases after a non-positive pivot */
   int32_t refine_steps;     /* total refinement steps */
   int32_t pcg_steps;        /* total PCG iterations */
-  int32_t fp64_fallbacks;   /* refactorisations in FP64 after a missed tolerance */
+  int32_t fp64_fallbacks;   /* refactorisations in the fallback arithmetic after a missed
+                               tolerance (see ipm_options.fallback_fp64) */
   int32_t perturbed_pivots; /* low-precision pivots replaced (static pivoting) */
   double objective;         /* f(x) at the returned point */
   double kkt;               /* scaled KKT residual (see ipm_solve) */

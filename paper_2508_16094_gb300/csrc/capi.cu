@@ -289,7 +289,6 @@ double d2h_scalar(ipm_ctx *c, const double *p) {
 ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   if (c->state < 3) throw Fail{IPM_ERR_STATE, "kkt_factor before kkt_assemble"};
   if (prec < IPM_FP64 || prec > IPM_TF32X3) throw Fail{IPM_ERR_ARG, "unknown precision"};
-  if (prec == IPM_BF16) throw Fail{IPM_ERR_UNSUPPORTED, "BF16 factorisation not available"};
   if (prec == IPM_FP64 && c->storage_bytes < 8)
     throw Fail{IPM_ERR_NOMEM, "factor storage sized for FP32; FP64 factor needs storage_fp64"};
   int32_t init[ST_COUNT] = {INT32_MAX, 0, 0, 0, 0, 0, 0, 0};
@@ -303,7 +302,7 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   } else {
     if (!c->tcp.ready()) throw Fail{IPM_ERR_UNSUPPORTED, "tensor-core factor not prepared"};
     c->tcp.factor(c->dp, c->plan, c->kval, (float *)c->L, (float *)c->U, c->dinv, c->status,
-                  prec == IPM_TF32X3 ? 3 : 1, c->st);
+                  prec == IPM_TF32X3 ? 3 : (prec == IPM_BF16 ? 16 : 1), c->st);
   }
   if (prec == IPM_FP32)  // explicit inverses of the diagonal blocks for the persistent solve
     launch_dinv(c->dp, c->plan, (const float *)c->L, c->dinv, c->st);  // (the TF32 paths write them)
@@ -951,11 +950,18 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       }
       CK(cudaEventRecord(ev[2], c->st));
       res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
-      if (stt != IPM_OK && o.fallback_fp64 && o.precision != IPM_FP64 && c->storage_bytes == 8) {
+      // A solve that missed accept_tol with a low-precision factor: refactor in
+      // the most accurate arithmetic the storage allows and solve again.
+      const int fb_prec = c->storage_bytes == 8 ? IPM_FP64 : IPM_TF32X3;
+      auto can_escalate = [&]() {
+        return o.fallback_fp64 && c->factor_prec != fb_prec && c->factor_prec != IPM_FP64 &&
+               (fb_prec == IPM_FP64 || c->tcp.ready());
+      };
+      if (stt != IPM_OK && can_escalate()) {
         res.fp64_fallbacks++;
         c->learned_active = false;
         c->refine_override = c->pcg_override = -1;
-        stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
+        stt = factor_with_retry(c, wv, jv, fb_prec, delta_p, &res);
         if (stt == IPM_OK)
           stt = direction(c, jv, b, cc, wv, x, s, lam, nullptr, c->vdx, c->vds, c->vdl, &si);
       }
@@ -971,6 +977,14 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
         if (with_stale) res.learned_pcg_steps += (int32_t)(c->pcg_steps - pcg0);
         if (with_stale && (stt != IPM_OK || !(c->last_rel <= o.ir_tol))) {
           stt = refactor();
+          if (stt == IPM_OK)
+            stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+        }
+        if (stt != IPM_OK && can_escalate()) {  // the corrector missed accept_tol
+          res.fp64_fallbacks++;
+          c->learned_active = false;
+          c->refine_override = c->pcg_override = -1;
+          stt = factor_with_retry(c, wv, jv, fb_prec, delta_p, &res);
           if (stt == IPM_OK)
             stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
         }
@@ -1001,7 +1015,7 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return (ipm_status)res.status;
   });
-  if (rs != IPM_OK && res.status == IPM_OK) res.status = rs;
+  res.status = rs;  // also the status of an error that ended the call early
   if (res_out) *res_out = res;
   return rs;
 }

@@ -336,7 +336,7 @@ void build_plan(const Problem &P, const Symbolic &S, Plan &plan, int nb, int nbs
     F.first = S.super[s];
     F.ncol = S.super[s + 1] - S.super[s];
     F.nrow = (int32_t)(S.srp[s + 1] - S.srp[s]);
-    F.ld = (int32_t)round_up(F.ncol, 4);
+    F.ld = (int32_t)round_up(F.ncol, 8);  // 16-byte rows for TMA in FP32 and in BF16
     F.uld = (int32_t)round_up(std::max(F.nrow, 1), 4);
     F.loff = loff;
     loff += round_up((int64_t)(F.ncol + F.nrow) * F.ld, 32);
@@ -631,7 +631,7 @@ void validate_plan(const Problem &P, const Symbolic &S, const Plan &pl) {
   auto nf = [&](int32_t s) { return (int64_t)pl.fronts[s].ncol + pl.fronts[s].nrow; };
   for (int32_t s = 0; s < ns; s++) {
     const FrontInfo &F = pl.fronts[s];
-    need(F.ncol > 0 && F.nrow >= 0 && F.ld >= F.ncol && F.ld % 4 == 0, "front shape");
+    need(F.ncol > 0 && F.nrow >= 0 && F.ld >= F.ncol && F.ld % 8 == 0, "front shape");
     need(F.loff >= 0 && F.loff + nf(s) * F.ld <= pl.l_entries, "panel inside factor storage");
     need(F.nrow == 0 || (F.uoff >= 0 && F.uoff + (int64_t)F.nrow * F.uld <= pl.u_entries),
          "update matrix inside update storage");

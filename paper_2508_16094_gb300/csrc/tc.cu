@@ -18,6 +18,7 @@
 // on an mbarrier is bounded by a clock limit; on expiry the CTA records
 // ST_TIMEOUT, skips the rest of its work and still releases its tensor memory.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -34,6 +35,11 @@ namespace gipm {
 namespace {
 
 constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kSyrkN = 256;
+// Operand arithmetic of a kernel instantiation ("SPLIT"): 1 TF32, 3 the
+// 3-term split TF32, kBf16 BF16 operands (kind::f16) for the updates of
+// finished entries, read from their BF16 copy, with the panel solve in TF32.
+constexpr int kBf16 = 16;
+constexpr int kTileKBf = 64;  // BF16 elements per 128-byte operand row
 constexpr int kMaxClusters = 76;  // CTA pairs of the persistent SYRK (152 SMs)
 constexpr int kSuper = 512;  // columns per super-step of the left-looking panel updates
 constexpr int kAheadFronts = 2;  // levels with at most this many fronts run the look-ahead
@@ -150,6 +156,21 @@ __device__ __forceinline__ void stage_row(uint8_t *buf, int row, const float (&v
     *reinterpret_cast<float4 *>(rowp + ((j ^ (row & 7)) << 4)) =
         make_float4(f(v[4 * j]), f(v[4 * j + 1]), f(v[4 * j + 2]), f(v[4 * j + 3]));
 }
+// Writes 32 values of one row of a 32 x 32 BF16 box (64-byte rows, no swizzle),
+// rounded to nearest even.
+__device__ __forceinline__ void stage_row_bf16(uint8_t *buf, int row, const float (&v)[32]) {
+  uint8_t *rowp = buf + row * 64;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * j + 2 * h], v[8 * j + 2 * h + 1]);
+      w[h] = *reinterpret_cast<const uint32_t *>(&b2);
+    }
+    *reinterpret_cast<uint4 *>(rowp + 16 * j) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
 // Wait until at most N of this thread's bulk groups still read shared memory.
 template <int N>
 __device__ __forceinline__ void bulk_wait_read() {
@@ -188,6 +209,24 @@ template <int BN>
 __host__ __device__ constexpr uint32_t tf32_idesc() {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
          ((uint32_t)(kTileM >> 4) << 24);
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16 with BF16 A and B (format 1),
+// FP32 accumulator, both K-major, N = BN, M = 128.
+template <int BN>
+__host__ __device__ constexpr uint32_t bf16_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(kTileM >> 4) << 24);
+}
+
+// One 128 x BN x 16 BF16 product (32 bytes of K per operand row, like one TF32 step).
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
@@ -251,13 +290,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // 2-5 form their low parts in shared memory.
 // Geometry of one task (see the task encoding above).
 struct Geo {
-  int mode, arow, brow, K, M, N, ax0, bx0, nk;
+  int mode, arow, brow, K, M, N, ax0, bx0, nk, kstep;
+  bool bf;  // BF16 operands (kind::f16) from the BF16 copy of the panel
   const CUtensorMap *amap, *bmap, *lomap;
 };
 
+template <int SPLIT>
 __device__ __forceinline__ Geo task_geo(const DevPlan &dp, const Task &tk, const CUtensorMap *maps,
                                         const CUtensorMap *maps_lo, const CUtensorMap *inv_map,
-                                        int nb) {
+                                        const CUtensorMap *maps_bf, int nb) {
   const FrontInfo F = dp.fronts[tk.front];
   const int nf = F.ncol + F.nrow;
   Geo g;
@@ -269,11 +310,16 @@ __device__ __forceinline__ Geo task_geo(const DevPlan &dp, const Task &tk, const
   g.arow = tk.a;
   g.M = min(kTileM, nf - tk.a);
   g.N = min(nb, F.ncol - k);
+  g.bf = false;
   if (g.mode == 0) {  // K range [kbeg, kend) of the update of block column k
     const int kbeg = ((tk.c >> 2) & 0x7FFF) * kTileN, kend = ((tk.c >> 17) & 0x7FFF) * kTileN;
     g.brow = k;
     g.ax0 = g.bx0 = kbeg;
     g.K = kend - kbeg;
+    if (SPLIT == kBf16) {  // finished entries: their BF16 copy
+      g.bf = true;
+      g.amap = g.bmap = maps_bf + tk.front;
+    }
   } else {
     g.ax0 = k;
     g.bx0 = 0;
@@ -281,7 +327,8 @@ __device__ __forceinline__ Geo task_geo(const DevPlan &dp, const Task &tk, const
     g.bmap = inv_map;
     g.K = g.N;
   }
-  g.nk = (g.K + kTileK - 1) / kTileK;
+  g.kstep = g.bf ? kTileKBf : kTileK;
+  g.nk = (g.K + g.kstep - 1) / g.kstep;
   return g;
 }
 
@@ -294,7 +341,8 @@ __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(DevPlan dp, const Task *__restrict__ tasks, int ntask,
                    const CUtensorMap *__restrict__ maps, const CUtensorMap *__restrict__ maps_lo,
                    const CUtensorMap *__restrict__ inv_map, const CUtensorMap *__restrict__ lmaps,
-                   const CUtensorMap *__restrict__ llomaps, int nb, int32_t *status) {
+                   const CUtensorMap *__restrict__ llomaps, const CUtensorMap *__restrict__ maps_bf,
+                   const CUtensorMap *__restrict__ lbfmaps, int nb, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -344,16 +392,16 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {  // TMA producer
       uint32_t g = 0;
       for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x) {
-        const Geo G = task_geo(dp, tasks[t], maps, maps_lo, inv_map, nb);
+        const Geo G = task_geo<SPLIT>(dp, tasks[t], maps, maps_lo, inv_map, maps_bf, nb);
         const bool pre = SPLIT == 3 && G.mode != 2;  // low parts loaded with the tiles
         for (int kt = 0; kt < G.nk; kt++, g++) {
           const int s = g % S;
           const uint32_t round = g / S;
           if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
           mbar_arrive_expect_tx(&full[s], (pre ? 2 : 1) * (kTileBytes + kBB));
-          tma_load_2d(sA + s * kTileBytes, G.amap, &full[s], G.ax0 + kt * kTileK, G.arow);
+          tma_load_2d(sA + s * kTileBytes, G.amap, &full[s], G.ax0 + kt * G.kstep, G.arow);
           for (int h = 0; h < CF::kB; h++)  // a 256-row B tile is two 128-row boxes
-            tma_load_2d(sB + s * kBB + h * kTileBytes, G.bmap, &full[s], G.bx0 + kt * kTileK,
+            tma_load_2d(sB + s * kBB + h * kTileBytes, G.bmap, &full[s], G.bx0 + kt * G.kstep,
                         G.brow + 128 * h);
           if (pre) {
             tma_load_2d(sAl + s * kTileBytes, G.lomap, &full[s], G.ax0 + kt * kTileK, G.arow);
@@ -370,10 +418,11 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       constexpr uint32_t idesc = tf32_idesc<BN>();
+      constexpr uint32_t idesc_bf = bf16_idesc<BN>();
       uint32_t g = 0;
       int i = 0;
       for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
-        const Geo G = task_geo(dp, tasks[t], maps, maps_lo, inv_map, nb);
+        const Geo G = task_geo<SPLIT>(dp, tasks[t], maps, maps_lo, inv_map, maps_bf, nb);
         const bool conv = SPLIT == 3 && G.mode == 2;
         const int a = i & 1;
         if (!mbar_wait(&accempty[a], ((i >> 1) & 1) ^ 1, status)) { *abort_flag = 1; break; }
@@ -390,8 +439,10 @@ __global__ void __launch_bounds__(192, 1)
           const uint64_t ald = sw128_desc(smem_u32(sAl + s * kTileBytes));
           const uint64_t bld = sw128_desc(smem_u32(sBl + s * kBB));
 #pragma unroll
-          for (int k4 = 0; k4 < kTileK / 8; k4++) {  // 8 TF32 = 32 bytes per MMA along K
-            if (SPLIT == 3) {  // small terms first: A_lo B + A B_lo, then A B
+          for (int k4 = 0; k4 < kTileK / 8; k4++) {  // 8 TF32 (16 BF16) = 32 bytes per MMA along K
+            if (SPLIT == kBf16 && G.bf) {
+              mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc_bf, (kt | k4) != 0);
+            } else if (SPLIT == 3) {  // small terms first: A_lo B + A B_lo, then A B
               mma_tf32(acc, ald + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
               mma_tf32(acc, ad + 2 * k4, bld + 2 * k4, idesc, 1);
               mma_tf32(acc, ad + 2 * k4, bd + 2 * k4, idesc, 1);
@@ -414,7 +465,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t g = 0;
     int i = 0;
     for (int t = blockIdx.x; t < ntask && !*abort_flag; t += gridDim.x, i++) {
-      const Geo G = task_geo(dp, tasks[t], maps, maps_lo, inv_map, nb);
+      const Geo G = task_geo<SPLIT>(dp, tasks[t], maps, maps_lo, inv_map, maps_bf, nb);
       if (SPLIT == 3 && G.mode == 2) {
         // low parts x - tf32(x) of both operand tiles (tf32 keeps the top 19 bits)
         const int tt = threadIdx.x - 64;
@@ -453,11 +504,13 @@ __global__ void __launch_bounds__(192, 1)
             __syncwarp();
             stage_row(stg, lane, v, [](float x) { return x; });
             if (SPLIT == 3) stage_row(stg + 4096, lane, v, [](float x) { return lo1(x); });
+            if (SPLIT == kBf16) stage_row_bf16(stg + 4096, lane, v);  // the entries' BF16 copy
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
               tma_store_2d(cm, stg, x0 + 32 * cb, y);
               if (SPLIT == 3) tma_store_2d(llomaps + tk.front, stg + 4096, x0 + 32 * cb, y);
+              if (SPLIT == kBf16) tma_store_2d(lbfmaps + tk.front, stg + 4096, x0 + 32 * cb, y);
             }
             nissued = 0;  // a later reduction stages into the buffer read first
           } else {
@@ -499,7 +552,8 @@ struct PairGeo {
   int cy, cx, rows, N;     // target origin (rows, columns), its row count, columns of the tile
   bool panel;              // target is the panel (mode 0), else the update matrix
 };
-__device__ __forceinline__ PairGeo pair_geo(const FrontInfo &F, const Task &tk, int rank) {
+__device__ __forceinline__ PairGeo pair_geo(const FrontInfo &F, const Task &tk, int rank,
+                                            int kstep) {
   PairGeo g;
   int K;
   if ((tk.c & 3) == 1) {
@@ -523,7 +577,7 @@ __device__ __forceinline__ PairGeo pair_geo(const FrontInfo &F, const Task &tk, 
     g.panel = true;
   }
   g.cx = tk.b;
-  g.nk = (K + kTileK - 1) / kTileK;
+  g.nk = (K + kstep - 1) / kstep;
   return g;
 }
 
@@ -540,8 +594,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     tc_pair_kernel(DevPlan dp, const Task *__restrict__ pairs, int npair,
                    const CUtensorMap *__restrict__ maps, const CUtensorMap *__restrict__ maps_lo,
                    const CUtensorMap *__restrict__ umaps, const CUtensorMap *__restrict__ lmaps,
-                   int32_t *status) {
+                   const CUtensorMap *__restrict__ maps_bf, int32_t *status) {
   constexpr int BN = 256;
+  constexpr int KS = SPLIT == kBf16 ? kTileKBf : kTileK;  // elements per k-step
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -595,12 +650,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
       for (int p = cid; p < npair && !*abort_flag; p += ncl) {
         const Task tk = pairs[p];
         const FrontInfo F = dp.fronts[tk.front];
-        const CUtensorMap *amap = maps + tk.front, *lomap = maps_lo + tk.front;
-        const PairGeo G = pair_geo(F, tk, (int)rank);
+        const CUtensorMap *amap = (SPLIT == kBf16 ? maps_bf : maps) + tk.front,
+                          *lomap = maps_lo + tk.front;
+        const PairGeo G = pair_geo(F, tk, (int)rank, KS);
         for (int kt = 0; kt < G.nk; kt++, g++) {
           const int st = g % S;
           const uint32_t round = g / S;
-          const int x = G.x0 + kt * kTileK;
+          const int x = G.x0 + kt * KS;
           if (!mbar_wait(&empty[st], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
           mbar_arrive_expect_tx(&full[st], (SPLIT == 3 ? 2 : 1) * (kTileBytes + kBB));
           tma_load_2d(sA + st * kTileBytes, amap, &full[st], x, G.arow);
@@ -617,13 +673,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      constexpr uint32_t idesc = tf32_idesc<BN>();
+      constexpr uint32_t idesc = SPLIT == kBf16 ? bf16_idesc<BN>() : tf32_idesc<BN>();
       uint32_t g = 0;
       int i = 0;
       for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
         const Task tk = pairs[p];
         const FrontInfo F = dp.fronts[tk.front];
-        const int nk = pair_geo(F, tk, (int)rank).nk;
+        const int nk = pair_geo(F, tk, (int)rank, KS).nk;
         const int a = i & 1;
         if (!mbar_wait(&accempty[a], ((i >> 1) & 1) ^ 1, status)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -639,7 +695,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
           const uint64_t bld = sw128_desc(smem_u32(sBl + st * kBB));
 #pragma unroll
           for (int k4 = 0; k4 < kTileK / 8; k4++) {
-            if (SPLIT == 3) {
+            if (SPLIT == kBf16) {
+              mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
+            } else if (SPLIT == 3) {
               mma_tf32(acc, ald + 2 * k4, bd + 2 * k4, idesc, (kt | k4) != 0);
               mma_tf32(acc, ad + 2 * k4, bld + 2 * k4, idesc, 1);
               mma_tf32(acc, ad + 2 * k4, bd + 2 * k4, idesc, 1);
@@ -667,7 +725,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     for (int p = cid; p < npair && !*abort_flag; p += ncl, i++) {
       const Task tk = pairs[p];
       const FrontInfo F = dp.fronts[tk.front];
-      const PairGeo G = pair_geo(F, tk, (int)rank);
+      const PairGeo G = pair_geo(F, tk, (int)rank, KS);
       const int a = i & 1;
       if (!mbar_wait(&accfull[a], (i >> 1) & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1005,8 +1063,9 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
   d_potrf_ = up(potrf_);
   d_trsm_ = up(trsm_);
   d_pairs_ = up(pairs_);
-  // L, Llo (32 x 128 boxes), the inverse scratch, U, L, Llo (32 x 32 boxes)
-  d_maps_ = cv.take<CUtensorMap>(5 * std::max(nfronts_, 1) + 1);
+  // L, Llo (32 x 128 boxes), the inverse scratch, U, L, Llo (32 x 32 boxes),
+  // the BF16 copy (64 x 128 boxes, then 32 x 32 boxes)
+  d_maps_ = cv.take<CUtensorMap>(7 * std::max(nfronts_, 1) + 1);
   d_inv_ = cv.take<float>((size_t)max_slots_ * kTileM * kTileN);
   ready_ = false;
 }
@@ -1082,6 +1141,28 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream
     const FrontInfo &F = plan.fronts[s];
     box32(Llo + F.loff, "low-part panel", s, F.ncol, F.ncol + F.nrow, F.ld);
   }
+  // The BF16 copy of the finished panel entries lives in the low-part buffer
+  // (the two are never needed by the same factorisation), each panel at the
+  // same element offset and row stride as in L: operand loads in 64 x 128
+  // boxes (128-byte swizzled rows), epilogue stores in 32 x 32 boxes.
+  __nv_bfloat16 *Lbf = reinterpret_cast<__nv_bfloat16 *>(Llo);
+  auto bfmap = [&](size_t s, uint32_t bx, uint32_t by, CUtensorMapSwizzle sw) {
+    const FrontInfo &F = plan.fronts[s];
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)F.ncol, (cuuint64_t)(F.ncol + F.nrow)};
+    cuuint64_t strides[1] = {(cuuint64_t)F.ld * sizeof(__nv_bfloat16)};
+    cuuint32_t box[2] = {bx, by};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)(Lbf + F.loff), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                     by == 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      throw std::runtime_error("cuTensorMapEncodeTiled failed for the BF16 panel " + std::to_string(s));
+    maps.push_back(m);
+  };
+  for (size_t s = 0; s < nfr; s++) bfmap(s, kTileKBf, kTileM, CU_TENSOR_MAP_SWIZZLE_128B);
+  for (size_t s = 0; s < nfr; s++) bfmap(s, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!maps.empty())
     if (cudaMemcpyAsync(d_maps_, maps.data(), maps.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -1091,6 +1172,10 @@ void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream
   cudaFuncSetAttribute(tc_gemm_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, 128>::smem);
   cudaFuncSetAttribute(tc_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<1, kSyrkN>::smem);
   cudaFuncSetAttribute(tc_pair_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3, kSyrkN>::smem);
+  cudaFuncSetAttribute(tc_gemm_kernel<kBf16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Cfg<kBf16, 128>::smem);
+  cudaFuncSetAttribute(tc_pair_kernel<kBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Cfg<kBf16, kSyrkN>::smem);
   ready_ = true;
 }
 
@@ -1111,9 +1196,11 @@ static void gemm_launch(int ntask, int ctas, const DevPlan &dp, const Task *task
                         const CUtensorMap *maps, int nfronts, int32_t *status, cudaStream_t st) {
   const CUtensorMap *maps_lo = maps + nfronts, *inv_map = maps + 2 * nfronts;
   const CUtensorMap *lmaps = inv_map + 1 + nfronts, *llomaps = lmaps + nfronts;
+  const CUtensorMap *maps_bf = llomaps + nfronts, *lbfmaps = maps_bf + nfronts;
   note_launch();
   tc_gemm_kernel<SPLIT, BN><<<std::min(ntask, std::max(ctas, 1)), 192, Cfg<SPLIT, BN>::smem, st>>>(
-      dp, tasks, ntask, maps, maps_lo, inv_map, lmaps, llomaps, TcPlan::kNb, status);
+      dp, tasks, ntask, maps, maps_lo, inv_map, lmaps, llomaps, maps_bf, lbfmaps, TcPlan::kNb,
+      status);
 }
 
 // Pair kernel on at most ctas CTAs (clusters of two, each pair of tiles ncl apart).
@@ -1121,11 +1208,11 @@ template <int SPLIT>
 static void pair_launch(int npair, int ctas, const DevPlan &dp, const Task *pairs,
                         const CUtensorMap *maps, int nfronts, int32_t *status, cudaStream_t st) {
   const CUtensorMap *maps_lo = maps + nfronts, *umaps = maps + 2 * nfronts + 1;
-  const CUtensorMap *lmaps = umaps + nfronts;
+  const CUtensorMap *lmaps = umaps + nfronts, *maps_bf = lmaps + 2 * nfronts;
   const int ncl = std::max(1, std::min({npair, ctas / 2, kMaxClusters}));
   note_launch();
-  tc_pair_kernel<SPLIT><<<2 * ncl, 192, Cfg<SPLIT, kSyrkN>::smem, st>>>(dp, pairs, npair, maps,
-                                                                      maps_lo, umaps, lmaps, status);
+  tc_pair_kernel<SPLIT><<<2 * ncl, 192, Cfg<SPLIT, kSyrkN>::smem, st>>>(
+      dp, pairs, npair, maps, maps_lo, umaps, lmaps, maps_bf, status);
 }
 
 TcPlan::~TcPlan() {
@@ -1136,8 +1223,9 @@ TcPlan::~TcPlan() {
 
 void TcPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, float *L, float *U,
                     float *Dinv, int32_t *status, int split, cudaStream_t st) {
-  auto gemm3 = split == 3 ? gemm_launch<3, 128> : gemm_launch<1, 128>;
-  auto pair3 = split == 3 ? pair_launch<3> : pair_launch<1>;
+  auto gemm3 = split == 3 ? gemm_launch<3, 128>
+                          : (split == kBf16 ? gemm_launch<kBf16, 128> : gemm_launch<1, 128>);
+  auto pair3 = split == 3 ? pair_launch<3> : (split == kBf16 ? pair_launch<kBf16> : pair_launch<1>);
   const CUtensorMap *maps = static_cast<const CUtensorMap *>(d_maps_);
   if (L != L_ || U != U_) throw std::runtime_error("tensor maps were encoded for other factor buffers");
   if (!side_) throw std::runtime_error("tensor-core factor streams not created");

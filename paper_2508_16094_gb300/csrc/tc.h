@@ -33,7 +33,9 @@ class TcPlan {
   void encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream_t st);
   bool ready() const { return ready_; }
   // split = 1: plain TF32 products; split = 3: A_lo B + A B_lo + A B
-  // (FP32-accurate products on tensor cores; L must be the encoded buffer)
+  // (FP32-accurate products on tensor cores); split = 16: BF16 products
+  // (kind::f16) for every update by finished entries, read from their BF16
+  // copy, with the panel solves in TF32 (L must be the encoded buffer)
   // Dinv (may be null): also write the diagonal-block inverses in the layout of
   // the persistent solve. Work forks onto the side stream and joins back into
   // st before the call's last launch, so st alone orders the result.
@@ -56,7 +58,7 @@ class TcPlan {
   int nfronts_ = 0, max_slots_ = 1;
   float *d_inv_ = nullptr;  // inverses of the diagonal blocks of one step (max_slots_ x 128 x 128)
   Task *d_gemm_ = nullptr, *d_potrf_ = nullptr, *d_trsm_ = nullptr, *d_pairs_ = nullptr;
-  void *d_maps_ = nullptr;  // 3 nfronts_ + 1 CUtensorMap (128 bytes each)
+  void *d_maps_ = nullptr;  // 7 nfronts_ + 1 CUtensorMap (128 bytes each)
   float *L_ = nullptr, *Llo_ = nullptr, *U_ = nullptr;
   cudaStream_t side_ = nullptr;                              // look-ahead stream (low priority)
   cudaEvent_t ev_main_ = nullptr, ev_side_ = nullptr;        // fork / join

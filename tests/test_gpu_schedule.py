@@ -6,7 +6,8 @@ On the grid LPs the relaxed amalgamation gives a root supernode of 1,680
 and on the root level the update of the next super-step runs ahead on the
 second stream. A factor that dropped or doubled such an update would leave
 L L^T - K of the size of the entries it missed; a correct split-TF32 factor has
-a backward error near FP32 rounding and a plain TF32 factor near 2^-11.
+a backward error near FP32 rounding, a plain TF32 factor near 2^-11 and a
+factor with BF16 updates near 2^-8.
 
 K is built on the host from its definition (A^T diag(D_A) A + diag(D_l + D_u)
 + delta I, scipy, FP64) and permuted to the factor's final numbering."""
@@ -22,7 +23,7 @@ pytestmark = pytest.mark.gpu
 import paper_2508_16094_gb300 as gb  # noqa: E402
 
 SUPER = 512  # columns per super-step of the tensor-core schedule
-BACKWARD = {gb.IPM_TF32X3: 2e-6, gb.IPM_TF32: 5e-3}
+BACKWARD = {gb.IPM_TF32X3: 2e-6, gb.IPM_TF32: 5e-3, gb.IPM_BF16: 2e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -72,7 +73,8 @@ def _factor_csc(ctx, n):
     return sp.csc_matrix((vals, (rows, cols)), shape=(n, n)), ex
 
 
-@pytest.mark.parametrize("prec", [gb.IPM_TF32X3, gb.IPM_TF32], ids=["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", [gb.IPM_TF32X3, gb.IPM_TF32, gb.IPM_BF16],
+                         ids=["tf32x3", "tf32", "bf16"])
 @pytest.mark.parametrize("G", [24, 32])
 def test_factor_backward_error_at_super_step_schedule(G, prec):
     lp, ctx, info, K = _setup(G, prec)
@@ -106,7 +108,8 @@ def test_factor_backward_error_at_super_step_schedule(G, prec):
     assert worst <= 20 * BACKWARD[prec], worst
 
 
-@pytest.mark.parametrize("prec", [gb.IPM_TF32X3, gb.IPM_TF32], ids=["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", [gb.IPM_TF32X3, gb.IPM_TF32, gb.IPM_BF16],
+                         ids=["tf32x3", "tf32", "bf16"])
 def test_unrefined_solve_backward_error_grid40(prec):
     """40^3 (seven super-steps on a 4,720-column root): one solve with the
     factor and no refinement has the normwise backward error of the factor."""

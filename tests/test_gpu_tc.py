@@ -1,4 +1,4 @@
-"""Tensor-core (tcgen05, TF32) factorisation vs the CPU oracle.
+"""Tensor-core (tcgen05: TF32, split TF32, BF16) factorisation vs the CPU oracle.
 
 TF32 keeps 10 explicit mantissa bits, so the factor itself is only accurate to
 about 1e-3 relative; FP64 refinement must then recover a 1e-10 solve residual
@@ -40,10 +40,14 @@ def _dense_factor(ctx, S, n):
 
 
 TF32X3_BACKWARD = 2e-6  # 3-term split: products about as accurate as FP32 FMA
+# BF16 keeps 7 explicit mantissa bits (unit roundoff 2^-8 for the operands of
+# the updates); the panel solves stay TF32 and the diagonal blocks FP32
+BF16_BACKWARD = 2e-2
 
 
-@pytest.mark.parametrize("prec,bound", [(gb.IPM_TF32, TF32_BACKWARD), (gb.IPM_TF32X3, TF32X3_BACKWARD)],
-                         ids=["tf32", "tf32x3"])
+@pytest.mark.parametrize("prec,bound", [(gb.IPM_TF32, TF32_BACKWARD), (gb.IPM_TF32X3, TF32X3_BACKWARD),
+                                        (gb.IPM_BF16, BF16_BACKWARD)],
+                         ids=["tf32", "tf32x3", "bf16"])
 @pytest.mark.parametrize("name", ["grid15", "random600", "grid7x9x5"])
 def test_tf32_factor_backward_error(name, prec, bound):
     lp, perm = _problem(name)
@@ -59,6 +63,11 @@ def test_tf32_factor_backward_error(name, prec, bound):
     assert err <= bound
     if prec == gb.IPM_TF32:
         assert err >= 1e-5  # the products really ran in TF32
+    if prec == gb.IPM_BF16:  # the updates really ran in BF16: coarser than TF32
+        ctx.kkt_factor(gb.IPM_TF32)
+        Lt = _dense_factor(ctx, S, lp.n)
+        err_tf32 = np.linalg.norm(Lt @ Lt.T - K) / np.linalg.norm(K)
+        assert err >= 2 * err_tf32, (err, err_tf32)
     # the same factor in FP32 FMA arithmetic is far more accurate: TF32 really ran
     ctx.kkt_factor(gb.IPM_FP32)
     L32 = _dense_factor(ctx, S, lp.n)
@@ -68,7 +77,8 @@ def test_tf32_factor_backward_error(name, prec, bound):
     assert np.abs(L - oracle.l_dense(S, lval)).max() <= 0.05 * np.abs(lval).max()
 
 
-@pytest.mark.parametrize("prec", [gb.IPM_TF32, gb.IPM_TF32X3], ids=["tf32", "tf32x3"])
+@pytest.mark.parametrize("prec", [gb.IPM_TF32, gb.IPM_TF32X3, gb.IPM_BF16],
+                         ids=["tf32", "tf32x3", "bf16"])
 @pytest.mark.parametrize("name", ["grid15", "random600"])
 def test_tf32_solve_refined_to_1e10(name, prec):
     lp, perm = _problem(name)
@@ -85,11 +95,14 @@ def test_tf32_solve_refined_to_1e10(name, prec):
     assert np.abs(K @ x.cpu().numpy() - b).max() <= 4e-10 * np.abs(b).max()
 
 
-@pytest.mark.parametrize("prec", [gb.IPM_TF32, gb.IPM_TF32X3], ids=["tf32", "tf32x3"])
+@pytest.mark.parametrize("prec", [gb.IPM_TF32, gb.IPM_TF32X3, gb.IPM_BF16],
+                         ids=["tf32", "tf32x3", "bf16"])
 @pytest.mark.parametrize("name", ["grid15", "random600"])
 def test_tf32_ipm_matches_oracle(name, prec):
     lp, perm = _problem(name)
-    ctx, info = _ctx(lp, perm, precision=prec, storage_fp64=0, tol=1e-6)
+    # a BF16 factor whose PCG misses the acceptance tolerance is redone in split TF32
+    ctx, info = _ctx(lp, perm, precision=prec, storage_fp64=0, tol=1e-6,
+                     fallback_fp64=1 if prec == gb.IPM_BF16 else 0)
     S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, perm)
     ref = oracle.ipm_lp(S, lp, tol=1e-6)
     mt = lp.m + 2 * lp.n
@@ -100,3 +113,5 @@ def test_tf32_ipm_matches_oracle(name, prec):
     assert res.status == 0, res.as_dict()
     assert res.kkt <= 1e-6
     assert abs(res.objective - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+    if prec == gb.IPM_BF16:  # BF16 factors carried some iterations themselves
+        assert res.fp64_fallbacks < res.iterations, res.as_dict()
