@@ -100,9 +100,11 @@ typedef struct {
   double ir_tol;         /* stop once ||b - K x||_inf <= ir_tol ||b||_inf (1e-10) */
   int32_t pcg_max;       /* PCG iterations per solve (100) */
   int32_t fallback_fp64; /* after a linear solve that misses accept_tol with a TF32/BF16/FP32
-                            factor, refactor in the most accurate arithmetic the storage
-                            allows (FP64 with FP64 storage, else the split TF32) and solve
-                            again; counted in ipm_result.fp64_fallbacks (0) */
+                            factor, or a low-precision factor that had to perturb pivots,
+                            refactor in the most accurate arithmetic the storage allows
+                            (FP64 with FP64 storage, else the split TF32), solve again and
+                            keep that arithmetic for the rest of ipm_solve; counted in
+                            ipm_result.fp64_fallbacks (0) */
   double accept_tol;     /* a solve that misses ir_tol but reaches accept_tol is used (1e-6) */
   int32_t verbose;       /* print one line per interior-point iteration to stderr */
   int32_t warm_start;    /* 1: ipm_solve starts from the x, s, lambda it is given (0) */
@@ -112,7 +114,22 @@ typedef struct {
   int32_t learned_probes;/* probes per training sample (1..8); > 0 also reserves the learned
                             buffers when learned = 0 (0) */
   int32_t learned_pcg_max; /* PCG iterations allowed before falling back to refactoring (30) */
+  int32_t formulation;   /* linear system solved for each Newton direction of (3), read by
+                            kkt_analyze (Sec. 3, "Condensed KKT Systems"); the bound rows are
+                            folded into H = W + delta_p I + D_l + D_u in the last two:
+                            IPM_FORM_PRIMAL (5)  K = W + delta_p I + J^T D J (order n, SPD);
+                            IPM_FORM_DUAL (6)    D_G^{-1} + A H^{-1} A^T (order m, SPD; W
+                                                 diagonal or absent);
+                            IPM_FORM_AUGMENTED (4)  [H, A^T; A, -D_G^{-1}] (order n + m,
+                                                 quasi-definite, signed LDL^T in FP64/FP32)
+                            (IPM_FORM_PRIMAL) */
 } ipm_options;
+
+typedef enum {
+  IPM_FORM_PRIMAL = 0,
+  IPM_FORM_DUAL = 1,
+  IPM_FORM_AUGMENTED = 2
+} ipm_formulation;
 
 /* Default options (values in brackets above). */
 IPM_API void ipm_default_options(ipm_options *opts);

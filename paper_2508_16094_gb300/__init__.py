@@ -17,10 +17,12 @@ from . import build as _build
 
 __all__ = ["IpmError", "IpmContext", "Options", "load", "build", "lib_path",
            "IPM_FP64", "IPM_FP32", "IPM_TF32", "IPM_BF16", "IPM_TF32X3",
-           "IPM_REFINE_NONE", "IPM_REFINE_IR", "IPM_REFINE_PCG"]
+           "IPM_REFINE_NONE", "IPM_REFINE_IR", "IPM_REFINE_PCG", "IPM_FORM_PRIMAL",
+           "IPM_FORM_DUAL", "IPM_FORM_AUGMENTED"]
 
 IPM_FP64, IPM_FP32, IPM_TF32, IPM_BF16, IPM_TF32X3 = 0, 1, 2, 3, 4
 IPM_REFINE_NONE, IPM_REFINE_IR, IPM_REFINE_PCG = 0, 1, 2
+IPM_FORM_PRIMAL, IPM_FORM_DUAL, IPM_FORM_AUGMENTED = 0, 1, 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_NOMEM", 5: "ERR_NOT_SPD",
           6: "ERR_NUMERIC", 7: "ERR_MAXITER", 8: "ERR_TIMEOUT", 9: "ERR_STALL",
           10: "ERR_UNSUPPORTED"}
@@ -48,7 +50,8 @@ class Options(C.Structure):
                 ("refine", C.c_int32), ("ir_max", C.c_int32), ("ir_tol", C.c_double),
                 ("pcg_max", C.c_int32), ("fallback_fp64", C.c_int32), ("accept_tol", C.c_double),
                 ("verbose", C.c_int32), ("warm_start", C.c_int32), ("learned", C.c_int32),
-                ("learned_probes", C.c_int32), ("learned_pcg_max", C.c_int32)]
+                ("learned_probes", C.c_int32), ("learned_pcg_max", C.c_int32),
+                ("formulation", C.c_int32)]
 
 
 class SymbolicInfo(C.Structure):
@@ -270,11 +273,11 @@ class IpmContext:
                                                    _dp(dx), _dp(ds), _dp(dl)))
 
     def kkt_order(self) -> int:
-        """Order of the condensed matrix the context factors."""
-        return self.n
+        """Order of the matrix the context factors (n, m or n + m by formulation)."""
+        return int(self.info.n) if self.info is not None else self.n
 
     def kkt_symbolic_export(self) -> dict:
-        n, ns = self.n, self.info.nsuper
+        n, ns = self.kkt_order(), self.info.nsuper
         out = dict(perm=np.empty(n, np.int32), parent=np.empty(n, np.int32),
                    colcount=np.empty(n, np.int32), super=np.empty(ns + 1, np.int32),
                    sparent=np.empty(ns, np.int32), slevel=np.empty(ns, np.int32),

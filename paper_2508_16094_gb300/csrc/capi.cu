@@ -14,6 +14,7 @@
 #include <stdexcept>
 
 #include "../../include/gb300_ipm.h"
+#include "forms.h"
 #include "ipm_kernels.h"
 #include "launch.h"
 #include "learned.h"
@@ -65,6 +66,21 @@ struct ipm_ctx {
   IpmScalars *sc = nullptr;
   int32_t *status = nullptr, *col2s = nullptr;
   TcPlan tcp;
+  // formulations (4) and (6): `sys` is the context of that system's matrix
+  // (its pattern, symbolic analysis, factor and solves); this context keeps
+  // the interior-point vectors and builds sys's inputs with the map kernels
+  // of forms.cu
+  int form = IPM_FORM_PRIMAL;
+  ipm_ctx *sys = nullptr;
+  std::vector<int8_t> sign_orig;  // pivot signs of a quasi-definite system (original numbering)
+  std::vector<int64_t> wdiag_h;   // per variable: index of W_jj in W's values, or -1
+  std::vector<int32_t> aug_kind_h;
+  std::vector<int64_t> aug_idx_h;
+  int64_t *wdiag = nullptr, *aug_idx = nullptr;
+  int32_t *aug_kind = nullptr;
+  double *hdiag = nullptr, *rtil = nullptr, *qv = nullptr, *sysb = nullptr, *sysx = nullptr,
+         *sysw = nullptr, *sysD = nullptr, *sysj = nullptr;
+  size_t outer_need = 0;  // bytes of this context's own part of the workspace
   // inputs of the last assembly (device pointers, used by the residual)
   const double *cur_jvals = nullptr, *cur_D = nullptr, *cur_wvals = nullptr;
   double cur_delta_p = 0.0;
@@ -73,6 +89,7 @@ struct ipm_ctx {
   int64_t refine_steps = 0, pcg_steps = 0;
   double last_rel = 0.0;
   VecOps vec() const { return VecOps{dp, st, partial}; }
+  ~ipm_ctx() { delete sys; }
 };
 
 namespace gipm {
@@ -205,6 +222,29 @@ void layout(ipm_ctx *c, char *base) {
   }
   c->dl_ = const_cast<double *>(upload(cv, P.l, st));
   c->du_ = const_cast<double *>(upload(cv, P.u, st));
+  if (!c->sign_orig.empty()) {  // pivot signs of a quasi-definite system, final numbering
+    std::vector<int8_t> sg(P.n);
+    for (int32_t k = 0; k < P.n; k++) sg[k] = c->sign_orig[c->S.perm[k]];
+    d.sgn = upload(cv, sg, st);
+  } else {
+    d.sgn = nullptr;
+  }
+  if (c->form != IPM_FORM_PRIMAL) {  // inputs of the formulation's system
+    const size_t nsys = c->form == IPM_FORM_DUAL ? (size_t)std::max<int32_t>(P.m, 1)
+                                                 : (size_t)P.n + (size_t)P.m;
+    c->wdiag = const_cast<int64_t *>(upload(cv, c->wdiag_h, st));
+    c->aug_kind = const_cast<int32_t *>(upload(cv, c->aug_kind_h, st));
+    c->aug_idx = const_cast<int64_t *>(upload(cv, c->aug_idx_h, st));
+    c->hdiag = cv.take<double>(std::max<int32_t>(P.n, 1));
+    c->rtil = cv.take<double>(std::max<int32_t>(P.n, 1));
+    c->qv = cv.take<double>(std::max<int32_t>(P.m, 1));
+    c->sysb = cv.take<double>(std::max<size_t>(nsys, 1));
+    c->sysx = cv.take<double>(std::max<size_t>(nsys, 1));
+    c->sysw = cv.take<double>(std::max<size_t>(c->form == IPM_FORM_DUAL ? (size_t)P.m
+                                                                         : c->aug_kind_h.size(), 1));
+    c->sysD = cv.take<double>(std::max<int32_t>(P.n, 1));
+    c->sysj = cv.take<double>(std::max<int64_t>(P.jp.back(), 1));
+  }
   c->tcp.layout(cv, st);
   d.n = P.n;
   d.m = P.m;
@@ -291,6 +331,8 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   if (prec < IPM_FP64 || prec > IPM_TF32X3) throw Fail{IPM_ERR_ARG, "unknown precision"};
   if (prec == IPM_FP64 && c->storage_bytes < 8)
     throw Fail{IPM_ERR_NOMEM, "factor storage sized for FP32; FP64 factor needs storage_fp64"};
+  if (c->dp.sgn && prec != IPM_FP64 && prec != IPM_FP32)
+    throw Fail{IPM_ERR_UNSUPPORTED, "the signed factorisation of a quasi-definite system runs in FP64 or FP32"};
   int32_t init[ST_COUNT] = {INT32_MAX, 0, 0, 0, 0, 0, 0, 0};
   CK(cudaMemcpyAsync(c->status, init, sizeof(init), cudaMemcpyHostToDevice, c->st));
   if (prec == IPM_FP64) {
@@ -359,7 +401,13 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
     V.absmax(c->P.n, b, amax);
     V.inv_scale(amax, scale);
     V.permute_in<float>(b, scale, c->fsa);
-    launch_fp32_solve(c, 0);
+    if (c->dp.sgn) {  // K = L S L^T: forward sweep, S, backward sweep
+      launch_fp32_solve(c, 1);
+      launch_sign<float>(c->dp, c->fsb, c->st);
+      launch_fp32_solve(c, 2);
+    } else {
+      launch_fp32_solve(c, 0);
+    }
     V.permute_out<float>(c->fsx, scale, out, accumulate);
   }
 }
@@ -499,11 +547,85 @@ void set_assembly(ipm_ctx *c, const double *wv, const double *jv, const double *
   if (c->state < 3) c->state = 3;
 }
 
+// ---- formulations (4) and (6) ------------------------------------------------
+// The formulation's matrix from W, J, D and delta_p (device pointers that stay
+// valid while the system is in use): H, then the system's own inputs, then the
+// system context's assembly.
+void form_assemble(ipm_ctx *c, const double *wv, const double *jv, const double *D, double dp) {
+  FormOps F{c->dp, c->st};
+  F.hdiag(wv, c->wdiag, D, dp, c->hdiag);
+  ipm_status st;
+  if (c->form == IPM_FORM_DUAL) {
+    F.dual_values((int64_t)c->P.ji.size(), jv, D, c->hdiag, c->sysD, c->sysj, c->sysw);
+    st = kkt_assemble(c->sys, c->sysw, c->sysj, c->sysD, 0.0);
+  } else {
+    F.aug_values((int64_t)c->aug_kind_h.size(), c->aug_kind, c->aug_idx, c->hdiag, wv, jv, D,
+                 c->sysw);
+    st = kkt_assemble(c->sys, c->sysw, nullptr, nullptr, 0.0);
+  }
+  if (st != IPM_OK) throw Fail{st, c->sys->err};
+  c->cur_jvals = jv;
+  c->cur_D = D;
+  c->cur_wvals = wv;
+  c->cur_delta_p = dp;
+  if (c->state < 3) c->state = 3;
+}
+
+void assemble_any(ipm_ctx *c, const double *wv, const double *jv, const double *D, double dp) {
+  if (c->sys) form_assemble(c, wv, jv, D, dp);
+  else set_assembly(c, wv, jv, D, dp);
+}
+
+// Factor the context's system (the formulation's, if any).
+ipm_status factor_any(ipm_ctx *c, int prec, int32_t *bad) {
+  if (!c->sys) return do_factor(c, prec, bad);
+  if (c->state < 3) throw Fail{IPM_ERR_STATE, "kkt_factor before kkt_assemble"};
+  const ipm_status st = do_factor(c->sys, prec, bad);
+  c->factor_prec = prec;
+  c->last_perturbed = c->sys->last_perturbed;
+  c->state = c->sys->state;
+  if (st != IPM_OK) c->err = c->sys->err;
+  return st;
+}
+
+// Newton direction through (6) or (4) (see forms.h), then rows 2-3 of (3).
+ipm_status form_direction(ipm_ctx *c, const double *jvals, const double *cc, const double *wvals,
+                          const double *x, const double *s, const double *lam, const double *w,
+                          double *dx, double *ds, double *dl, ipm_solve_info *si) {
+  VecOps V = c->vec();
+  FormOps F{c->dp, c->st};
+  const int64_t n = c->P.n, m = c->P.m;
+  F.rhs_rows(c->vD, c->vg, w, lam, c->vt, c->qv);
+  V.jtv(jvals, c->vt, 1.0, wvals, x, cc, c->rtil);  // r~ = c + W x + J^T t
+  int refine = c->refine_override >= 0 ? c->refine_override : c->opts.refine;
+  ipm_status stt;
+  if (c->form == IPM_FORM_DUAL) {
+    F.div(c->rtil, c->hdiag, 1.0, c->vz);  // u = H^{-1} r~
+    V.jv(jvals, c->vz, c->vjx);            // A u
+    F.sub(m, c->qv, c->vjx, c->sysb);      // q - A u
+    stt = do_solve(c->sys, c->sysb, c->sysx, refine, si);
+    F.pad_rows(c->sysx, c->vt);            // [y; 0]
+    V.jtv(jvals, c->vt, 1.0, nullptr, nullptr, c->rtil, c->vrd);  // r~ + A^T y
+    F.div(c->vrd, c->hdiag, -1.0, dx);
+  } else {
+    if (refine == IPM_REFINE_PCG) refine = IPM_REFINE_IR;  // indefinite: no conjugate gradients
+    F.neg_concat(c->rtil, n, c->qv, m, c->sysb);  // -[r~; q]
+    stt = do_solve(c->sys, c->sysb, c->sysx, refine, si);
+    CK(cudaMemcpyAsync(dx, c->sysx, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  }
+  c->last_rel = c->sys->last_rel;
+  V.jv(jvals, dx, c->vjx);
+  V.jfull(c->vjx, dx, c->vjd);
+  V.recover(c->vD, c->vg, w, s, lam, c->vjd, ds, dl);
+  return stt;
+}
+
 // Newton direction at (x, s, lambda) with target w (w == nullptr: zero), reusing
 // the factor held by the context (assembled with D = (delta_d + s/lambda)^{-1}).
 ipm_status direction(ipm_ctx *c, const double *jvals, const double *b, const double *cc,
                      const double *wvals, const double *x, const double *s, const double *lam,
                      const double *w, double *dx, double *ds, double *dl, ipm_solve_info *si) {
+  if (c->sys) return form_direction(c, jvals, cc, wvals, x, s, lam, w, dx, ds, dl, si);
   VecOps V = c->vec();
   V.rhs_rows(c->vD, c->vg, w, lam, c->vt);
   // r_p = c + W x + J^T (D (g - w/lam) - lam); for the NLP, cc is grad f itself
@@ -529,9 +651,9 @@ void eval_g(ipm_ctx *c, const double *jvals, const double *b, const double *x) {
 ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jvals, int prec,
                              double &delta_p, ipm_result *res) {
   for (int tries = 0;; tries++) {
-    set_assembly(c, wvals, jvals, c->vD, delta_p);
+    assemble_any(c, wvals, jvals, c->vD, delta_p);
     int32_t bad = -1;
-    ipm_status stt = do_factor(c, prec, &bad);
+    ipm_status stt = factor_any(c, prec, &bad);
     if (res) {
       res->factorizations++;
       res->perturbed_pivots += c->last_perturbed;
@@ -593,6 +715,108 @@ void learned_init_weights(ipm_ctx *c) {
 // up (and the array committed) on the first call for that device.
 double *noalloc_scratch(int dev);
 
+// Symbolic analysis for the formulations (6) and (4): the pattern of the
+// system's matrix, a context `sys` that analyses and later factors it, and
+// this context's own (small) layout of interior-point vectors.
+//  (6): order m, sys's Jacobian J' = A^T (rows = variables, CSR of A^T), its
+//       W' = diag(D_G^{-1}) and its D' = 1 / H: K' = W' + J'^T D' J'.
+//  (4): order n + m, no Jacobian, sys's W' = the lower triangle of
+//       [H, A^T; A, -D_G^{-1}] (columns j < n: W's rows with the diagonal,
+//       then n + i for A_ij != 0; column n + i: its diagonal), pivot signs +1
+//       on the first n and -1 on the last m variables.
+ipm_status analyze_form(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info) {
+  const Problem &P = c->P;
+  const int32_t n = P.n, m = P.m;
+  const int64_t nnz = (int64_t)P.ji.size();
+  if (c->opts.learned != 0 || c->opts.learned_probes > 0)
+    throw Fail{IPM_ERR_UNSUPPORTED, "the learned correction uses the primal condensed formulation"};
+  c->wdiag_h.assign(n, -1);
+  if (!P.wp.empty())
+    for (int32_t j = 0; j < n; j++)
+      for (int64_t e = P.wp[j]; e < P.wp[j + 1]; e++) {
+        if (P.wi[e] == j) c->wdiag_h[j] = e;
+        else if (c->form == IPM_FORM_DUAL)
+          throw Fail{IPM_ERR_UNSUPPORTED, "the dual condensed formulation needs a diagonal W"};
+      }
+  std::vector<int64_t> sp(1, 0), swp;
+  std::vector<int32_t> si, swi;
+  int32_t ns, ms;
+  c->aug_kind_h.clear();
+  c->aug_idx_h.clear();
+  if (c->form == IPM_FORM_DUAL) {
+    ns = m;
+    ms = n;
+    sp = P.jtp;
+    si.resize(nnz);
+    for (int64_t e = 0; e < nnz; e++) si[e] = P.jrow[P.jtpos[e]];
+    swp.resize((size_t)m + 1);
+    swi.resize(m);
+    for (int32_t i = 0; i <= m; i++) swp[i] = i;
+    for (int32_t i = 0; i < m; i++) swi[i] = i;
+  } else {
+    ns = n + m;
+    ms = 0;
+    swp.assign((size_t)ns + 1, 0);
+    for (int32_t j = 0; j < n; j++) {
+      c->aug_kind_h.push_back(AUG_HDIAG);  // the diagonal first (W's rows are >= j)
+      c->aug_idx_h.push_back(j);
+      swi.push_back(j);
+      if (!P.wp.empty())
+        for (int64_t e = P.wp[j]; e < P.wp[j + 1]; e++)
+          if (P.wi[e] != j) {
+            c->aug_kind_h.push_back(AUG_W);
+            c->aug_idx_h.push_back(e);
+            swi.push_back(P.wi[e]);
+          }
+      for (int64_t t = P.jtp[j]; t < P.jtp[j + 1]; t++) {  // rows of J in ascending order
+        c->aug_kind_h.push_back(AUG_J);
+        c->aug_idx_h.push_back(P.jtpos[t]);
+        swi.push_back(n + P.jrow[P.jtpos[t]]);
+      }
+      swp[j + 1] = (int64_t)swi.size();
+    }
+    for (int32_t i = 0; i < m; i++) {
+      c->aug_kind_h.push_back(AUG_DINV);
+      c->aug_idx_h.push_back(i);
+      swi.push_back(n + i);
+      swp[(size_t)n + i + 1] = (int64_t)swi.size();
+    }
+    // W's rows of a column must ascend (checked again by ipm_create)
+    for (int32_t j = 0; j < n; j++)
+      for (int64_t e = swp[j] + 1; e < swp[j + 1]; e++)
+        if (swi[e] <= swi[e - 1]) throw Fail{IPM_ERR_ARG, "W rows must be ascending within a column"};
+  }
+  ipm_options so = c->opts;
+  so.formulation = IPM_FORM_PRIMAL;
+  so.learned = 0;
+  so.learned_probes = 0;
+  if (c->form == IPM_FORM_AUGMENTED && so.refine == IPM_REFINE_PCG) so.refine = IPM_REFINE_IR;
+  ipm_ctx *sys = nullptr;
+  ipm_status st = ipm_create(ns, ms, sp.data(), si.empty() ? nullptr : si.data(), swp.data(),
+                             swi.empty() ? nullptr : swi.data(), nullptr, nullptr, &so, c->st, &sys);
+  if (st != IPM_OK) throw Fail{st, "system context of the formulation"};
+  delete c->sys;
+  c->sys = sys;
+  if (c->form == IPM_FORM_AUGMENTED) {
+    sys->sign_orig.assign((size_t)ns, 1);
+    for (int32_t i = 0; i < m; i++) sys->sign_orig[(size_t)n + i] = -1;
+  }
+  st = kkt_analyze(sys, perm, info);
+  if (st != IPM_OK) throw Fail{st, sys->err};
+  c->S = Symbolic{};  // this context factors nothing itself
+  c->plan = Plan{};
+  c->storage_bytes = sys->storage_bytes;
+  layout(c, nullptr);
+  c->outer_need = c->ws_need;
+  c->ws_need = ((c->outer_need + 255) & ~size_t(255)) + sys->ws_need + 256;
+  c->state = 1;
+  if (info) {
+    info->m_tot = P.mt;
+    info->workspace_bytes = (int64_t)c->ws_need;
+  }
+  return IPM_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -617,6 +841,7 @@ void ipm_default_options(ipm_options *o) {
   o->learned = 0;
   o->learned_probes = 0;
   o->learned_pcg_max = 30;
+  o->formulation = IPM_FORM_PRIMAL;
 }
 
 ipm_status ipm_create(int32_t n, int32_t m, const int64_t *jp, const int32_t *ji,
@@ -706,6 +931,12 @@ ipm_status kkt_analyze(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info)
   if (!c) return IPM_ERR_ARG;
   return guarded(c, [&]() -> ipm_status {
     const int32_t n = c->P.n;
+    c->form = c->opts.formulation;
+    if (c->form < IPM_FORM_PRIMAL || c->form > IPM_FORM_AUGMENTED)
+      throw Fail{IPM_ERR_ARG, "unknown formulation"};
+    if (c->form != IPM_FORM_PRIMAL) return analyze_form(c, perm, info);
+    delete c->sys;
+    c->sys = nullptr;
     if (perm) {
       std::vector<char> seen(n, 0);
       for (int32_t k = 0; k < n; k++) {
@@ -752,8 +983,15 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     c->ws = base;
     c->ws_bytes = bytes;
     CK(cudaGetDevice(&c->device));
+    const size_t total = c->ws_need;
     layout(c, base);
     CK(cudaStreamSynchronize(c->st));
+    if (c->sys) {  // the formulation's system takes the rest of the buffer
+      c->ws_need = total;
+      char *sub = base + ((c->outer_need + 255) & ~size_t(255));
+      const ipm_status st = ipm_set_workspace(c->sys, sub, bytes - (size_t)(sub - (char *)buf));
+      if (st != IPM_OK) throw Fail{st, c->sys->err};
+    }
     // Commit the allocation-free solve's static array on this device now,
     // while the caller is handing over memory anyway: a later
     // kkt_solve_noalloc then loads no module and commits nothing.
@@ -763,7 +1001,7 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
     c->have_stale = false;
     if (c->lb_on) learned_init_weights(c);
     try {  // tensor maps of the FP32 panels for the tensor-core path
-      c->tcp.encode(c->plan, (float *)c->L, c->Llo, (float *)c->U, c->st);
+      if (!c->sys) c->tcp.encode(c->plan, (float *)c->L, c->Llo, (float *)c->U, c->st);
     } catch (const std::exception &e) {
       c->err = std::string("tensor-core path unavailable: ") + e.what();
     }
@@ -783,7 +1021,7 @@ ipm_status kkt_assemble(ipm_ctx *c, const double *wv, const double *jv, const do
     if (nj > 0) CK(cudaMemcpyAsync(c->jv_copy, jv, nj * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     if (c->P.mt > 0) CK(cudaMemcpyAsync(c->D_copy, D, c->P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     if (wv && nw > 0) CK(cudaMemcpyAsync(c->wv_copy, wv, nw * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-    set_assembly(c, wv ? c->wv_copy : nullptr, c->jv_copy, c->D_copy, delta_p);
+    assemble_any(c, wv ? c->wv_copy : nullptr, c->jv_copy, c->D_copy, delta_p);
     c->state = 3;
     return IPM_OK;
   });
@@ -791,7 +1029,7 @@ ipm_status kkt_assemble(ipm_ctx *c, const double *wv, const double *jv, const do
 
 ipm_status kkt_factor(ipm_ctx *c, int32_t precision, int32_t *bad_col) {
   if (!c) return IPM_ERR_ARG;
-  return guarded(c, [&]() -> ipm_status { return do_factor(c, precision, bad_col); });
+  return guarded(c, [&]() -> ipm_status { return factor_any(c, precision, bad_col); });
 }
 
 ipm_status kkt_solve(ipm_ctx *c, const double *b, double *x, int32_t nrhs, int32_t refine,
@@ -800,12 +1038,16 @@ ipm_status kkt_solve(ipm_ctx *c, const double *b, double *x, int32_t nrhs, int32
   return guarded(c, [&]() -> ipm_status {
     // right-hand side k occupies b[k n .. (k+1) n); each is solved (and
     // refined) on its own, the info reports the totals and the worst residual
-    const int64_t n = c->P.n;
+    // (with a formulation (4) or (6), n is the order of its system)
+    ipm_ctx *t = c->sys ? c->sys : c;
+    if (c->sys && c->state < 4) throw Fail{IPM_ERR_STATE, "kkt_solve before kkt_factor"};
+    const int64_t n = t->P.n;
     ipm_solve_info all{0, 0, 0.0};
     ipm_status worst = IPM_OK;
     for (int32_t k = 0; k < nrhs; k++) {
       ipm_solve_info one{};
-      const ipm_status st = do_solve(c, b + k * n, x + k * n, refine, &one);
+      const ipm_status st = do_solve(t, b + k * n, x + k * n, refine, &one);
+      if (st != IPM_OK && t != c) c->err = t->err;
       all.iterations += one.iterations;
       all.used_pcg = std::max(all.used_pcg, one.used_pcg);
       all.rel_residual = std::max(all.rel_residual, one.rel_residual);
@@ -844,6 +1086,7 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
     const ipm_options &o = c->opts;
     VecOps V = c->vec();
     c->refine_steps = c->pcg_steps = 0;
+    if (c->sys) c->sys->refine_steps = c->sys->pcg_steps = 0;
     // starting point (unless warm-started from the caller's x, s, lambda)
     if (!o.warm_start) {
       c->have_stale = false;  // a held factor belongs to another run
@@ -875,6 +1118,16 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
     double delta_p = o.delta_p;
     res.status = IPM_ERR_MAXITER;
     ipm_status stt = IPM_OK;
+    // Arithmetic of the factor: starts at o.precision; after an escalation
+    // (fallback_fp64) it stays at the fallback arithmetic for the rest of the
+    // solve, since the condensed matrix only gets worse conditioned as mu -> 0.
+    int prec_now = o.precision;
+    const int fb_prec = c->storage_bytes == 8 ? IPM_FP64 : IPM_TF32X3;
+    const ipm_ctx *fac = c->sys ? c->sys : c;  // the context that holds the factor
+    auto can_escalate = [&]() {
+      return o.fallback_fp64 && c->factor_prec != fb_prec && c->factor_prec != IPM_FP64 &&
+             (fb_prec == IPM_FP64 || (fac->tcp.ready() && !fac->dp.sgn));
+    };
     int it = 0;
     for (it = 0; it <= o.max_iter; it++) {
       eval_g(c, jv, b, x);
@@ -914,7 +1167,14 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       auto refactor = [&]() -> ipm_status {
         c->learned_active = false;
         c->refine_override = c->pcg_override = -1;
-        ipm_status f = factor_with_retry(c, wv, jv, o.precision, delta_p, &res);
+        ipm_status f = factor_with_retry(c, wv, jv, prec_now, delta_p, &res);
+        // a low-precision factor that had to perturb pivots has broken down:
+        // redo it in the fallback arithmetic before solving with it
+        if (f == IPM_OK && c->last_perturbed > 0 && can_escalate()) {
+          res.fp64_fallbacks++;
+          prec_now = fb_prec;
+          f = factor_with_retry(c, wv, jv, prec_now, delta_p, &res);
+        }
         if (f == IPM_OK) {
           factored = true;
           save_stale(c, jv);
@@ -952,13 +1212,9 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
       // A solve that missed accept_tol with a low-precision factor: refactor in
       // the most accurate arithmetic the storage allows and solve again.
-      const int fb_prec = c->storage_bytes == 8 ? IPM_FP64 : IPM_TF32X3;
-      auto can_escalate = [&]() {
-        return o.fallback_fp64 && c->factor_prec != fb_prec && c->factor_prec != IPM_FP64 &&
-               (fb_prec == IPM_FP64 || c->tcp.ready());
-      };
       if (stt != IPM_OK && can_escalate()) {
         res.fp64_fallbacks++;
+        prec_now = fb_prec;
         c->learned_active = false;
         c->refine_override = c->pcg_override = -1;
         stt = factor_with_retry(c, wv, jv, fb_prec, delta_p, &res);
@@ -982,6 +1238,7 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
         }
         if (stt != IPM_OK && can_escalate()) {  // the corrector missed accept_tol
           res.fp64_fallbacks++;
+          prec_now = fb_prec;
           c->learned_active = false;
           c->refine_override = c->pcg_override = -1;
           stt = factor_with_retry(c, wv, jv, fb_prec, delta_p, &res);
@@ -1009,8 +1266,8 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
     for (auto &e : ev) cudaEventDestroy(e);
     CK(cudaStreamSynchronize(c->st));
     res.iterations = it;
-    res.refine_steps = (int32_t)c->refine_steps;
-    res.pcg_steps = (int32_t)c->pcg_steps;
+    res.refine_steps = (int32_t)(c->refine_steps + (c->sys ? c->sys->refine_steps : 0));
+    res.pcg_steps = (int32_t)(c->pcg_steps + (c->sys ? c->sys->pcg_steps : 0));
     res.time_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return (ipm_status)res.status;
@@ -1024,6 +1281,8 @@ ipm_status kkt_symbolic_export(const ipm_ctx *c, int32_t *perm, int32_t *parent,
                                int32_t *super, int32_t *sparent, int32_t *slevel, int64_t *srp,
                                int32_t *sri) {
   if (!c || c->state < 1) return c ? IPM_ERR_STATE : IPM_ERR_ARG;
+  if (c->sys)  // the formulation's system
+    return kkt_symbolic_export(c->sys, perm, parent, colcount, super, sparent, slevel, srp, sri);
   const Symbolic &S = c->S;
   auto cp = [](auto *dst, const auto &v) {
     if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
@@ -1041,6 +1300,11 @@ ipm_status kkt_symbolic_export(const ipm_ctx *c, int32_t *perm, int32_t *parent,
 
 ipm_status kkt_export_assembled(ipm_ctx *c, double *h_out) {
   if (!c || !h_out) return IPM_ERR_ARG;
+  if (c->sys) {
+    const ipm_status st = kkt_export_assembled(c->sys, h_out);
+    if (st != IPM_OK) c->err = c->sys->err;
+    return st;
+  }
   return guarded(c, [&]() -> ipm_status {
     if (c->state < 3) throw Fail{IPM_ERR_STATE, "nothing assembled"};
     const int64_t nk = c->dp.nk;
@@ -1055,6 +1319,11 @@ ipm_status kkt_export_assembled(ipm_ctx *c, double *h_out) {
 ipm_status kkt_factor_entries(ipm_ctx *c, int64_t count, const int32_t *rows, const int32_t *cols,
                               double *out) {
   if (!c || count < 0 || (count > 0 && (!rows || !cols || !out))) return IPM_ERR_ARG;
+  if (c->sys) {
+    const ipm_status st = kkt_factor_entries(c->sys, count, rows, cols, out);
+    if (st != IPM_OK) c->err = c->sys->err;
+    return st;
+  }
   return guarded(c, [&]() -> ipm_status {
     if (c->state < 4) throw Fail{IPM_ERR_STATE, "no factor"};
     if (count == 0) return IPM_OK;
@@ -1082,6 +1351,7 @@ int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0;
 
 ipm_status kkt_test_solve_timeout(ipm_ctx *c, uint32_t spins, int32_t withheld_cta) {
   if (!c || spins == 0 || withheld_cta < 0) return IPM_ERR_ARG;
+  if (c->sys) return kkt_test_solve_timeout(c->sys, spins, withheld_cta);
   c->test_spins = spins;
   c->test_withhold = withheld_cta;
   return IPM_OK;
@@ -1089,6 +1359,11 @@ ipm_status kkt_test_solve_timeout(ipm_ctx *c, uint32_t spins, int32_t withheld_c
 
 ipm_status kkt_time_kernel(ipm_ctx *c, int32_t kernel, int32_t reps, double *ms) {
   if (!c || !ms || reps < 1) return IPM_ERR_ARG;
+  if (c->sys) {
+    const ipm_status st = kkt_time_kernel(c->sys, kernel, reps, ms);
+    if (st != IPM_OK) c->err = c->sys->err;
+    return st;
+  }
   return guarded(c, [&]() -> ipm_status {
     if (kernel == 0 && c->state < 3) throw Fail{IPM_ERR_STATE, "nothing assembled"};
     if (kernel != 0 && c->state < 4) throw Fail{IPM_ERR_STATE, "no factor"};
@@ -1266,6 +1541,7 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
   double *scratch = nullptr;
   ipm_status rs = guarded(c, [&]() -> ipm_status {
     if (c->state < 2) throw Fail{IPM_ERR_STATE, "ipm_solve_grid_nlp before ipm_set_workspace"};
+    if (c->sys) throw Fail{IPM_ERR_UNSUPPORTED, "the grid NLP uses the primal condensed formulation"};
     GridNlp p;
     if (!grid_from(pp, p)) throw Fail{IPM_ERR_ARG, "invalid grid NLP parameters"};
     const Problem &P = c->P;
@@ -1505,6 +1781,11 @@ int64_t kkt_solve_noalloc_capacity(void) { return (int64_t)kNoAllocDoubles; }
 
 ipm_status kkt_solve_noalloc(ipm_ctx *c, const double *b, double *x) {
   if (!c || !b || !x) return IPM_ERR_ARG;
+  if (c->sys) {  // the formulation's system (b, x: its order)
+    const ipm_status st = kkt_solve_noalloc(c->sys, b, x);
+    if (st != IPM_OK) c->err = c->sys->err;
+    return st;
+  }
   return guarded(c, [&]() -> ipm_status {
     if (c->state < 1) throw Fail{IPM_ERR_STATE, "kkt_solve_noalloc before kkt_analyze"};
     const size_t need = noalloc_need(c);

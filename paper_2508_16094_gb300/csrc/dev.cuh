@@ -22,6 +22,9 @@ struct DevPlan {
   const int64_t *k_slot, *k_poff, *k_w, *k_orig;
   const int32_t *k_pa, *k_pb, *k_diag;
   const int32_t *perm;  // final new -> old
+  // Pivot signs (final numbering) of a signed factorisation K = L S L^T of a
+  // quasi-definite matrix (S = diag(sgn)); nullptr for Cholesky (S = I).
+  const int8_t *sgn;
   // problem structure
   const int64_t *jp, *jtp;
   const int32_t *ji, *jrow, *jtpos;

@@ -149,11 +149,14 @@ __global__ void kadd_kernel(DevPlan dp, int64_t q0, int64_t q1, const double *__
   }
 }
 
-// C[M x N] -= A[M x K] * B[N x K]^T for one 64x64 tile (rows of A and B are
-// contiguous along K), 256 threads, 4x4 outputs per thread.
+// C[M x N] -= A[M x K] * S * B[N x K]^T for one 64x64 tile (rows of A and B
+// are contiguous along K), 256 threads, 4x4 outputs per thread; S = diag(sk)
+// holds the pivot signs of the K columns of a signed factorisation (sk ==
+// nullptr: S = I).
 template <typename T>
 __device__ __forceinline__ void gemm_nt_tile(T *C, int64_t ldc, const T *A, int64_t lda,
-                                             const T *B, int64_t ldb, int M, int N, int K) {
+                                             const T *B, int64_t ldb, int M, int N, int K,
+                                             const int8_t *sk) {
   constexpr int BK = 16;
   __shared__ T As[BK][kGemmTile + 4], Bs[BK][kGemmTile + 4];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -167,7 +170,9 @@ __device__ __forceinline__ void gemm_nt_tile(T *C, int64_t ldc, const T *A, int6
     for (int q = 0; q < 4; q++) {
       const int e = tid + 256 * q, r = e / BK, kk = e % BK;
       As[kk][r] = (r < M && k0 + kk < K) ? A[(int64_t)r * lda + k0 + kk] : T(0);
-      Bs[kk][r] = (r < N && k0 + kk < K) ? B[(int64_t)r * ldb + k0 + kk] : T(0);
+      T bv = (r < N && k0 + kk < K) ? B[(int64_t)r * ldb + k0 + kk] : T(0);
+      if (sk && k0 + kk < K && sk[k0 + kk] < 0) bv = -bv;
+      Bs[kk][r] = bv;
     }
     __syncthreads();
 #pragma unroll
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(256) gemm_ll_kernel(DevPlan dp, int32_t task0,
   const int kb = min(nb, F.ncol - k), M = min(kGemmTile, nf - i0);
   T *P = L + F.loff;
   gemm_nt_tile<T>(P + (int64_t)i0 * F.ld + k, F.ld, P + (int64_t)i0 * F.ld, F.ld,
-                  P + (int64_t)k * F.ld, F.ld, M, kb, k);
+                  P + (int64_t)k * F.ld, F.ld, M, kb, k, dp.sgn ? dp.sgn + F.first : nullptr);
 }
 
 // Update matrix U = F22 - L21 L21^T, one 64x64 lower tile per block.
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(256) syrk_kernel(DevPlan dp, int32_t task0,
   const int M = min(kGemmTile, F.nrow - i0), N = min(kGemmTile, F.nrow - j0);
   const T *P = L + F.loff + (int64_t)F.ncol * F.ld;
   gemm_nt_tile<T>(U + F.uoff + (int64_t)i0 * F.uld + j0, F.uld, P + (int64_t)i0 * F.ld, F.ld,
-                  P + (int64_t)j0 * F.ld, F.ld, M, N, F.ncol);
+                  P + (int64_t)j0 * F.ld, F.ld, M, N, F.ncol, dp.sgn ? dp.sgn + F.first : nullptr);
 }
 
 template <typename T> __device__ __forceinline__ T big_pivot();
@@ -229,7 +234,10 @@ template <> __device__ __forceinline__ double big_pivot<double>() { return 1e64;
 
 // Cholesky of one diagonal block (kb <= nb <= 128) in shared memory. A pivot
 // that is not positive is either reported (smallest failing column kept) or
-// replaced by a large value (static pivoting) and counted.
+// replaced by a large value (static pivoting) and counted. With pivot signs
+// (dp.sgn, a quasi-definite matrix) the block is factored as L S L^T: the
+// pivot d_j must have the sign s_j, L_jj = sqrt(s_j d_j), the column below is
+// divided by s_j L_jj and the trailing update is -= L_ij s_j L_cj.
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__restrict__ tasks,
                                                     int nb, T *__restrict__ L, int32_t *status,
@@ -238,6 +246,7 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__re
   const FrontInfo F = dp.fronts[tk.front];
   const int k = tk.a, kb = min(nb, F.ncol - k), ls = nb + 1;
   T *A = L + F.loff + (int64_t)k * F.ld + k;
+  const int8_t *sg = dp.sgn ? dp.sgn + F.first + k : nullptr;
   extern __shared__ unsigned char smem_raw[];
   T *Ad = reinterpret_cast<T *>(smem_raw);  // [nb][nb + 1]
   const int tid = threadIdx.x;
@@ -247,8 +256,9 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__re
   }
   __syncthreads();
   for (int j = 0; j < kb; j++) {
+    const T sj = (sg && sg[j] < 0) ? T(-1) : T(1);
     if (tid == 0) {
-      T d = Ad[j * ls + j];
+      T d = sj * Ad[j * ls + j];
       if (!(d > T(0)) || !(d < big_pivot<T>() * big_pivot<T>())) {
         if (perturb) {
           d = big_pivot<T>();
@@ -261,13 +271,13 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__re
       Ad[j * ls + j] = sqrt(d);
     }
     __syncthreads();
-    const T ljj = Ad[j * ls + j];
+    const T ljj = sj * Ad[j * ls + j];
     for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i * ls + j] /= ljj;
     __syncthreads();
     const int w = kb - j - 1;
     for (int e = tid; e < w * w; e += blockDim.x) {
       const int i = j + 1 + e / w, c = j + 1 + e % w;
-      if (c <= i) Ad[i * ls + c] = fma(-Ad[i * ls + j], Ad[c * ls + j], Ad[i * ls + c]);
+      if (c <= i) Ad[i * ls + c] = fma(-sj * Ad[i * ls + j], Ad[c * ls + j], Ad[i * ls + c]);
     }
     __syncthreads();
   }
@@ -278,7 +288,8 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__re
 }
 
 // Rows below the diagonal block: X <- X L_kk^{-T} (row-wise forward
-// substitution), kTrsmRows rows per block, kb <= nb <= 128.
+// substitution), kTrsmRows rows per block, kb <= nb <= 128; with pivot signs
+// X <- X L_kk^{-T} S_k.
 template <typename T>
 __global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, const Task *__restrict__ tasks,
                                                          int nb, T *__restrict__ L) {
@@ -301,12 +312,16 @@ __global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, const Task 
     X[r * ls + c] = Xg[(int64_t)r * F.ld + c];
   }
   __syncthreads();
+  const int8_t *sg = dp.sgn ? dp.sgn + F.first + k : nullptr;
   if (tid < rows) {
     T *x = X + tid * ls;
     for (int c = 0; c < kb; c++) {
       T v = x[c];
-      for (int c2 = 0; c2 < c; c2++) v = fma(-x[c2], Lk[c * ls + c2], v);
-      x[c] = v / Lk[c * ls + c];
+      for (int c2 = 0; c2 < c; c2++) {
+        const T l = (sg && sg[c2] < 0) ? -Lk[c * ls + c2] : Lk[c * ls + c2];
+        v = fma(-x[c2], l, v);
+      }
+      x[c] = v / ((sg && sg[c] < 0) ? -Lk[c * ls + c] : Lk[c * ls + c]);
     }
   }
   __syncthreads();

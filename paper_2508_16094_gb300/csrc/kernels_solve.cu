@@ -10,6 +10,8 @@
 // Backward (L^T x = y), levels descending: subtract L21^T x(rows below) with a
 // fixed-order reduction, then block columns from last to first: solve the
 // transposed diagonal block and update the columns to its left.
+#include <algorithm>
+
 #include "launch.h"
 
 namespace gipm {
@@ -152,7 +154,25 @@ __global__ void __launch_bounds__(256) upd_bwd_kernel(DevPlan dp, int32_t task0,
   y[F.first + c] -= v;
 }
 
+// y <- S y between the sweeps of a signed factor K = L S L^T (final numbering).
+template <typename V>
+__global__ void sign_kernel(int32_t n, const int8_t *__restrict__ sgn, V *__restrict__ y) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    if (sgn[k] < 0) y[k] = -y[k];
+}
+
 }  // namespace
+
+template <typename V>
+void launch_sign(const DevPlan &dp, V *y, cudaStream_t st) {
+  if (!dp.sgn || dp.n <= 0) return;
+  const int g = (int)std::min<int64_t>((dp.n + 255) / 256, 152 * 16);
+  note_launch();
+  sign_kernel<V><<<g, 256, 0, st>>>(dp.n, dp.sgn, y);
+}
+template void launch_sign<float>(const DevPlan &, float *, cudaStream_t);
+template void launch_sign<double>(const DevPlan &, double *, cudaStream_t);
 
 template <typename T, typename V>
 void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st) {
@@ -169,6 +189,7 @@ void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, c
       if (g1 > g0) { note_launch(); upd_fwd_kernel<T, V><<<g1 - g0, 256, 0, st>>>(dp, g0, nbs, L, y, t); }
     }
   }
+  launch_sign<V>(dp, y, st);  // K = L S L^T: y <- S L^{-1} b before the backward sweep
   for (int li = nlev - 1; li >= 0; li--) {
     const LevelPlan &LP = plan.levels[li];
     if (LP.rg_e > LP.rg_b)
@@ -191,6 +212,7 @@ static cudaError_t preload_one() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)rows_bwd_kernel<T, V>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)diag_bwd_kernel<T, V>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)upd_bwd_kernel<T, V>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)sign_kernel<V>);
   return e;
 }
 

@@ -29,9 +29,14 @@ template <typename T>
 void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L, cudaStream_t st);
 
 // Triangular solves with the factor: y (final numbering, length n) is
-// overwritten by L^{-T} L^{-1} y. t: update-vector scratch (plan.t_entries).
+// overwritten by L^{-T} L^{-1} y (L^{-T} S L^{-1} y for a signed factor,
+// dp.sgn). t: update-vector scratch (plan.t_entries).
 template <typename T, typename V>
 void launch_solve(const DevPlan &dp, const Plan &plan, const T *L, V *y, V *t, cudaStream_t st);
+
+// y <- S y with the pivot signs of a signed factor (no-op without dp.sgn).
+template <typename V>
+void launch_sign(const DevPlan &dp, V *y, cudaStream_t st);
 
 // Loads the level-solve kernels (FP64 and FP32) so that a later first launch
 // commits no device memory (lazy module loading); used by the allocation-free solve.

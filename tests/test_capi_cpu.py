@@ -118,3 +118,47 @@ def test_grid_nlp_pattern_matches_generator():
             assert np.array_equal(pt[a], b), a
     with pytest.raises(gb.IpmError):
         gb.ipm_grid_nlp_pattern(1)
+
+
+@pytest.mark.parametrize("form", ["dual", "augmented"])
+@pytest.mark.parametrize("case", ["grid5", "random120"])
+def test_formulation_symbolic_bit_exact_vs_oracle(lib, form, case):
+    """The systems of the dual condensed (6) and augmented (4) formulations:
+    the library builds their pattern and analyses it like the oracle does the
+    pattern it builds on its own (oracle/forms.py)."""
+    from oracle import forms
+    if case == "grid5":
+        lp = gen.grid_lp(5, seed=2)
+        nd = gen.nd_order_grid3d(5, leaf=16)
+        perm = nd if form == "dual" else np.concatenate([[p, lp.n + p] for p in nd]).astype(np.int32)
+    else:
+        lp = gen.random_lp(120, 80, 3, seed=6)
+        perm = None
+    o = gb.default_options(formulation=gb.IPM_FORM_DUAL if form == "dual" else gb.IPM_FORM_AUGMENTED)
+    ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u, options=o)
+    info = ctx.kkt_analyze(perm)
+    got = ctx.kkt_symbolic_export()
+    mt = lp.m + 2 * lp.n
+    one = np.ones(mt)
+    if form == "dual":
+        S, _, _ = forms.dual_system(lp, one, one, np.ones(lp.n), 1e-8, 1e-8, perm)
+        assert info.n == lp.m and ctx.kkt_order() == lp.m
+    else:
+        S, _, _ = forms.augmented_system(lp, one, one, np.ones(lp.n), 1e-8, 1e-8, perm)
+        assert info.n == lp.n + lp.m and ctx.kkt_order() == lp.n + lp.m
+    for k in ["perm", "parent", "colcount", "super", "sparent", "slevel", "srp", "sri"]:
+        np.testing.assert_array_equal(got[k], getattr(S, k), err_msg=k)
+    assert info.nnz_l == S.nnz_l and info.m_tot == mt
+
+
+def test_dual_formulation_rejects_a_full_hessian(lib):
+    n = 4
+    rp = np.array([0, 2, 4], np.int64)
+    cl = np.array([0, 1, 2, 3], np.int32)
+    wp = np.array([0, 2, 3, 4, 5], np.int64)  # W has the off-diagonal entry (1, 0)
+    wi = np.array([0, 1, 1, 2, 3], np.int32)
+    o = gb.default_options(formulation=gb.IPM_FORM_DUAL)
+    ctx = gb.IpmContext(n, 2, rp, cl, None, None, wp, wi, options=o)
+    with pytest.raises(gb.IpmError) as e:
+        ctx.kkt_analyze(None)
+    assert e.value.status == 10  # IPM_ERR_UNSUPPORTED
