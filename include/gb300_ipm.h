@@ -427,12 +427,12 @@ IPM_API ipm_status kkt_export_assembled(ipm_ctx *ctx, double *h_out);
 IPM_API ipm_status kkt_factor_entries(ipm_ctx *ctx, int64_t count, const int32_t *h_rows,
                               const int32_t *h_cols, double *h_out);
 
-/* Test of the bounded device-side waits: the next launch of the persistent
- * FP32 triangular solve (kkt_solve with an FP32-storage factor) polls each
- * grid barrier at most `spins` times, and its CTA `withheld_cta` leaves the
- * launch at its first barrier without arriving, so the other CTAs' waits run
- * out. That kkt_solve then returns IPM_ERR_TIMEOUT and resets the barrier
- * state; the context stays usable. Applies to one launch only.
+/* Test of the bounded device-side waits: in the next launch of the persistent
+ * FP32 triangular solve (kkt_solve with an FP32-storage factor) every wait
+ * polls its flag at most `spins` times, and CTA `withheld_cta` abandons the
+ * first task it takes, so the tasks that need its result wait until their
+ * limit runs out. That kkt_solve then returns IPM_ERR_TIMEOUT; the context
+ * stays usable. Applies to one launch only.
  * Errors: IPM_ERR_ARG for spins == 0 or a negative CTA index. */
 IPM_API ipm_status kkt_test_solve_timeout(ipm_ctx *ctx, uint32_t spins, int32_t withheld_cta);
 

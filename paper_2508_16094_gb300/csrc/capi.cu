@@ -48,7 +48,7 @@ struct ipm_ctx {
   double *jv_copy = nullptr, *D_copy = nullptr, *wv_copy = nullptr;  // inputs kept for refinement
   float *Llo = nullptr;  // low parts of the split-TF32 factor
   float *dinv = nullptr, *fsa = nullptr, *fsb = nullptr, *fsx = nullptr;  // persistent FP32 solve
-  unsigned *psbar = nullptr;  // its grid-barrier state
+  unsigned *psflags = nullptr;  // its tickets, flags and counters
   float *pspart = nullptr;    // its partial sums
   // learned correction of a stale factor
   LearnedBufs lb;
@@ -186,7 +186,7 @@ void layout(ipm_ctx *c, char *base) {
   d.fs_inv = upload(cv, pl.fs_inv, st);
   d.fs_first_slot = upload(cv, pl.fs_first_slot, st);
   d.ps_tasks = upload(cv, pl.ps_tasks, st);
-  d.ps_phases = upload(cv, pl.ps_phases, st);
+  d.ps_pbase = upload(cv, pl.ps_pbase, st);
   d.fs_dinv_off = upload(cv, pl.fs_dinv_off, st);
   d.k_slot = upload(cv, pl.k_slot, st);
   d.k_poff = upload(cv, pl.k_poff, st);
@@ -271,9 +271,8 @@ void layout(ipm_ctx *c, char *base) {
   c->fsa = cv.take<float>(n);
   c->fsb = cv.take<float>(n);
   c->fsx = cv.take<float>(n);
-  c->psbar = cv.take<unsigned>(kPsBarrierWords);
-  c->pspart = cv.take<float>(pl.ps_part_entries);
-  if (base) CK(cudaMemsetAsync(c->psbar, 0, kPsBarrierWords * sizeof(unsigned), st));
+  c->psflags = cv.take<unsigned>(std::max<int64_t>(pl.ps_flag_words, 32));
+  c->pspart = cv.take<float>(std::max<int64_t>(pl.ps_part_entries, 1));
   {  // learned-correction buffers (only when enabled)
     LearnedBufs &B = c->lb;
     const bool on = c->opts.learned != 0 || c->opts.learned_probes > 0;
@@ -372,7 +371,7 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
 // sweeps (fsa -> fsx), 1 forward only (fsa -> fsb), 2 backward only (fsb -> fsx)
 void launch_fp32_solve(ipm_ctx *c, int which) {
   launch_psolve(c->dp, c->plan, (const float *)c->L, c->dinv, c->fsa, c->fsb, c->fsx,
-                reinterpret_cast<float *>(c->tv), c->pspart, c->psbar, c->status, which != 2, which != 1,
+                reinterpret_cast<float *>(c->tv), c->pspart, c->psflags, c->status, which != 2, which != 1,
                 c->st, c->test_spins, c->test_withhold);
   c->test_spins = 0;
   c->test_withhold = -1;
@@ -412,16 +411,16 @@ void apply_factor(ipm_ctx *c, const double *b, double *out, bool accumulate) {
   }
 }
 
-// A grid barrier of the persistent solve that ran out of time leaves its state
-// inconsistent: reset it and report the timeout.
+// A wait of the persistent solve that ran out of time: the launch drained and
+// its result is invalid; clear the word (each launch zeroes its own flags) and
+// report the timeout.
 void check_solve_barrier(ipm_ctx *c) {
   int32_t flag = 0;
   CK(cudaMemcpyAsync(&flag, c->status + ST_SOLVE_TIMEOUT, sizeof(flag), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   if (flag) {
     CK(cudaMemsetAsync(c->status + ST_SOLVE_TIMEOUT, 0, sizeof(int32_t), c->st));
-    CK(cudaMemsetAsync(c->psbar, 0, kPsBarrierWords * sizeof(unsigned), c->st));
-    throw Fail{IPM_ERR_TIMEOUT, "a grid barrier of the persistent solve ran out of time"};
+    throw Fail{IPM_ERR_TIMEOUT, "a bounded wait of the persistent solve ran out of time"};
   }
 }
 

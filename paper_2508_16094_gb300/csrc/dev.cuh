@@ -16,7 +16,7 @@ struct DevPlan {
   const Task *build, *gemm, *potrf, *trsm, *syrk, *gath, *sdiag, *sgemv, *rgemv;
   const int64_t *toff;
   const Task *fs_inv, *ps_tasks;  // persistent FP32 solve
-  const SolvePhase *ps_phases;
+  const int64_t *ps_pbase;        // per front: first partial-sum row of its backward tasks
   const int64_t *fs_dinv_off;
   const int32_t *fs_first_slot;  // per front: slot of its first diagonal block
   const int64_t *k_slot, *k_poff, *k_w, *k_orig;

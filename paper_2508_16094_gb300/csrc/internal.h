@@ -51,18 +51,20 @@ struct Task {
   int32_t front, a, b, c;
 };
 
-// One phase of the persistent solve: tasks [begin, end) of one kind.
-enum SolvePhaseKind : int32_t {
-  PS_FWD_GATHER = 0,  // (front, first row of a 256-row chunk, slot of block 0 or -1)
-  PS_FWD_STEP = 1,    // (front, first row of a 128-row chunk, block column j, slot of block j+128 or -1)
-  PS_BWD_PART = 2,    // (front, first column of a 128-column block, first row below the front
-                      //  of a 128-row chunk, partial-sum slot)
-  PS_BWD_ROWS = 3,    // (front, first column of a 128-column block, slot if it is the last block
-                      //  or -1, first partial-sum slot of the block)
-  PS_BWD_STEP = 4     // (front, first column of a 128-column chunk, block row j, slot of block j-128 or -1)
-};
-struct SolvePhase {
-  int32_t begin, end, kind, pad;
+// A task of the persistent FP32 solve. Tasks run in the order of the plan
+// (a ticket taken from a global counter), and a task waits only for tasks
+// earlier in that order (flags and counters in device memory), so the solve
+// needs no grid barrier and cannot deadlock. Blocks are 128 wide.
+enum SolveTaskKind : int32_t {
+  WS_FWD_DIAG = 0,   // (front, a = block i): gather the children's update entries for
+                     // the block's rows, subtract L_ij y_j for j < i as each y_j is
+                     // published, y_i = L_ii^{-1} (.) (explicit inverse), publish y_i
+  WS_FWD_BELOW = 1,  // (front, a = first row below the front of a 128-row chunk): gather,
+                     // add L_rj y_j for every block j, store the front's update vector
+  WS_BWD_PART = 2,   // (front, a = column block cb, b = first row below of a 128-row
+                     // chunk): partial sums L_{r,cb}^T x_r once the parent front is done
+  WS_BWD_DIAG = 3    // (front, a = column block cb): the partial sums, L_{i,cb}^T x_i for
+                     // i > cb as each x_i is published, x_cb = L_cc^{-T} (.), publish x_cb
 };
 
 // Work of one level of the supernodal tree, as ranges into the task arrays.
@@ -98,19 +100,21 @@ struct Plan {
   std::vector<Task> gath_tasks, sdiag_tasks, sgemv_tasks, rgemv_tasks;
   std::vector<int64_t> toff;         // per front: offset of its solve update vector (length nrow)
   int64_t t_entries = 0;
-  // fused FP32 solve: explicit inverses of the 128-wide diagonal blocks
   // persistent FP32 solve: inverses of the 128-wide diagonal blocks (slot s:
-  // jb rows of round_up(jb, 4) floats at fs_dinv_off[s]) and the phases of the
-  // two sweeps, each a range of ps_tasks separated by a grid barrier
+  // jb rows of round_up(jb, 4) floats at fs_dinv_off[s]; the slots of a front
+  // are consecutive from fs_first_slot[front]) and its task list, forward
+  // tasks first. Flags (32-bit words): [0, 32) tickets, then per slot "y
+  // published", "x published", "partial sums done", per front "update-vector
+  // chunks done", "column blocks done".
   std::vector<Task> fs_inv;                  // (front, first column, slot)
-  std::vector<int32_t> fs_first_slot;        // per front: slot of block 0 (consecutive after it)
+  std::vector<int32_t> fs_first_slot;        // per front: slot of block 0
   std::vector<int64_t> fs_dinv_off;
   int64_t fs_dinv_entries = 0;
-  std::vector<Task> ps_tasks;
-  std::vector<SolvePhase> ps_phases;         // forward phases, then backward ones
-  int32_t ps_fwd_phases = 0;
-  int32_t ps_max_tasks = 0;                  // largest phase
-  int64_t ps_part_entries = 0;               // partial sums of the backward row phases (floats)
+  std::vector<Task> ps_tasks;                // (front, a, b, kind)
+  int32_t ps_fwd_tasks = 0;
+  std::vector<int64_t> ps_pbase;             // per front: first partial-sum row (128 floats each)
+  int64_t ps_part_entries = 0;               // floats of partial sums
+  int64_t ps_flag_words = 0;
   // K entries in level-major order
   std::vector<int64_t> k_slot;   // element offset of L(i, j) in the factor storage
   std::vector<int64_t> k_poff;   // products [k_poff[q], k_poff[q+1])

@@ -1,17 +1,23 @@
-// Persistent supernodal triangular solves for FP32 factors (TF32/TF32x3/FP32).
+// Persistent supernodal triangular solves for FP32 factors (TF32/TF32x3/BF16/FP32).
 //
 // After each factorisation one launch inverts every 128-wide diagonal block of
 // L (explicit inverse, rows padded to a multiple of 4 floats). A solve is then
-// ONE cooperative launch that walks the phases of the plan (forward sweep
-// leaves -> root, backward sweep root -> leaves) with a grid barrier between
-// phases. Per block step only the update of the rows (forward) or columns
-// (backward) outside the diagonal block is spread over the grid; the block that
-// owns the next diagonal block finishes its own update and then applies that
-// block's inverse, so each step costs one barrier and the inverse is read once.
-// Three vectors keep every read of a phase disjoint from its writes: a (right-
-// hand side, updated in place), b (forward result, then updated in place by the
-// backward sweep) and x (solution); t holds the update vectors of the fronts.
-// Vectors written inside the launch are read through L2 (ld.global.cg).
+// ONE launch of a persistent kernel whose CTAs take the tasks of the plan in
+// order from a global ticket counter (forward sweep leaves -> root, backward
+// sweep root -> leaves). Instead of grid barriers between phases, each task
+// waits only for the results it reads, published through flags and counters
+// in device memory: a diagonal block of the forward sweep subtracts
+// L_ij y_j as each y_j of its front appears (a wavefront down the front's
+// blocks), rows below a front take every y_j and then count towards the
+// front's update vector, which the parent's gathers wait for; the backward
+// sweep mirrors this with partial sums over the rows below a front (waiting
+// for the parent front) and x_i published block by block. A task waits only
+// for earlier tasks, so the schedule cannot deadlock, and every wait is
+// bounded: on expiry the status word is set and the whole launch drains.
+// Three vectors keep reads disjoint from writes: a (right-hand side), b
+// (forward result) and x (solution); t holds the fronts' update vectors.
+// Vectors written inside the launch are read through L2 (ld.global.cg), and
+// the loads of L for a block are issued before its wait.
 #include <algorithm>
 #include <stdexcept>
 #include <string>
@@ -68,15 +74,15 @@ struct PsArgs {
   DevPlan dp;
   const float *L, *Dinv;
   float *a, *b, *x, *t, *part;
-  int32_t p0, p1;   // phases [p0, p1)
-  unsigned *bar;    // [2..3] 64-bit arrival counter of the grid barrier
-  int32_t *status;  // ST_SOLVE_TIMEOUT
-  unsigned spins;   // polls before a barrier wait gives up
-  int32_t withhold; // test of the bounded wait: this CTA leaves at its first barrier (-1: none)
+  int32_t q0, q1;    // tasks [q0, q1) of the plan
+  unsigned *flags;   // plan.ps_flag_words words, zeroed before the launch
+  int32_t *status;   // ST_SOLVE_TIMEOUT
+  unsigned spins;    // polls before a wait gives up
+  int32_t withhold;  // test of the bounded wait: this CTA abandons its first task (-1: none)
+  int32_t nslot, nfr;
 };
 
-constexpr int kMaxGrid = 1024;  // CTAs of one cooperative solve launch
-constexpr int kRC = 128;  // rows below a front per partial-sum task
+constexpr int kRC = 128;  // rows below a front per task
 constexpr long long kCopySpinCycles = 2000000000ll;  // bounded wait on a staging copy (~1 s)
 
 __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
@@ -93,42 +99,19 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident): one
-// 64-bit arrival counter (words 2-3 of the barrier state) that only grows. A
-// CTA adds 1 (release) and waits (acquire) until the counter reaches the next
-// multiple of the grid size above the value it found, so launches need no
-// reset as long as every barrier of the previous one completed (after a
-// timeout the host zeroes the state). Every wait is bounded (max_spins polls);
-// on a timeout the status word is set and all CTAs return false; a CTA that
-// sees the word set by another one stops waiting too. The CTA `withhold`
-// (tests of the bounded wait) returns false at once without arriving, so the
-// other CTAs' waits run out.
-__device__ bool grid_barrier(unsigned *bar, int32_t *status, unsigned max_spins, int withhold) {
-  __shared__ int ok;
-  __syncthreads();
-  if ((int)blockIdx.x == withhold) return false;
-  if (threadIdx.x == 0) {
-    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(bar + 2);
-    unsigned long long old, v;
-    __threadfence();
-    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(ctr) : "memory");
-    const unsigned long long G = gridDim.x, target = (old / G + 1) * G;
-    unsigned spins = 0;
-    while (true) {
-      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
-      if (v >= target) break;
-      if (++spins > max_spins) {
-        atomicExch(status + ST_SOLVE_TIMEOUT, 1);
-        break;
-      }
-      if ((spins & 63u) == 0 && *(volatile int32_t *)(status + ST_SOLVE_TIMEOUT) != 0) break;
-      __nanosleep(16);
-    }
-    __threadfence();
-    ok = *(volatile int32_t *)(status + ST_SOLVE_TIMEOUT) == 0;
-  }
-  __syncthreads();
-  return ok != 0;
+// Flag words (see Plan): tickets, then per slot y / x published and partial
+// sums done, per front update-vector chunks and column blocks done.
+__device__ __forceinline__ unsigned *f_ticket(const PsArgs &A) { return A.flags; }
+__device__ __forceinline__ unsigned *f_y(const PsArgs &A, int slot) { return A.flags + 32 + slot; }
+__device__ __forceinline__ unsigned *f_x(const PsArgs &A, int slot) { return A.flags + 32 + A.nslot + slot; }
+__device__ __forceinline__ unsigned *f_part(const PsArgs &A, int slot) {
+  return A.flags + 32 + 2 * A.nslot + slot;
+}
+__device__ __forceinline__ unsigned *f_tvec(const PsArgs &A, int front) {
+  return A.flags + 32 + 3 * A.nslot + front;
+}
+__device__ __forceinline__ unsigned *f_front(const PsArgs &A, int front) {
+  return A.flags + 32 + 3 * A.nslot + A.nfr + front;
 }
 
 // Shared scratch of one CTA (dynamic shared memory).
@@ -141,6 +124,8 @@ struct PsShared {
   float4 red4[kT / 32][32];     // per-row-group column sums
   unsigned long long mbar;      // completion of the staging copy
   uint32_t parity;              // its phase
+  int tk;                       // this CTA's current task
+  int ok;                       // verdict of the last wait
 };
 
 // Thread 0: start the bulk copy of a diagonal-block inverse into S.di.
@@ -257,103 +242,167 @@ __device__ void diag_bwd(const PsArgs &A, PsShared &S, const FrontInfo &F, int j
   }
 }
 
-// forward gather: a[cols] -= sum of the children's update entries, t[rows] =
-// that sum; the chunk holding block 0 then solves it
-__device__ void fwd_gather(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
-  const DevPlan &dp = A.dp;
-  const bool owner = tk.b >= 0;
-  if (owner && threadIdx.x == 0) stage_dinv(A, S, tk.b, min(kB, F.ncol));
-  const int nf = F.ncol + F.nrow, p = tk.a + threadIdx.x;
-  if (p < nf) {
-    float v = 0.f;
-    for (int ci = F.child_begin; ci < F.child_end; ci++) {
-      const int32_t ch = dp.children[ci];
-      const int32_t q = dp.inv[dp.fronts[ch].inv_off + p];
-      if (q >= 0) v += ldcg(A.t + dp.toff[ch] + q);
+// Thread 0 polls *w until it reaches target (acquire), at most A.spins times
+// and only while no other wait of the launch has run out; the CTA then shares
+// the verdict. On expiry the status word is set, and every later wait of the
+// launch gives up at once.
+__device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsigned target) {
+  __syncthreads();  // every thread has read the previous verdict
+  if (threadIdx.x == 0) {
+    unsigned v, spins = 0;
+    int ok = 1;
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(w) : "memory");
+      if (v >= target) break;
+      if ((spins & 63u) == 0 && *(volatile int32_t *)(A.status + ST_SOLVE_TIMEOUT) != 0) {
+        ok = 0;
+        break;
+      }
+      if (++spins > A.spins) {
+        atomicExch(A.status + ST_SOLVE_TIMEOUT, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
     }
-    if (p < F.ncol) {
-      const float y = ldcg(A.a + F.first + p) - v;
-      A.a[F.first + p] = y;
-      if (p < kB) S.sv[p] = y;
-    } else {
-      A.t[dp.toff[tk.front] + p - F.ncol] = v;
-    }
+    S.ok = ok;
   }
-  if (owner) {
-    if (threadIdx.x < kB && threadIdx.x >= min(kB, F.ncol)) S.sv[threadIdx.x] = 0.f;
-    if (wait_dinv(A, S)) diag_fwd(A, S, F, 0);
+  __syncthreads();
+  return S.ok != 0;
+}
+
+// After this CTA's writes: make them visible, then count one more on *w (release).
+__device__ void signal(unsigned *w) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(w) : "memory");
   }
 }
 
-// forward step of block column j: rows [i0, i0 + 128) below the block take
-// L[r, j:j+jb] y_j (warp w: rows i0 + 16w .. + 15, every load issued before
-// y_j arrives); the chunk right below the block then solves the next one
-__device__ void fwd_step(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+__device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F) {
   const DevPlan &dp = A.dp;
-  const int nf = F.ncol + F.nrow, i0 = tk.a, j = tk.b, jb = min(kB, F.ncol - j);
-  const bool owner = tk.c >= 0;
-  if (owner && threadIdx.x == 0) stage_dinv(A, S, tk.c, min(kB, F.ncol - (j + kB)));
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane;
-  const int rw = i0 + 16 * warp, r1 = min(i0 + kB, nf), r = rw + lane;
-  float4 l[16];
-  const float *P = A.L + F.loff + (int64_t)rw * F.ld + j + c;
+  for (int ci = F.child_begin; ci < F.child_end; ci++) {
+    const int32_t ch = dp.children[ci];
+    if (!wait_flag(A, S, f_tvec(A, ch), (dp.fronts[ch].nrow + kRC - 1) / kRC)) return false;
+  }
+  return true;
+}
+
+// Sum of the children's update entries at front position p.
+__device__ __forceinline__ float gather_children(const PsArgs &A, const FrontInfo &F, int p) {
+  const DevPlan &dp = A.dp;
+  float v = 0.f;
+  for (int ci = F.child_begin; ci < F.child_end; ci++) {
+    const int32_t ch = dp.children[ci];
+    const int32_t q = dp.inv[dp.fronts[ch].inv_off + p];
+    if (q >= 0) v += ldcg(A.t + dp.toff[ch] + q);
+  }
+  return v;
+}
+
+// Forward, diagonal block i of front s: rows j0 .. j0 + jb of the front.
+// warp w: rows 16w .. 16w + 15, lane: columns 4 lane .. 4 lane + 3 of block j
+// (the loads of block j are issued before y_j is waited for).
+__device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+  const DevPlan &dp = A.dp;
+  const int i = tk.a, j0 = kB * i, jb = min(kB, F.ncol - j0), slot0 = dp.fs_first_slot[tk.front];
+  if (threadIdx.x == 0) stage_dinv(A, S, slot0 + i, jb);
+  bool ok = wait_children(A, S, F);
+  if (ok && threadIdx.x < kB)
+    S.sv[threadIdx.x] = threadIdx.x < jb
+                            ? ldcg(A.a + F.first + j0 + threadIdx.x) - gather_children(A, F, j0 + threadIdx.x)
+                            : 0.f;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
+  float racc = 0.f;
+  for (int j = 0; j < i && ok; j++) {
+    float4 l[16];
+    const float *P = A.L + F.loff + (int64_t)(j0 + rw) * F.ld + kB * j + c;
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    l[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < jb && rw + k < r1) l[k] = __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld));
+    for (int k = 0; k < 16; k++)
+      l[k] = rw + k < jb ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    ok = wait_flag(A, S, f_y(A, slot0 + j), 1);
+    if (!ok) break;
+    if (threadIdx.x < kB) S.sy[threadIdx.x] = ldcg(A.b + F.first + kB * j + threadIdx.x);
+    __syncthreads();
+    const float4 y4 = *reinterpret_cast<const float4 *>(S.sy + c);
+    float p[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) p[k] = l[k].x * y4.x + l[k].y * y4.y + l[k].z * y4.z + l[k].w * y4.w;
+    racc += rows16_reduce(S, p);
+    __syncthreads();  // S.sy is refilled for the next block
   }
-  float *dst = nullptr;
-  float old = 0.f;
-  if (lane < 16 && r < r1) {
-    dst = r < F.ncol ? A.a + F.first + r : A.t + dp.toff[tk.front] + r - F.ncol;
-    old = ldcg(dst);
-  }
-  if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jb ? ldcg(A.b + F.first + j + threadIdx.x) : 0.f;
   __syncthreads();
-  if (rw < r1) {
+  if (ok && lane < 16 && rw + lane < jb) S.sv[rw + lane] -= racc;
+  __syncthreads();
+  const bool got = wait_dinv(A, S);  // the staged copy always lands before S.di is reused
+  if (ok && got) {
+    diag_fwd(A, S, F, j0);
+    signal(f_y(A, slot0 + i));
+  }
+}
+
+// Forward, rows r0 .. r0 + nr below front s: the children's entries plus
+// L_rj y_j over every block j of the front, into the front's update vector.
+__device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+  const DevPlan &dp = A.dp;
+  const int r0 = tk.a, nr = min(kRC, F.nrow - r0), nb = (F.ncol + kB - 1) / kB;
+  const int slot0 = dp.fs_first_slot[tk.front];
+  bool ok = wait_children(A, S, F);
+  if (ok && threadIdx.x < nr) S.xs[threadIdx.x] = gather_children(A, F, F.ncol + r0 + threadIdx.x);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
+  float racc = 0.f;
+  for (int j = 0; j < nb && ok; j++) {
+    const int jbj = min(kB, F.ncol - kB * j);
+    float4 l[16];
+    const float *P = A.L + F.loff + (int64_t)(F.ncol + r0 + rw) * F.ld + kB * j + c;
+#pragma unroll
+    for (int k = 0; k < 16; k++)
+      l[k] = (c < jbj && rw + k < nr) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    ok = wait_flag(A, S, f_y(A, slot0 + j), 1);
+    if (!ok) break;
+    if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jbj ? ldcg(A.b + F.first + kB * j + threadIdx.x) : 0.f;
+    __syncthreads();
     const float4 y4 = *reinterpret_cast<const float4 *>(S.sy + c);
     float p[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-      float4 v = l[k];
-      if (c + 1 >= jb) v.y = 0.f;
-      if (c + 2 >= jb) v.z = 0.f;
-      if (c + 3 >= jb) v.w = 0.f;
+      float4 v = l[k];  // padding columns past ncol never enter the sums
+      if (c + 1 >= jbj) v.y = 0.f;
+      if (c + 2 >= jbj) v.z = 0.f;
+      if (c + 3 >= jbj) v.w = 0.f;
       p[k] = v.x * y4.x + v.y * y4.y + v.z * y4.z + v.w * y4.w;
     }
-    const float s = rows16_reduce(S, p);
-    if (dst) {
-      if (r < F.ncol) {
-        const float y = old - s;
-        *dst = y;
-        if (owner) S.sv[r - i0] = y;
-      } else {
-        *dst = old + s;
-      }
-    }
-  }
-  if (owner) {
-    const int jbn = min(kB, F.ncol - (j + kB));
+    racc += rows16_reduce(S, p);
     __syncthreads();
-    if (threadIdx.x < kB && threadIdx.x >= jbn) S.sv[threadIdx.x] = 0.f;
-    if (wait_dinv(A, S)) diag_fwd(A, S, F, j + kB);
+  }
+  __syncthreads();
+  if (ok) {
+    if (lane < 16 && rw + lane < nr) A.t[dp.toff[tk.front] + r0 + rw + lane] = S.xs[rw + lane] + racc;
+    signal(f_tvec(A, tk.front));
   }
 }
 
-// backward, rows below the front, one 128-row chunk: partial sums
-// part[slot][c] = sum_r L[ncol + r0 + r, c0 + c] x[row r]; thread (g, q):
-// columns 4q .. 4q + 3, rows 16g .. 16g + 15 (loads issued before x arrives)
+// Backward, rows r0 .. r0 + nr below front s and column block cb: partial sums
+// part[c] = sum_r L[ncol + r0 + r, c0 + c] x[row r] once the parent front (and
+// so every ancestor holding those rows) is solved; thread (g, q): columns 4q ..
+// 4q + 3, rows 16g .. 16g + 15 (loads issued before the wait).
 __device__ void bwd_part(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
   const DevPlan &dp = A.dp;
-  const int c0 = tk.a, r0 = tk.b, nr = min(kRC, F.nrow - r0);
+  const int cb = tk.a, r0 = tk.b, c0 = kB * cb, nr = min(kRC, F.nrow - r0);
+  const int nbl = (F.nrow + kRC - 1) / kRC;
   const int q = threadIdx.x % 32, g = threadIdx.x / 32, c = c0 + 4 * q;
   float4 l[16];
   const float *P = A.L + F.loff + (int64_t)(F.ncol + r0 + 16 * g) * F.ld + c;
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    l[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < F.ncol && 16 * g + k < nr) l[k] = __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld));
-  }
+  for (int k = 0; k < 16; k++)
+    l[k] = (c < F.ncol && 16 * g + k < nr) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (F.parent >= 0 &&
+      !wait_flag(A, S, f_front(A, F.parent), (dp.fronts[F.parent].ncol + kB - 1) / kB))
+    return;
   if (threadIdx.x < nr) S.xs[threadIdx.x] = ldcg(A.x + dp.sri[F.rows_off + r0 + threadIdx.x]);
   __syncthreads();
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -363,75 +412,85 @@ __device__ void bwd_part(const PsArgs &A, PsShared &S, const Task &tk, const Fro
   S.red4[g][q] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
-    float4 s = S.red4[0][q];
+    float4 sm = S.red4[0][q];
 #pragma unroll
     for (int h = 1; h < kT / 32; h++) {
       const float4 o = S.red4[h][q];
-      s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
+      sm.x += o.x; sm.y += o.y; sm.z += o.z; sm.w += o.w;
     }
-    reinterpret_cast<float4 *>(A.part + (int64_t)tk.c * kB)[q] = s;
+    const int64_t row = dp.ps_pbase[tk.front] + (int64_t)cb * nbl + r0 / kRC;
+    reinterpret_cast<float4 *>(A.part + row * kB)[q] = sm;
   }
+  signal(f_part(A, dp.fs_first_slot[tk.front] + cb));
 }
 
-// backward, rows below the front, final: b[cols] -= the partial sums of the
-// block in chunk order; the last block of the front is then solved. Padding
-// columns past ncol carry products of padding entries and are never stored.
-__device__ void bwd_rows(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
-  const int c0 = tk.a, nparts = (F.nrow + kRC - 1) / kRC;
-  const bool owner = tk.b >= 0;
-  if (owner && threadIdx.x == 0) stage_dinv(A, S, tk.b, min(kB, F.ncol - c0));
-  if (threadIdx.x < kB) {
-    const int c = c0 + threadIdx.x;
-    float s = 0.f;
-    for (int k = 0; k < nparts; k++) s += ldcg(A.part + (int64_t)(tk.c + k) * kB + threadIdx.x);
-    if (c < F.ncol) {
-      const float v = ldcg(A.b + F.first + c) - s;
-      A.b[F.first + c] = v;
-      S.sv[threadIdx.x] = v;
+// Backward, column block cb of front s: the partial sums in chunk order, then
+// L[block i, block cb]^T x_i for i > cb as each x_i is published, then
+// x_cb = L_cc^{-T} (.) with the staged inverse.
+__device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+  const DevPlan &dp = A.dp;
+  const int cb = tk.a, c0 = kB * cb, jb = min(kB, F.ncol - c0), nb = (F.ncol + kB - 1) / kB;
+  const int nbl = (F.nrow + kRC - 1) / kRC, slot0 = dp.fs_first_slot[tk.front];
+  if (threadIdx.x == 0) stage_dinv(A, S, slot0 + cb, jb);
+  bool ok = true;
+  if (nbl > 0) ok = wait_flag(A, S, f_part(A, slot0 + cb), nbl);  // implies the parent is done
+  else if (F.parent >= 0)
+    ok = wait_flag(A, S, f_front(A, F.parent), (dp.fronts[F.parent].ncol + kB - 1) / kB);
+  if (ok && threadIdx.x < kB) {
+    float v = 0.f;
+    if (threadIdx.x < jb) {
+      const float *pp = A.part + (dp.ps_pbase[tk.front] + (int64_t)cb * nbl) * kB + threadIdx.x;
+      float ps = 0.f;
+      for (int k = 0; k < nbl; k++) ps += ldcg(pp + (int64_t)k * kB);
+      v = ldcg(A.b + F.first + c0 + threadIdx.x) - ps;
     }
+    S.sv[threadIdx.x] = v;
   }
-  if (owner && wait_dinv(A, S)) diag_bwd(A, S, F, c0);
-}
-
-// backward step of block row j: columns [c0, c0 + 128) left of the block take
-// L[j:j+jb, c]^T x_j (loads issued before x_j arrives); the chunk holding the
-// block left of j then solves it
-__device__ void bwd_step(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
-  const int c0 = tk.a, j = tk.b, jb = min(kB, F.ncol - j);
-  const bool owner = tk.c >= 0;
-  if (owner && threadIdx.x == 0) stage_dinv(A, S, tk.c, kB);
   const int q = threadIdx.x % 32, g = threadIdx.x / 32, c = c0 + 4 * q;
-  const float *P = A.L + F.loff + (int64_t)(j + 16 * g) * F.ld + c;
-  float4 l[16];
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    l[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (16 * g + k < jb) l[k] = __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld));
-  }
-  float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
-  float *bp = A.b + F.first + c;
-  if (threadIdx.x < 32) old = make_float4(ldcg(bp), ldcg(bp + 1), ldcg(bp + 2), ldcg(bp + 3));
-  if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jb ? ldcg(A.x + F.first + j + threadIdx.x) : 0.f;
-  __syncthreads();
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = nb - 1; i > cb && ok; i--) {
+    const int jbi = min(kB, F.ncol - kB * i);
+    float4 l[16];
+    const float *P = A.L + F.loff + (int64_t)(kB * i + 16 * g) * F.ld + c;
 #pragma unroll
-  for (int k = 0; k < 16; k++) acc = fma4(l[k], S.sy[16 * g + k], acc);
+    for (int k = 0; k < 16; k++)
+      l[k] = (c < F.ncol && 16 * g + k < jbi) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    ok = wait_flag(A, S, f_x(A, slot0 + i), 1);
+    if (!ok) break;
+    if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jbi ? ldcg(A.x + F.first + kB * i + threadIdx.x) : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc = fma4(l[k], S.sy[16 * g + k], acc);
+    __syncthreads();
+  }
+  __syncthreads();
   S.red4[g][q] = acc;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    float4 s = S.red4[0][q];
+  if (ok && threadIdx.x < 32) {
+    float4 sm = S.red4[0][q];
 #pragma unroll
     for (int h = 1; h < kT / 32; h++) {
       const float4 o = S.red4[h][q];
-      s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
+      sm.x += o.x; sm.y += o.y; sm.z += o.z; sm.w += o.w;
     }
-    const float v0 = old.x - s.x, v1 = old.y - s.y, v2 = old.z - s.z, v3 = old.w - s.w;
-    bp[0] = v0; bp[1] = v1; bp[2] = v2; bp[3] = v3;
-    S.sv[4 * q] = v0; S.sv[4 * q + 1] = v1; S.sv[4 * q + 2] = v2; S.sv[4 * q + 3] = v3;
+    const float d[4] = {sm.x, sm.y, sm.z, sm.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (4 * q + k < jb) S.sv[4 * q + k] -= d[k];
   }
-  if (owner && wait_dinv(A, S)) diag_bwd(A, S, F, j - kB);
+  __syncthreads();
+  const bool got = wait_dinv(A, S);
+  if (ok && got) {
+    diag_bwd(A, S, F, c0);
+    signal(f_x(A, slot0 + cb));
+    if (threadIdx.x == 0)  // the release of signal() above already ordered the writes
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(f_front(A, tk.front)) : "memory");
+  }
 }
 
+// Persistent solve: every CTA takes tasks in plan order from the global ticket
+// counter until the range is exhausted.
 __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
   extern __shared__ __align__(128) unsigned char ps_smem[];
   PsShared &S = *reinterpret_cast<PsShared *>(ps_smem);
@@ -439,42 +498,32 @@ __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.parity = 0;
+    S.tk = (int)atomicAdd(f_ticket(A), 1u) + A.q0;
   }
   __syncthreads();
-  for (int p = A.p0; p < A.p1; p++) {
-    const SolvePhase ph = A.dp.ps_phases[p];
-    int q = ph.begin + blockIdx.x;
-    Task tk{};
-    FrontInfo F{};
-    if (q < ph.end) {
-      tk = A.dp.ps_tasks[q];
-      F = A.dp.fronts[tk.front];
+  bool first = true;
+  while (true) {
+    const int qt = S.tk;
+    if (qt >= A.q1) break;
+    if (first && (int)blockIdx.x == A.withhold) break;  // the task is abandoned
+    first = false;
+    unsigned nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(f_ticket(A), 1u);  // the next ticket, fetched early
+    const Task tk = A.dp.ps_tasks[qt];
+    const FrontInfo F = A.dp.fronts[tk.front];
+    switch (tk.c) {
+      case WS_FWD_DIAG: fwd_diag(A, S, tk, F); break;
+      case WS_FWD_BELOW: fwd_below(A, S, tk, F); break;
+      case WS_BWD_PART: bwd_part(A, S, tk, F); break;
+      default: bwd_diag(A, S, tk, F); break;
     }
-    while (q < ph.end) {
-      const int qn = q + gridDim.x;  // prefetch the next task of this CTA
-      Task tkn{};
-      FrontInfo Fn{};
-      if (qn < ph.end) {
-        tkn = A.dp.ps_tasks[qn];
-        Fn = A.dp.fronts[tkn.front];
-      }
-      switch (ph.kind) {
-        case PS_FWD_GATHER: fwd_gather(A, S, tk, F); break;
-        case PS_FWD_STEP: fwd_step(A, S, tk, F); break;
-        case PS_BWD_PART: bwd_part(A, S, tk, F); break;
-        case PS_BWD_ROWS: bwd_rows(A, S, tk, F); break;
-        default: bwd_step(A, S, tk, F); break;
-      }
-      __syncthreads();  // shared scratch is reused by the next task
-      tk = tkn;
-      F = Fn;
-      q = qn;
-    }
-    if (p + 1 < A.p1 && !grid_barrier(A.bar, A.status, A.spins, A.withhold)) return;
+    __syncthreads();  // every thread has read S.tk; the shared scratch is free
+    if (threadIdx.x == 0) S.tk = (int)nxt + A.q0;
+    __syncthreads();
   }
 }
 
-int psolve_grid(int max_tasks) {
+int psolve_grid(int ntask) {
   static int per_device[64] = {0};
   int dev = 0;
   ck(cudaGetDevice(&dev), "cudaGetDevice");
@@ -489,7 +538,7 @@ int psolve_grid(int max_tasks) {
        "occupancy");
     g = std::max(1, sms * std::min(nb, 2));
   }
-  return std::max(1, std::min(g, max_tasks));
+  return std::max(1, std::min(g, ntask));
 }
 
 }  // namespace
@@ -509,20 +558,19 @@ void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Din
 }
 
 void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv, float *a,
-                   float *b, float *x, float *t, float *part, unsigned *bar, int32_t *status, bool fwd,
-                   bool bwd, cudaStream_t st, unsigned test_spins, int test_withhold) {
-  const int32_t p0 = fwd ? 0 : plan.ps_fwd_phases;
-  const int32_t p1 = bwd ? (int32_t)plan.ps_phases.size() : plan.ps_fwd_phases;
-  if (p1 <= p0) return;
-  const int grid = psolve_grid(plan.ps_max_tasks);
-  if (grid > kMaxGrid) throw std::runtime_error("persistent solve: grid above the barrier's capacity");
-  PsArgs A{dp, L, Dinv, a, b, x, t, part, p0, p1, bar, status,
-           test_spins ? test_spins : kBarrierSpins, test_withhold};
-  void *args[] = {&A};
+                   float *b, float *x, float *t, float *part, unsigned *flags, int32_t *status,
+                   bool fwd, bool bwd, cudaStream_t st, unsigned test_spins, int test_withhold) {
+  const int32_t q0 = fwd ? 0 : plan.ps_fwd_tasks;
+  const int32_t q1 = bwd ? (int32_t)plan.ps_tasks.size() : plan.ps_fwd_tasks;
+  if (q1 <= q0) return;
+  ck(cudaMemsetAsync(flags, 0, (size_t)plan.ps_flag_words * sizeof(unsigned), st), "solve flags");
+  const int grid = psolve_grid(q1 - q0);
+  PsArgs A{dp, L, Dinv, a, b, x, t, part, q0, q1, flags, status,
+           test_spins ? test_spins : kBarrierSpins, test_withhold,
+           (int32_t)plan.fs_dinv_off.size(), (int32_t)plan.fronts.size()};
   note_launch();
-  ck(cudaLaunchCooperativeKernel((const void *)psolve_kernel, dim3(grid), dim3(kT), args,
-                                 sizeof(PsShared), st),
-     "cooperative solve launch");
+  psolve_kernel<<<grid, kT, sizeof(PsShared), st>>>(A);
+  ck(cudaGetLastError(), "solve launch");
 }
 
 }  // namespace gipm

@@ -43,15 +43,14 @@ void launch_sign(const DevPlan &dp, V *y, cudaStream_t st);
 cudaError_t preload_level_solve();
 
 // Persistent FP32 solve: inverses of the 128-wide diagonal blocks (after each
-// FP32 factorisation), then x = L^{-T} L^{-1} a in one cooperative launch, with
-// b the forward result and t the update vectors. fwd/bwd select the sweeps:
-// forward only maps a to b = L^{-1} a; backward only maps b to x = L^{-T} b
-// (b is overwritten). part: plan.ps_part_entries floats of scratch. bar:
-// kPsBarrierWords zeroed words of grid-barrier state; a barrier that waits too
-// long sets status[ST_SOLVE_TIMEOUT] and the launch returns. test_spins (0:
-// the default of seconds) bounds each barrier wait; test_withhold >= 0 makes
-// that CTA leave at its first barrier (tests of the bounded wait).
-constexpr int kPsBarrierWords = 32 + 1024;
+// FP32 factorisation), then x = L^{-T} L^{-1} a in one launch, with b the
+// forward result and t the update vectors. fwd/bwd select the sweeps: forward
+// only maps a to b = L^{-1} a; backward only maps b to x = L^{-T} b. part:
+// plan.ps_part_entries floats of scratch; flags: plan.ps_flag_words words
+// (zeroed by the launch). A wait that runs out sets status[ST_SOLVE_TIMEOUT]
+// and the launch drains. test_spins (0: the default of seconds) bounds each
+// wait; test_withhold >= 0 makes that CTA abandon its first task (tests of
+// the bounded wait).
 void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Dinv, cudaStream_t st);
 void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv, float *a,
                    float *b, float *x, float *t, float *part, unsigned *bar, int32_t *status, bool fwd,

@@ -761,153 +761,113 @@ namespace gipm {
 // publishes the solved block), backward tasks over the columns [0, j) in
 // chunks of 256 (at least one, which publishes the solved block).
 void build_fused_solve(Plan &pl) {
-  constexpr int B = 128, GR = 256, RC = 128;
+  constexpr int B = 128, RC = 128;
+  const int32_t nfr = (int32_t)pl.fronts.size();
   pl.fs_inv.clear();
   pl.fs_dinv_off.clear();
   pl.fs_dinv_entries = 0;
   pl.ps_tasks.clear();
-  pl.ps_phases.clear();
-  std::vector<std::vector<int32_t>> slot_of(pl.fronts.size());
-  pl.fs_first_slot.assign(pl.fronts.size(), 0);
-  for (size_t s = 0; s < pl.fronts.size(); s++) {
+  pl.fs_first_slot.assign(nfr, 0);
+  for (int32_t s = 0; s < nfr; s++) {
     const FrontInfo &F = pl.fronts[s];
     pl.fs_first_slot[s] = (int32_t)pl.fs_dinv_off.size();
     for (int32_t j = 0; j < F.ncol; j += B) {
       const int32_t jb = std::min(B, F.ncol - j);
       const int32_t slot = (int32_t)pl.fs_dinv_off.size();
-      slot_of[s].push_back(slot);
       pl.fs_dinv_off.push_back(pl.fs_dinv_entries);
       pl.fs_dinv_entries += (int64_t)jb * round_up(jb, 4);  // keeps every slot 16-byte aligned
-      pl.fs_inv.push_back({(int32_t)s, j, slot, 0});
+      pl.fs_inv.push_back({s, j, slot, 0});
     }
   }
   pl.fs_dinv_entries = std::max<int64_t>(pl.fs_dinv_entries, 4);
-  auto close_phase = [&](int32_t begin, int32_t kind) {
-    const int32_t end = (int32_t)pl.ps_tasks.size();
-    if (end > begin) pl.ps_phases.push_back({begin, end, kind, 0});
-  };
   auto nblk = [&](int32_t s) { return (pl.fronts[s].ncol + B - 1) / B; };
-  // forward sweep, leaves to root: gather the children's update vectors (the
-  // chunk holding block 0 then solves it), then per block step update the rows
-  // below the block (the chunk holding the next block then solves that one)
+  // forward, leaves to root, level by level: the diagonal chunks of every front
+  // of the level (ascending), then the chunks of rows below the fronts
   for (const LevelPlan &LP : pl.levels) {
-    int32_t b0 = (int32_t)pl.ps_tasks.size();
-    int32_t steps = 0;
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = pl.level_fronts[t];
-      const FrontInfo &F = pl.fronts[s];
-      steps = std::max(steps, nblk(s));
-      for (int32_t p0 = 0; p0 < F.ncol + F.nrow; p0 += GR)
-        pl.ps_tasks.push_back({s, p0, (p0 == 0 && F.ncol > 0) ? slot_of[s][0] : -1, 0});
+      for (int32_t i = 0; i < nblk(s); i++) pl.ps_tasks.push_back({s, i, 0, WS_FWD_DIAG});
     }
-    close_phase(b0, PS_FWD_GATHER);
-    for (int32_t k = 0; k < steps; k++) {
-      b0 = (int32_t)pl.ps_tasks.size();
-      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
-        const int32_t s = pl.level_fronts[t];
-        const FrontInfo &F = pl.fronts[s];
-        if (k >= nblk(s)) continue;
-        const int32_t j = k * B, jb = std::min(B, F.ncol - j);
-        for (int32_t i0 = j + jb; i0 < F.ncol + F.nrow; i0 += B) {
-          const bool owner = i0 == j + B && i0 < F.ncol;
-          pl.ps_tasks.push_back({s, i0, j, owner ? slot_of[s][k + 1] : -1});
-        }
-      }
-      close_phase(b0, PS_FWD_STEP);
+    for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+      const int32_t s = pl.level_fronts[t];
+      for (int32_t r0 = 0; r0 < pl.fronts[s].nrow; r0 += RC) pl.ps_tasks.push_back({s, r0, 0, WS_FWD_BELOW});
     }
   }
-  pl.ps_fwd_phases = (int32_t)pl.ps_phases.size();
-  // backward sweep, root to leaves: the columns of each front take the rows
-  // below it (partial sums over 128-row chunks, then a fixed-order sum per
-  // column block; the last block is then solved), then per block step, last to
-  // first, the columns left of the block take it (the block just left of it is
-  // then solved)
-  pl.ps_part_entries = B;
+  pl.ps_fwd_tasks = (int32_t)pl.ps_tasks.size();
+  // backward, root to leaves, level by level: the partial sums over the rows
+  // below every front of the level, then the column blocks (last to first)
+  pl.ps_pbase.assign(nfr, 0);
+  int64_t prow = 0;
+  for (int32_t s = 0; s < nfr; s++) {
+    pl.ps_pbase[s] = prow;
+    prow += (int64_t)nblk(s) * ((pl.fronts[s].nrow + RC - 1) / RC);
+  }
+  pl.ps_part_entries = std::max<int64_t>(prow, 1) * B;
   for (int32_t li = (int32_t)pl.levels.size() - 1; li >= 0; li--) {
     const LevelPlan &LP = pl.levels[li];
-    int32_t b0 = (int32_t)pl.ps_tasks.size();
-    int32_t steps = 0, nparts = 0;
-    std::vector<Task> fin;
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = pl.level_fronts[t];
-      const FrontInfo &F = pl.fronts[s];
-      steps = std::max(steps, nblk(s));
-      for (int32_t c0 = 0; c0 < F.ncol; c0 += B) {
-        fin.push_back({s, c0, c0 + B >= F.ncol ? slot_of[s][c0 / B] : -1, nparts});
-        for (int32_t r0 = 0; r0 < F.nrow; r0 += RC) pl.ps_tasks.push_back({s, c0, r0, nparts++});
-      }
+      for (int32_t cb = 0; cb < nblk(s); cb++)
+        for (int32_t r0 = 0; r0 < pl.fronts[s].nrow; r0 += RC) pl.ps_tasks.push_back({s, cb, r0, WS_BWD_PART});
     }
-    pl.ps_part_entries = std::max<int64_t>(pl.ps_part_entries, (int64_t)nparts * B);
-    close_phase(b0, PS_BWD_PART);
-    b0 = (int32_t)pl.ps_tasks.size();
-    pl.ps_tasks.insert(pl.ps_tasks.end(), fin.begin(), fin.end());
-    close_phase(b0, PS_BWD_ROWS);
-    for (int32_t k = steps - 1; k >= 1; k--) {
-      b0 = (int32_t)pl.ps_tasks.size();
-      for (int32_t t = LP.front_b; t < LP.front_e; t++) {
-        const int32_t s = pl.level_fronts[t];
-        if (k >= nblk(s)) continue;
-        const int32_t j = k * B;
-        for (int32_t c0 = 0; c0 < j; c0 += B)
-          pl.ps_tasks.push_back({s, c0, j, c0 == j - B ? slot_of[s][k - 1] : -1});
-      }
-      close_phase(b0, PS_BWD_STEP);
+    for (int32_t t = LP.front_b; t < LP.front_e; t++) {
+      const int32_t s = pl.level_fronts[t];
+      for (int32_t cb = nblk(s) - 1; cb >= 0; cb--) pl.ps_tasks.push_back({s, cb, 0, WS_BWD_DIAG});
     }
   }
-  pl.ps_max_tasks = 0;
-  for (const SolvePhase &ph : pl.ps_phases) pl.ps_max_tasks = std::max(pl.ps_max_tasks, ph.end - ph.begin);
-  // range checks (the kernels mask only the chunk edges)
+  const int64_t nslot = (int64_t)pl.fs_dinv_off.size();
+  pl.ps_flag_words = 32 + 3 * nslot + 2 * (int64_t)nfr;
+  // range checks (the kernel masks only the chunk edges), and the order every
+  // wait of the kernel relies on: a task waits only for earlier tasks
   auto need = [](bool ok, const char *w) {
     if (!ok) throw std::runtime_error(std::string("solve plan check failed: ") + w);
   };
-  const int32_t nslot = (int32_t)pl.fs_dinv_off.size();
-  auto slot_ok = [&](const Task &t, int32_t j, int32_t slot) {
+  for (const Task &t : pl.fs_inv)
+    need(t.b >= 0 && t.b < nslot && t.b == pl.fs_first_slot[t.front] + t.a / B &&
+             pl.fs_dinv_off[t.b] % 4 == 0,
+         "inverse task");
+  std::vector<int32_t> fwd_diag_seen(nfr, 0), fwd_below_seen(nfr, 0), bwd_diag_seen(nfr, 0);
+  std::vector<int32_t> bwd_part_seen(nfr, 0), level_of(nfr, -1);
+  for (size_t li = 0; li < pl.levels.size(); li++)
+    for (int32_t t = pl.levels[li].front_b; t < pl.levels[li].front_e; t++) level_of[pl.level_fronts[t]] = (int32_t)li;
+  auto nbelow = [&](int32_t s) { return (pl.fronts[s].nrow + RC - 1) / RC; };
+  for (size_t q = 0; q < pl.ps_tasks.size(); q++) {
+    const Task &t = pl.ps_tasks[q];
+    need(t.front >= 0 && t.front < nfr, "task front");
     const FrontInfo &F = pl.fronts[t.front];
-    if (slot < 0) return true;
-    const int32_t jb = std::min(B, F.ncol - j);
-    return j >= 0 && j < F.ncol && j % B == 0 && slot < nslot && slot == slot_of[t.front][j / B] &&
-           pl.fs_dinv_off[slot] + (int64_t)jb * round_up(jb, 4) <= pl.fs_dinv_entries &&
-           pl.fs_dinv_off[slot] % 4 == 0;
-  };
-  for (const Task &t : pl.fs_inv) need(slot_ok(t, t.a, t.b) && t.b >= 0, "inverse task");
-  for (size_t p = 0; p < pl.ps_phases.size(); p++) {
-    const SolvePhase &ph = pl.ps_phases[p];
-    need(ph.begin >= 0 && ph.begin < ph.end && ph.end <= (int32_t)pl.ps_tasks.size(), "phase range");
-    need((p < (size_t)pl.ps_fwd_phases) == (ph.kind <= PS_FWD_STEP) && ph.kind >= 0 &&
-             ph.kind <= PS_BWD_STEP,
-         "phase order");
-    for (int32_t q = ph.begin; q < ph.end; q++) {
-      const Task &t = pl.ps_tasks[q];
-      need(t.front >= 0 && t.front < (int32_t)pl.fronts.size(), "task front");
-      const FrontInfo &F = pl.fronts[t.front];
-      const int32_t nf = F.ncol + F.nrow;
-      need(F.ld % 4 == 0 && F.loff % 4 == 0, "panel alignment");
-      switch (ph.kind) {
-        case PS_FWD_GATHER:
-          need(t.a >= 0 && t.a < nf && t.a % GR == 0 && slot_ok(t, 0, t.b), "forward gather task");
-          break;
-        case PS_FWD_STEP:
-          need(t.b >= 0 && t.b < F.ncol && t.b % B == 0 && t.a >= t.b + std::min(B, F.ncol - t.b) &&
-                   t.a < nf && slot_ok(t, t.b + B, t.c) && (t.c < 0 || t.a == t.b + B),
-               "forward step task");
-          break;
-        case PS_BWD_PART:
-          need(t.a >= 0 && t.a < F.ncol && t.a % B == 0 && t.b >= 0 && t.b < F.nrow && t.b % RC == 0 &&
-                   t.c >= 0 && ((int64_t)t.c + 1) * B <= pl.ps_part_entries,
-               "backward partial task");
-          break;
-        case PS_BWD_ROWS:
-          need(t.a >= 0 && t.a < F.ncol && t.a % B == 0 && slot_ok(t, t.a, t.b) && t.c >= 0 &&
-                   ((int64_t)t.c + (F.nrow + RC - 1) / RC) * B <= pl.ps_part_entries,
-               "backward rows task");
-          break;
-        default:
-          need(t.b >= B && t.b < F.ncol && t.b % B == 0 && t.a >= 0 && t.a + B <= t.b &&
-                   t.a % B == 0 && slot_ok(t, t.b - B, t.c) && (t.c < 0 || t.a == t.b - B),
-               "backward step task");
-      }
+    need(F.ld % 4 == 0 && F.loff % 4 == 0, "panel alignment");
+    need((q < (size_t)pl.ps_fwd_tasks) == (t.c <= WS_FWD_BELOW) && t.c >= 0 && t.c <= WS_BWD_DIAG,
+         "task order");
+    const int32_t s = t.front;
+    switch (t.c) {
+      case WS_FWD_DIAG:
+        need(t.a == fwd_diag_seen[s]++ && t.a < nblk(s), "forward diagonal task");
+        for (int32_t ci = F.child_begin; ci < F.child_end; ci++)  // children complete before
+          need(fwd_below_seen[pl.children[ci]] == nbelow(pl.children[ci]), "forward child order");
+        break;
+      case WS_FWD_BELOW:
+        need(t.a == RC * fwd_below_seen[s]++ && t.a < F.nrow && fwd_diag_seen[s] == nblk(s),
+             "forward below task");
+        for (int32_t ci = F.child_begin; ci < F.child_end; ci++)
+          need(fwd_below_seen[pl.children[ci]] == nbelow(pl.children[ci]), "forward child order");
+        break;
+      case WS_BWD_PART:
+        need(t.a >= 0 && t.a < nblk(s) && t.b >= 0 && t.b < F.nrow && t.b % RC == 0 &&
+                 (F.parent < 0 || bwd_diag_seen[F.parent] == nblk(F.parent)) &&
+                 pl.ps_pbase[s] + (int64_t)t.a * nbelow(s) + t.b / RC < pl.ps_part_entries / B,
+             "backward partial task");
+        bwd_part_seen[s]++;
+        break;
+      default:
+        need(t.a == nblk(s) - 1 - bwd_diag_seen[s]++ && t.a >= 0 &&
+                 bwd_part_seen[s] == nblk(s) * nbelow(s) &&
+                 (F.parent < 0 || bwd_diag_seen[F.parent] == nblk(F.parent)),
+             "backward diagonal task");
     }
   }
+  for (int32_t s = 0; s < nfr; s++)
+    need(fwd_diag_seen[s] == nblk(s) && fwd_below_seen[s] == nbelow(s) && bwd_diag_seen[s] == nblk(s),
+         "every block solved once per sweep");
 }
 
 }  // namespace gipm

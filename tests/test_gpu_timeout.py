@@ -1,11 +1,10 @@
-"""The bounded wait of the persistent solve's grid barrier runs out, and the
-context recovers.
+"""The bounded waits of the persistent solve run out, and the context recovers.
 
-A CTA that leaves the launch without arriving at the barrier (the test hook
-of kkt_test_solve_timeout) stands in for a CTA that never gets there; with a
-short poll limit every other CTA gives up, records the timeout and returns.
-Nothing faults or hangs: the kernel ends, kkt_solve reports IPM_ERR_TIMEOUT,
-the host resets the barrier state, and the next solve is correct."""
+A CTA that abandons the first task it takes (the test hook of
+kkt_test_solve_timeout) stands in for a result that never arrives; with a
+short poll limit the tasks waiting for it give up, record the timeout, and the
+launch drains. Nothing faults or hangs: the kernel ends, kkt_solve reports
+IPM_ERR_TIMEOUT, and the next solves are correct."""
 import numpy as np
 import pytest
 
@@ -52,9 +51,9 @@ def test_solve_barrier_timeout_is_reported_and_recovered(withheld):
     st = ctx._lib.kkt_solve(ctx.handle, gb._dp(dev(b)), gb._dp(x), 1, gb.IPM_REFINE_NONE, None)
     torch.cuda.synchronize()  # the launch ended: the stream drains
     assert st == IPM_ERR_TIMEOUT
-    assert "grid barrier" in ctx._lib.ipm_last_error(ctx.handle).decode()
+    assert "bounded wait" in ctx._lib.ipm_last_error(ctx.handle).decode()
 
-    # the barrier state was reset: the next solves run to the FP64 target
+    # the next solves run to the FP64 target
     for _ in range(2):
         si = ctx.kkt_solve(dev(b), x, gb.IPM_REFINE_IR)
         r = np.abs(K @ x.cpu().numpy() - b).max() / np.abs(b).max()
