@@ -461,14 +461,15 @@ def run_ours(args, ws, rank):
     if prec == 4:
         roof["products_frac"] = 3 * achieved / peak
 
-    # HBM rooflines of the solve and the assembly kernels (bytes per SURVEY's
-    # definitions: solve 2 x 4 B per stored L entry + vectors; assembly 8 B per
-    # J value, per D entry, per product operand pair read once and per K entry)
+    # HBM rooflines of the solve and the assembly kernels, algorithmic bytes:
+    # solve 2 x 4 B per entry of L (nnz(L): both sweeps read the factor once)
+    # plus its three FP32 vectors; assembly 8 B per J value, per D entry and
+    # per K entry written
     hbm = pk["hbm_gbs"]
     extra_roof = {}
     if prec != 0:
         t_sol = ctx.kkt_time_kernel(1, reps=5)
-        sb = 2 * 4 * info.factor_entries + 4 * 3 * lp.n
+        sb = 2 * 4 * info.nnz_l + 4 * 3 * lp.n  # both sweeps read L once; a, b, x
         extra_roof["psolve_kernel"] = {"bound": "hbm", "achieved": sb / (t_sol * 1e-3) / 1e9,
                                        "peak": hbm, "unit": "GB/s",
                                        "frac": sb / (t_sol * 1e-3) / 1e9 / hbm,

@@ -606,6 +606,37 @@ ipm_status form_direction(ipm_ctx *c, const double *jvals, const double *cc, con
     F.pad_rows(c->sysx, c->vt);            // [y; 0]
     V.jtv(jvals, c->vt, 1.0, nullptr, nullptr, c->rtil, c->vrd);  // r~ + A^T y
     F.div(c->vrd, c->hdiag, -1.0, dx);
+    // Recovering d_x through H^{-1} amplifies the reduced solve's error where
+    // H is near delta_p (H^{-1} up to 1 / delta_p), so (d_x, y) is refined on
+    // the augmented system (4), FP64 residuals, with the factor of (6):
+    //   K6 dy = A H^{-1} r1 - r2,  dx = H^{-1} (r1 - A^T dy).
+    double *sN = c->scal + 56;  // scalars: |r1|, |r2|, |r~|, |q|
+    V.absmax(n, c->rtil, sN + 2);
+    V.absmax(m, c->qv, sN + 3);
+    for (int r = 0; r < 3 && stt == IPM_OK; r++) {
+      F.pad_rows(c->sysx, c->vt);
+      V.jtv(jvals, c->vt, 1.0, nullptr, nullptr, nullptr, c->vp);  // A^T y
+      F.aug_res_n(c->rtil, c->hdiag, dx, c->vp, c->vc);            // r1
+      V.jv(jvals, dx, c->vjx);                                     // A d_x
+      F.aug_res_m(c->qv, c->vjx, c->vD, c->sysx, c->vtA);          // r2
+      V.absmax(n, c->vc, sN + 0);
+      V.absmax(m, c->vtA, sN + 1);
+      double h4[4];
+      CK(cudaMemcpyAsync(h4, sN, sizeof(h4), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (!(std::max(h4[0], h4[1]) > c->opts.ir_tol * std::max(h4[2], h4[3]))) break;
+      F.div(c->vc, c->hdiag, 1.0, c->vz);                 // H^{-1} r1
+      V.jv(jvals, c->vz, c->vjx);                         // A H^{-1} r1
+      F.lincomb(m, 1.0, c->vjx, -1.0, c->vtA, c->sysb);   // - r2
+      ipm_solve_info s2{};
+      stt = do_solve(c->sys, c->sysb, c->sysb, refine, &s2);  // dy (in place)
+      F.pad_rows(c->sysb, c->vt);
+      V.jtv(jvals, c->vt, -1.0, nullptr, nullptr, c->vc, c->vp);  // r1 - A^T dy
+      F.div(c->vp, c->hdiag, 1.0, c->vz);                         // dx correction
+      F.lincomb(n, 1.0, dx, 1.0, c->vz, dx);
+      F.lincomb(m, 1.0, c->sysx, 1.0, c->sysb, c->sysx);
+      c->refine_steps++;
+    }
   } else {
     if (refine == IPM_REFINE_PCG) refine = IPM_REFINE_IR;  // indefinite: no conjugate gradients
     F.neg_concat(c->rtil, n, c->qv, m, c->sysb);  // -[r~; q]
@@ -729,6 +760,8 @@ ipm_status analyze_form(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info
   const int64_t nnz = (int64_t)P.ji.size();
   if (c->opts.learned != 0 || c->opts.learned_probes > 0)
     throw Fail{IPM_ERR_UNSUPPORTED, "the learned correction uses the primal condensed formulation"};
+  if (c->form == IPM_FORM_DUAL && m == 0)
+    throw Fail{IPM_ERR_ARG, "the dual condensed formulation needs general rows (m >= 1)"};
   c->wdiag_h.assign(n, -1);
   if (!P.wp.empty())
     for (int32_t j = 0; j < n; j++)

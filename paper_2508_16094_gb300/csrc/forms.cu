@@ -94,7 +94,42 @@ __global__ void pad_rows_kernel(int64_t mt, int32_t m, const double *__restrict_
   FORM_STRIDE(i, mt) out[i] = i < m ? y[i] : 0.0;
 }
 
+// Residual of the augmented system (4) at (d_x, y): the first n rows and the
+// last m rows.
+__global__ void aug_res_n_kernel(int64_t n, const double *__restrict__ rt, const double *__restrict__ h,
+                                 const double *__restrict__ dx, const double *__restrict__ aty,
+                                 double *__restrict__ r1) {
+  FORM_STRIDE(j, n) r1[j] = -rt[j] - h[j] * dx[j] - aty[j];
+}
+__global__ void aug_res_m_kernel(int64_t m, const double *__restrict__ q, const double *__restrict__ adx,
+                                 const double *__restrict__ D, const double *__restrict__ y,
+                                 double *__restrict__ r2) {
+  FORM_STRIDE(i, m) r2[i] = -q[i] - adx[i] + y[i] / D[i];
+}
+__global__ void lincomb_kernel(int64_t k, double a, const double *__restrict__ x, double b,
+                               const double *__restrict__ y, double *__restrict__ out) {
+  FORM_STRIDE(i, k) out[i] = a * x[i] + b * y[i];
+}
+
 }  // namespace
+
+void FormOps::aug_res_n(const double *rt, const double *h, const double *dx, const double *aty,
+                        double *r1) const {
+  note_launch();
+  aug_res_n_kernel<<<blocks_for(dp.n), 256, 0, st>>>(dp.n, rt, h, dx, aty, r1);
+}
+void FormOps::aug_res_m(const double *q, const double *adx, const double *D, const double *y,
+                        double *r2) const {
+  if (dp.m <= 0) return;
+  note_launch();
+  aug_res_m_kernel<<<blocks_for(dp.m), 256, 0, st>>>(dp.m, q, adx, D, y, r2);
+}
+void FormOps::lincomb(int64_t k, double a, const double *x, double b, const double *y,
+                      double *out) const {
+  if (k <= 0) return;
+  note_launch();
+  lincomb_kernel<<<blocks_for(k), 256, 0, st>>>(k, a, x, b, y, out);
+}
 
 void FormOps::hdiag(const double *wv, const int64_t *wdiag, const double *D, double delta_p,
                     double *h) const {

@@ -47,6 +47,15 @@ struct FormOps {
   void neg_concat(const double *a, int64_t na, const double *b, int64_t nb, double *out) const;
   // out (m_tot) = [y (m); 0]
   void pad_rows(const double *y, double *out) const;
+  // residual of (4) at (d_x, y): r1 = -r~ - H d_x - A^T y (n), r2 = -q - A d_x +
+  // D_G^{-1} y (m)
+  void aug_res_n(const double *rt, const double *h, const double *dx, const double *aty,
+                 double *r1) const;
+  void aug_res_m(const double *q, const double *adx, const double *D, const double *y,
+                 double *r2) const;
+  // out = a x + b y (k entries; out may alias x or y)
+  void lincomb(int64_t k, double a, const double *x, double b, const double *y,
+               double *out) const;
 };
 
 }  // namespace gipm

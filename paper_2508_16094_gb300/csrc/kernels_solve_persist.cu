@@ -80,6 +80,7 @@ struct PsArgs {
   unsigned spins;    // polls before a wait gives up
   int32_t withhold;  // test of the bounded wait: this CTA abandons its first task (-1: none)
   int32_t nslot, nfr;
+  int32_t fwd_here;  // the forward sweep runs in this launch: backward blocks wait for their y
 };
 
 constexpr int kRC = 128;  // rows below a front per task
@@ -432,9 +433,11 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
   const int cb = tk.a, c0 = kB * cb, jb = min(kB, F.ncol - c0), nb = (F.ncol + kB - 1) / kB;
   const int nbl = (F.nrow + kRC - 1) / kRC, slot0 = dp.fs_first_slot[tk.front];
   if (threadIdx.x == 0) stage_dinv(A, S, slot0 + cb, jb);
-  bool ok = true;
-  if (nbl > 0) ok = wait_flag(A, S, f_part(A, slot0 + cb), nbl);  // implies the parent is done
-  else if (F.parent >= 0)
+  // b of this block is the forward result: published by this launch's forward
+  // task of the block, or complete before a backward-only launch
+  bool ok = !A.fwd_here || wait_flag(A, S, f_y(A, slot0 + cb), 1);
+  if (ok && nbl > 0) ok = wait_flag(A, S, f_part(A, slot0 + cb), nbl);  // implies the parent is done
+  else if (ok && F.parent >= 0)
     ok = wait_flag(A, S, f_front(A, F.parent), (dp.fronts[F.parent].ncol + kB - 1) / kB);
   if (ok && threadIdx.x < kB) {
     float v = 0.f;
@@ -567,7 +570,7 @@ void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const fl
   const int grid = psolve_grid(q1 - q0);
   PsArgs A{dp, L, Dinv, a, b, x, t, part, q0, q1, flags, status,
            test_spins ? test_spins : kBarrierSpins, test_withhold,
-           (int32_t)plan.fs_dinv_off.size(), (int32_t)plan.fronts.size()};
+           (int32_t)plan.fs_dinv_off.size(), (int32_t)plan.fronts.size(), fwd && bwd ? 1 : 0};
   note_launch();
   psolve_kernel<<<grid, kT, sizeof(PsShared), st>>>(A);
   ck(cudaGetLastError(), "solve launch");
