@@ -313,6 +313,45 @@ IPM_API ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t
                                     double *d_kkt, int32_t *d_iters, int32_t *d_status,
                                     ipm_mpc_config *best, float *h_ms);
 
+/* --- symbolic analysis of batched patterns on the GPU ----------------------
+ * Sec. 2 computes the fill-reducing ordering and the analysis once, serially,
+ * and reuses them; Sec. 6 names batch solvers for many problems of one family
+ * as the open direction. For a batch of constraint-Jacobian patterns J_b
+ * (m_b x n_b, CSR; the problems' K_b = J_b^T J_b + I, a W that is diagonal
+ * adds nothing) with orderings P_b, one launch computes per pattern, in the
+ * final numbering (P_b followed by the postorder, children and roots visited
+ * in ascending order, as kkt_analyze numbers columns): the elimination tree,
+ * the column counts of L (diagonal included) and the starts of the
+ * fundamental supernodes. The results are exactly those of kkt_analyze on the
+ * same pattern (the tree, postorder and counts are unique). */
+typedef struct {
+  int32_t count;            /* patterns */
+  const int32_t *h_n;       /* host: variables of each pattern */
+  const int32_t *h_m;       /* host: rows of J of each pattern */
+  const int64_t *h_nnz;     /* host: entries of J of each pattern */
+  const int64_t *d_rowptr;  /* device: m_b + 1 offsets into d_col per pattern (absolute
+                               offsets), patterns one after the other */
+  const int32_t *d_col;     /* device: column indices in [0, n_b) (any order within a row) */
+  const int32_t *d_perm;    /* device: orderings new -> old, n_b each, one after the other;
+                               NULL for the identity */
+} ipm_pattern_batch;
+
+/* Workspace bytes of ipm_symbolic_batched (host only). Errors: IPM_ERR_ARG. */
+IPM_API ipm_status ipm_symbolic_batched_workspace(const ipm_pattern_batch *b, size_t *bytes);
+/* One launch on `stream` over every pattern (one CTA per pattern); returns
+ * after the stream has finished it. Outputs (device, n_b entries per pattern,
+ * one after the other): d_post (final numbering new -> original index),
+ * d_parent (elimination tree in the final numbering, -1 at roots), d_colcount,
+ * d_sstart (1 where a fundamental supernode starts). d_work: at least the
+ * workspace bytes, 256-byte aligned, owned by the caller.
+ * Errors: IPM_ERR_NOMEM for a small or misaligned workspace; IPM_ERR_ARG if a
+ * pattern has a column index or an ordering entry out of range (or a repeated
+ * ordering entry): *h_bad (may be NULL) receives the first such pattern, -1
+ * if none; IPM_ERR_CUDA if a CUDA call fails. */
+IPM_API ipm_status ipm_symbolic_batched(const ipm_pattern_batch *b, void *d_work, size_t bytes,
+                                        void *stream, int32_t *d_post, int32_t *d_parent,
+                                        int32_t *d_colcount, int32_t *d_sstart, int32_t *h_bad);
+
 /* --- grid NLP (the nonlinear problem class of Sec. 2, equalities as pairs) ---
  * min 1/2 ||u - u_t||^2 + alpha/2 ||v||^2 over u, v on an nx x nx grid of
  * interior points (spacing h = 1/(nx+1), u = 0 on the boundary) subject to
@@ -445,7 +484,9 @@ IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);
  * Eq. (5) on the inputs of the last kkt_assemble (rewrites the same K);
  * 1: the persistent FP32 triangular solve (both sweeps) with the current
  * FP32-storage factor; 2: the FP64 level-scheduled triangular solve with the
- * current FP64 factor. The solves overwrite the context's solve scratch only.
+ * current FP64 factor; 3 and 4: the persistent FP32 solve's forward sweep
+ * alone and its backward sweep alone. The solves overwrite the context's
+ * solve scratch only.
  * Errors: IPM_ERR_STATE if the data the kernel needs is missing. */
 IPM_API ipm_status kkt_time_kernel(ipm_ctx *ctx, int32_t kernel, int32_t reps, double *ms);
 

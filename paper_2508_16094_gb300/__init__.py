@@ -33,7 +33,8 @@ EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze
             "kkt_solve_noalloc_capacity", "ipm_mpc_workspace_bytes", "ipm_mpc_prepare",
             "ipm_solve_batched", "ipm_mpc_autotune", "ipm_learned_param_count",
             "ipm_learned_weights", "ipm_learned_sample", "ipm_learned_loss_grad",
-            "ipm_learned_train", "ipm_grid_nlp_sizes", "ipm_grid_nlp_pattern",
+            "ipm_learned_train", "ipm_symbolic_batched_workspace", "ipm_symbolic_batched",
+            "ipm_grid_nlp_sizes", "ipm_grid_nlp_pattern",
             "ipm_solve_grid_nlp", "ipm_last_error", "ipm_destroy"]
 
 
@@ -132,6 +133,8 @@ def load() -> C.CDLL:
         "ipm_mpc_prepare": (I32, [P, P, C.c_size_t, P]),
         "ipm_solve_batched": (I32, [P, P, P, C.c_size_t, D, I32, P, P, P, P, P, P]),
         "ipm_mpc_autotune": (I32, [P, P, C.c_size_t, D, I32, P, P, P, P, P, P, P, P]),
+        "ipm_symbolic_batched_workspace": (I32, [P, P]),
+        "ipm_symbolic_batched": (I32, [P, P, C.c_size_t, P, P, P, P, P, P]),
         "ipm_grid_nlp_sizes": (I32, [P, P, P, P]),
         "ipm_grid_nlp_pattern": (I32, [P] * 7),
         "ipm_solve_grid_nlp": (I32, [P] * 7),
@@ -424,6 +427,57 @@ class BatchedMPC:
             C.c_void_p(self.stream) if self.stream else None, _dp(self.z), _dp(self.obj),
             _dp(self.kkt), _dp(self.iters), _dp(self.status), C.byref(cfg), ms))
         return cfg, list(ms)
+
+
+# --- symbolic analysis of batched patterns on the GPU ----------------------------
+class PatternBatch(C.Structure):
+    _fields_ = [("count", C.c_int32), ("h_n", C.c_void_p), ("h_m", C.c_void_p),
+                ("h_nnz", C.c_void_p), ("d_rowptr", C.c_void_p), ("d_col", C.c_void_p),
+                ("d_perm", C.c_void_p)]
+
+
+def symbolic_batched(patterns, perms=None, stream=None):
+    """ipm_symbolic_batched over a list of (n, rowptr, col) host patterns (CSR
+    of J) and optional orderings (new -> old). Returns (post, parent, colcount,
+    sstart) as lists of numpy arrays, one per pattern, and the launch's device
+    time in milliseconds (CUDA events around the call)."""
+    import torch
+    lib = load()
+    cnt = len(patterns)
+    h_n = np.array([p[0] for p in patterns], np.int32)
+    h_m = np.array([len(p[1]) - 1 for p in patterns], np.int32)
+    h_nnz = np.array([int(p[1][-1]) for p in patterns], np.int64)
+    offs = np.concatenate([[0], np.cumsum(h_nnz)])[:-1]
+    rp = np.concatenate([np.asarray(p[1], np.int64) + o for p, o in zip(patterns, offs)])
+    cl = np.concatenate([np.asarray(p[2], np.int32) for p in patterns]) if h_nnz.sum() else np.zeros(1, np.int32)
+    d_rp = torch.as_tensor(rp, device="cuda")
+    d_cl = torch.as_tensor(cl, device="cuda")
+    d_pm = None
+    if perms is not None:
+        d_pm = torch.as_tensor(np.concatenate([np.asarray(q, np.int32) for q in perms]), device="cuda")
+    b = PatternBatch(cnt, _hp(h_n), _hp(h_m), _hp(h_nnz), C.c_void_p(d_rp.data_ptr()),
+                     C.c_void_p(d_cl.data_ptr()), C.c_void_p(d_pm.data_ptr()) if d_pm is not None else None)
+    nb = C.c_size_t()
+    st = lib.ipm_symbolic_batched_workspace(C.byref(b), C.byref(nb))
+    if st != 0:
+        raise IpmError(st, "symbolic batch workspace")
+    work = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+    wptr = (work.data_ptr() + 255) // 256 * 256
+    N = int(h_n.sum())
+    outs = [torch.empty(max(N, 1), dtype=torch.int32, device="cuda") for _ in range(4)]
+    bad = C.c_int32(-1)
+    s = torch.cuda.current_stream() if stream is None else stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    st = lib.ipm_symbolic_batched(C.byref(b), C.c_void_p(wptr), nb.value, C.c_void_p(s.cuda_stream),
+                                  *[C.c_void_p(t.data_ptr()) for t in outs], C.byref(bad))
+    e1.record(s)
+    torch.cuda.synchronize()
+    if st != 0:
+        raise IpmError(st, f"symbolic batch: pattern {bad.value}")
+    host = [t.cpu().numpy() for t in outs]
+    cuts = np.cumsum(h_n)[:-1]
+    return [np.split(h, cuts) for h in host], e0.elapsed_time(e1)
 
 
 # --- grid NLP -----------------------------------------------------------------

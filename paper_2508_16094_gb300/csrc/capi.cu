@@ -1399,13 +1399,14 @@ ipm_status kkt_time_kernel(ipm_ctx *c, int32_t kernel, int32_t reps, double *ms)
   return guarded(c, [&]() -> ipm_status {
     if (kernel == 0 && c->state < 3) throw Fail{IPM_ERR_STATE, "nothing assembled"};
     if (kernel != 0 && c->state < 4) throw Fail{IPM_ERR_STATE, "no factor"};
-    if (kernel == 1 && c->factor_prec == IPM_FP64)
+    if ((kernel == 1 || kernel == 3 || kernel == 4) && c->factor_prec == IPM_FP64)
       throw Fail{IPM_ERR_STATE, "the persistent solve needs an FP32-storage factor"};
     if (kernel == 2 && c->factor_prec != IPM_FP64)
       throw Fail{IPM_ERR_STATE, "the level solve is timed on an FP64 factor"};
-    if (kernel < 0 || kernel > 2) throw Fail{IPM_ERR_ARG, "unknown kernel id"};
+    if (kernel < 0 || kernel > 4) throw Fail{IPM_ERR_ARG, "unknown kernel id"};
     // the solves' work does not depend on the values: zero right-hand sides
-    if (kernel == 1) CK(cudaMemsetAsync(c->fsa, 0, c->P.n * sizeof(float), c->st));
+    if (kernel == 1 || kernel == 3) CK(cudaMemsetAsync(c->fsa, 0, c->P.n * sizeof(float), c->st));
+    if (kernel == 4) CK(cudaMemsetAsync(c->fsb, 0, c->P.n * sizeof(float), c->st));
     if (kernel == 2) CK(cudaMemsetAsync(c->yv, 0, c->P.n * sizeof(double), c->st));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1416,6 +1417,8 @@ ipm_status kkt_time_kernel(ipm_ctx *c, int32_t kernel, int32_t reps, double *ms)
         launch_assemble(c->dp, c->cur_jvals, c->cur_D, c->cur_wvals, c->cur_delta_p, c->kval, c->st);
       else if (kernel == 1)
         launch_fp32_solve(c, 0);
+      else if (kernel == 3 || kernel == 4)
+        launch_fp32_solve(c, kernel == 3 ? 1 : 2);
       else
         launch_solve<double, double>(c->dp, c->plan, (const double *)c->L, c->yv, c->tv, c->st);
     }
@@ -1426,7 +1429,7 @@ ipm_status kkt_time_kernel(ipm_ctx *c, int32_t kernel, int32_t reps, double *ms)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
-    if (kernel == 1) check_solve_barrier(c);
+    if (kernel == 1 || kernel >= 3) check_solve_barrier(c);
     *ms = (double)t / reps;
     return IPM_OK;
   });
