@@ -21,8 +21,14 @@ them for nonconvex problems; both sides implement exactly these):
   * step: tau = max(0.99, 1 - mu); one common alpha = min(alpha_s, alpha_lambda)
     from the fraction to the boundary; backtracking (halving, at most 10 times)
     on phi = f - mu sum ln s + nu ||g(x) - s||_1 with the Armijo factor 1e-4
-    along D phi = grad f . dx - mu sum ds / s - nu ||g - s||_1, allowing for
-    rounding 10 eps |phi| (a direction with D phi >= 0 takes the full alpha);
+    along the one-sided directional derivative D phi = grad f . dx - mu sum
+    ds / s + nu D||g - s||_1, where D||g - s||_1 = sum sign(g - s) (J dx - ds)
+    over rows with g != s plus |J dx - ds| over the others (the step solves
+    the regularised system (3), which leaves delta_d d_lambda in g - s: on the
+    rows of an equality pair, whose slacks both stay positive, that is all
+    of g - s, so the linear model's -||g - s||_1 would promise a decrease no
+    step can give), allowing for rounding 10 eps |phi| (a direction with
+    D phi >= 0 takes the full alpha);
     nu = max(nu, ||lambda + d_lambda||_inf + 1);
   * inertia: a non-positive pivot raises delta_p by 100x (from 1e-8) and refactors.
 """
@@ -159,7 +165,10 @@ def ipm_grid_nlp(S, P, tol=1e-6, max_iter=200, delta_p=1e-8, delta_d=1e-8, ir_ma
         nu = max(nu, float(np.max(np.abs(lam + dl))) + 1.0)
         viol = float(np.sum(np.abs(g - s)))
         phi0 = f - mu * float(np.sum(np.log(s))) + nu * viol
-        dphi = float(grad @ dx) - mu * float(np.sum(ds / s)) - nu * viol
+        jdx = g_full(P, dx, _jv_times(P, jv, dx)) + _bound_offsets(P)
+        r, t = g - s, jdx - ds
+        dtheta = float(np.sum(np.where(r > 0, t, np.where(r < 0, -t, np.abs(t)))))
+        dphi = float(grad @ dx) - mu * float(np.sum(ds / s)) + nu * dtheta
         if dphi < 0.0:
             for _ in range(MAX_HALVINGS):
                 xt, st = x + alpha * dx, s + alpha * ds
@@ -172,6 +181,23 @@ def ipm_grid_nlp(S, P, tol=1e-6, max_iter=200, delta_p=1e-8, delta_d=1e-8, ir_ma
     f, h, jv, grad = evaluate(P, x)
     return dict(objective=f, kkt=kkt, iterations=it, status=status, mu=np.array(mus), x=x, s=s,
                 lam=lam)
+
+
+def _jv_times(P, jv, d):
+    """J_h d (the linearisation of h, pattern order values)."""
+    rows = np.repeat(np.arange(P.m), np.diff(P.rowptr))
+    out = np.zeros(P.m)
+    np.add.at(out, rows, jv * d[P.col])
+    return out[:P.N * P.N]
+
+
+def _bound_offsets(P):
+    """g_full is affine in x on the bound rows: g_full(P, d, J_h d) carries the
+    bounds' constants, which the linear term J d must not; this undoes them."""
+    NN = P.N * P.N
+    if not P.v_bounded:
+        return np.zeros(P.m)
+    return np.concatenate([np.zeros(P.m), np.full(NN, P.v_lo), np.full(NN, -P.v_hi)])
 
 
 def h_rows(h):

@@ -1712,8 +1712,15 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       nu = std::max(nu, dt[2] + 1.0);
       nlp_merit_terms(mt, s, c->vg, terms, c->partial, c->st);
       d2h(terms, mt2, 2);
+      // derivative of nu ||g - s||_1 along the step actually solved: the
+      // regularised system (3) leaves O(delta_d d_lambda) in g - s, which is
+      // all there is on the rows of an equality pair (both slacks stay
+      // positive), so -nu ||g - s||_1 would promise a decrease no step can give
+      double dth;
+      nlp_dtheta(mt, c->vg, s, c->vjd, c->vds, terms + 2, c->partial, c->st);
+      d2h(terms + 2, &dth, 1);
       const double phi0 = f - mu * mt2[0] + nu * mt2[1];
-      const double dphi = dt[0] - mu * dt[1] - nu * mt2[1];
+      const double dphi = dt[0] - mu * dt[1] + nu * dth;
       if (dphi < 0.0) {
         for (int hv = 0; hv < 10; hv++) {
           nlp_trial(n, mt, x, c->vdx, s, c->vds, alpha, xt, stv, c->st);

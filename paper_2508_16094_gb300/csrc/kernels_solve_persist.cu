@@ -127,6 +127,7 @@ struct PsShared {
   uint32_t parity;              // its phase
   int tk;                       // this CTA's current task
   int ok;                       // verdict of the last wait
+  int ready;                    // blocks of the running chain known to be published
 };
 
 // Thread 0: start the bulk copy of a diagonal-block inverse into S.di.
@@ -272,6 +273,29 @@ __device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsig
   return S.ok != 0;
 }
 
+// Wait for block j of a chain whose flags are published in order (each
+// producer acquired its predecessor's flag before releasing its own), with
+// `last` the last block this task needs: one acquire of the last flag makes
+// every earlier block visible, so a task behind the chain waits once and then
+// streams its blocks without polling. S.ready holds the highest block known
+// published (reset by the caller to -1).
+__device__ bool wait_chain(const PsArgs &A, PsShared &S, const unsigned *flags, int j, int last,
+                           int step) {
+  if ((step > 0 ? j <= S.ready : j >= S.ready) && S.ready >= 0) return true;
+  __syncthreads();  // every thread has read S.ready and the previous verdict
+  if (threadIdx.x == 0) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flags + last) : "memory");
+    if (v >= 1u) S.ready = last;
+  }
+  __syncthreads();
+  if (S.ready == last) return true;
+  if (!wait_flag(A, S, flags + j, 1)) return false;
+  if (threadIdx.x == 0) S.ready = j;
+  __syncthreads();
+  return true;
+}
+
 // After this CTA's writes: make them visible, then count one more on *w (release).
 __device__ void signal(unsigned *w) {
   __syncthreads();
@@ -316,6 +340,8 @@ __device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
                             : 0.f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
   float racc = 0.f;
+  if (threadIdx.x == 0) S.ready = -1;
+  __syncthreads();  // no thread reads the previous task's value
   for (int j = 0; j < i && ok; j++) {
     float4 l[16];
     const float *P = A.L + F.loff + (int64_t)(j0 + rw) * F.ld + kB * j + c;
@@ -323,7 +349,7 @@ __device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
     for (int k = 0; k < 16; k++)
       l[k] = rw + k < jb ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
                          : make_float4(0.f, 0.f, 0.f, 0.f);
-    ok = wait_flag(A, S, f_y(A, slot0 + j), 1);
+    ok = wait_chain(A, S, f_y(A, slot0), j, i - 1, 1);
     if (!ok) break;
     if (threadIdx.x < kB) S.sy[threadIdx.x] = ldcg(A.b + F.first + kB * j + threadIdx.x);
     __syncthreads();
@@ -354,6 +380,8 @@ __device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const Fr
   if (ok && threadIdx.x < nr) S.xs[threadIdx.x] = gather_children(A, F, F.ncol + r0 + threadIdx.x);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
   float racc = 0.f;
+  if (threadIdx.x == 0) S.ready = -1;
+  __syncthreads();  // no thread reads the previous task's value
   for (int j = 0; j < nb && ok; j++) {
     const int jbj = min(kB, F.ncol - kB * j);
     float4 l[16];
@@ -362,7 +390,7 @@ __device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const Fr
     for (int k = 0; k < 16; k++)
       l[k] = (c < jbj && rw + k < nr) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-    ok = wait_flag(A, S, f_y(A, slot0 + j), 1);
+    ok = wait_chain(A, S, f_y(A, slot0), j, nb - 1, 1);
     if (!ok) break;
     if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jbj ? ldcg(A.b + F.first + kB * j + threadIdx.x) : 0.f;
     __syncthreads();
@@ -451,6 +479,8 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
   }
   const int q = threadIdx.x % 32, g = threadIdx.x / 32, c = c0 + 4 * q;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (threadIdx.x == 0) S.ready = -1;
+  __syncthreads();  // no thread reads the previous task's value
   for (int i = nb - 1; i > cb && ok; i--) {
     const int jbi = min(kB, F.ncol - kB * i);
     float4 l[16];
@@ -459,7 +489,7 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
     for (int k = 0; k < 16; k++)
       l[k] = (c < F.ncol && 16 * g + k < jbi) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-    ok = wait_flag(A, S, f_x(A, slot0 + i), 1);
+    ok = wait_chain(A, S, f_x(A, slot0), i, cb + 1, -1);
     if (!ok) break;
     if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jbi ? ldcg(A.x + F.first + kB * i + threadIdx.x) : 0.f;
     __syncthreads();

@@ -113,6 +113,20 @@ __global__ void merit_kernel(int64_t mt, const double *__restrict__ s, const dou
   block_store<2>(v, mx, partial);
 }
 
+// One-sided derivative of sum |g - s| along t = J dx - ds: sign(g - s) t where
+// g != s, |t| where g == s.
+__global__ void dtheta_kernel(int64_t mt, const double *__restrict__ g, const double *__restrict__ s,
+                              const double *__restrict__ jdx, const double *__restrict__ ds,
+                              double *partial) {
+  double v[1] = {0.0};
+  NLP_GRID(k, mt) {
+    const double r = g[k] - s[k], t = jdx[k] - ds[k];
+    v[0] += r > 0.0 ? t : (r < 0.0 ? -t : fabs(t));
+  }
+  const int mx[1] = {0};
+  block_store<1>(v, mx, partial);
+}
+
 __global__ void dir_kernel(int64_t n, int64_t mt, const double *__restrict__ grad,
                            const double *__restrict__ dx, const double *__restrict__ s,
                            const double *__restrict__ ds, const double *__restrict__ lam,
@@ -203,6 +217,14 @@ void nlp_dir_terms(int64_t n, int64_t mt, const double *grad, const double *dx, 
   dir_kernel<<<kNlpRedBlocks, kT, 0, st>>>(n, mt, grad, dx, s, ds, lam, dl, partial);
   note_launch();
   final_kernel<3><<<1, 32, 0, st>>>(partial, kNlpRedBlocks, make_int3(0, 0, 1), out);
+}
+
+void nlp_dtheta(int64_t mt, const double *g, const double *s, const double *jdx, const double *ds,
+                double *out, double *partial, cudaStream_t st) {
+  note_launch();
+  dtheta_kernel<<<kNlpRedBlocks, kT, 0, st>>>(mt, g, s, jdx, ds, partial);
+  note_launch();
+  final_kernel<1><<<1, 32, 0, st>>>(partial, kNlpRedBlocks, make_int3(0, 0, 0), out);
 }
 
 void nlp_barrier_err(int64_t mt, const double *s, const double *lam, double mu, double *out,

@@ -35,6 +35,10 @@ void nlp_merit_terms(int64_t mt, const double *s, const double *g, double *out, 
 void nlp_dir_terms(int64_t n, int64_t mt, const double *grad, const double *dx, const double *s,
                    const double *ds, const double *lam, const double *dl, double *out,
                    double *partial, cudaStream_t st);
+// out[0] = one-sided derivative of sum |g - s| along (J dx - ds): sum of
+// sign(g - s) (J dx - ds) over rows with g != s plus |J dx - ds| over the rest
+void nlp_dtheta(int64_t mt, const double *g, const double *s, const double *jdx, const double *ds,
+                double *out, double *partial, cudaStream_t st);
 // out[0] = max |s lambda - mu|
 void nlp_barrier_err(int64_t mt, const double *s, const double *lam, double mu, double *out,
                      double *partial, cudaStream_t st);
