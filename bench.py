@@ -228,7 +228,7 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
     return out
 
 
-def nlp_measure(N: int, max_iter: int = 60):
+def nlp_measure(N: int, max_iter: int = 150):
     """Grid NLP (512^2 grid, cubic PDE constraint as inequality pairs, -1 <= v <= 1):
     the FP64 factor against the split-TF32 factor with FP64 fallback, from the
     cold start, at most max_iter iterations towards a 1e-6 KKT residual."""
