@@ -14,7 +14,9 @@
 // i for i < 12, lower and upper bound of variable i). Rows of L blocks move
 // between lanes with width-16 shuffles. Instances come from an atomic queue
 // ordered by horizon (longest first) so a persistent grid stays balanced.
-// The FP32 variant factors and solves in FP32 and refines in FP64.
+// The FP32 variant assembles, factors and solves in FP32 and refines in FP64
+// on a residual evaluated matrix-free from A, B and D (J v, scaled by D, J^T),
+// so the FP64 pipe only carries the refinement.
 #include <cfloat>
 #include <cmath>
 #include <stdexcept>
@@ -65,6 +67,7 @@ struct Inst {
   double *z, *dz, *rhs, *tv, *corr, *res;  // 16 per stage
   double *s, *lam, *D, *g, *w, *ds, *dl;   // NSLOT per stage
   double *Kd, *Ko;                         // 256 per stage (row-major)
+  TF *Kf, *Kof;                            // the same storage as K blocks of type TF
   TF *Ld, *Lo;                             // 256 per stage (row-major)
 };
 
@@ -95,6 +98,8 @@ __device__ Inst<TF> make_inst(const MpcArgs &a, int inst) {
   I.dl = I.ds + T * NSLOT;
   I.Kd = I.dl + T * NSLOT;
   I.Ko = I.Kd + T * 256;
+  I.Kf = reinterpret_cast<TF *>(I.Kd);
+  I.Kof = reinterpret_cast<TF *>(I.Ko);
   I.Ld = reinterpret_cast<TF *>(I.Ko + T * 256);
   I.Lo = I.Ld + T * 256;
   return I;
@@ -160,7 +165,8 @@ __device__ void jt_rows(const Group &G, const Inst<TF> &I, const double *rowv, d
   }
 }
 
-// K = W + J^T D J + diag(bounds) + delta_p I as diagonal (Kd) and sub-diagonal (Ko) blocks.
+// K = W + J^T D J + diag(bounds) + delta_p I as diagonal (Kf) and sub-diagonal
+// (Kof) blocks, computed and stored in the arithmetic TF.
 template <typename TF>
 __device__ void assemble(const Group &G, const Inst<TF> &I, double delta_p) {
   const int i = G.lane;
@@ -168,37 +174,38 @@ __device__ void assemble(const Group &G, const Inst<TF> &I, double delta_p) {
     const double *Dk = I.D + k * NSLOT;
     const double *Bk = I.B + (int64_t)k * NX * NU;
     const double *Ak = I.A + (int64_t)k * NX * NX;
-    double *kd = I.Kd + (int64_t)k * 256 + i * NS;
+    TF *kd = I.Kf + (int64_t)k * 256 + i * NS;
+    TF dsum[NX];  // D of the dynamics pair of each row of stage k
+    for (int r = 0; r < NX; r++) dsum[r] = TF(Dk[r] + Dk[16 + r]);
     for (int c = 0; c < NS; c++) {
-      double v = 0.0;
+      TF v = TF(0);
       if (i < NU && c < NU) {
-        for (int r = 0; r < NX; r++) v += Bk[r * NU + i] * (Dk[r] + Dk[16 + r]) * Bk[r * NU + c];
+        for (int r = 0; r < NX; r++) v += TF(Bk[r * NU + i]) * dsum[r] * TF(Bk[r * NU + c]);
       } else if (i < NU) {
-        v = -Bk[(c - NU) * NU + i] * (Dk[c - NU] + Dk[16 + c - NU]);
+        v = -TF(Bk[(c - NU) * NU + i]) * dsum[c - NU];
       } else if (c < NU) {
-        v = -(Dk[i - NU] + Dk[16 + i - NU]) * Bk[(i - NU) * NU + c];
+        v = -dsum[i - NU] * TF(Bk[(i - NU) * NU + c]);
       } else if (i == c) {
-        v = Dk[i - NU] + Dk[16 + i - NU];
+        v = dsum[i - NU];
       }
       if (i >= NU && c >= NU && k + 1 < I.T) {
         const double *A1 = I.A + (int64_t)(k + 1) * NX * NX;
         const double *D1 = I.D + (k + 1) * NSLOT;
         for (int r = 0; r < NX; r++)
-          v += A1[r * NX + i - NU] * (D1[r] + D1[16 + r]) * A1[r * NX + c - NU];
+          v += TF(A1[r * NX + i - NU]) * TF(D1[r] + D1[16 + r]) * TF(A1[r * NX + c - NU]);
       }
-      if (i == c) v += wdiag(I.Q, I.R, i) + delta_p + Dk[32 + i] + Dk[48 + i];
+      if (i == c) v += TF(wdiag(I.Q, I.R, i) + delta_p + Dk[32 + i] + Dk[48 + i]);
       kd[c] = v;
     }
     if (k > 0) {
-      double *ko = I.Ko + (int64_t)k * 256 + i * NS;
+      TF *ko = I.Kof + (int64_t)k * 256 + i * NS;
       for (int c = 0; c < NS; c++) {
-        double v = 0.0;
+        TF v = TF(0);
         if (c >= NU) {
           if (i < NU) {
-            for (int r = 0; r < NX; r++)
-              v += Bk[r * NU + i] * (Dk[r] + Dk[16 + r]) * Ak[r * NX + c - NU];
+            for (int r = 0; r < NX; r++) v += TF(Bk[r * NU + i]) * dsum[r] * TF(Ak[r * NX + c - NU]);
           } else {
-            v = -(Dk[i - NU] + Dk[16 + i - NU]) * Ak[(i - NU) * NX + c - NU];
+            v = -dsum[i - NU] * TF(Ak[(i - NU) * NX + c - NU]);
           }
         }
         ko[c] = v;
@@ -222,7 +229,7 @@ __device__ bool factor(const Group &G, const Inst<TF> &I, int &perturbed) {
   bool ok = true;
   for (int k = 0; k < I.T; k++) {
     TF srow[NS];
-    const double *kd = I.Kd + (int64_t)k * 256 + i * NS;
+    const TF *kd = I.Kf + (int64_t)k * 256 + i * NS;
 #pragma unroll
     for (int c = 0; c < NS; c++) srow[c] = TF(kd[c]);
     if (k > 0) {  // S = Kd - Lo Lo^T
@@ -257,7 +264,7 @@ __device__ bool factor(const Group &G, const Inst<TF> &I, int &perturbed) {
 #pragma unroll
     for (int c = 0; c < NS; c++) ld[c] = c <= i ? srow[c] : TF(0);
     if (k + 1 < I.T) {  // L_{k+1,k} = Ko_{k+1} L_kk^{-T}: row i by forward substitution
-      const double *ko = I.Ko + (int64_t)(k + 1) * 256 + i * NS;
+      const TF *ko = I.Kof + (int64_t)(k + 1) * 256 + i * NS;
       TF x[NS];
 #pragma unroll
       for (int c = 0; c < NS; c++) {
@@ -328,24 +335,22 @@ __device__ void block_solve(const Group &G, const Inst<TF> &I, const double *in,
   }
 }
 
-// res = in - K v (FP64, from the assembled blocks)
-template <typename TF>
-__device__ void kresid(const Group &G, const Inst<TF> &I, const double *in, const double *v,
-                       double *res) {
+// res = in - K v in FP64, matrix-free: K v = W v + J^T D J v + delta_p v over
+// every row of g (dynamics pairs and bounds). rows: NSLOT per stage of scratch.
+__device__ void kresid(const Group &G, const Inst<double> &I, const double *in, const double *v,
+                       double *res, double *rows, double delta_p) {
   const int i = G.lane;
+  eval_rows<double>(G, I, v, nullptr, 0.0, 0.0, rows, false);  // J v
+  for (int k = 0; k < I.T; k++)
+    for (int kind = 0; kind < 4; kind++) {
+      const int q = k * NSLOT + kind * 16 + i;
+      rows[q] = row_valid(kind, i) ? I.D[q] * rows[q] : 0.0;
+    }
+  __syncwarp(G.mask);
+  jt_rows<double>(G, I, rows, 1.0, v, nullptr, res);  // J^T D J v + W v
   for (int k = 0; k < I.T; k++) {
-    const double *kd = I.Kd + (int64_t)k * 256 + i * NS;
-    double a = 0.0;
-    for (int c = 0; c < NS; c++) a += kd[c] * v[k * NS + c];
-    if (k > 0) {
-      const double *ko = I.Ko + (int64_t)k * 256 + i * NS;
-      for (int c = 0; c < NS; c++) a += ko[c] * v[(k - 1) * NS + c];
-    }
-    if (k + 1 < I.T) {
-      const double *ko1 = I.Ko + (int64_t)(k + 1) * 256;
-      for (int m = 0; m < NS; m++) a += ko1[m * NS + i] * v[(k + 1) * NS + m];
-    }
-    res[k * NS + i] = in[k * NS + i] - a;
+    const int q = k * NS + i;
+    res[q] = in[q] - res[q] - delta_p * v[q];
   }
 }
 
@@ -362,7 +367,8 @@ __device__ bool kfactor(const Group &G, const Views &V, bool f32, int &perturbed
 // Solve K out = in. FP64 factor: one block solve. FP32 factor: block solve plus
 // FP64 refinement on the residual in - K out; returns false when that does not
 // reach 1e-8 relative (the caller then refactors this instance in FP64).
-__device__ bool ksolve(const Group &G, const Views &V, bool f32, const double *in, double *out) {
+__device__ bool ksolve(const Group &G, const Views &V, bool f32, const double *in, double *out,
+                       double delta_p) {
   const Inst<double> &I = V.d;
   const int i = G.lane;
   if (!f32) {
@@ -377,7 +383,7 @@ __device__ bool ksolve(const Group &G, const Views &V, bool f32, const double *i
   double rn = 0.0;
   for (int step = 0; step < 4; step++) {
     __syncwarp(G.mask);
-    kresid<double>(G, I, in, out, I.res);
+    kresid(G, I, in, out, I.res, I.dl, delta_p);  // dl is free during a solve
     __syncwarp(G.mask);
     rn = 0.0;
     for (int k = 0; k < I.T; k++) {
@@ -399,7 +405,8 @@ __device__ bool ksolve(const Group &G, const Views &V, bool f32, const double *i
 
 // One Newton direction with complementarity target w (nullptr: zero); returns
 // false when an FP32 solve missed its tolerance.
-__device__ bool direction(const Group &G, const Views &V, const double *w, bool f32) {
+__device__ bool direction(const Group &G, const Views &V, const double *w, bool f32,
+                          double delta_p) {
   const Inst<double> &I = V.d;
   const int i = G.lane;
   // row values D (g - w/lam) - lam, then rhs = -(W z + J^T(...))
@@ -414,7 +421,7 @@ __device__ bool direction(const Group &G, const Views &V, const double *w, bool 
   jt_rows<double>(G, I, I.ds, 1.0, I.z, nullptr, I.rhs);
   for (int k = 0; k < I.T; k++) I.rhs[k * NS + i] = -I.rhs[k * NS + i];
   __syncwarp(G.mask);
-  const bool ok = __all_sync(G.mask, ksolve(G, V, f32, I.rhs, I.dz));
+  const bool ok = __all_sync(G.mask, ksolve(G, V, f32, I.rhs, I.dz, delta_p));
   if (!ok) return false;
   eval_rows<double>(G, I, I.dz, nullptr, 0.0, 0.0, I.dl, false);  // J dz into dl (temporarily)
   __syncwarp(G.mask);
@@ -515,7 +522,8 @@ __device__ void solve_instance(const Group &G, const MpcArgs &a, int inst, bool 
     __syncwarp(G.mask);
     bool fok = false;
     for (int tries = 0; tries < 12 && !fok; tries++) {
-      assemble<double>(G, I, delta_p);
+      if (f32) assemble<float>(G, V.f, delta_p);
+      else assemble<double>(G, I, delta_p);
       __syncwarp(G.mask);
       fok = __all_sync(G.mask, kfactor(G, V, f32, perturbed));
       if (!fok) delta_p *= 100.0;
@@ -523,11 +531,13 @@ __device__ void solve_instance(const Group &G, const MpcArgs &a, int inst, bool 
     }
     if (!fok) { status = 5; break; }
     // predictor; an FP32 solve that misses its tolerance switches this instance to FP64
-    if (!direction(G, V, nullptr, f32)) {
+    if (!direction(G, V, nullptr, f32, delta_p)) {
       f32 = false;
+      assemble<double>(G, I, delta_p);
+      __syncwarp(G.mask);
       kfactor(G, V, false, perturbed);
       __syncwarp(G.mask);
-      direction(G, V, nullptr, false);
+      direction(G, V, nullptr, false, delta_p);
     }
     double apa, ada;
     step_lengths(G, I, 1.0, apa, ada);
@@ -547,11 +557,13 @@ __device__ void solve_instance(const Group &G, const MpcArgs &a, int inst, bool 
       }
     __syncwarp(G.mask);
     // corrector
-    if (!direction(G, V, I.w, f32)) {
+    if (!direction(G, V, I.w, f32, delta_p)) {
       f32 = false;
+      assemble<double>(G, I, delta_p);
+      __syncwarp(G.mask);
       kfactor(G, V, false, perturbed);
       __syncwarp(G.mask);
-      direction(G, V, I.w, false);
+      direction(G, V, I.w, false, delta_p);
     }
     double ap, ad;
     step_lengths(G, I, fmax(0.99, 1.0 - mu), ap, ad);
