@@ -230,8 +230,9 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
 
 def nlp_measure(N: int, max_iter: int = 150):
     """Grid NLP (512^2 grid, cubic PDE constraint as inequality pairs, -1 <= v <= 1):
-    the FP64 factor against the split-TF32 factor with FP64 fallback, from the
-    cold start, at most max_iter iterations towards a 1e-6 KKT residual."""
+    the FP64 factor against the split-TF32 and BF16 factors with FP64 fallback
+    (once a low-precision factor breaks down, FP64 for the rest), from the cold
+    start, at most max_iter iterations towards a 1e-6 KKT residual."""
     import torch
     import paper_2508_16094_gb300 as gb
     P = gen.grid_nlp(N, seed=5)
@@ -239,7 +240,7 @@ def nlp_measure(N: int, max_iter: int = 150):
     ut = torch.as_tensor(P.ut, dtype=torch.float64, device="cuda")
     out = {"workload": f"grid NLP {N}^2 (n = m = {P.n}), alpha 5e-3, |v| <= 1, seed 5",
            "max_iter": max_iter}
-    for name, prec in (("fp64", gb.IPM_FP64), ("tf32x3", gb.IPM_TF32X3)):
+    for name, prec in (("fp64", gb.IPM_FP64), ("tf32x3", gb.IPM_TF32X3), ("bf16", gb.IPM_BF16)):
         o = gb.default_options(precision=prec, tol=1e-6, max_iter=max_iter, storage_fp64=1,
                                fallback_fp64=1)
         G = gb.GridNLP(N, perm=perm, options=o)
@@ -255,10 +256,13 @@ def nlp_measure(N: int, max_iter: int = 150):
                      "iterations": int(r.iterations), "objective": r.objective,
                      "kkt": float(f"{r.kkt:.3e}"), "primal": float(f"{r.primal_res:.3e}"),
                      "dual": float(f"{r.dual_res:.3e}"), "fp64_fallbacks": int(r.fp64_fallbacks),
+                     "factorizations": int(r.factorizations),
                      "regularizations": int(r.regularizations), "refine_steps": int(r.refine_steps),
                      "factor_flops": G.info.flops}
         G.ctx.close()
-    out["objective_rel_diff_tf32x3_vs_fp64"] = abs(out["tf32x3"]["objective"] - out["fp64"]["objective"]) / max(1.0, abs(out["fp64"]["objective"]))
+    for name in ("tf32x3", "bf16"):
+        out[name]["objective_rel_diff_vs_fp64"] = float(
+            f"{abs(out[name]['objective'] - out['fp64']['objective']) / max(1.0, abs(out['fp64']['objective'])):.2e}")
     return out
 
 

@@ -388,8 +388,9 @@ IPM_API ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *p, int64_t *h_jrowpt
  * (at most 10 times) until the merit f - mu sum ln s + nu ||g - s||_1 decreases
  * by 1e-4 alpha times its directional derivative (up to 10 eps |merit|). A
  * non-positive pivot raises delta_p 100-fold and refactors; an FP32 factor
- * that had to perturb a pivot is redone in FP64 when fallback_fp64 is set and
- * the storage holds FP64 (else delta_p is raised). The pair formulation makes
+ * that had to perturb a pivot (or whose solve misses its tolerance) is redone
+ * in FP64 when fallback_fp64 is set and the storage holds FP64 (else delta_p
+ * is raised), and the remaining iterations factor in FP64. The pair formulation makes
  * the interior degenerate (both slacks of a pair vanish): on fine grids the
  * dual residual can stall above tol while the objective has converged.
  * d_ut: target (nx^2, device); d_x (n), d_s, d_lambda (m_tot): outputs (device).

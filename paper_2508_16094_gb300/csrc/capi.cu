@@ -1631,6 +1631,9 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
     const double cscale = std::max(1.0, d2h_scalar(c, c->scal + 20));
     res.status = IPM_ERR_MAXITER;
     ipm_status stt = IPM_OK;
+    // arithmetic of the factor: o.precision until a low-precision factor has
+    // to be redone in FP64, FP64 from then on (K only gets worse conditioned)
+    int prec_now = o.precision;
     int it = 0;
     for (it = 0; it <= o.max_iter; it++) {
       const double f = eval_at(x, c->vg);
@@ -1666,12 +1669,13 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       V.scaling(s, lam, o.delta_d, c->vD);
       double delta_p = o.delta_p;
       for (int tries = 0; tries < 12; tries++) {
-        stt = factor_with_retry(c, wv, jv, o.precision, delta_p, &res);
+        stt = factor_with_retry(c, wv, jv, prec_now, delta_p, &res);
         if (stt != IPM_OK || c->factor_prec == IPM_FP64 || c->last_perturbed == 0) break;
         // the FP32 factor met a non-positive pivot: an FP64 factor tells a
         // rounding breakdown from true indefiniteness (which it regularises)
         if (o.fallback_fp64 && c->storage_bytes == 8) {
           res.fp64_fallbacks++;
+          prec_now = IPM_FP64;
           stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
           break;
         }
@@ -1687,8 +1691,9 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
         if (o.refine == IPM_REFINE_PCG) c->refine_override = IPM_REFINE_IR;
         stt = direction(c, jv, nullptr, grad, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
         c->nlp_grad = false;
-        if (stt != IPM_OK && o.fallback_fp64 && o.precision != IPM_FP64 && c->storage_bytes == 8) {
+        if (stt != IPM_OK && o.fallback_fp64 && c->factor_prec != IPM_FP64 && c->storage_bytes == 8) {
           res.fp64_fallbacks++;
+          prec_now = IPM_FP64;
           stt = factor_with_retry(c, wv, jv, IPM_FP64, delta_p, &res);
           if (stt == IPM_OK) {
             c->nlp_grad = true;
