@@ -469,12 +469,14 @@ IPM_API ipm_status kkt_factor_entries(ipm_ctx *ctx, int64_t count, const int32_t
 
 /* Test of the bounded device-side waits: in the next launch of the persistent
  * FP32 triangular solve (kkt_solve with an FP32-storage factor) every wait
- * polls its flag at most `spins` times, and CTA `withheld_cta` abandons the
- * first task it takes, so the tasks that need its result wait until their
- * limit runs out. That kkt_solve then returns IPM_ERR_TIMEOUT; the context
- * stays usable. Applies to one launch only.
- * Errors: IPM_ERR_ARG for spins == 0 or a negative CTA index. */
-IPM_API ipm_status kkt_test_solve_timeout(ipm_ctx *ctx, uint32_t spins, int32_t withheld_cta);
+ * polls its flag at most `spins` times, and the task at position
+ * `withheld_task` of the solve's task order (0 = the first block of the first
+ * front's forward sweep) is abandoned by the CTA that takes it, so the tasks
+ * that need its result wait until their limit runs out. That kkt_solve then
+ * returns IPM_ERR_TIMEOUT; the context stays usable. Applies to one launch
+ * only; a position past the launch's tasks withholds nothing.
+ * Errors: IPM_ERR_ARG for spins == 0 or a negative position. */
+IPM_API ipm_status kkt_test_solve_timeout(ipm_ctx *ctx, uint32_t spins, int32_t withheld_task);
 
 /* Low-precision pivots replaced by the last kkt_factor. */
 IPM_API int32_t ipm_last_perturbed(const ipm_ctx *ctx);

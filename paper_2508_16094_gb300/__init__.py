@@ -346,10 +346,11 @@ class IpmContext:
         self._check(self._lib.kkt_time_kernel(self.handle, int(kernel), int(reps), C.byref(ms)))
         return ms.value
 
-    def kkt_test_solve_timeout(self, spins: int, withheld_cta: int = 0):
-        """Make the next persistent solve's grid-barrier waits run out (test
-        of the bounded wait; see the header)."""
-        self._check(self._lib.kkt_test_solve_timeout(self.handle, int(spins), int(withheld_cta)))
+    def kkt_test_solve_timeout(self, spins: int, withheld_task: int = 0):
+        """Make the next persistent solve's bounded waits run out: every wait
+        polls at most ``spins`` times and the task at position
+        ``withheld_task`` of the solve's task order is abandoned."""
+        self._check(self._lib.kkt_test_solve_timeout(self.handle, int(spins), int(withheld_task)))
 
     def ipm_last_perturbed(self) -> int:
         return int(self._lib.ipm_last_perturbed(self.handle))

@@ -60,7 +60,7 @@ struct ipm_ctx {
   bool have_stale = false;      // lb.D_old / diag_old / mu[0] describe the held factor
   int refine_override = -1, pcg_override = -1;
   unsigned test_spins = 0;   // next persistent solve launch only: barrier poll limit
-  int test_withhold = -1;    // ... and the CTA that leaves at its first barrier
+  int test_withhold = -1;    // ... and the ticket of the task it abandons
   double *lb_loss = nullptr;
   double *scal = nullptr, *partial = nullptr;
   IpmScalars *sc = nullptr;
@@ -187,6 +187,8 @@ void layout(ipm_ctx *c, char *base) {
   d.fs_first_slot = upload(cv, pl.fs_first_slot, st);
   d.ps_tasks = upload(cv, pl.ps_tasks, st);
   d.ps_pbase = upload(cv, pl.ps_pbase, st);
+  d.ps_kid_chunks = upload(cv, pl.ps_kid_chunks, st);
+  d.ps_parent_blocks = upload(cv, pl.ps_parent_blocks, st);
   d.fs_dinv_off = upload(cv, pl.fs_dinv_off, st);
   d.k_slot = upload(cv, pl.k_slot, st);
   d.k_poff = upload(cv, pl.k_poff, st);
@@ -1381,11 +1383,11 @@ ipm_status kkt_factor_entries(ipm_ctx *c, int64_t count, const int32_t *rows, co
 
 int32_t ipm_last_perturbed(const ipm_ctx *c) { return c ? c->last_perturbed : 0; }
 
-ipm_status kkt_test_solve_timeout(ipm_ctx *c, uint32_t spins, int32_t withheld_cta) {
-  if (!c || spins == 0 || withheld_cta < 0) return IPM_ERR_ARG;
-  if (c->sys) return kkt_test_solve_timeout(c->sys, spins, withheld_cta);
+ipm_status kkt_test_solve_timeout(ipm_ctx *c, uint32_t spins, int32_t withheld_task) {
+  if (!c || spins == 0 || withheld_task < 0) return IPM_ERR_ARG;
+  if (c->sys) return kkt_test_solve_timeout(c->sys, spins, withheld_task);
   c->test_spins = spins;
-  c->test_withhold = withheld_cta;
+  c->test_withhold = withheld_task;
   return IPM_OK;
 }
 

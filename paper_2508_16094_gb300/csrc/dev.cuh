@@ -17,6 +17,8 @@ struct DevPlan {
   const int64_t *toff;
   const Task *fs_inv, *ps_tasks;  // persistent FP32 solve
   const int64_t *ps_pbase;        // per front: first partial-sum row of its backward tasks
+  const int32_t *ps_kid_chunks;   // per front: below-front chunks of all its children
+  const int32_t *ps_parent_blocks;  // per front: diagonal blocks of its parent
   const int64_t *fs_dinv_off;
   const int32_t *fs_first_slot;  // per front: slot of its first diagonal block
   const int64_t *k_slot, *k_poff, *k_w, *k_orig;

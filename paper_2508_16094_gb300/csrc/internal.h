@@ -105,7 +105,7 @@ struct Plan {
   // are consecutive from fs_first_slot[front]) and its task list, forward
   // tasks first. Flags (32-bit words): [0, 32) tickets, then per slot "y
   // published", "x published", "partial sums done", per front "update-vector
-  // chunks done", "column blocks done".
+  // chunks of its children done", "column blocks done".
   std::vector<Task> fs_inv;                  // (front, first column, slot)
   std::vector<int32_t> fs_first_slot;        // per front: slot of block 0
   std::vector<int64_t> fs_dinv_off;
@@ -113,6 +113,8 @@ struct Plan {
   std::vector<Task> ps_tasks;                // (front, a, b, kind)
   int32_t ps_fwd_tasks = 0;
   std::vector<int64_t> ps_pbase;             // per front: first partial-sum row (128 floats each)
+  std::vector<int32_t> ps_kid_chunks;        // per front: below-front chunks of all its children
+  std::vector<int32_t> ps_parent_blocks;     // per front: diagonal blocks of its parent (0 at roots)
   int64_t ps_part_entries = 0;               // floats of partial sums
   int64_t ps_flag_words = 0;
   // K entries in level-major order

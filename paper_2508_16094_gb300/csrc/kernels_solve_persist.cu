@@ -78,12 +78,13 @@ struct PsArgs {
   unsigned *flags;   // plan.ps_flag_words words, zeroed before the launch
   int32_t *status;   // ST_SOLVE_TIMEOUT
   unsigned spins;    // polls before a wait gives up
-  int32_t withhold;  // test of the bounded wait: this CTA abandons its first task (-1: none)
+  int32_t withhold;  // test of the bounded wait: the task of this ticket is abandoned (-1: none)
   int32_t nslot, nfr;
   int32_t fwd_here;  // the forward sweep runs in this launch: backward blocks wait for their y
 };
 
 constexpr int kRC = 128;  // rows below a front per task
+constexpr int kMaxKids = 32;  // children staged in shared memory for the gathers
 constexpr long long kCopySpinCycles = 2000000000ll;  // bounded wait on a staging copy (~1 s)
 
 __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
@@ -108,6 +109,8 @@ __device__ __forceinline__ unsigned *f_x(const PsArgs &A, int slot) { return A.f
 __device__ __forceinline__ unsigned *f_part(const PsArgs &A, int slot) {
   return A.flags + 32 + 2 * A.nslot + slot;
 }
+// per front: chunks of rows below its children that are done (the children's
+// update vectors are complete once it reaches ps_kid_chunks[front])
 __device__ __forceinline__ unsigned *f_tvec(const PsArgs &A, int front) {
   return A.flags + 32 + 3 * A.nslot + front;
 }
@@ -128,6 +131,11 @@ struct PsShared {
   int tk;                       // this CTA's current task
   int ok;                       // verdict of the last wait
   int ready;                    // blocks of the running chain known to be published
+  int nkids;                    // children of the task's front staged below
+  int64_t kid_inv[kMaxKids];    // their child -> front map offsets
+  int64_t kid_toff[kMaxKids];   // their update-vector offsets
+  Task next_task;               // the next task and its front, loaded during this one
+  FrontInfo next_front;
 };
 
 // Thread 0: start the bulk copy of a diagonal-block inverse into S.di.
@@ -305,23 +313,42 @@ __device__ void signal(unsigned *w) {
   }
 }
 
-__device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F) {
+// Wait until the update vectors of all children of front s are complete (one
+// counter per front), and stage the children's map and vector offsets.
+__device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F, int s) {
   const DevPlan &dp = A.dp;
-  for (int ci = F.child_begin; ci < F.child_end; ci++) {
-    const int32_t ch = dp.children[ci];
-    if (!wait_flag(A, S, f_tvec(A, ch), (dp.fronts[ch].nrow + kRC - 1) / kRC)) return false;
+  const int nk = F.child_end - F.child_begin;
+  if (threadIdx.x < min(nk, kMaxKids)) {
+    const int32_t ch = dp.children[F.child_begin + threadIdx.x];
+    S.kid_inv[threadIdx.x] = dp.fronts[ch].inv_off;
+    S.kid_toff[threadIdx.x] = dp.toff[ch];
   }
-  return true;
+  if (threadIdx.x == 0) S.nkids = nk;
+  if (nk == 0) {
+    __syncthreads();
+    return true;
+  }
+  return wait_flag(A, S, f_tvec(A, s), (unsigned)dp.ps_kid_chunks[s]);  // (syncs first)
 }
 
-// Sum of the children's update entries at front position p.
-__device__ __forceinline__ float gather_children(const PsArgs &A, const FrontInfo &F, int p) {
+// Sum of the children's update entries at front position p (after wait_children).
+__device__ __forceinline__ float gather_children(const PsArgs &A, const PsShared &S,
+                                                 const FrontInfo &F, int p) {
   const DevPlan &dp = A.dp;
   float v = 0.f;
-  for (int ci = F.child_begin; ci < F.child_end; ci++) {
-    const int32_t ch = dp.children[ci];
-    const int32_t q = dp.inv[dp.fronts[ch].inv_off + p];
-    if (q >= 0) v += ldcg(A.t + dp.toff[ch] + q);
+  const int nk = S.nkids;
+  for (int k = 0; k < nk; k++) {
+    int64_t io, to;
+    if (k < kMaxKids) {
+      io = S.kid_inv[k];
+      to = S.kid_toff[k];
+    } else {
+      const int32_t ch = dp.children[F.child_begin + k];
+      io = dp.fronts[ch].inv_off;
+      to = dp.toff[ch];
+    }
+    const int32_t q = dp.inv[io + p];
+    if (q >= 0) v += ldcg(A.t + to + q);
   }
   return v;
 }
@@ -333,10 +360,10 @@ __device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
   const DevPlan &dp = A.dp;
   const int i = tk.a, j0 = kB * i, jb = min(kB, F.ncol - j0), slot0 = dp.fs_first_slot[tk.front];
   if (threadIdx.x == 0) stage_dinv(A, S, slot0 + i, jb);
-  bool ok = wait_children(A, S, F);
+  bool ok = wait_children(A, S, F, tk.front);
   if (ok && threadIdx.x < kB)
     S.sv[threadIdx.x] = threadIdx.x < jb
-                            ? ldcg(A.a + F.first + j0 + threadIdx.x) - gather_children(A, F, j0 + threadIdx.x)
+                            ? ldcg(A.a + F.first + j0 + threadIdx.x) - gather_children(A, S, F, j0 + threadIdx.x)
                             : 0.f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
   float racc = 0.f;
@@ -376,8 +403,8 @@ __device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const Fr
   const DevPlan &dp = A.dp;
   const int r0 = tk.a, nr = min(kRC, F.nrow - r0), nb = (F.ncol + kB - 1) / kB;
   const int slot0 = dp.fs_first_slot[tk.front];
-  bool ok = wait_children(A, S, F);
-  if (ok && threadIdx.x < nr) S.xs[threadIdx.x] = gather_children(A, F, F.ncol + r0 + threadIdx.x);
+  bool ok = wait_children(A, S, F, tk.front);
+  if (ok && threadIdx.x < nr) S.xs[threadIdx.x] = gather_children(A, S, F, F.ncol + r0 + threadIdx.x);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
   float racc = 0.f;
   if (threadIdx.x == 0) S.ready = -1;
@@ -410,7 +437,7 @@ __device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const Fr
   __syncthreads();
   if (ok) {
     if (lane < 16 && rw + lane < nr) A.t[dp.toff[tk.front] + r0 + rw + lane] = S.xs[rw + lane] + racc;
-    signal(f_tvec(A, tk.front));
+    signal(f_tvec(A, F.parent));  // rows below a front exist only below a parent
   }
 }
 
@@ -429,8 +456,7 @@ __device__ void bwd_part(const PsArgs &A, PsShared &S, const Task &tk, const Fro
   for (int k = 0; k < 16; k++)
     l[k] = (c < F.ncol && 16 * g + k < nr) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-  if (F.parent >= 0 &&
-      !wait_flag(A, S, f_front(A, F.parent), (dp.fronts[F.parent].ncol + kB - 1) / kB))
+  if (F.parent >= 0 && !wait_flag(A, S, f_front(A, F.parent), (unsigned)dp.ps_parent_blocks[tk.front]))
     return;
   if (threadIdx.x < nr) S.xs[threadIdx.x] = ldcg(A.x + dp.sri[F.rows_off + r0 + threadIdx.x]);
   __syncthreads();
@@ -466,7 +492,7 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
   bool ok = !A.fwd_here || wait_flag(A, S, f_y(A, slot0 + cb), 1);
   if (ok && nbl > 0) ok = wait_flag(A, S, f_part(A, slot0 + cb), nbl);  // implies the parent is done
   else if (ok && F.parent >= 0)
-    ok = wait_flag(A, S, f_front(A, F.parent), (dp.fronts[F.parent].ncol + kB - 1) / kB);
+    ok = wait_flag(A, S, f_front(A, F.parent), (unsigned)dp.ps_parent_blocks[tk.front]);
   if (ok && threadIdx.x < kB) {
     float v = 0.f;
     if (threadIdx.x < jb) {
@@ -527,31 +553,55 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
 __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
   extern __shared__ __align__(128) unsigned char ps_smem[];
   PsShared &S = *reinterpret_cast<PsShared *>(ps_smem);
+  // Thread 32 keeps one ticket ahead: while a task runs it already holds the
+  // next task (loaded into registers) and the ticket after it, so a task never
+  // starts with the atomic and the two dependent loads of its own description.
+  // A CTA's current ticket is always the smallest it holds, so every task
+  // still waits only for tasks that are running or done.
+  unsigned nxt = 0;
+  Task tn{};
+  FrontInfo fn{};
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.parity = 0;
-    S.tk = (int)atomicAdd(f_ticket(A), 1u) + A.q0;
+  }
+  if (threadIdx.x == 32) {
+    const int q = (int)atomicAdd(f_ticket(A), 1u) + A.q0;
+    nxt = atomicAdd(f_ticket(A), 1u);
+    S.tk = q;
+    if (q < A.q1) {
+      S.next_task = A.dp.ps_tasks[q];
+      S.next_front = A.dp.fronts[S.next_task.front];
+    }
   }
   __syncthreads();
-  bool first = true;
   while (true) {
     const int qt = S.tk;
     if (qt >= A.q1) break;
-    if (first && (int)blockIdx.x == A.withhold) break;  // the task is abandoned
-    first = false;
-    unsigned nxt = 0;
-    if (threadIdx.x == 0) nxt = atomicAdd(f_ticket(A), 1u);  // the next ticket, fetched early
-    const Task tk = A.dp.ps_tasks[qt];
-    const FrontInfo F = A.dp.fronts[tk.front];
-    switch (tk.c) {
+    const Task tk = S.next_task;
+    const FrontInfo F = S.next_front;
+    int qn = (int)nxt + A.q0;
+    if (threadIdx.x == 32) {
+      if (qn < A.q1) tn = A.dp.ps_tasks[qn];  // issued now, consumed after the task
+      nxt = atomicAdd(f_ticket(A), 1u);
+    }
+    if (qt == A.withhold) {
+      // abandoned (test of the bounded waits): the tasks that need its result
+      // run out of time
+    } else switch (tk.c) {
       case WS_FWD_DIAG: fwd_diag(A, S, tk, F); break;
       case WS_FWD_BELOW: fwd_below(A, S, tk, F); break;
       case WS_BWD_PART: bwd_part(A, S, tk, F); break;
       default: bwd_diag(A, S, tk, F); break;
     }
-    __syncthreads();  // every thread has read S.tk; the shared scratch is free
-    if (threadIdx.x == 0) S.tk = (int)nxt + A.q0;
+    __syncthreads();  // the shared scratch (and S.next_*) is free
+    if (threadIdx.x == 32) {
+      if (qn < A.q1) fn = A.dp.fronts[tn.front];
+      S.tk = qn;
+      S.next_task = tn;
+      S.next_front = fn;
+    }
     __syncthreads();
   }
 }

@@ -49,7 +49,7 @@ cudaError_t preload_level_solve();
 // plan.ps_part_entries floats of scratch; flags: plan.ps_flag_words words
 // (zeroed by the launch). A wait that runs out sets status[ST_SOLVE_TIMEOUT]
 // and the launch drains. test_spins (0: the default of seconds) bounds each
-// wait; test_withhold >= 0 makes that CTA abandon its first task (tests of
+// wait; test_withhold >= 0 abandons the task of that ticket (tests of
 // the bounded wait).
 void launch_dinv(const DevPlan &dp, const Plan &plan, const float *L, float *Dinv, cudaStream_t st);
 void launch_psolve(const DevPlan &dp, const Plan &plan, const float *L, const float *Dinv, float *a,

@@ -815,6 +815,15 @@ void build_fused_solve(Plan &pl) {
       for (int32_t cb = nblk(s) - 1; cb >= 0; cb--) pl.ps_tasks.push_back({s, cb, 0, WS_BWD_DIAG});
     }
   }
+  pl.ps_kid_chunks.assign(nfr, 0);
+  pl.ps_parent_blocks.assign(nfr, 0);
+  for (int32_t s = 0; s < nfr; s++) {
+    const int32_t par = pl.fronts[s].parent;
+    if (par >= 0) {
+      pl.ps_kid_chunks[par] += (pl.fronts[s].nrow + RC - 1) / RC;
+      pl.ps_parent_blocks[s] = nblk(par);
+    }
+  }
   const int64_t nslot = (int64_t)pl.fs_dinv_off.size();
   pl.ps_flag_words = 32 + 3 * nslot + 2 * (int64_t)nfr;
   // range checks (the kernel masks only the chunk edges), and the order every
@@ -865,9 +874,16 @@ void build_fused_solve(Plan &pl) {
              "backward diagonal task");
     }
   }
-  for (int32_t s = 0; s < nfr; s++)
+  for (int32_t s = 0; s < nfr; s++) {
     need(fwd_diag_seen[s] == nblk(s) && fwd_below_seen[s] == nbelow(s) && bwd_diag_seen[s] == nblk(s),
          "every block solved once per sweep");
+    int32_t kids = 0;  // the chunk counter a front waits for covers exactly its children
+    for (int32_t ci = pl.fronts[s].child_begin; ci < pl.fronts[s].child_end; ci++) {
+      need(pl.fronts[pl.children[ci]].parent == s, "child list");
+      kids += nbelow(pl.children[ci]);
+    }
+    need(kids == pl.ps_kid_chunks[s], "children's chunk count");
+  }
 }
 
 }  // namespace gipm

@@ -1,9 +1,9 @@
 """The bounded waits of the persistent solve run out, and the context recovers.
 
-A CTA that abandons the first task it takes (the test hook of
-kkt_test_solve_timeout) stands in for a result that never arrives; with a
-short poll limit the tasks waiting for it give up, record the timeout, and the
-launch drains. Nothing faults or hangs: the kernel ends, kkt_solve reports
+An abandoned task (the test hook of kkt_test_solve_timeout: the first or the
+second forward task of the solve's order) stands in for a result that never
+arrives; with a short poll limit the tasks waiting for it give up, record the
+timeout, and the launch drains. Nothing faults or hangs: the kernel ends, kkt_solve reports
 IPM_ERR_TIMEOUT, and the next solves are correct."""
 import numpy as np
 import pytest
@@ -47,7 +47,7 @@ def test_solve_barrier_timeout_is_reported_and_recovered(withheld):
     b = gen.normal(4, lp.n)
     x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
 
-    ctx.kkt_test_solve_timeout(spins=2000, withheld_cta=withheld)
+    ctx.kkt_test_solve_timeout(spins=2000, withheld_task=withheld)
     st = ctx._lib.kkt_solve(ctx.handle, gb._dp(dev(b)), gb._dp(x), 1, gb.IPM_REFINE_NONE, None)
     torch.cuda.synchronize()  # the launch ended: the stream drains
     assert st == IPM_ERR_TIMEOUT
