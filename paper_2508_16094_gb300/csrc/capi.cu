@@ -188,6 +188,7 @@ void layout(ipm_ctx *c, char *base) {
   d.ps_tasks = upload(cv, pl.ps_tasks, st);
   d.ps_pbase = upload(cv, pl.ps_pbase, st);
   d.ps_kid_chunks = upload(cv, pl.ps_kid_chunks, st);
+  d.ps_recs = upload(cv, pl.ps_recs, st);
   d.ps_parent_blocks = upload(cv, pl.ps_parent_blocks, st);
   d.fs_dinv_off = upload(cv, pl.fs_dinv_off, st);
   d.k_slot = upload(cv, pl.k_slot, st);
@@ -679,9 +680,10 @@ void eval_g(ipm_ctx *c, const double *jvals, const double *b, const double *x) {
 }
 
 // Factor with the regularisation raised after a non-positive pivot (inertia
-// correction reduced to "Cholesky succeeds" for the SPD condensed system).
+// correction reduced to "Cholesky succeeds" for the SPD condensed system), at
+// most max_tries times.
 ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jvals, int prec,
-                             double &delta_p, ipm_result *res) {
+                             double &delta_p, ipm_result *res, int max_tries = 12) {
   for (int tries = 0;; tries++) {
     assemble_any(c, wvals, jvals, c->vD, delta_p);
     int32_t bad = -1;
@@ -691,7 +693,7 @@ ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jval
       res->perturbed_pivots += c->last_perturbed;
     }
     if (stt == IPM_OK) return IPM_OK;
-    if (stt != IPM_ERR_NOT_SPD || tries >= 12) return stt;
+    if (stt != IPM_ERR_NOT_SPD || tries >= max_tries) return stt;
     delta_p = delta_p > 0 ? delta_p * 100.0 : 1e-8;
     if (res) res->regularizations++;
   }
@@ -1162,6 +1164,23 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       return o.fallback_fp64 && c->factor_prec != fb_prec && c->factor_prec != IPM_FP64 &&
              (fb_prec == IPM_FP64 || (fac->tcp.ready() && !fac->dp.sgn));
     };
+    // The iterate before a step taken with a low-precision factor: a step
+    // that made the KKT residual grow tenfold is taken back and the iteration
+    // redone in the fallback arithmetic (the direction's error, not the
+    // method, made it grow).
+    double *keep = nullptr;
+    double prev_kkt = 0.0;
+    bool low_step = false;
+    const int64_t nkeep = P.n + 2 * P.mt;
+    if (o.fallback_fp64 && o.precision != IPM_FP64 && o.precision != fb_prec)
+      CK(cudaMallocAsync(&keep, nkeep * sizeof(double), c->st));
+    struct KeepFree {
+      double *&p;
+      cudaStream_t st;
+      ~KeepFree() {
+        if (p) cudaFreeAsync(p, st);
+      }
+    } keep_free{keep, c->st};
     int it = 0;
     for (it = 0; it <= o.max_iter; it++) {
       eval_g(c, jv, b, x);
@@ -1186,6 +1205,20 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
         res.status = IPM_ERR_NUMERIC;
         break;
       }
+      if (keep && low_step && res.kkt > 10.0 * prev_kkt && can_escalate()) {
+        CK(cudaMemcpyAsync(x, keep, P.n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(s, keep + P.n, P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(lam, keep + P.n + P.mt, P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        if (o.verbose)
+          std::fprintf(stderr, "ipm it %3d: KKT grew from %.3e, step taken back, fallback arithmetic\n", it,
+                       prev_kkt);
+        res.fp64_fallbacks++;
+        prec_now = fb_prec;
+        low_step = false;
+        c->have_stale = false;
+        it--;
+        continue;
+      }
       if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
       if (it == o.max_iter) break;
       CK(cudaEventRecord(ev[0], c->st));
@@ -1201,10 +1234,13 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       auto refactor = [&]() -> ipm_status {
         c->learned_active = false;
         c->refine_override = c->pcg_override = -1;
-        ipm_status f = factor_with_retry(c, wv, jv, prec_now, delta_p, &res);
-        // a low-precision factor that had to perturb pivots has broken down:
-        // redo it in the fallback arithmetic before solving with it
-        if (f == IPM_OK && c->last_perturbed > 0 && can_escalate()) {
+        // a low-precision factor that had to perturb pivots, or met a pivot
+        // of the wrong sign, has broken down by rounding: redo it in the
+        // fallback arithmetic before solving with it (and raise delta_p only
+        // for a breakdown in that arithmetic)
+        const bool esc = can_escalate();
+        ipm_status f = factor_with_retry(c, wv, jv, prec_now, delta_p, &res, esc ? 0 : 12);
+        if (esc && (f == IPM_ERR_NOT_SPD || (f == IPM_OK && c->last_perturbed > 0))) {
           res.fp64_fallbacks++;
           prec_now = fb_prec;
           f = factor_with_retry(c, wv, jv, prec_now, delta_p, &res);
@@ -1286,6 +1322,13 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       res.worst_rel_residual = std::max(res.worst_rel_residual, si.rel_residual);
       if (stt != IPM_OK) { res.status = stt; break; }
       CK(cudaEventRecord(ev[3], c->st));
+      if (keep) {
+        CK(cudaMemcpyAsync(keep, x, P.n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(keep + P.n, s, P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(keep + P.n + P.mt, lam, P.mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        low_step = c->factor_prec != IPM_FP64 && c->factor_prec != fb_prec;
+        prev_kkt = res.kkt;
+      }
       V.ftb(s, c->vds, lam, c->vdl, c->scal + 32, c->sc, false);
       V.update(c->sc, x, c->vdx, s, c->vds, lam, c->vdl);
       CK(cudaEventRecord(ev[4], c->st));

@@ -18,6 +18,7 @@ struct DevPlan {
   const Task *fs_inv, *ps_tasks;  // persistent FP32 solve
   const int64_t *ps_pbase;        // per front: first partial-sum row of its backward tasks
   const int32_t *ps_kid_chunks;   // per front: below-front chunks of all its children
+  const SolveRec *ps_recs;        // per task: the task with its front's data
   const int32_t *ps_parent_blocks;  // per front: diagonal blocks of its parent
   const int64_t *fs_dinv_off;
   const int32_t *fs_first_slot;  // per front: slot of its first diagonal block

@@ -51,6 +51,20 @@ struct Task {
   int32_t front, a, b, c;
 };
 
+// One task of the persistent FP32 solve with everything it reads of its front,
+// so a CTA fetches what its next task needs in a single 112-byte copy.
+struct SolveRec {
+  Task task;
+  FrontInfo front;
+  int64_t toff;   // the front's update vector
+  int64_t pbase;  // its first partial-sum row of the backward sweep
+  int32_t slot0;  // slot of its first diagonal block
+  int32_t kid_chunks;     // below-front chunks of all its children
+  int32_t parent_blocks;  // diagonal blocks of its parent (0 at a root)
+  int32_t pad;
+};
+static_assert(sizeof(SolveRec) == 112 && sizeof(SolveRec) % 16 == 0, "SolveRec layout");
+
 // A task of the persistent FP32 solve. Tasks run in the order of the plan
 // (a ticket taken from a global counter), and a task waits only for tasks
 // earlier in that order (flags and counters in device memory), so the solve
@@ -61,8 +75,9 @@ enum SolveTaskKind : int32_t {
                      // published, y_i = L_ii^{-1} (.) (explicit inverse), publish y_i
   WS_FWD_BELOW = 1,  // (front, a = first row below the front of a 128-row chunk): gather,
                      // add L_rj y_j for every block j, store the front's update vector
-  WS_BWD_PART = 2,   // (front, a = column block cb, b = first row below of a 128-row
-                     // chunk): partial sums L_{r,cb}^T x_r once the parent front is done
+  WS_BWD_PART = 2,   // (front, b = first row below of a 128-row chunk): partial sums
+                     // L_{r,cb}^T x_r of every column block cb, last first, once the
+                     // parent front is done
   WS_BWD_DIAG = 3    // (front, a = column block cb): the partial sums, L_{i,cb}^T x_i for
                      // i > cb as each x_i is published, x_cb = L_cc^{-T} (.), publish x_cb
 };
@@ -113,6 +128,7 @@ struct Plan {
   std::vector<Task> ps_tasks;                // (front, a, b, kind)
   int32_t ps_fwd_tasks = 0;
   std::vector<int64_t> ps_pbase;             // per front: first partial-sum row (128 floats each)
+  std::vector<SolveRec> ps_recs;             // per task: the task and its front's data
   std::vector<int32_t> ps_kid_chunks;        // per front: below-front chunks of all its children
   std::vector<int32_t> ps_parent_blocks;     // per front: diagonal blocks of its parent (0 at roots)
   int64_t ps_part_entries = 0;               // floats of partial sums

@@ -121,7 +121,6 @@ __device__ __forceinline__ unsigned *f_front(const PsArgs &A, int front) {
 // Shared scratch of one CTA (dynamic shared memory).
 struct PsShared {
   float di[kB * kB];            // staged inverse of a diagonal block (TMA bulk copy)
-  float sy[kB];                 // block vector of a step
   float sv[kB];                 // values handed to the diagonal-block solve
   float xs[kRC];                // solution entries of the rows below a front
   float red[kT / 32][16][33];   // per-warp transpose reduction of 16 row sums
@@ -134,8 +133,7 @@ struct PsShared {
   int nkids;                    // children of the task's front staged below
   int64_t kid_inv[kMaxKids];    // their child -> front map offsets
   int64_t kid_toff[kMaxKids];   // their update-vector offsets
-  Task next_task;               // the next task and its front, loaded during this one
-  FrontInfo next_front;
+  alignas(16) SolveRec rec[2];  // the running task's record and the next one's
 };
 
 // Thread 0: start the bulk copy of a diagonal-block inverse into S.di.
@@ -304,18 +302,17 @@ __device__ bool wait_chain(const PsArgs &A, PsShared &S, const unsigned *flags, 
   return true;
 }
 
-// After this CTA's writes: make them visible, then count one more on *w (release).
+// After this CTA's writes: count one more on *w. The barrier orders every
+// thread's writes before thread 0's release add, and a release is cumulative,
+// so a consumer that acquires the count sees all of them.
 __device__ void signal(unsigned *w) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(w) : "memory");
-  }
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(w) : "memory");
 }
 
 // Wait until the update vectors of all children of front s are complete (one
 // counter per front), and stage the children's map and vector offsets.
-__device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F, int s) {
+__device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F, const SolveRec &R) {
   const DevPlan &dp = A.dp;
   const int nk = F.child_end - F.child_begin;
   if (threadIdx.x < min(nk, kMaxKids)) {
@@ -328,7 +325,7 @@ __device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F, 
     __syncthreads();
     return true;
   }
-  return wait_flag(A, S, f_tvec(A, s), (unsigned)dp.ps_kid_chunks[s]);  // (syncs first)
+  return wait_flag(A, S, f_tvec(A, R.task.front), (unsigned)R.kid_chunks);  // (syncs first)
 }
 
 // Sum of the children's update entries at front position p (after wait_children).
@@ -353,20 +350,57 @@ __device__ __forceinline__ float gather_children(const PsArgs &A, const PsShared
   return v;
 }
 
+// The CTA's next ticket and its task record (registers of thread 32), taken
+// once the running task has passed its last wait: the atomic and the load of
+// the record then overlap the task's remaining work, and no CTA ever holds a
+// ticket while it waits, so the smallest unfinished ticket is always running.
+struct Next {
+  int q;
+  bool have;
+};
+
+__device__ __forceinline__ void take_next(const PsArgs &A, Next &N) {
+  if (threadIdx.x == 32 && !N.have) {
+    N.q = (int)atomicAdd(f_ticket(A), 1u) + A.q0;  // the result is first read after the task
+    N.have = true;
+  }
+}
+
+// Thread 32: start the asynchronous copy of record q into S.rec[buf], and
+// warm L2 with the record one grid further on.
+__device__ __forceinline__ void fetch_rec(const PsArgs &A, PsShared &S, int q, int buf) {
+  if (q >= A.q1) return;
+  const char *src = reinterpret_cast<const char *>(A.dp.ps_recs + q);
+  const uint32_t dst = smem_u32(&S.rec[buf]);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(SolveRec) / 16); k++)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * k), "l"(src + 16 * k)
+                 : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  const int ahead = min(q + (int)gridDim.x, A.q1 - 1);
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(A.dp.ps_recs + ahead));
+}
+
 // Forward, diagonal block i of front s: rows j0 .. j0 + jb of the front.
 // warp w: rows 16w .. 16w + 15, lane: columns 4 lane .. 4 lane + 3 of block j
 // (the loads of block j are issued before y_j is waited for).
-__device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+__device__ void fwd_diag(const PsArgs &A, PsShared &S, const SolveRec &R, Next &N) {
+  const Task &tk = R.task;
+  const FrontInfo &F = R.front;
   const DevPlan &dp = A.dp;
-  const int i = tk.a, j0 = kB * i, jb = min(kB, F.ncol - j0), slot0 = dp.fs_first_slot[tk.front];
+  const int i = tk.a, j0 = kB * i, jb = min(kB, F.ncol - j0), slot0 = R.slot0;
   if (threadIdx.x == 0) stage_dinv(A, S, slot0 + i, jb);
-  bool ok = wait_children(A, S, F, tk.front);
+  bool ok = wait_children(A, S, F, R);
   if (ok && threadIdx.x < kB)
     S.sv[threadIdx.x] = threadIdx.x < jb
                             ? ldcg(A.a + F.first + j0 + threadIdx.x) - gather_children(A, S, F, j0 + threadIdx.x)
                             : 0.f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
-  float racc = 0.f;
+  // per-thread partial row sums over the lane's 4 columns of every block,
+  // reduced across the warp once after the last block
+  float acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) acc[k] = 0.f;
   if (threadIdx.x == 0) S.ready = -1;
   __syncthreads();  // no thread reads the previous task's value
   for (int j = 0; j < i && ok; j++) {
@@ -378,15 +412,14 @@ __device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
                          : make_float4(0.f, 0.f, 0.f, 0.f);
     ok = wait_chain(A, S, f_y(A, slot0), j, i - 1, 1);
     if (!ok) break;
-    if (threadIdx.x < kB) S.sy[threadIdx.x] = ldcg(A.b + F.first + kB * j + threadIdx.x);
-    __syncthreads();
-    const float4 y4 = *reinterpret_cast<const float4 *>(S.sy + c);
-    float p[16];
+    const float *yb = A.b + F.first + kB * j + c;  // block j < i is a full block
+    const float4 y4 = make_float4(ldcg(yb), ldcg(yb + 1), ldcg(yb + 2), ldcg(yb + 3));
 #pragma unroll
-    for (int k = 0; k < 16; k++) p[k] = l[k].x * y4.x + l[k].y * y4.y + l[k].z * y4.z + l[k].w * y4.w;
-    racc += rows16_reduce(S, p);
-    __syncthreads();  // S.sy is refilled for the next block
+    for (int k = 0; k < 16; k++)
+      acc[k] = fmaf(l[k].x, y4.x, fmaf(l[k].y, y4.y, fmaf(l[k].z, y4.z, fmaf(l[k].w, y4.w, acc[k]))));
   }
+  take_next(A, N);
+  const float racc = rows16_reduce(S, acc);
   __syncthreads();
   if (ok && lane < 16 && rw + lane < jb) S.sv[rw + lane] -= racc;
   __syncthreads();
@@ -399,14 +432,18 @@ __device__ void fwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
 
 // Forward, rows r0 .. r0 + nr below front s: the children's entries plus
 // L_rj y_j over every block j of the front, into the front's update vector.
-__device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+__device__ void fwd_below(const PsArgs &A, PsShared &S, const SolveRec &R, Next &N) {
+  const Task &tk = R.task;
+  const FrontInfo &F = R.front;
   const DevPlan &dp = A.dp;
   const int r0 = tk.a, nr = min(kRC, F.nrow - r0), nb = (F.ncol + kB - 1) / kB;
-  const int slot0 = dp.fs_first_slot[tk.front];
-  bool ok = wait_children(A, S, F, tk.front);
+  const int slot0 = R.slot0;
+  bool ok = wait_children(A, S, F, R);
   if (ok && threadIdx.x < nr) S.xs[threadIdx.x] = gather_children(A, S, F, F.ncol + r0 + threadIdx.x);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, c = 4 * lane, rw = 16 * warp;
-  float racc = 0.f;
+  float acc[16];  // partial row sums, reduced once after the last block
+#pragma unroll
+  for (int k = 0; k < 16; k++) acc[k] = 0.f;
   if (threadIdx.x == 0) S.ready = -1;
   __syncthreads();  // no thread reads the previous task's value
   for (int j = 0; j < nb && ok; j++) {
@@ -419,84 +456,101 @@ __device__ void fwd_below(const PsArgs &A, PsShared &S, const Task &tk, const Fr
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
     ok = wait_chain(A, S, f_y(A, slot0), j, nb - 1, 1);
     if (!ok) break;
-    if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jbj ? ldcg(A.b + F.first + kB * j + threadIdx.x) : 0.f;
-    __syncthreads();
-    const float4 y4 = *reinterpret_cast<const float4 *>(S.sy + c);
-    float p[16];
+    // columns past ncol (the padding of the last block) never enter the sums
+    const float *yb = A.b + F.first + kB * j + c;
+    const float4 y4 = make_float4(c < jbj ? ldcg(yb) : 0.f, c + 1 < jbj ? ldcg(yb + 1) : 0.f,
+                                  c + 2 < jbj ? ldcg(yb + 2) : 0.f, c + 3 < jbj ? ldcg(yb + 3) : 0.f);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-      float4 v = l[k];  // padding columns past ncol never enter the sums
+      float4 v = l[k];
       if (c + 1 >= jbj) v.y = 0.f;
       if (c + 2 >= jbj) v.z = 0.f;
       if (c + 3 >= jbj) v.w = 0.f;
-      p[k] = v.x * y4.x + v.y * y4.y + v.z * y4.z + v.w * y4.w;
+      acc[k] = fmaf(v.x, y4.x, fmaf(v.y, y4.y, fmaf(v.z, y4.z, fmaf(v.w, y4.w, acc[k]))));
     }
-    racc += rows16_reduce(S, p);
-    __syncthreads();
   }
+  take_next(A, N);
+  const float racc = rows16_reduce(S, acc);
   __syncthreads();
   if (ok) {
-    if (lane < 16 && rw + lane < nr) A.t[dp.toff[tk.front] + r0 + rw + lane] = S.xs[rw + lane] + racc;
+    if (lane < 16 && rw + lane < nr) A.t[R.toff + r0 + rw + lane] = S.xs[rw + lane] + racc;
     signal(f_tvec(A, F.parent));  // rows below a front exist only below a parent
   }
 }
 
-// Backward, rows r0 .. r0 + nr below front s and column block cb: partial sums
-// part[c] = sum_r L[ncol + r0 + r, c0 + c] x[row r] once the parent front (and
-// so every ancestor holding those rows) is solved; thread (g, q): columns 4q ..
-// 4q + 3, rows 16g .. 16g + 15 (loads issued before the wait).
-__device__ void bwd_part(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+// Backward, rows r0 .. r0 + nr below front s: once the parent front (and so
+// every ancestor holding those rows) is solved, the partial sums
+// part[cb][c] = sum_r L[ncol + r0 + r, 128 cb + c] x[row r] of every column
+// block, last block first (the order of the front's backward chain), each
+// published as it is written. Thread (g, q): columns 4q .. 4q + 3, rows
+// 16g .. 16g + 15; the loads of the next block are issued before the
+// reduction of the current one.
+__device__ void bwd_part(const PsArgs &A, PsShared &S, const SolveRec &R, Next &N) {
+  const Task &tk = R.task;
+  const FrontInfo &F = R.front;
   const DevPlan &dp = A.dp;
-  const int cb = tk.a, r0 = tk.b, c0 = kB * cb, nr = min(kRC, F.nrow - r0);
+  const int r0 = tk.b, nr = min(kRC, F.nrow - r0), nb = (F.ncol + kB - 1) / kB;
   const int nbl = (F.nrow + kRC - 1) / kRC;
-  const int q = threadIdx.x % 32, g = threadIdx.x / 32, c = c0 + 4 * q;
+  const int q = threadIdx.x % 32, g = threadIdx.x / 32;
+  const float *P = A.L + F.loff + (int64_t)(F.ncol + r0 + 16 * g) * F.ld + 4 * q;
   float4 l[16];
-  const float *P = A.L + F.loff + (int64_t)(F.ncol + r0 + 16 * g) * F.ld + c;
+  auto load = [&](int cb) {
+    const int c = kB * cb + 4 * q;
 #pragma unroll
-  for (int k = 0; k < 16; k++)
-    l[k] = (c < F.ncol && 16 * g + k < nr) ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld))
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-  if (F.parent >= 0 && !wait_flag(A, S, f_front(A, F.parent), (unsigned)dp.ps_parent_blocks[tk.front]))
+    for (int k = 0; k < 16; k++)
+      l[k] = (c < F.ncol && 16 * g + k < nr)
+                 ? __ldg(reinterpret_cast<const float4 *>(P + (int64_t)k * F.ld + kB * cb))
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  load(nb - 1);
+  const int32_t xrow = threadIdx.x < nr ? dp.sri[F.rows_off + r0 + threadIdx.x] : 0;
+  if (F.parent >= 0 && !wait_flag(A, S, f_front(A, F.parent), (unsigned)R.parent_blocks))
     return;
-  if (threadIdx.x < nr) S.xs[threadIdx.x] = ldcg(A.x + dp.sri[F.rows_off + r0 + threadIdx.x]);
+  take_next(A, N);
+  if (threadIdx.x < nr) S.xs[threadIdx.x] = ldcg(A.x + xrow);
   __syncthreads();
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int cb = nb - 1; cb >= 0; cb--) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-  for (int k = 0; k < 16; k++)
-    if (16 * g + k < nr) acc = fma4(l[k], S.xs[16 * g + k], acc);
-  S.red4[g][q] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float4 sm = S.red4[0][q];
+    for (int k = 0; k < 16; k++)
+      if (16 * g + k < nr) acc = fma4(l[k], S.xs[16 * g + k], acc);
+    if (cb > 0) load(cb - 1);
+    S.red4[g][q] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float4 sm = S.red4[0][q];
 #pragma unroll
-    for (int h = 1; h < kT / 32; h++) {
-      const float4 o = S.red4[h][q];
-      sm.x += o.x; sm.y += o.y; sm.z += o.z; sm.w += o.w;
+      for (int h = 1; h < kT / 32; h++) {
+        const float4 o = S.red4[h][q];
+        sm.x += o.x; sm.y += o.y; sm.z += o.z; sm.w += o.w;
+      }
+      const int64_t row = R.pbase + (int64_t)cb * nbl + r0 / kRC;
+      reinterpret_cast<float4 *>(A.part + row * kB)[q] = sm;
     }
-    const int64_t row = dp.ps_pbase[tk.front] + (int64_t)cb * nbl + r0 / kRC;
-    reinterpret_cast<float4 *>(A.part + row * kB)[q] = sm;
+    signal(f_part(A, R.slot0 + cb));  // (its barrier also frees S.red4)
   }
-  signal(f_part(A, dp.fs_first_slot[tk.front] + cb));
 }
 
 // Backward, column block cb of front s: the partial sums in chunk order, then
 // L[block i, block cb]^T x_i for i > cb as each x_i is published, then
 // x_cb = L_cc^{-T} (.) with the staged inverse.
-__device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const FrontInfo &F) {
+__device__ void bwd_diag(const PsArgs &A, PsShared &S, const SolveRec &R, Next &N) {
+  const Task &tk = R.task;
+  const FrontInfo &F = R.front;
   const DevPlan &dp = A.dp;
   const int cb = tk.a, c0 = kB * cb, jb = min(kB, F.ncol - c0), nb = (F.ncol + kB - 1) / kB;
-  const int nbl = (F.nrow + kRC - 1) / kRC, slot0 = dp.fs_first_slot[tk.front];
+  const int nbl = (F.nrow + kRC - 1) / kRC, slot0 = R.slot0;
   if (threadIdx.x == 0) stage_dinv(A, S, slot0 + cb, jb);
   // b of this block is the forward result: published by this launch's forward
   // task of the block, or complete before a backward-only launch
   bool ok = !A.fwd_here || wait_flag(A, S, f_y(A, slot0 + cb), 1);
   if (ok && nbl > 0) ok = wait_flag(A, S, f_part(A, slot0 + cb), nbl);  // implies the parent is done
   else if (ok && F.parent >= 0)
-    ok = wait_flag(A, S, f_front(A, F.parent), (unsigned)dp.ps_parent_blocks[tk.front]);
+    ok = wait_flag(A, S, f_front(A, F.parent), (unsigned)R.parent_blocks);
   if (ok && threadIdx.x < kB) {
     float v = 0.f;
     if (threadIdx.x < jb) {
-      const float *pp = A.part + (dp.ps_pbase[tk.front] + (int64_t)cb * nbl) * kB + threadIdx.x;
+      const float *pp = A.part + (R.pbase + (int64_t)cb * nbl) * kB + threadIdx.x;
       float ps = 0.f;
       for (int k = 0; k < nbl; k++) ps += ldcg(pp + (int64_t)k * kB);
       v = ldcg(A.b + F.first + c0 + threadIdx.x) - ps;
@@ -517,12 +571,12 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
                                               : make_float4(0.f, 0.f, 0.f, 0.f);
     ok = wait_chain(A, S, f_x(A, slot0), i, cb + 1, -1);
     if (!ok) break;
-    if (threadIdx.x < kB) S.sy[threadIdx.x] = threadIdx.x < jbi ? ldcg(A.x + F.first + kB * i + threadIdx.x) : 0.f;
-    __syncthreads();
+    // lane k < 16 loads x of row 16 g + k of block i; the warp shares them
+    const float xv = (q < 16 && 16 * g + q < jbi) ? ldcg(A.x + F.first + kB * i + 16 * g + q) : 0.f;
 #pragma unroll
-    for (int k = 0; k < 16; k++) acc = fma4(l[k], S.sy[16 * g + k], acc);
-    __syncthreads();
+    for (int k = 0; k < 16; k++) acc = fma4(l[k], __shfl_sync(0xffffffffu, xv, k), acc);
   }
+  take_next(A, N);
   __syncthreads();
   S.red4[g][q] = acc;
   __syncthreads();
@@ -553,14 +607,12 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const Task &tk, const Fro
 __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
   extern __shared__ __align__(128) unsigned char ps_smem[];
   PsShared &S = *reinterpret_cast<PsShared *>(ps_smem);
-  // Thread 32 keeps one ticket ahead: while a task runs it already holds the
-  // next task (loaded into registers) and the ticket after it, so a task never
-  // starts with the atomic and the two dependent loads of its own description.
-  // A CTA's current ticket is always the smallest it holds, so every task
-  // still waits only for tasks that are running or done.
-  unsigned nxt = 0;
-  Task tn{};
-  FrontInfo fn{};
+  // Thread 32 takes the tickets: the first here, each next one inside the
+  // running task once it has passed its last wait (take_next), or right after
+  // a task that ended early; the next task's record is copied into the other
+  // shared buffer while the CTA finishes the current one.
+  Next N{0, false};
+  int cur = 0;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -568,41 +620,33 @@ __global__ void __launch_bounds__(kT, 2) psolve_kernel(PsArgs A) {
   }
   if (threadIdx.x == 32) {
     const int q = (int)atomicAdd(f_ticket(A), 1u) + A.q0;
-    nxt = atomicAdd(f_ticket(A), 1u);
+    fetch_rec(A, S, q, 0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     S.tk = q;
-    if (q < A.q1) {
-      S.next_task = A.dp.ps_tasks[q];
-      S.next_front = A.dp.fronts[S.next_task.front];
-    }
   }
   __syncthreads();
   while (true) {
     const int qt = S.tk;
     if (qt >= A.q1) break;
-    const Task tk = S.next_task;
-    const FrontInfo F = S.next_front;
-    int qn = (int)nxt + A.q0;
-    if (threadIdx.x == 32) {
-      if (qn < A.q1) tn = A.dp.ps_tasks[qn];  // issued now, consumed after the task
-      nxt = atomicAdd(f_ticket(A), 1u);
-    }
+    const SolveRec &R = S.rec[cur];
+    N.have = false;
     if (qt == A.withhold) {
       // abandoned (test of the bounded waits): the tasks that need its result
       // run out of time
-    } else switch (tk.c) {
-      case WS_FWD_DIAG: fwd_diag(A, S, tk, F); break;
-      case WS_FWD_BELOW: fwd_below(A, S, tk, F); break;
-      case WS_BWD_PART: bwd_part(A, S, tk, F); break;
-      default: bwd_diag(A, S, tk, F); break;
+    } else switch (R.task.c) {
+      case WS_FWD_DIAG: fwd_diag(A, S, R, N); break;
+      case WS_FWD_BELOW: fwd_below(A, S, R, N); break;
+      case WS_BWD_PART: bwd_part(A, S, R, N); break;
+      default: bwd_diag(A, S, R, N); break;
     }
-    __syncthreads();  // the shared scratch (and S.next_*) is free
+    take_next(A, N);  // a task that gave up early
     if (threadIdx.x == 32) {
-      if (qn < A.q1) fn = A.dp.fronts[tn.front];
-      S.tk = qn;
-      S.next_task = tn;
-      S.next_front = fn;
+      fetch_rec(A, S, N.q, cur ^ 1);
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      S.tk = N.q;
     }
-    __syncthreads();
+    __syncthreads();  // the next record has landed; the shared scratch is free
+    cur ^= 1;
   }
 }
 

@@ -794,8 +794,9 @@ void build_fused_solve(Plan &pl) {
     }
   }
   pl.ps_fwd_tasks = (int32_t)pl.ps_tasks.size();
-  // backward, root to leaves, level by level: the partial sums over the rows
-  // below every front of the level, then the column blocks (last to first)
+  // backward, root to leaves, level by level: the partial sums of every
+  // 128-row chunk below every front of the level (one task per chunk, all
+  // column blocks), then the column blocks (last to first)
   pl.ps_pbase.assign(nfr, 0);
   int64_t prow = 0;
   for (int32_t s = 0; s < nfr; s++) {
@@ -807,8 +808,7 @@ void build_fused_solve(Plan &pl) {
     const LevelPlan &LP = pl.levels[li];
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = pl.level_fronts[t];
-      for (int32_t cb = 0; cb < nblk(s); cb++)
-        for (int32_t r0 = 0; r0 < pl.fronts[s].nrow; r0 += RC) pl.ps_tasks.push_back({s, cb, r0, WS_BWD_PART});
+      for (int32_t r0 = 0; r0 < pl.fronts[s].nrow; r0 += RC) pl.ps_tasks.push_back({s, 0, r0, WS_BWD_PART});
     }
     for (int32_t t = LP.front_b; t < LP.front_e; t++) {
       const int32_t s = pl.level_fronts[t];
@@ -861,15 +861,15 @@ void build_fused_solve(Plan &pl) {
           need(fwd_below_seen[pl.children[ci]] == nbelow(pl.children[ci]), "forward child order");
         break;
       case WS_BWD_PART:
-        need(t.a >= 0 && t.a < nblk(s) && t.b >= 0 && t.b < F.nrow && t.b % RC == 0 &&
+        need(t.a == 0 && t.b == RC * bwd_part_seen[s] && t.b < F.nrow &&
                  (F.parent < 0 || bwd_diag_seen[F.parent] == nblk(F.parent)) &&
-                 pl.ps_pbase[s] + (int64_t)t.a * nbelow(s) + t.b / RC < pl.ps_part_entries / B,
+                 pl.ps_pbase[s] + (int64_t)(nblk(s) - 1) * nbelow(s) + t.b / RC < pl.ps_part_entries / B,
              "backward partial task");
         bwd_part_seen[s]++;
         break;
       default:
         need(t.a == nblk(s) - 1 - bwd_diag_seen[s]++ && t.a >= 0 &&
-                 bwd_part_seen[s] == nblk(s) * nbelow(s) &&
+                 bwd_part_seen[s] == nbelow(s) &&
                  (F.parent < 0 || bwd_diag_seen[F.parent] == nblk(F.parent)),
              "backward diagonal task");
     }
@@ -883,6 +883,12 @@ void build_fused_solve(Plan &pl) {
       kids += nbelow(pl.children[ci]);
     }
     need(kids == pl.ps_kid_chunks[s], "children's chunk count");
+  }
+  pl.ps_recs.resize(pl.ps_tasks.size());
+  for (size_t q = 0; q < pl.ps_tasks.size(); q++) {
+    const int32_t s = pl.ps_tasks[q].front;
+    pl.ps_recs[q] = SolveRec{pl.ps_tasks[q], pl.fronts[s], pl.toff[s], pl.ps_pbase[s],
+                             pl.fs_first_slot[s], pl.ps_kid_chunks[s], pl.ps_parent_blocks[s], 0};
   }
 }
 
