@@ -252,9 +252,10 @@ __device__ void diag_bwd(const PsArgs &A, PsShared &S, const FrontInfo &F, int j
 
 // Thread 0 polls *w until it reaches target (acquire), at most A.spins times
 // and only while no other wait of the launch has run out; the CTA then shares
-// the verdict. On expiry the status word is set, and every later wait of the
-// launch gives up at once.
-__device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsigned target) {
+// the verdict (and, on success, S.ready = ready unless ready < -1). On expiry
+// the status word is set, and every later wait of the launch gives up at once.
+__device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsigned target,
+                          int ready = -2) {
   __syncthreads();  // every thread has read the previous verdict
   if (threadIdx.x == 0) {
     unsigned v, spins = 0;
@@ -274,6 +275,7 @@ __device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsig
       __nanosleep(32);
     }
     S.ok = ok;
+    if (ok && ready >= -1) S.ready = ready;
   }
   __syncthreads();
   return S.ok != 0;
@@ -296,10 +298,7 @@ __device__ bool wait_chain(const PsArgs &A, PsShared &S, const unsigned *flags, 
   }
   __syncthreads();
   if (S.ready == last) return true;
-  if (!wait_flag(A, S, flags + j, 1)) return false;
-  if (threadIdx.x == 0) S.ready = j;
-  __syncthreads();
-  return true;
+  return wait_flag(A, S, flags + j, 1, j);
 }
 
 // After this CTA's writes: count one more on *w. The barrier orders every
@@ -328,14 +327,13 @@ __device__ bool wait_children(const PsArgs &A, PsShared &S, const FrontInfo &F, 
   return wait_flag(A, S, f_tvec(A, R.task.front), (unsigned)R.kid_chunks);  // (syncs first)
 }
 
-// Sum of the children's update entries at front position p (after wait_children).
+// Sum of the children's update entries at front position p (after
+// wait_children), in child order; the map entries of two children are loaded
+// together, then their update entries.
 __device__ __forceinline__ float gather_children(const PsArgs &A, const PsShared &S,
                                                  const FrontInfo &F, int p) {
   const DevPlan &dp = A.dp;
-  float v = 0.f;
-  const int nk = S.nkids;
-  for (int k = 0; k < nk; k++) {
-    int64_t io, to;
+  auto offs = [&](int k, int64_t &io, int64_t &to) {
     if (k < kMaxKids) {
       io = S.kid_inv[k];
       to = S.kid_toff[k];
@@ -344,6 +342,23 @@ __device__ __forceinline__ float gather_children(const PsArgs &A, const PsShared
       io = dp.fronts[ch].inv_off;
       to = dp.toff[ch];
     }
+  };
+  float v = 0.f;
+  const int nk = S.nkids;
+  int k = 0;
+  for (; k + 1 < nk; k += 2) {
+    int64_t io0, to0, io1, to1;
+    offs(k, io0, to0);
+    offs(k + 1, io1, to1);
+    const int32_t q0 = dp.inv[io0 + p], q1 = dp.inv[io1 + p];
+    const float t0 = q0 >= 0 ? ldcg(A.t + to0 + q0) : 0.f;
+    const float t1 = q1 >= 0 ? ldcg(A.t + to1 + q1) : 0.f;
+    if (q0 >= 0) v += t0;
+    if (q1 >= 0) v += t1;
+  }
+  if (k < nk) {
+    int64_t io, to;
+    offs(k, io, to);
     const int32_t q = dp.inv[io + p];
     if (q >= 0) v += ldcg(A.t + to + q);
   }
@@ -419,11 +434,11 @@ __device__ void fwd_diag(const PsArgs &A, PsShared &S, const SolveRec &R, Next &
       acc[k] = fmaf(l[k].x, y4.x, fmaf(l[k].y, y4.y, fmaf(l[k].z, y4.z, fmaf(l[k].w, y4.w, acc[k]))));
   }
   take_next(A, N);
-  const float racc = rows16_reduce(S, acc);
-  __syncthreads();
+  const float racc = rows16_reduce(S, acc);  // rows of this warp only
   if (ok && lane < 16 && rw + lane < jb) S.sv[rw + lane] -= racc;
-  __syncthreads();
-  const bool got = wait_dinv(A, S);  // the staged copy always lands before S.di is reused
+  // the staged copy always lands before S.di is reused; the wait ends with a
+  // barrier, after which every row of S.sv is final
+  const bool got = wait_dinv(A, S);
   if (ok && got) {
     diag_fwd(A, S, F, j0);
     signal(f_y(A, slot0 + i));
@@ -577,7 +592,6 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const SolveRec &R, Next &
     for (int k = 0; k < 16; k++) acc = fma4(l[k], __shfl_sync(0xffffffffu, xv, k), acc);
   }
   take_next(A, N);
-  __syncthreads();
   S.red4[g][q] = acc;
   __syncthreads();
   if (ok && threadIdx.x < 32) {
@@ -592,8 +606,7 @@ __device__ void bwd_diag(const PsArgs &A, PsShared &S, const SolveRec &R, Next &
     for (int k = 0; k < 4; k++)
       if (4 * q + k < jb) S.sv[4 * q + k] -= d[k];
   }
-  __syncthreads();
-  const bool got = wait_dinv(A, S);
+  const bool got = wait_dinv(A, S);  // (ends with a barrier)
   if (ok && got) {
     diag_bwd(A, S, F, c0);
     signal(f_x(A, slot0 + cb));
