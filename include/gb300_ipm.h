@@ -100,11 +100,16 @@ typedef struct {
   double ir_tol;         /* stop once ||b - K x||_inf <= ir_tol ||b||_inf (1e-10) */
   int32_t pcg_max;       /* PCG iterations per solve (100) */
   int32_t fallback_fp64; /* after a linear solve that misses accept_tol with a TF32/BF16/FP32
-                            factor, or a low-precision factor that had to perturb pivots,
-                            refactor in the most accurate arithmetic the storage allows
-                            (FP64 with FP64 storage, else the split TF32), solve again and
-                            keep that arithmetic for the rest of ipm_solve; counted in
-                            ipm_result.fp64_fallbacks (0) */
+                            factor, or a low-precision factor that had to perturb pivots or
+                            met a pivot of the wrong sign, refactor in the most accurate
+                            arithmetic the storage allows (FP64 with FP64 storage, else the
+                            split TF32), solve again and keep that arithmetic for the rest of
+                            ipm_solve; a step taken with a low-precision factor after which the
+                            KKT residual exceeds 10x the previous one is taken back (the
+                            iterate before it is restored) and redone in that arithmetic.
+                            Counted in ipm_result.fp64_fallbacks (0). When precision is below
+                            that arithmetic, ipm_solve allocates n + 2 m_tot doubles on the
+                            context's stream for the kept iterate */
   double accept_tol;     /* a solve that misses ir_tol but reaches accept_tol is used (1e-6) */
   int32_t verbose;       /* print one line per interior-point iteration to stderr */
   int32_t warm_start;    /* 1: ipm_solve starts from the x, s, lambda it is given (0) */
@@ -390,11 +395,14 @@ IPM_API ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *p, int64_t *h_jrowpt
  * non-positive pivot raises delta_p 100-fold and refactors; an FP32 factor
  * that had to perturb a pivot (or whose solve misses its tolerance) is redone
  * in FP64 when fallback_fp64 is set and the storage holds FP64 (else delta_p
- * is raised), and the remaining iterations factor in FP64. The pair formulation makes
+ * is raised), and the remaining iterations factor in FP64; with the same
+ * setting, a low-precision step after which the KKT residual exceeds 10x the
+ * previous one is taken back (x, s, lambda, mu and the merit penalty
+ * restored) and redone in FP64. The pair formulation makes
  * the interior degenerate (both slacks of a pair vanish): on fine grids the
  * dual residual can stall above tol while the objective has converged.
  * d_ut: target (nx^2, device); d_x (n), d_s, d_lambda (m_tot): outputs (device).
- * Allocates 3 n + 4 m_tot + nnz(J) doubles of scratch on the context's stream
+ * Allocates 4 n + 6 m_tot + nnz(J) doubles of scratch on the context's stream
  * for the call. res: as for ipm_solve. Errors: IPM_ERR_ARG if the context's
  * pattern is not the grid NLP's; otherwise as ipm_solve. */
 IPM_API ipm_status ipm_solve_grid_nlp(ipm_ctx *ctx, const ipm_grid_nlp *p, const double *d_ut,

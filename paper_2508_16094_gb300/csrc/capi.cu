@@ -1645,10 +1645,10 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
     c->refine_steps = c->pcg_steps = 0;
     const int64_t nnz = (int64_t)P.ji.size();
     c->bwd_measure = true;
-    const size_t words = (size_t)(3 * n + 4 * mt + nnz);
+    const size_t words = (size_t)(4 * n + 6 * mt + nnz);
     CK(cudaMallocAsync(&scratch, words * sizeof(double), c->st));
     double *jv = scratch, *hrows = jv + nnz, *grad = hrows + mt, *wv = grad + n, *zero = wv + n,
-           *xt = zero + mt, *stv = xt + n, *gt = stv + mt;
+           *xt = zero + mt, *stv = xt + n, *gt = stv + mt, *keep = gt + mt;  // keep: x, s, lambda
     CK(cudaMemsetAsync(zero, 0, mt * sizeof(double), c->st));
     double *d_f = c->scal + 44, *terms = c->scal + 48;
     auto d2h = [&](const double *d, double *h, int cnt) {
@@ -1679,6 +1679,11 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
     // arithmetic of the factor: o.precision until a low-precision factor has
     // to be redone in FP64, FP64 from then on (K only gets worse conditioned)
     int prec_now = o.precision;
+    // the iterate (and mu, nu) before a step taken with a low-precision factor:
+    // a step after which the KKT residual is more than 10x the previous one is
+    // taken back and redone in FP64, as in ipm_solve
+    double prev_kkt = 0.0, keep_mu = 0.0, keep_nu = 0.0;
+    bool low_step = false;
     int it = 0;
     for (it = 0; it <= o.max_iter; it++) {
       const double f = eval_at(x, c->vg);
@@ -1697,12 +1702,35 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       if (o.verbose)
         std::fprintf(stderr, "nlp it %3d f % .10e kkt %.3e (p %.2e d %.2e c %.2e) mu %.2e\n", it, f,
                      res.kkt, res.primal_res, res.dual_res, res.compl_res, mu);
+      if (low_step && res.kkt > 10.0 * prev_kkt && o.fallback_fp64 && c->storage_bytes == 8) {
+        CK(cudaMemcpyAsync(x, keep, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(s, keep + n, mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(lam, keep + n + mt, mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        if (o.verbose)
+          std::fprintf(stderr, "nlp it %3d: KKT grew from %.3e, step taken back, FP64 from here\n", it,
+                       prev_kkt);
+        mu = keep_mu;
+        nu = keep_nu;
+        res.fp64_fallbacks++;
+        prec_now = IPM_FP64;
+        low_step = false;
+        it--;
+        continue;
+      }
       if (!std::isfinite(res.kkt) || !std::isfinite(h.mu) || !std::isfinite(f)) {
         res.status = IPM_ERR_NUMERIC;
         break;
       }
       if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
       if (it == o.max_iter) break;
+      if (prec_now != IPM_FP64) {
+        CK(cudaMemcpyAsync(keep, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(keep + n, s, mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(keep + n + mt, lam, mt * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        keep_mu = mu;
+        keep_nu = nu;
+        prev_kkt = res.kkt;
+      }
       // monotone barrier update once the barrier problem is solved to 10 mu
       nlp_barrier_err(mt, s, lam, mu, terms, c->partial, c->st);
       double berr;
@@ -1786,6 +1814,7 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       set_sc(offsetof(IpmScalars, alpha_p), alpha);
       set_sc(offsetof(IpmScalars, alpha_d), alpha);
       V.update(c->sc, x, c->vdx, s, c->vds, lam, c->vdl);
+      low_step = c->factor_prec != IPM_FP64;
     }
     res.iterations = it;
     CK(cudaStreamSynchronize(c->st));

@@ -70,6 +70,18 @@ def test_split_tf32_factor_matches_oracle():
     assert res.objective == pytest.approx(ref["objective"], rel=1e-6)
 
 
+def test_bf16_factor_with_fallback_matches_oracle():
+    """BF16 factors with the FP64 fallback: a step after which the KKT residual
+    grows tenfold is taken back and redone in FP64, so the solve still reaches
+    the oracle's optimum."""
+    P = gen.grid_nlp(40, seed=34)
+    res, x, s, lam = _solve(P, precision=gb.IPM_BF16, tol=1e-6, fallback_fp64=1)
+    ref = _oracle(P, tol=1e-6)
+    assert res.status == 0 and res.kkt <= 1e-6
+    assert res.objective == pytest.approx(ref["objective"], rel=1e-6)
+    assert np.all(s > 0) and np.all(lam > 0)
+
+
 def test_rejects_foreign_pattern():
     lp = gen.grid_lp(4, seed=1)
     ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u)
