@@ -118,7 +118,7 @@ __device__ __forceinline__ double xprev(const double *v, const double *x0, int k
 // out[slot] = J v (linear part) for every valid row; with x0 != nullptr and
 // lb/ub the constant parts of g are included (out = g(v)).
 template <typename TF>
-__device__ void eval_rows(const Group &G, const Inst<TF> &I, const double *v, const double *x0,
+__device__ __noinline__ void eval_rows(const Group &G, const Inst<TF> &I, const double *v, const double *x0,
                           double umax, double xmax, double *out, bool constant) {
   const int i = G.lane;
   for (int k = 0; k < I.T; k++) {
@@ -140,7 +140,7 @@ __device__ void eval_rows(const Group &G, const Inst<TF> &I, const double *v, co
 
 // out (16 per stage) = base + sgn * J^T rowv + (W z if z)
 template <typename TF>
-__device__ void jt_rows(const Group &G, const Inst<TF> &I, const double *rowv, double sgn,
+__device__ __noinline__ void jt_rows(const Group &G, const Inst<TF> &I, const double *rowv, double sgn,
                         const double *z, const double *base, double *out) {
   const int i = G.lane;
   for (int k = 0; k < I.T; k++) {
@@ -168,7 +168,7 @@ __device__ void jt_rows(const Group &G, const Inst<TF> &I, const double *rowv, d
 // K = W + J^T D J + diag(bounds) + delta_p I as diagonal (Kf) and sub-diagonal
 // (Kof) blocks, computed and stored in the arithmetic TF.
 template <typename TF>
-__device__ void assemble(const Group &G, const Inst<TF> &I, double delta_p) {
+__device__ __noinline__ void assemble(const Group &G, const Inst<TF> &I, double delta_p) {
   const int i = G.lane;
   for (int k = 0; k < I.T; k++) {
     const double *Dk = I.D + k * NSLOT;
@@ -221,7 +221,7 @@ template <> __device__ __forceinline__ double big_piv<double>() { return 1e64; }
 // Block Cholesky of the block-tridiagonal K. Returns false on a non-positive
 // pivot in FP64 (caller raises delta_p); FP32 replaces such pivots.
 template <typename TF>
-__device__ bool factor(const Group &G, const Inst<TF> &I, int &perturbed) {
+__device__ __noinline__ bool factor(const Group &G, const Inst<TF> &I, int &perturbed) {
   const int i = G.lane;
   TF lo[NS];  // row i of L_{k,k-1}
 #pragma unroll
@@ -286,7 +286,7 @@ __device__ bool factor(const Group &G, const Inst<TF> &I, int &perturbed) {
 
 // out = K^{-1} in via the block factor (arithmetic in TF); work: 16 per stage.
 template <typename TF>
-__device__ void block_solve(const Group &G, const Inst<TF> &I, const double *in, double *out,
+__device__ __noinline__ void block_solve(const Group &G, const Inst<TF> &I, const double *in, double *out,
                             double *work) {
   const int i = G.lane;
   TF yprev = TF(0);
@@ -337,7 +337,7 @@ __device__ void block_solve(const Group &G, const Inst<TF> &I, const double *in,
 
 // res = in - K v in FP64, matrix-free: K v = W v + J^T D J v + delta_p v over
 // every row of g (dynamics pairs and bounds). rows: NSLOT per stage of scratch.
-__device__ void kresid(const Group &G, const Inst<double> &I, const double *in, const double *v,
+__device__ __noinline__ void kresid(const Group &G, const Inst<double> &I, const double *in, const double *v,
                        double *res, double *rows, double delta_p) {
   const int i = G.lane;
   eval_rows<double>(G, I, v, nullptr, 0.0, 0.0, rows, false);  // J v
@@ -405,7 +405,7 @@ __device__ bool ksolve(const Group &G, const Views &V, bool f32, const double *i
 
 // One Newton direction with complementarity target w (nullptr: zero); returns
 // false when an FP32 solve missed its tolerance.
-__device__ bool direction(const Group &G, const Views &V, const double *w, bool f32,
+__device__ __noinline__ bool direction(const Group &G, const Views &V, const double *w, bool f32,
                           double delta_p) {
   const Inst<double> &I = V.d;
   const int i = G.lane;
