@@ -190,6 +190,22 @@ IPM_API ipm_status ipm_create(int32_t n, int32_t m, const int64_t *h_j_rowptr, c
                       const int64_t *h_w_colptr, const int32_t *h_w_row, const double *h_l,
                       const double *h_u, const ipm_options *opts, void *stream, ipm_ctx **out);
 
+/* The pattern of a problem as one argument: J (m x n, CSR), W (lower CSC, both
+ * pointers NULL for an LP) and the bounds (length n, NULL = none, +-INFINITY
+ * allowed), all host memory. */
+typedef struct {
+  const int64_t *j_rowptr;
+  const int32_t *j_col;
+  const int64_t *w_colptr;
+  const int32_t *w_row;
+  const double *l, *u;
+} ipm_pattern;
+
+/* ipm_create with the pattern given as one struct (copied; no pointer kept).
+ * Errors: IPM_ERR_ARG for p == NULL; otherwise as ipm_create. */
+IPM_API ipm_status ipm_create_pattern(int32_t n, int32_t m, const ipm_pattern *p,
+                                      const ipm_options *opts, void *stream, ipm_ctx **out);
+
 /* Replace the options of a context (copied). Takes effect at the next call;
  * storage_fp64 is read by kkt_analyze only. Errors: IPM_ERR_ARG for NULL. */
 IPM_API ipm_status ipm_set_options(ipm_ctx *ctx, const ipm_options *opts);
@@ -408,6 +424,23 @@ IPM_API ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *p, int64_t *h_jrowpt
 IPM_API ipm_status ipm_solve_grid_nlp(ipm_ctx *ctx, const ipm_grid_nlp *p, const double *d_ut,
                                       double *d_x, double *d_s, double *d_lambda,
                                       ipm_result *res);
+
+/* One problem for ipm_solve_problem: an LP or QP (the values of J, b, c and
+ * W on the context's pattern, device memory, d_wvals NULL for an LP) or the
+ * grid NLP (its parameters, host, and the target d_ut, device). */
+typedef enum { IPM_PROBLEM_LPQP = 0, IPM_PROBLEM_GRID_NLP = 1 } ipm_problem_kind;
+typedef struct {
+  int32_t kind; /* ipm_problem_kind */
+  const double *d_jvals, *d_b, *d_c, *d_wvals;
+  const ipm_grid_nlp *nlp;
+  const double *d_ut;
+} ipm_problem;
+
+/* Solve one problem: ipm_solve for IPM_PROBLEM_LPQP, ipm_solve_grid_nlp for
+ * IPM_PROBLEM_GRID_NLP, with the same outputs. Errors: IPM_ERR_ARG for NULL
+ * or an unknown kind; otherwise those of the call it makes. */
+IPM_API ipm_status ipm_solve_problem(ipm_ctx *ctx, const ipm_problem *p, double *d_x, double *d_s,
+                                     double *d_lambda, ipm_result *res);
 
 /* --- learned correction of a stale factor --------------------------------
  * Not in the paper (its iterative-solver discussion in Sec. 1 is the nearest

@@ -35,7 +35,8 @@ EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze
             "ipm_learned_weights", "ipm_learned_sample", "ipm_learned_loss_grad",
             "ipm_learned_train", "ipm_symbolic_batched_workspace", "ipm_symbolic_batched",
             "ipm_grid_nlp_sizes", "ipm_grid_nlp_pattern",
-            "ipm_solve_grid_nlp", "ipm_last_error", "ipm_destroy"]
+            "ipm_solve_grid_nlp", "ipm_create_pattern", "ipm_solve_problem", "ipm_last_error",
+            "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -138,6 +139,8 @@ def load() -> C.CDLL:
         "ipm_grid_nlp_sizes": (I32, [P, P, P, P]),
         "ipm_grid_nlp_pattern": (I32, [P] * 7),
         "ipm_solve_grid_nlp": (I32, [P] * 7),
+        "ipm_create_pattern": (I32, [I32, I32, P, P, P, P]),
+        "ipm_solve_problem": (I32, [P, P, P, P, P, P]),
         "ipm_last_error": (C.c_char_p, [P]),
         "ipm_destroy": (None, [P]),
     }
@@ -179,6 +182,35 @@ def _dp(t):
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return C.c_void_p(t.data_ptr())
+
+
+class PatternDesc(C.Structure):
+    """ipm_pattern (host pointers)."""
+    _fields_ = [("j_rowptr", C.c_void_p), ("j_col", C.c_void_p), ("w_colptr", C.c_void_p),
+                ("w_row", C.c_void_p), ("l", C.c_void_p), ("u", C.c_void_p)]
+
+
+class ProblemDesc(C.Structure):
+    """ipm_problem (device pointers; nlp: host ipm_grid_nlp)."""
+    _fields_ = [("kind", C.c_int32), ("d_jvals", C.c_void_p), ("d_b", C.c_void_p),
+                ("d_c", C.c_void_p), ("d_wvals", C.c_void_p), ("nlp", C.c_void_p),
+                ("d_ut", C.c_void_p)]
+
+
+def ipm_create_pattern(n, m, j_rowptr, j_col, l=None, u=None, w_colptr=None, w_row=None,
+                       options: "Options | None" = None):
+    """ipm_create_pattern: returns the raw context handle (c_void_p) and the
+    host arrays it was built from; release it with ipm_destroy."""
+    lib = load()
+    keep = [_np(j_rowptr, np.int64), _np(j_col, np.int32), _np(w_colptr, np.int64),
+            _np(w_row, np.int32), _np(l, np.float64), _np(u, np.float64)]
+    p = PatternDesc(*[_hp(a) for a in keep])
+    o = options if options is not None else default_options()
+    h = C.c_void_p()
+    st = lib.ipm_create_pattern(int(n), int(m), C.byref(p), C.byref(o), None, C.byref(h))
+    if st != 0:
+        raise IpmError(st, "")
+    return h, keep
 
 
 class IpmContext:
@@ -266,6 +298,22 @@ class IpmContext:
         res = Result()
         st = self._lib.ipm_solve(self.handle, _dp(jvals), _dp(b), _dp(c), _dp(wvals), _dp(x),
                                  _dp(s), _dp(lam), C.byref(res))
+        if raise_on_error:
+            self._check(st)
+        return res
+
+    def ipm_solve_problem(self, x, s, lam, jvals=None, b=None, c=None, wvals=None, nlp=None,
+                          ut=None, raise_on_error=False) -> Result:
+        """ipm_solve_problem: an LP/QP (jvals, b, c, wvals) or, with nlp (an
+        ipm_grid_nlp struct) and ut, the grid NLP."""
+        p = ProblemDesc()
+        if nlp is None:
+            p.kind, p.d_jvals, p.d_b, p.d_c, p.d_wvals = 0, _dp(jvals), _dp(b), _dp(c), _dp(wvals)
+        else:
+            p.kind, p.nlp, p.d_ut = 1, C.cast(C.pointer(nlp), C.c_void_p), _dp(ut)
+        res = Result()
+        st = self._lib.ipm_solve_problem(self.handle, C.byref(p), _dp(x), _dp(s), _dp(lam),
+                                         C.byref(res))
         if raise_on_error:
             self._check(st)
         return res

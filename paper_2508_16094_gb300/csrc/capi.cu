@@ -880,6 +880,12 @@ void ipm_default_options(ipm_options *o) {
   o->formulation = IPM_FORM_PRIMAL;
 }
 
+ipm_status ipm_create_pattern(int32_t n, int32_t m, const ipm_pattern *p, const ipm_options *opts,
+                              void *stream, ipm_ctx **out) {
+  if (!p) return IPM_ERR_ARG;
+  return ipm_create(n, m, p->j_rowptr, p->j_col, p->w_colptr, p->w_row, p->l, p->u, opts, stream, out);
+}
+
 ipm_status ipm_create(int32_t n, int32_t m, const int64_t *jp, const int32_t *ji,
                       const int64_t *wp, const int32_t *wi, const double *l, const double *u,
                       const ipm_options *opts, void *stream, ipm_ctx **out) {
@@ -1612,6 +1618,16 @@ ipm_status ipm_grid_nlp_pattern(const ipm_grid_nlp *pp, int64_t *h_jrowptr, int3
     return IPM_ERR_NOMEM;
   }
   return IPM_OK;
+}
+
+ipm_status ipm_solve_problem(ipm_ctx *c, const ipm_problem *p, double *x, double *s, double *lam,
+                             ipm_result *res) {
+  if (!c || !p) return IPM_ERR_ARG;
+  switch (p->kind) {
+    case IPM_PROBLEM_LPQP: return ipm_solve(c, p->d_jvals, p->d_b, p->d_c, p->d_wvals, x, s, lam, res);
+    case IPM_PROBLEM_GRID_NLP: return ipm_solve_grid_nlp(c, p->nlp, p->d_ut, x, s, lam, res);
+    default: return IPM_ERR_ARG;
+  }
 }
 
 ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *ut, double *x,

@@ -162,3 +162,24 @@ def test_dual_formulation_rejects_a_full_hessian(lib):
     with pytest.raises(gb.IpmError) as e:
         ctx.kkt_analyze(None)
     assert e.value.status == 10  # IPM_ERR_UNSUPPORTED
+
+
+def test_create_pattern_matches_create():
+    """ipm_create_pattern (the pattern as one struct) builds the same context
+    as ipm_create: identical symbolic analysis, and a NULL pattern is refused."""
+    lp = gen.grid_lp(6, 5, 4, seed=7)
+    perm = np.ascontiguousarray(gen.nd_order_grid3d(6, 5, 4), dtype=np.int32)
+    h, keep = gb.ipm_create_pattern(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u)
+    lib = gb.load()
+    try:
+        info = gb.SymbolicInfo()
+        assert lib.kkt_analyze(h, perm.ctypes.data_as(C.c_void_p), C.byref(info)) == 0
+        ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u)
+        ref = ctx.kkt_analyze(perm)
+        for f in ("n", "nnz_l", "nsuper", "nlevels", "flops", "workspace_bytes"):
+            assert getattr(info, f) == getattr(ref, f), f
+    finally:
+        lib.ipm_destroy(h)
+    out = C.c_void_p()
+    o = gb.default_options()
+    assert lib.ipm_create_pattern(4, 4, None, C.byref(o), None, C.byref(out)) == 1

@@ -201,3 +201,34 @@ def test_small_lp_workload():
     res = ctx.ipm_solve(dev(lp.val), dev(lp.b), dev(lp.c), x, s, lam)
     assert res.status == 0 and res.kkt <= 1e-8
     assert abs(res.objective - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+
+
+def test_solve_problem_matches_ipm_solve():
+    """ipm_solve_problem with an LP description gives ipm_solve's result bit
+    for bit (the same path), and refuses an unknown kind."""
+    lp = gen.grid_lp(8, seed=41)
+    perm = gen.nd_order_grid3d(8)
+    out = []
+    for use_struct in (False, True):
+        ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u,
+                            options=gb.default_options(precision=gb.IPM_TF32X3, storage_fp64=0,
+                                                       tol=1e-8))
+        ctx.kkt_analyze(perm)
+        ctx.ipm_set_workspace()
+        x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+        s = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        lam = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        jv, b, c = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (lp.val, lp.b, lp.c))
+        if use_struct:
+            res = ctx.ipm_solve_problem(x, s, lam, jvals=jv, b=b, c=c)
+            p = gb.ProblemDesc()
+            p.kind = 7
+            assert ctx._lib.ipm_solve_problem(ctx.handle, gb.C.byref(p), gb._dp(x), gb._dp(s),
+                                              gb._dp(lam), None) == 1
+        else:
+            res = ctx.ipm_solve(jv, b, c, x, s, lam)
+        assert res.status == 0
+        out.append((res.objective, res.iterations, x.cpu().numpy()))
+        ctx.close()
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][2], out[1][2])
