@@ -66,6 +66,7 @@ struct Inst {
   const double *A, *B, *Q, *R, *x0;
   double *z, *dz, *rhs, *tv, *corr, *res;  // 16 per stage
   double *s, *lam, *D, *g, *w, *ds, *dl;   // NSLOT per stage
+  double *il;                              // NSLOT per stage: 1 / lambda of the iteration
   double *Kd, *Ko;                         // 256 per stage (row-major)
   TF *Kf, *Kof;                            // the same storage as K blocks of type TF
   TF *Ld, *Lo;                             // 256 per stage (row-major)
@@ -96,7 +97,8 @@ __device__ Inst<TF> make_inst(const MpcArgs &a, int inst) {
   I.w = I.g + T * NSLOT;
   I.ds = I.w + T * NSLOT;
   I.dl = I.ds + T * NSLOT;
-  I.Kd = I.dl + T * NSLOT;
+  I.il = I.dl + T * NSLOT;
+  I.Kd = I.il + T * NSLOT;
   I.Ko = I.Kd + T * 256;
   I.Kf = reinterpret_cast<TF *>(I.Kd);
   I.Kof = reinterpret_cast<TF *>(I.Ko);
@@ -414,7 +416,7 @@ __device__ __noinline__ bool direction(const Group &G, const Views &V, const dou
     for (int kind = 0; kind < 4; kind++) {
       const int q = k * NSLOT + kind * 16 + i;
       if (!row_valid(kind, i)) { I.ds[q] = 0.0; continue; }
-      const double wl = w ? w[q] / I.lam[q] : 0.0;
+      const double wl = w ? w[q] * I.il[q] : 0.0;
       I.ds[q] = I.D[q] * (I.g[q] - wl) - I.lam[q];
     }
   __syncwarp(G.mask);
@@ -429,27 +431,31 @@ __device__ __noinline__ bool direction(const Group &G, const Views &V, const dou
     for (int kind = 0; kind < 4; kind++) {
       const int q = k * NSLOT + kind * 16 + i;
       if (!row_valid(kind, i)) { I.dl[q] = 0.0; I.ds[q] = 0.0; continue; }
-      const double wl = w ? w[q] / I.lam[q] : 0.0;
+      const double wl = w ? w[q] * I.il[q] : 0.0;
       const double d = I.D[q] * (wl - I.g[q] - I.dl[q]);
       I.dl[q] = d;
-      I.ds[q] = -I.s[q] + wl - (I.s[q] / I.lam[q]) * d;
+      I.ds[q] = -I.s[q] + wl - (I.s[q] * I.il[q]) * d;
     }
   __syncwarp(G.mask);
   return true;
 }
 
-// largest step in (0, 1] keeping v + alpha dv >= (1 - tau) v, for s and lambda
+// largest step in (0, 1] keeping v + alpha dv >= (1 - tau) v, for s and lambda.
+// The smallest ratio v / (-dv) of each lane is tracked as a fraction (n, d),
+// compared by cross products (all factors positive), and divided out once.
 __device__ void step_lengths(const Group &G, const Inst<double> &I, double tau, double &ap,
                              double &ad) {
-  double mp = DBL_MAX, md = DBL_MAX;
+  double pn = 1.0, pd = 0.0, dn = 1.0, dd = 0.0;  // (1, 0): no bound yet
   const int i = G.lane;
   for (int k = 0; k < I.T; k++)
     for (int kind = 0; kind < 4; kind++) {
       if (!row_valid(kind, i)) continue;
       const int q = k * NSLOT + kind * 16 + i;
-      if (I.ds[q] < 0.0) mp = fmin(mp, -I.s[q] / I.ds[q]);
-      if (I.dl[q] < 0.0) md = fmin(md, -I.lam[q] / I.dl[q]);
+      const double ds = I.ds[q], dl = I.dl[q];
+      if (ds < 0.0 && I.s[q] * pd < pn * -ds) { pn = I.s[q]; pd = -ds; }
+      if (dl < 0.0 && I.lam[q] * dd < dn * -dl) { dn = I.lam[q]; dd = -dl; }
     }
+  double mp = pd > 0.0 ? pn / pd : DBL_MAX, md = dd > 0.0 ? dn / dd : DBL_MAX;
   mp = min16(G, mp);
   md = min16(G, md);
   ap = fmin(1.0, tau * mp);
@@ -517,7 +523,10 @@ __device__ void solve_instance(const Group &G, const MpcArgs &a, int inst, bool 
     for (int k = 0; k < T; k++)
       for (int kind = 0; kind < 4; kind++) {
         const int q = k * NSLOT + kind * 16 + i;
-        I.D[q] = row_valid(kind, i) ? 1.0 / (a.delta_d + I.s[q] / I.lam[q]) : 0.0;
+        // one division per row and iteration: 1 / lambda, kept for the directions
+        const double il = row_valid(kind, i) ? 1.0 / I.lam[q] : 0.0;
+        I.il[q] = il;
+        I.D[q] = row_valid(kind, i) ? 1.0 / (a.delta_d + I.s[q] * il) : 0.0;
       }
     __syncwarp(G.mask);
     bool fok = false;

@@ -7,7 +7,7 @@ namespace gipm {
 
 // Workspace doubles per stage: 6 vectors x 16, 7 row arrays x 64 slots, two
 // FP64 16x16 blocks (K) and two 16x16 blocks of the factor (sized for FP64).
-constexpr int64_t kMpcStageDoubles = 6 * 16 + 7 * 64 + 2 * 256 + 2 * 256;
+constexpr int64_t kMpcStageDoubles = 6 * 16 + 8 * 64 + 2 * 256 + 2 * 256;
 
 struct MpcArgs {
   int count;
