@@ -69,7 +69,7 @@ struct Inst {
   double *il;                              // NSLOT per stage: 1 / lambda of the iteration
   double *Kd, *Ko;                         // 256 per stage (row-major)
   TF *Kf, *Kof;                            // the same storage as K blocks of type TF
-  TF *Ld, *Lo;                             // 256 per stage (row-major)
+  TF *Ld, *Lo;                             // 256 per stage (row-major; Ld keeps 1 / L_ii on its diagonal)
 };
 
 template <typename TF>
@@ -243,7 +243,8 @@ __device__ __noinline__ bool factor(const Group &G, const Inst<TF> &I, int &pert
         srow[c] -= acc;
       }
     }
-    // Cholesky of S, rows in registers
+    // Cholesky of S, rows in registers; lane i keeps 1 / L_ii (rdg)
+    TF rdg = TF(0);
 #pragma unroll
     for (int j = 0; j < NS; j++) {
       TF piv = bcast(G, srow[j], j);
@@ -252,9 +253,12 @@ __device__ __noinline__ bool factor(const Group &G, const Inst<TF> &I, int &pert
         else perturbed++;
         piv = sizeof(TF) == 8 ? TF(1) : big_piv<TF>();
       }
-      const TF ljj = sqrt(piv);
-      if (i == j) srow[j] = ljj;
-      if (i > j) srow[j] /= ljj;
+      const TF ljj = sqrt(piv), rjj = TF(1) / ljj;
+      if (i == j) {
+        srow[j] = ljj;
+        rdg = rjj;
+      }
+      if (i > j) srow[j] *= rjj;
       const TF lij = srow[j];
 #pragma unroll
       for (int c = j + 1; c < NS; c++) {
@@ -264,7 +268,7 @@ __device__ __noinline__ bool factor(const Group &G, const Inst<TF> &I, int &pert
     }
     TF *ld = I.Ld + (int64_t)k * 256 + i * NS;
 #pragma unroll
-    for (int c = 0; c < NS; c++) ld[c] = c <= i ? srow[c] : TF(0);
+    for (int c = 0; c < NS; c++) ld[c] = c < i ? srow[c] : (c == i ? rdg : TF(0));  // diagonal: 1 / L_ii
     if (k + 1 < I.T) {  // L_{k+1,k} = Ko_{k+1} L_kk^{-T}: row i by forward substitution
       const TF *ko = I.Kof + (int64_t)(k + 1) * 256 + i * NS;
       TF x[NS];
@@ -273,7 +277,7 @@ __device__ __noinline__ bool factor(const Group &G, const Inst<TF> &I, int &pert
         TF v = TF(ko[c]);
 #pragma unroll
         for (int m = 0; m < c; m++) v -= x[m] * bcast(G, srow[m], c);
-        x[c] = v / bcast(G, srow[c], c);
+        x[c] = v * bcast(G, rdg, c);
       }
       TF *lop = I.Lo + (int64_t)(k + 1) * 256 + i * NS;
 #pragma unroll
@@ -306,7 +310,7 @@ __device__ __noinline__ void block_solve(const Group &G, const Inst<TF> &I, cons
     TF y = TF(0);
 #pragma unroll
     for (int j = 0; j < NS; j++) {
-      const TF yj = bcast(G, t / lrow[j], j);  // lane j: t_j / L_jj
+      const TF yj = bcast(G, t * lrow[j], j);  // lane j: t_j / L_jj (the diagonal holds 1 / L_jj)
       if (i == j) y = yj;
       if (i > j) t -= lrow[j] * yj;
     }
@@ -328,7 +332,7 @@ __device__ __noinline__ void block_solve(const Group &G, const Inst<TF> &I, cons
     TF x = TF(0);
 #pragma unroll
     for (int j = NS - 1; j >= 0; j--) {
-      const TF xj = bcast(G, t / lcol[j], j);  // lane j: t_j / L_jj
+      const TF xj = bcast(G, t * lcol[j], j);  // lane j: t_j / L_jj (the diagonal holds 1 / L_jj)
       if (i == j) x = xj;
       if (i < j) t -= lcol[j] * xj;
     }
