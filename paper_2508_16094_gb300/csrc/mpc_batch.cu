@@ -527,10 +527,17 @@ __device__ void solve_instance(const Group &G, const MpcArgs &a, int inst, bool 
     for (int k = 0; k < T; k++)
       for (int kind = 0; kind < 4; kind++) {
         const int q = k * NSLOT + kind * 16 + i;
-        // one division per row and iteration: 1 / lambda, kept for the directions
-        const double il = row_valid(kind, i) ? 1.0 / I.lam[q] : 0.0;
-        I.il[q] = il;
-        I.D[q] = row_valid(kind, i) ? 1.0 / (a.delta_d + I.s[q] * il) : 0.0;
+        // one division per row and iteration: with t = delta_d lambda + s and
+        // r = 1 / (lambda t), 1 / lambda = t r (kept for the directions) and
+        // D = 1 / (delta_d + s / lambda) = lambda^2 r
+        if (row_valid(kind, i)) {
+          const double lm = I.lam[q], t = fma(a.delta_d, lm, I.s[q]), r = 1.0 / (lm * t);
+          I.il[q] = t * r;
+          I.D[q] = (lm * lm) * r;
+        } else {
+          I.il[q] = 0.0;
+          I.D[q] = 0.0;
+        }
       }
     __syncwarp(G.mask);
     bool fok = false;
