@@ -266,6 +266,88 @@ def nlp_measure(N: int, max_iter: int = 150):
     return out
 
 
+def learned_sweep(G: int, n_train: int = 64, n_test: int = 16, first_seed: int = 3001):
+    """The learned correction's seed sweep on the G^3 member of the grid-LP
+    family: the network is trained on the interior-point iterates of n_train
+    seeds (staleness 1-3, 4 probes per sample), then n_test held-out seeds are
+    solved from the cold start to KKT <= 1e-6 with the FP64 factor, the
+    split-TF32 factor refactored every iteration, and the latter with the
+    learned skip (learned = 1) and with the uncorrected stale factor (the
+    E = 0 ablation, learned = 2). Per form: refactorisations skipped, the
+    times, and their shifted geometric mean (shift 10 s, SGM10)."""
+    import torch
+    import paper_2508_16094_gb300 as gb
+    from paper_2508_16094_gb300 import learned as GL
+    perm = gen.nd_order_grid3d(G)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    lp0 = gen.grid_lp(G, seed=first_seed)
+
+    def mk(**kw):
+        ctx = gb.IpmContext(lp0.n, lp0.m, lp0.rowptr, lp0.col, lp0.l, lp0.u,
+                            options=gb.default_options(tol=1e-6, max_iter=200, **kw))
+        ctx.kkt_analyze(perm)
+        ctx.ipm_set_workspace()
+        return ctx
+
+    def run(ctx, jv, b, c, **kw):
+        ctx.ipm_set_options(warm_start=0, **kw)
+        x = torch.empty(lp0.n, dtype=torch.float64, device="cuda")
+        s = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        lam = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.ipm_solve(jv, b, c, x, s, lam)
+        torch.cuda.synchronize()
+        return {"s": time.perf_counter() - t0, "status": int(r.status), "iters": int(r.iterations),
+                "fact": int(r.factorizations), "skips": int(r.learned_skips),
+                "pcg": int(r.pcg_steps), "obj": r.objective}
+
+    ctx = mk(precision=gb.IPM_TF32X3, storage_fp64=0, learned_probes=4)
+    t0 = time.perf_counter()
+    samples = []
+    train = [first_seed + k for k in range(n_train)]
+    test = [first_seed + n_train + k for k in range(n_test)]
+    for sd in train:
+        lp = gen.grid_lp(G, seed=sd)
+        jv, b, c = dev(lp.val), dev(lp.b), dev(lp.c)
+        traj = GL.trajectory(ctx, jv, b, c, 60)
+        samples += GL.collect(ctx, jv, b, c, traj, staleness=(1, 2, 3), seed=sd)
+    t_collect = time.perf_counter() - t0
+    hist = GL.train(ctx, samples, epochs=30, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0 - t_collect
+    n_samples = len(samples)
+    del samples
+    c64 = mk(precision=gb.IPM_FP64, storage_fp64=1)
+    lpw = gen.grid_lp(G, seed=test[0])
+    run(c64, dev(lpw.val), dev(lpw.b), dev(lpw.c), max_iter=1)  # first touch
+    run(ctx, dev(lpw.val), dev(lpw.b), dev(lpw.c), max_iter=1, learned=0)
+    forms = {"fp64": (c64, {}), "tf32x3": (ctx, {"learned": 0}),
+             "tf32x3_learned": (ctx, {"learned": 1}), "tf32x3_stale_E0": (ctx, {"learned": 2})}
+    per = {k: [] for k in forms}
+    for sd in test:
+        lp = gen.grid_lp(G, seed=sd)
+        jv, b, c = dev(lp.val), dev(lp.b), dev(lp.c)
+        for name, (cx, kw) in forms.items():
+            per[name].append(run(cx, jv, b, c, max_iter=200, **kw))
+    c64.close()
+    ctx.close()
+    out = {"workload": f"grid LP {G}^3 family (n={lp0.n}): network trained on {n_train} seeds "
+                       f"({n_samples} samples), evaluated on {n_test} held-out seeds to KKT <= 1e-6",
+           "collect_s": round(t_collect, 1), "train_s": round(t_train, 1),
+           "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]}
+    ref = [r["obj"] for r in per["fp64"]]
+    for name, rs in per.items():
+        ts = np.array([r["s"] for r in rs])
+        out[name] = {"sgm10_s": round(float(np.exp(np.mean(np.log(ts + 10.0))) - 10.0), 4),
+                     "mean_s": round(float(ts.mean()), 4), "converged": int(sum(r["status"] == 0 for r in rs)),
+                     "refactorisations": int(sum(r["fact"] for r in rs)),
+                     "skips": int(sum(r["skips"] for r in rs)), "pcg": int(sum(r["pcg"] for r in rs)),
+                     "iterations": int(sum(r["iters"] for r in rs)),
+                     "max_obj_rel_diff_vs_fp64": float(f"{max(abs(r['obj'] - o) / max(1.0, abs(o)) for r, o in zip(rs, ref)):.2e}")}
+    return out
+
+
 def world():
     """(world size, rank) from the launcher's environment (no process group:
     neither arm exchanges data between ranks)."""
@@ -556,6 +638,9 @@ def run_ours(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--learned-sweep", type=int, default=0, metavar="G",
+                    help="only run the learned correction's seed sweep on the G^3 grid-LP family "
+                         "(64 training and 16 held-out seeds) and print its JSON line")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -573,6 +658,11 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank = world()
+    if args.learned_sweep > 0:
+        import paper_2508_16094_gb300 as gb
+        gb.build()
+        print(json.dumps({"learned_sweep": learned_sweep(args.learned_sweep)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
     else:
