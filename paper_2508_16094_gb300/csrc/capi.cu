@@ -56,6 +56,7 @@ struct ipm_ctx {
   bool lb_on = false;           // learned buffers sized for n (fixed by the layout)
   bool nlp_grad = false;        // direction(): cc is the whole gradient (no W x term)
   bool bwd_measure = false;     // do_solve: normwise backward error instead of ||r|| / ||b||
+  bool warm_x = false;          // do_solve: start from the incoming x (x + M^-1 (b - K x))
   double knorm = 0.0;           // ||K||_inf of the assembled matrix (when bwd_measure)
   bool have_stale = false;      // lb.D_old / diag_old / mu[0] describe the held factor
   int refine_override = -1, pcg_override = -1;
@@ -461,8 +462,15 @@ ipm_status do_solve(ipm_ctx *c, const double *b, double *x, int refine, ipm_solv
     bwd = h2[0] / (c->knorm * h2[4] + bn);
     return h2[0] / bn;
   };
-  apply_factor(c, bb, xx, false);
-  double rel = residual(xx);
+  double rel;
+  if (c->warm_x) {  // x holds a nearby solution (the predictor's direction)
+    CK(cudaMemcpyAsync(xx, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    residual(xx);
+    apply_factor(c, r, xx, true);
+  } else {
+    apply_factor(c, bb, xx, false);
+  }
+  rel = residual(xx);
   int iters = 0, used_pcg = 0;
   if (refine != IPM_REFINE_NONE && refine != IPM_REFINE_PCG) {
     double prev = rel;
@@ -1305,7 +1313,15 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       {
         const int64_t pcg0 = c->pcg_steps;
         const bool with_stale = c->learned_active;
+        // the corrector's system differs from the predictor's only in its
+        // right-hand side: its solve starts from the predictor's d_x
+        struct Reset {
+          bool &f;
+          ~Reset() { f = false; }  // also when the direction throws
+        } reset{c->warm_x};
+        c->warm_x = !c->sys && !with_stale;
         stt = direction(c, jv, b, cc, wv, x, s, lam, c->vw, c->vdx, c->vds, c->vdl, &si);
+        c->warm_x = false;
         if (with_stale) res.learned_pcg_steps += (int32_t)(c->pcg_steps - pcg0);
         if (with_stale && (stt != IPM_OK || !(c->last_rel <= o.ir_tol))) {
           stt = refactor();
