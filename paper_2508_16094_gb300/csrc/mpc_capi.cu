@@ -136,17 +136,20 @@ ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t bytes, 
       ipm_mpc_config c = *best;
       c.instances_per_cta = ipc;
       c.ctas = 152 * o * std::max(1, 32 / ipc);
-      // warm once, then time
+      // warm once, then the mean of two timed runs (single runs of the
+      // persistent launch vary by ~10% with the order instances reach SMs)
       ipm_status s = ipm_solve_batched(b, &c, d_work, bytes, tol, max_iter, stream, d_z, d_obj,
                                        d_kkt, d_iters, d_status);
       if (s != IPM_OK) return s;
       cudaEventRecord(e0, st);
-      ipm_solve_batched(b, &c, d_work, bytes, tol, max_iter, stream, d_z, d_obj, d_kkt, d_iters,
-                        d_status);
+      for (int rep = 0; rep < 2; rep++)
+        ipm_solve_batched(b, &c, d_work, bytes, tol, max_iter, stream, d_z, d_obj, d_kkt, d_iters,
+                          d_status);
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) return IPM_ERR_CUDA;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
+      ms *= 0.5f;
       if (h_ms) h_ms[idx] = ms;
       idx++;
       if (ms < best_ms) {
