@@ -426,20 +426,56 @@ IPM_API ipm_status ipm_solve_grid_nlp(ipm_ctx *ctx, const ipm_grid_nlp *p, const
                                       double *d_x, double *d_s, double *d_lambda,
                                       ipm_result *res);
 
+/* A nonlinear problem min f(x) s.t. g_G(x) >= 0 (m general rows), l <= x <= u
+ * (Sec. 1, problem (1)) given by evaluation callbacks on the context's
+ * patterns (J: m x n from ipm_create; W: its lower CSC pattern of the Hessian
+ * of the Lagrangian). The callbacks run the caller's device code on `stream`
+ * (the context's stream) and return 0 on success; any other value ends the
+ * solve with IPM_ERR_NUMERIC.
+ *   eval(user, d_x, d_f, d_grad, d_g, d_jvals): at x (n), f (one device
+ *     double), grad f (n), g_G(x) (m) and the values of J = dg_G/dx in the
+ *     pattern's CSR order;
+ *   hess(user, d_x, d_lambda, d_wvals): the values, in W's pattern order, of
+ *     the Hessian of f - lambda_G^T g_G at x, lambda_G = the first m entries of
+ *     d_lambda. */
+typedef struct {
+  void *user;
+  int32_t (*eval)(void *user, const double *d_x, double *d_f, double *d_grad, double *d_g,
+                  double *d_jvals, void *stream);
+  int32_t (*hess)(void *user, const double *d_x, const double *d_lambda, double *d_wvals,
+                  void *stream);
+} ipm_nlp;
+
+/* The interior-point method for a nonlinear problem through its callbacks,
+ * with the rules of ipm_solve_grid_nlp (monotone barrier, common step with
+ * the l1-merit backtracking, inertia by regularisation, the low-precision
+ * ladder with the take-back of a step that made the KKT residual grow
+ * tenfold, acceptance on the normwise backward error). The starting point is
+ * the box midpoint (1 inside a one-sided bound, 0 without bounds); the KKT
+ * residual scales the primal part by the largest finite bound (at least 1).
+ * Outputs and errors as ipm_solve; allocates 3 n + 6 m_tot + nnz(J) + nnz(W)
+ * doubles on the context's stream for the call. Grid NLP: ipm_solve_grid_nlp
+ * is this solver with the library's own evaluation kernels. */
+IPM_API ipm_status ipm_solve_nlp(ipm_ctx *ctx, const ipm_nlp *p, double *d_x, double *d_s,
+                                 double *d_lambda, ipm_result *res);
+
 /* One problem for ipm_solve_problem: an LP or QP (the values of J, b, c and
- * W on the context's pattern, device memory, d_wvals NULL for an LP) or the
- * grid NLP (its parameters, host, and the target d_ut, device). */
-typedef enum { IPM_PROBLEM_LPQP = 0, IPM_PROBLEM_GRID_NLP = 1 } ipm_problem_kind;
+ * W on the context's pattern, device memory, d_wvals NULL for an LP), the
+ * grid NLP (its parameters, host, and the target d_ut, device) or a
+ * nonlinear problem given by callbacks (fns). */
+typedef enum { IPM_PROBLEM_LPQP = 0, IPM_PROBLEM_GRID_NLP = 1, IPM_PROBLEM_NLP = 2 } ipm_problem_kind;
 typedef struct {
   int32_t kind; /* ipm_problem_kind */
   const double *d_jvals, *d_b, *d_c, *d_wvals;
   const ipm_grid_nlp *nlp;
   const double *d_ut;
+  const ipm_nlp *fns;
 } ipm_problem;
 
 /* Solve one problem: ipm_solve for IPM_PROBLEM_LPQP, ipm_solve_grid_nlp for
- * IPM_PROBLEM_GRID_NLP, with the same outputs. Errors: IPM_ERR_ARG for NULL
- * or an unknown kind; otherwise those of the call it makes. */
+ * IPM_PROBLEM_GRID_NLP, ipm_solve_nlp for IPM_PROBLEM_NLP, with the same
+ * outputs. Errors: IPM_ERR_ARG for NULL or an unknown kind; otherwise those of
+ * the call it makes. */
 IPM_API ipm_status ipm_solve_problem(ipm_ctx *ctx, const ipm_problem *p, double *d_x, double *d_s,
                                      double *d_lambda, ipm_result *res);
 

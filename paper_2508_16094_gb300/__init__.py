@@ -35,8 +35,8 @@ EXPORTED = ["ipm_default_options", "ipm_create", "ipm_set_options", "kkt_analyze
             "ipm_learned_weights", "ipm_learned_sample", "ipm_learned_loss_grad",
             "ipm_learned_train", "ipm_symbolic_batched_workspace", "ipm_symbolic_batched",
             "ipm_grid_nlp_sizes", "ipm_grid_nlp_pattern",
-            "ipm_solve_grid_nlp", "ipm_create_pattern", "ipm_solve_problem", "ipm_last_error",
-            "ipm_destroy"]
+            "ipm_solve_grid_nlp", "ipm_create_pattern", "ipm_solve_problem", "ipm_solve_nlp",
+            "ipm_last_error", "ipm_destroy"]
 
 
 class IpmError(RuntimeError):
@@ -141,6 +141,7 @@ def load() -> C.CDLL:
         "ipm_solve_grid_nlp": (I32, [P] * 7),
         "ipm_create_pattern": (I32, [I32, I32, P, P, P, P]),
         "ipm_solve_problem": (I32, [P, P, P, P, P, P]),
+        "ipm_solve_nlp": (I32, [P, P, P, P, P, P]),
         "ipm_last_error": (C.c_char_p, [P]),
         "ipm_destroy": (None, [P]),
     }
@@ -191,10 +192,34 @@ class PatternDesc(C.Structure):
 
 
 class ProblemDesc(C.Structure):
-    """ipm_problem (device pointers; nlp: host ipm_grid_nlp)."""
+    """ipm_problem (device pointers; nlp: host ipm_grid_nlp; fns: host ipm_nlp)."""
     _fields_ = [("kind", C.c_int32), ("d_jvals", C.c_void_p), ("d_b", C.c_void_p),
                 ("d_c", C.c_void_p), ("d_wvals", C.c_void_p), ("nlp", C.c_void_p),
-                ("d_ut", C.c_void_p)]
+                ("d_ut", C.c_void_p), ("fns", C.c_void_p)]
+
+
+NLP_EVAL = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                       C.c_void_p, C.c_void_p)
+NLP_HESS = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class NlpDesc(C.Structure):
+    """ipm_nlp: the evaluation callbacks of a nonlinear problem."""
+    _fields_ = [("user", C.c_void_p), ("eval", NLP_EVAL), ("hess", NLP_HESS)]
+
+
+def device_view(ptr, count: int):
+    """A float64 CUDA tensor aliasing `count` doubles of device memory at ptr
+    (no copy), for the callbacks of ipm_solve_nlp."""
+    import torch
+
+    class _Dev:
+        pass
+
+    d = _Dev()
+    d.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8",
+                                  "data": (int(ptr or 0), False), "version": 3}
+    return torch.as_tensor(d, device="cuda")
 
 
 def ipm_create_pattern(n, m, j_rowptr, j_col, l=None, u=None, w_colptr=None, w_row=None,
@@ -314,6 +339,39 @@ class IpmContext:
         res = Result()
         st = self._lib.ipm_solve_problem(self.handle, C.byref(p), _dp(x), _dp(s), _dp(lam),
                                          C.byref(res))
+        if raise_on_error:
+            self._check(st)
+        return res
+
+    def ipm_solve_nlp(self, eval_fn, hess_fn, x, s, lam, raise_on_error=False) -> Result:
+        """ipm_solve_nlp with Python callbacks on torch views of the device
+        arrays: eval_fn(x, f, grad, g, jvals) fills f (1), grad (n), g (m general
+        rows) and jvals (nnz(J)) at x; hess_fn(x, lam, wvals) fills wvals
+        (nnz(W)) at x, lam (m_tot; the first m entries are the general rows').
+        A callback that raises ends the solve with IPM_ERR_NUMERIC."""
+        n, m, m_tot = self.n, self.m, self.m_tot
+        nnz_j = len(self._keep[1]) if self._keep[1] is not None else 0
+        nnz_w = len(self._keep[3]) if self._keep[3] is not None else 0
+
+        def _eval(user, px, pf, pg, pgr, pjv, stream):
+            try:
+                eval_fn(device_view(px, n), device_view(pf, 1), device_view(pg, n),
+                        device_view(pgr, m), device_view(pjv, nnz_j))
+                return 0
+            except Exception:  # reported to the solver as a failed evaluation
+                return 1
+
+        def _hess(user, px, plam, pw, stream):
+            try:
+                hess_fn(device_view(px, n), device_view(plam, m_tot), device_view(pw, nnz_w))
+                return 0
+            except Exception:
+                return 1
+
+        fns = NlpDesc(None, NLP_EVAL(_eval), NLP_HESS(_hess))
+        res = Result()
+        st = self._lib.ipm_solve_nlp(self.handle, C.byref(fns), _dp(x), _dp(s), _dp(lam),
+                                     C.byref(res))
         if raise_on_error:
             self._check(st)
         return res

@@ -2,6 +2,7 @@
 // assembly/factor/solve drivers with FP64 refinement and PCG, and the
 // interior-point iteration.
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cfloat>
 #include <climits>
@@ -1642,44 +1643,43 @@ ipm_status ipm_solve_problem(ipm_ctx *c, const ipm_problem *p, double *x, double
   switch (p->kind) {
     case IPM_PROBLEM_LPQP: return ipm_solve(c, p->d_jvals, p->d_b, p->d_c, p->d_wvals, x, s, lam, res);
     case IPM_PROBLEM_GRID_NLP: return ipm_solve_grid_nlp(c, p->nlp, p->d_ut, x, s, lam, res);
+    case IPM_PROBLEM_NLP: return ipm_solve_nlp(c, p->fns, x, s, lam, res);
     default: return IPM_ERR_ARG;
   }
 }
 
-ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *ut, double *x,
-                              double *s, double *lam, ipm_result *res_out) {
-  if (!c || !pp || !ut || !x || !s || !lam) return IPM_ERR_ARG;
+}  // extern "C"
+
+// The nonlinear interior-point loop (Sec. 3 rules for a general problem; see
+// the header's ipm_solve_nlp) over evaluation callbacks: F.eval(x) writes f
+// (device scalar), grad f (n), the m general rows g_G(x) and J's values in the
+// context's pattern order; F.hess(x, lambda) the values of W (the Hessian of
+// f - lambda_G^T g_G) in the context's W pattern.
+struct NlpFns {
+  std::function<void(const double *x, double *d_f, double *grad, double *grows, double *jv)> eval;
+  std::function<void(const double *x, const double *lam, double *wv)> hess;
+};
+
+ipm_status nlp_solve(ipm_ctx *c, const NlpFns &F, double *x, double *s, double *lam,
+                     ipm_result *res_out, const char *who) {
   ipm_result res{};
   double *scratch = nullptr;
   ipm_status rs = guarded(c, [&]() -> ipm_status {
-    if (c->state < 2) throw Fail{IPM_ERR_STATE, "ipm_solve_grid_nlp before ipm_set_workspace"};
-    if (c->sys) throw Fail{IPM_ERR_UNSUPPORTED, "the grid NLP uses the primal condensed formulation"};
-    GridNlp p;
-    if (!grid_from(pp, p)) throw Fail{IPM_ERR_ARG, "invalid grid NLP parameters"};
+    if (c->state < 2) throw Fail{IPM_ERR_STATE, std::string(who) + " before ipm_set_workspace"};
+    if (c->sys) throw Fail{IPM_ERR_UNSUPPORTED, "the nonlinear solver uses the primal condensed formulation"};
     const Problem &P = c->P;
-    const int64_t NN = p.NN(), n = P.n, m = P.m, mt = P.mt;
-    {  // the context must carry this problem's patterns
-      std::vector<int64_t> rp;
-      std::vector<int32_t> cl;
-      grid_nlp_pattern(p, rp, cl);
-      bool ok = n == 2 * NN && m == 2 * NN && P.jp.size() == rp.size() && P.ji.size() == cl.size() &&
-                std::equal(rp.begin(), rp.end(), P.jp.begin()) &&
-                std::equal(cl.begin(), cl.end(), P.ji.begin()) && (int64_t)P.wp.size() == n + 1;
-      for (int64_t j = 0; ok && j < n; j++)
-        ok = P.wp[j] == j && P.wi[j] == (int32_t)j &&
-             std::isfinite(P.l[j]) == (p.v_bounded && j >= NN) &&
-             std::isfinite(P.u[j]) == (p.v_bounded && j >= NN);
-      if (!ok) throw Fail{IPM_ERR_ARG, "context pattern is not the grid NLP's"};
-    }
+    const int64_t n = P.n, m = P.m, mt = P.mt;
+    (void)m;
     const auto t_start = std::chrono::steady_clock::now();
     const ipm_options &o = c->opts;
     VecOps V = c->vec();
     c->refine_steps = c->pcg_steps = 0;
     const int64_t nnz = (int64_t)P.ji.size();
     c->bwd_measure = true;
-    const size_t words = (size_t)(4 * n + 6 * mt + nnz);
+    const int64_t nw = std::max<int64_t>((int64_t)P.wi.size(), 1);
+    const size_t words = (size_t)(3 * n + 6 * mt + nnz + nw);
     CK(cudaMallocAsync(&scratch, words * sizeof(double), c->st));
-    double *jv = scratch, *hrows = jv + nnz, *grad = hrows + mt, *wv = grad + n, *zero = wv + n,
+    double *jv = scratch, *hrows = jv + nnz, *grad = hrows + mt, *wv = grad + n, *zero = wv + nw,
            *xt = zero + mt, *stv = xt + n, *gt = stv + mt, *keep = gt + mt;  // keep: x, s, lambda
     CK(cudaMemsetAsync(zero, 0, mt * sizeof(double), c->st));
     double *d_f = c->scal + 44, *terms = c->scal + 48;
@@ -1687,8 +1687,8 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       CK(cudaMemcpyAsync(h, d, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
     };
-    auto eval_at = [&](const double *xx, double *gout) {  // f (returned), h, J, grad, g
-      nlp_eval(p, c->dp.jp, xx, ut, hrows, jv, grad, d_f, c->partial, c->st);
+    auto eval_at = [&](const double *xx, double *gout) {  // f (returned), g_G, J, grad, g
+      F.eval(xx, d_f, grad, hrows, jv);
       V.g(hrows, xx, zero, c->dl_, c->du_, gout);
       double f;
       d2h(d_f, &f, 1);
@@ -1698,12 +1698,25 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       CK(cudaMemcpyAsync(reinterpret_cast<char *>(c->sc) + off, &v, sizeof(double),
                          cudaMemcpyHostToDevice, c->st));
     };
-    // starting point
-    CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->st));
+    // starting point: the box midpoint, 1 inside a one-sided bound, else 0
+    {
+      std::vector<double> x0(n);
+      for (int64_t i = 0; i < n; i++) {
+        const bool fl = std::isfinite(P.l[i]), fu = std::isfinite(P.u[i]);
+        x0[i] = fl && fu ? 0.5 * (P.l[i] + P.u[i])
+                         : (fl ? std::max(0.0, P.l[i] + 1.0) : (fu ? std::min(0.0, P.u[i] - 1.0) : 0.0));
+      }
+      CK(cudaMemcpyAsync(x, x0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
     eval_at(x, c->vg);
     V.init_slack(c->vg, s, lam);
     double mu = 0.1, nu = 0.0;
-    const double bscale = p.v_bounded ? std::max(1.0, std::max(std::fabs(p.v_lo), std::fabs(p.v_hi))) : 1.0;
+    double bscale = 1.0;  // largest finite bound (at least 1)
+    for (int64_t i = 0; i < n; i++) {
+      if (std::isfinite(P.l[i])) bscale = std::max(bscale, std::fabs(P.l[i]));
+      if (std::isfinite(P.u[i])) bscale = std::max(bscale, std::fabs(P.u[i]));
+    }
     V.absmax(n, grad, c->scal + 20);
     const double cscale = std::max(1.0, d2h_scalar(c, c->scal + 20));
     res.status = IPM_ERR_MAXITER;
@@ -1770,7 +1783,7 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
       if (std::max(res.primal_res, std::max(res.dual_res, berr / fs)) <= 10.0 * mu)
         mu = std::max(o.tol / 10.0, std::min(0.2 * mu, std::pow(mu, 1.5)));
       // Newton direction with target mu; inertia by regularisation
-      nlp_hess(p, x, lam, wv, c->st);
+      F.hess(x, lam, wv);
       V.scaling(s, lam, o.delta_d, c->vD);
       double delta_p = o.delta_p;
       for (int tries = 0; tries < 12; tries++) {
@@ -1866,6 +1879,53 @@ ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *
     *res_out = res;
   }
   return rs;
+}
+
+extern "C" {
+
+ipm_status ipm_solve_grid_nlp(ipm_ctx *c, const ipm_grid_nlp *pp, const double *ut, double *x,
+                              double *s, double *lam, ipm_result *res_out) {
+  if (!c || !pp || !ut || !x || !s || !lam) return IPM_ERR_ARG;
+  GridNlp p;
+  ipm_status chk = guarded(c, [&]() -> ipm_status {
+    if (!grid_from(pp, p)) throw Fail{IPM_ERR_ARG, "invalid grid NLP parameters"};
+    const Problem &P = c->P;
+    const int64_t NN = p.NN(), n = P.n, m = P.m;
+    std::vector<int64_t> rp;  // the context must carry this problem's patterns
+    std::vector<int32_t> cl;
+    grid_nlp_pattern(p, rp, cl);
+    bool ok = n == 2 * NN && m == 2 * NN && P.jp.size() == rp.size() && P.ji.size() == cl.size() &&
+              std::equal(rp.begin(), rp.end(), P.jp.begin()) &&
+              std::equal(cl.begin(), cl.end(), P.ji.begin()) && (int64_t)P.wp.size() == n + 1;
+    for (int64_t j = 0; ok && j < n; j++)
+      ok = P.wp[j] == j && P.wi[j] == (int32_t)j &&
+           std::isfinite(P.l[j]) == (p.v_bounded && j >= NN) &&
+           std::isfinite(P.u[j]) == (p.v_bounded && j >= NN);
+    if (!ok) throw Fail{IPM_ERR_ARG, "context pattern is not the grid NLP's"};
+    return IPM_OK;
+  });
+  if (chk != IPM_OK) return chk;
+  NlpFns F;
+  F.eval = [&](const double *xx, double *d_f, double *grad, double *grows, double *jv) {
+    nlp_eval(p, c->dp.jp, xx, ut, grows, jv, grad, d_f, c->partial, c->st);
+  };
+  F.hess = [&](const double *xx, const double *lm, double *wv) { nlp_hess(p, xx, lm, wv, c->st); };
+  return nlp_solve(c, F, x, s, lam, res_out, "ipm_solve_grid_nlp");
+}
+
+ipm_status ipm_solve_nlp(ipm_ctx *c, const ipm_nlp *p, double *x, double *s, double *lam,
+                         ipm_result *res_out) {
+  if (!c || !p || !p->eval || !p->hess || !x || !s || !lam) return IPM_ERR_ARG;
+  NlpFns F;
+  F.eval = [&](const double *xx, double *d_f, double *grad, double *grows, double *jv) {
+    if (p->eval(p->user, xx, d_f, grad, grows, jv, c->st) != 0)
+      throw Fail{IPM_ERR_NUMERIC, "the problem's evaluation callback failed"};
+  };
+  F.hess = [&](const double *xx, const double *lm, double *wv) {
+    if (p->hess(p->user, xx, lm, wv, c->st) != 0)
+      throw Fail{IPM_ERR_NUMERIC, "the problem's Hessian callback failed"};
+  };
+  return nlp_solve(c, F, x, s, lam, res_out, "ipm_solve_nlp");
 }
 
 int64_t ipm_kernel_launches(void) { return gipm::launch_counter(); }

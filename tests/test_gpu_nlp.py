@@ -82,6 +82,54 @@ def test_bf16_factor_with_fallback_matches_oracle():
     assert np.all(s > 0) and np.all(lam > 0)
 
 
+def test_callback_nlp_matches_grid_path():
+    """ipm_solve_nlp with the problem given by callbacks (here the oracle's FP64
+    evaluation of the grid NLP, copied to the device) reaches the optimum of
+    the library's own grid-NLP path and of the oracle; a failing callback ends
+    the solve with IPM_ERR_NUMERIC."""
+    P = gen.grid_nlp(16, seed=35)
+    o = gb.default_options(precision=0, tol=1e-8, max_iter=200, storage_fp64=1)
+    G = gb.GridNLP(P.N, perm=gen.nd_order_grid_nlp(P.N), alpha=P.alpha, v_lo=P.v_lo, v_hi=P.v_hi,
+                   cubic=P.cubic, v_bounded=P.v_bounded, options=o)
+    n, mt = G.pat["n"], G.ctx.m_tot
+    m = G.pat["m"]
+
+    def bufs():
+        return (torch.empty(n, dtype=torch.float64, device="cuda"),
+                torch.empty(mt, dtype=torch.float64, device="cuda"),
+                torch.empty(mt, dtype=torch.float64, device="cuda"))
+
+    x1, s1, l1 = bufs()
+    r1 = G.ipm_solve_grid_nlp(dev(P.ut), x1, s1, l1)
+
+    def ev(x, f, grad, g, jv):
+        fx, h, jvals, gr = ON.evaluate(P, x.cpu().numpy())
+        f.copy_(torch.tensor([fx], dtype=torch.float64))
+        grad.copy_(torch.as_tensor(gr))
+        g.copy_(torch.as_tensor(ON.h_rows(h)))
+        jv.copy_(torch.as_tensor(jvals))
+
+    def hs(x, lam, wv):
+        wv.copy_(torch.as_tensor(ON.hessian_diag(P, x.cpu().numpy(), lam.cpu().numpy()[:m])))
+
+    x2, s2, l2 = bufs()
+    r2 = G.ctx.ipm_solve_nlp(ev, hs, x2, s2, l2)
+    ref = _oracle(P)
+    assert r1.status == 0 and r2.status == 0, (r1.as_dict(), r2.as_dict())
+    assert r2.kkt <= 1e-8
+    # a KKT residual of 1e-8 fixes the objective to about that relative accuracy
+    # (the evaluations differ in rounding: numpy on the host against the kernels)
+    assert r2.objective == pytest.approx(r1.objective, rel=1e-7)
+    assert r2.objective == pytest.approx(ref["objective"], rel=1e-6)
+    assert abs(r2.iterations - r1.iterations) <= 2
+
+    def bad(x, f, grad, g, jv):
+        raise RuntimeError("evaluation failed")
+
+    x3, s3, l3 = bufs()
+    assert G.ctx.ipm_solve_nlp(bad, hs, x3, s3, l3).status == 6  # IPM_ERR_NUMERIC
+
+
 def test_rejects_foreign_pattern():
     lp = gen.grid_lp(4, seed=1)
     ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u)
