@@ -34,6 +34,9 @@ import gen  # noqa: E402
 
 METRIC = "time-to-1e-6 KKT residual and factor TFLOP/s: mixed/learned vs FP64 on GB300"
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
+# time-to-1e-6 forms beyond a fixed precision: (precision, CG steps per
+# iteration above which ipm_solve moves to the split TF32 for the rest)
+LADDERS = {"tf32_then_tf32x3": (2, 16)}
 DTYPE = {"fp64": "f64", "fp32": "f32+f64", "tf32": "tf32+f64", "bf16": "bf16+f64",
          "tf32x3": "tf32x3+f64"}
 ORACLE_GRID = 24  # CPU sample: one oracle Newton direction on the 24^3 member of the family
@@ -404,12 +407,14 @@ def record_trajectory(ctx, jv, b, c, x, s, lam, max_iter=200):
     return traj, r
 
 
-def tti_run(ctx, jv, b, c, x, s, lam, prec, ref_obj=None):
+def tti_run(ctx, jv, b, c, x, s, lam, prec, ref_obj=None, cg_escalate=0):
     """Cold start to the 1e-6 KKT residual in one ipm_solve call."""
     import torch
     # TF32/BF16 factors fall back to a split-TF32 refactorisation when their
-    # PCG misses the acceptance tolerance (counted in "fallbacks")
-    ctx.ipm_set_options(max_iter=200, warm_start=0, tol=1e-6, precision=prec, fallback_fp64=1)
+    # PCG misses the acceptance tolerance (counted in "fallbacks"); with
+    # cg_escalate also once an iteration needs more CG steps than that
+    ctx.ipm_set_options(max_iter=200, warm_start=0, tol=1e-6, precision=prec, fallback_fp64=1,
+                        cg_escalate=cg_escalate)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = ctx.ipm_solve(jv, b, c, x, s, lam)
@@ -577,9 +582,14 @@ def run_ours(args, ws, rank):
             if not name or name == args.precision or name == "fp64":
                 continue
             try:
-                tti[name] = tti_run(ctx, jv, b, c, x, s, lam, PREC[name], ref)
+                if name in LADDERS:
+                    p0, esc = LADDERS[name]
+                    tti[name] = tti_run(ctx, jv, b, c, x, s, lam, p0, ref, cg_escalate=esc)
+                else:
+                    tti[name] = tti_run(ctx, jv, b, c, x, s, lam, PREC[name], ref)
             except Exception as e:  # an unsupported precision is reported, not fatal
                 tti[name] = {"error": str(e)[:120]}
+        ctx.ipm_set_options(cg_escalate=0)
 
     mpc = mpc_measure() if not args.no_mpc else None
     forms = forms_measure(args.forms_grid) if args.forms_grid > 0 else None
@@ -647,7 +657,7 @@ def main():
     ap.add_argument("--grid", type=int, default=100)
     ap.add_argument("--precision", choices=list(PREC), default="tf32x3")
     ap.add_argument("--no-tti", dest="tti", action="store_false")
-    ap.add_argument("--tti-forms", default="tf32,bf16",
+    ap.add_argument("--tti-forms", default="tf32,bf16,tf32_then_tf32x3",
                     help="other factor precisions timed to 1e-6 on the bench grid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mpc", action="store_true")

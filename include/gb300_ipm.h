@@ -128,6 +128,11 @@ typedef struct {
                             IPM_FORM_AUGMENTED (4)  [H, A^T; A, -D_G^{-1}] (order n + m,
                                                  quasi-definite, signed LDL^T in FP64/FP32)
                             (IPM_FORM_PRIMAL) */
+  int32_t cg_escalate;   /* with fallback_fp64: an interior-point iteration whose two solves
+                            took more than this many CG steps with a factor below the
+                            fallback arithmetic moves ipm_solve to that arithmetic from the
+                            next iteration on (a cheaper factor no longer pays for its extra
+                            CG steps); counted in ipm_result.fp64_fallbacks. 0: off (0) */
 } ipm_options;
 
 typedef enum {

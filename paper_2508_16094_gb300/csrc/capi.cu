@@ -887,6 +887,7 @@ void ipm_default_options(ipm_options *o) {
   o->learned_probes = 0;
   o->learned_pcg_max = 30;
   o->formulation = IPM_FORM_PRIMAL;
+  o->cg_escalate = 0;
 }
 
 ipm_status ipm_create_pattern(int32_t n, int32_t m, const ipm_pattern *p, const ipm_options *opts,
@@ -1236,6 +1237,7 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       }
       if (res.kkt <= o.tol) { res.status = IPM_OK; break; }
       if (it == o.max_iter) break;
+      const int64_t cg_iter0 = c->pcg_steps + (c->sys ? c->sys->pcg_steps : 0);
       CK(cudaEventRecord(ev[0], c->st));
       V.scaling(s, lam, o.delta_d, c->vD);
       CK(cudaEventRecord(ev[1], c->st));
@@ -1354,6 +1356,17 @@ ipm_status ipm_solve(ipm_ctx *c, const double *jv, const double *b, const double
       }
       V.ftb(s, c->vds, lam, c->vdl, c->scal + 32, c->sc, false);
       V.update(c->sc, x, c->vdx, s, c->vds, lam, c->vdl);
+      {  // cost-driven escalation (cg_escalate): CG steps of this iteration's two solves
+        const int64_t cg_now = c->pcg_steps + (c->sys ? c->sys->pcg_steps : 0);
+        if (o.cg_escalate > 0 && cg_now - cg_iter0 > o.cg_escalate && can_escalate()) {
+          if (o.verbose)
+            std::fprintf(stderr, "ipm it %3d: %lld CG steps, fallback arithmetic from here\n", it,
+                         (long long)(cg_now - cg_iter0));
+          res.fp64_fallbacks++;
+          prec_now = fb_prec;
+          c->have_stale = false;
+        }
+      }
       CK(cudaEventRecord(ev[4], c->st));
       CK(cudaEventSynchronize(ev[4]));
       float ms[4];

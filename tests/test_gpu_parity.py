@@ -232,3 +232,34 @@ def test_solve_problem_matches_ipm_solve():
         ctx.close()
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
+def test_cg_escalation_moves_to_split_tf32_and_matches_oracle():
+    """cg_escalate: a TF32 factor whose iteration needs more CG steps than the
+    limit moves ipm_solve to the split TF32 for the rest (counted once in
+    fp64_fallbacks), and the solve still reaches the oracle's optimum; with the
+    limit off the same TF32 solve never escalates on CG steps."""
+    G = 14
+    lp = gen.grid_lp(G, seed=43)
+    perm = gen.nd_order_grid3d(G)
+    S = oracle.analyze(lp.n, lp.m, lp.rowptr, lp.col, None)
+    ref = oracle.ipm_lp(S, lp, tol=1e-8)
+    out = {}
+    for esc in (0, 2):
+        ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u,
+                            options=gb.default_options(precision=gb.IPM_TF32, storage_fp64=0,
+                                                       tol=1e-8, fallback_fp64=1,
+                                                       cg_escalate=esc))
+        ctx.kkt_analyze(perm)
+        ctx.ipm_set_workspace()
+        x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+        s = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        lam = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        jv, b, c = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (lp.val, lp.b, lp.c))
+        res = ctx.ipm_solve(jv, b, c, x, s, lam)
+        out[esc] = res
+        assert res.status == 0, res.as_dict()
+        assert res.objective == pytest.approx(ref["objective"], rel=1e-6)
+        ctx.close()
+    assert out[2].fp64_fallbacks == 1
+    assert out[2].pcg_steps < out[0].pcg_steps
