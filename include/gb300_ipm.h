@@ -331,10 +331,13 @@ IPM_API ipm_status ipm_solve_batched(const ipm_mpc_batch *b, const ipm_mpc_confi
                                      void *d_work, size_t bytes, double tol, int32_t max_iter,
                                      void *stream, double *d_z, double *d_obj, double *d_kkt,
                                      int32_t *d_iters, int32_t *d_status);
-/* Autotuner: times instances_per_cta in {2, 4, 8, 16} x two grid sizes for the
- * precision in best->precision on this batch (one warm-up solve, then the mean
- * of two timed solves per shape) and writes the fastest shape to best; h_ms
- * (may be NULL) receives the 8 timings in that order. */
+/* Autotuner: times instances_per_cta in {2, 4, 8, 16} x four grid sizes (a
+ * quarter, half, one and two times the CTAs that fill the SMs' lanes; the
+ * smaller grids leave fewer slots than instances, so the work queue balances
+ * uneven horizons) for the precision in best->precision on this batch (one
+ * warm-up solve, then the mean of two timed solves per shape) and writes the
+ * fastest shape to best; h_ms (may be NULL) receives the 16 timings in that
+ * order (float[16]). */
 IPM_API ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t bytes, double tol,
                                     int32_t max_iter, void *stream, double *d_z, double *d_obj,
                                     double *d_kkt, int32_t *d_iters, int32_t *d_status,

@@ -528,7 +528,7 @@ class BatchedMPC:
 
     def ipm_mpc_autotune(self, precision=IPM_FP64, tol=1e-6, max_iter=100):
         cfg = MpcConfig(precision, 8, 0)
-        ms = (C.c_float * 8)()
+        ms = (C.c_float * 16)()
         self._check(self._lib.ipm_mpc_autotune(
             C.byref(self.batch), C.c_void_p(self.wptr), self.wbytes, float(tol), int(max_iter),
             C.c_void_p(self.stream) if self.stream else None, _dp(self.z), _dp(self.obj),

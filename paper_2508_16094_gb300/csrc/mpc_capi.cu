@@ -124,7 +124,10 @@ ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t bytes, 
                             ipm_mpc_config *best, float *h_ms) {
   if (!best) return IPM_ERR_ARG;
   const int ipcs[4] = {2, 4, 8, 16};
-  const int occ[2] = {1, 2};  // persistent CTAs per SM relative to the lane budget
+  // persistent CTAs per SM relative to the lane budget, in quarters: 1 and 2
+  // leave fewer slots than a large batch has instances, so the queue balances
+  // the uneven horizons; 4 and 8 start every instance at once
+  const int occ[4] = {1, 2, 4, 8};
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return IPM_ERR_CUDA;
@@ -135,7 +138,7 @@ ipm_status ipm_mpc_autotune(const ipm_mpc_batch *b, void *d_work, size_t bytes, 
     for (int o : occ) {
       ipm_mpc_config c = *best;
       c.instances_per_cta = ipc;
-      c.ctas = 152 * o * std::max(1, 32 / ipc);
+      c.ctas = std::max(1, 152 * o * std::max(1, 32 / ipc) / 4);
       // warm once, then the mean of two timed runs (single runs of the
       // persistent launch vary by ~10% with the order instances reach SMs)
       ipm_status s = ipm_solve_batched(b, &c, d_work, bytes, tol, max_iter, stream, d_z, d_obj,
