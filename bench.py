@@ -37,6 +37,10 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 # time-to-1e-6 forms beyond a fixed precision: (precision, CG steps per
 # iteration above which ipm_solve moves to the split TF32 for the rest)
 LADDERS = {"tf32_then_tf32x3": (2, 16)}
+# DRAM bytes (read + written) of one factorisation, from a one-pass ncu capture
+# of dram__bytes_read.sum and dram__bytes_write.sum over its launches (this
+# build's kernels), keyed by (grid, precision): the roofline's "traffic"
+FACTOR_TRAFFIC = {(100, "tf32x3"): 430.140e9 + 113.871e9}
 DTYPE = {"fp64": "f64", "fp32": "f32+f64", "tf32": "tf32+f64", "bf16": "bf16+f64",
          "tf32x3": "tf32x3+f64"}
 ORACLE_GRID = 24  # CPU sample: one oracle Newton direction on the 24^3 member of the family
@@ -545,7 +549,7 @@ def run_ours(args, ws, rank):
         peak = 1.25
         bound, peak_note = "alu", "nominal FP64 rate (1.25 TFLOP/s)"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": FACTOR_TRAFFIC.get((G, args.precision)),
             "kernel": "supernodal factorisation (all launches of kkt_factor)",
             "peak_source": peak_note, "duration_ms": round(t_fac, 3),
             "work": "sum over columns of colcount^2 (algorithmic)"}
