@@ -133,6 +133,15 @@ typedef struct {
                             fallback arithmetic moves ipm_solve to that arithmetic from the
                             next iteration on (a cheaper factor no longer pays for its extra
                             CG steps); counted in ipm_result.fp64_fallbacks. 0: off (0) */
+  int32_t fp64_tc;       /* read by kkt_analyze: 1 runs every FP64 Cholesky factorisation (IPM_FP64,
+                            and the FP64 fallback) with its dense updates on the tensor cores:
+                            each FP64 operand split into 7 BF16 slices, the slice products summed
+                            exactly in FP32 and combined in FP64 (Ozaki scheme; about FP64-
+                            accurate, Sec. 6 on the precision of condensed KKT systems); the
+                            diagonal blocks stay on the FP64 pipe. Sizes FP64 storage plus 14
+                            bytes per factor entry of slices. The signed LDL^T of (4) keeps the
+                            FMA path. Long updates are split over CTAs and summed with FP64
+                            atomics, so results may differ between runs in the last bits (0) */
 } ipm_options;
 
 typedef enum {

@@ -53,7 +53,8 @@ class Options(C.Structure):
                 ("pcg_max", C.c_int32), ("fallback_fp64", C.c_int32), ("accept_tol", C.c_double),
                 ("verbose", C.c_int32), ("warm_start", C.c_int32), ("learned", C.c_int32),
                 ("learned_probes", C.c_int32), ("learned_pcg_max", C.c_int32),
-                ("formulation", C.c_int32), ("cg_escalate", C.c_int32)]
+                ("formulation", C.c_int32), ("cg_escalate", C.c_int32),
+                ("fp64_tc", C.c_int32)]
 
 
 class SymbolicInfo(C.Structure):

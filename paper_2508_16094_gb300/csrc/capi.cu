@@ -20,6 +20,7 @@
 #include "launch.h"
 #include "learned.h"
 #include "nlp.h"
+#include "oz.h"
 #include "tc.h"
 
 using namespace gipm;
@@ -68,6 +69,8 @@ struct ipm_ctx {
   IpmScalars *sc = nullptr;
   int32_t *status = nullptr, *col2s = nullptr;
   TcPlan tcp;
+  OzPlan ozp;          // FP64 factor on tensor cores (Ozaki slices), with options.fp64_tc
+  bool oz_on = false;  // its task lists and slice storage were sized by kkt_analyze
   // formulations (4) and (6): `sys` is the context of that system's matrix
   // (its pattern, symbolic analysis, factor and solves); this context keeps
   // the interior-point vectors and builds sys's inputs with the map kernels
@@ -251,6 +254,7 @@ void layout(ipm_ctx *c, char *base) {
     c->sysj = cv.take<double>(std::max<int64_t>(P.jp.back(), 1));
   }
   c->tcp.layout(cv, st);
+  if (c->oz_on) c->ozp.layout(cv, st, true);
   d.n = P.n;
   d.m = P.m;
   d.nl = P.nl;
@@ -339,7 +343,12 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
     throw Fail{IPM_ERR_UNSUPPORTED, "the signed factorisation of a quasi-definite system runs in FP64 or FP32"};
   int32_t init[ST_COUNT] = {INT32_MAX, 0, 0, 0, 0, 0, 0, 0};
   CK(cudaMemcpyAsync(c->status, init, sizeof(init), cudaMemcpyHostToDevice, c->st));
-  if (prec == IPM_FP64) {
+  if (prec == IPM_FP64 && c->opts.fp64_tc && !c->dp.sgn) {
+    if (!c->ozp.ready())
+      throw Fail{IPM_ERR_UNSUPPORTED,
+                 "FP64 tensor-core factor not prepared (fp64_tc must be set before kkt_analyze)"};
+    c->ozp.factor(c->dp, c->plan, c->kval, (double *)c->L, (double *)c->U, c->status, c->st);
+  } else if (prec == IPM_FP64) {
     launch_factor_simt<double>(c->dp, c->plan, c->kval, (double *)c->L, (double *)c->U, c->status,
                                false, c->st);
   } else if (prec == IPM_FP32) {
@@ -888,6 +897,7 @@ void ipm_default_options(ipm_options *o) {
   o->learned_pcg_max = 30;
   o->formulation = IPM_FORM_PRIMAL;
   o->cg_escalate = 0;
+  o->fp64_tc = 0;
 }
 
 ipm_status ipm_create_pattern(int32_t n, int32_t m, const ipm_pattern *p, const ipm_options *opts,
@@ -986,6 +996,7 @@ ipm_status kkt_analyze(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info)
     c->form = c->opts.formulation;
     if (c->form < IPM_FORM_PRIMAL || c->form > IPM_FORM_AUGMENTED)
       throw Fail{IPM_ERR_ARG, "unknown formulation"};
+    c->oz_on = false;
     if (c->form != IPM_FORM_PRIMAL) return analyze_form(c, perm, info);
     delete c->sys;
     c->sys = nullptr;
@@ -1001,8 +1012,11 @@ ipm_status kkt_analyze(ipm_ctx *c, const int32_t *perm, ipm_symbolic_info *info)
     validate_plan(c->P, c->S, c->plan);
     build_fused_solve(c->plan);
     c->tcp.build(c->plan);
+    c->oz_on = c->opts.fp64_tc != 0 && c->sign_orig.empty();
+    if (c->oz_on) c->ozp.build(c->plan);
     const int so = c->opts.storage_fp64;
-    c->storage_bytes = (so == 1 || (so < 0 && (c->opts.precision == IPM_FP64 || c->opts.fallback_fp64))) ? 8 : 4;
+    c->storage_bytes = (so == 1 || c->oz_on ||
+                        (so < 0 && (c->opts.precision == IPM_FP64 || c->opts.fallback_fp64))) ? 8 : 4;
     layout(c, nullptr);
     c->state = 1;
     if (info) {
@@ -1056,6 +1070,11 @@ ipm_status ipm_set_workspace(ipm_ctx *c, void *buf, size_t bytes) {
       if (!c->sys) c->tcp.encode(c->plan, (float *)c->L, c->Llo, (float *)c->U, c->st);
     } catch (const std::exception &e) {
       c->err = std::string("tensor-core path unavailable: ") + e.what();
+    }
+    try {  // tensor maps of the slice planes of the FP64 tensor-core factor
+      if (c->oz_on) c->ozp.encode(c->plan, c->st);
+    } catch (const std::exception &e) {
+      c->err = std::string("FP64 tensor-core path unavailable: ") + e.what();
     }
     c->state = 2;
     return IPM_OK;

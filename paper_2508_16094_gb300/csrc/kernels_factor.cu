@@ -427,6 +427,11 @@ void launch_factor_entries(const DevPlan &dp, const T *L, const int32_t *col2s, 
 
 template void launch_build_level<float>(const DevPlan &, const LevelPlan &, const double *,
                                         float *, float *, cudaStream_t);
+template void launch_build_level<double>(const DevPlan &, const LevelPlan &, const double *,
+                                         double *, double *, cudaStream_t);
+template void launch_potrf<double>(const DevPlan &, const Task *, int, int, double *, int32_t *,
+                                   bool, cudaStream_t);
+template void launch_trsm<double>(const DevPlan &, const Task *, int, int, double *, cudaStream_t);
 template void launch_potrf<float>(const DevPlan &, const Task *, int, int, float *, int32_t *, bool,
                                   cudaStream_t);
 template void launch_trsm<float>(const DevPlan &, const Task *, int, int, float *, cudaStream_t);

@@ -26,6 +26,7 @@
 #include <string>
 
 #include "launch.h"
+#include "ptx.cuh"
 #include "tc.h"
 
 #include <cstring>
@@ -33,6 +34,8 @@
 namespace gipm {
 
 namespace {
+
+using namespace ptx;
 
 constexpr int kTileM = 128, kTileN = 128, kTileK = 32, kSyrkN = 256;
 // Operand arithmetic of a kernel instantiation ("SPLIT"): 1 TF32, 3 the
@@ -45,7 +48,6 @@ constexpr int kSuper = 512;  // columns per super-step of the left-looking panel
 constexpr int kAheadFronts = 2;  // levels with at most this many fronts run the look-ahead
 constexpr int kBandGroup = 16;   // row bands per group of the SYRK's tile order
 constexpr int kTileBytes = kTileM * kTileK * 4;  // 16 KB per 128-row operand tile
-constexpr long long kSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
 // Ring depth: as many stages as fit in ~200 KB (each stage: A and B tiles, and
 // their low parts when SPLIT == 3). BN = 256 tiles (SYRK) halve the operand
 // bytes per product of the B side.
@@ -60,54 +62,12 @@ template <int SPLIT, int BN> struct Cfg {
   static_assert(smem <= 227 * 1024, "tensor-core kernel shared memory");
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // x - tf32(x): what the tensor core drops from an FP32 operand (low 13 mantissa bits)
 __device__ __forceinline__ float lo1(float x) {
   return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 __device__ __forceinline__ float4 lo_part(float4 v) {
   return make_float4(lo1(v.x), lo1(v.y), lo1(v.z), lo1(v.w));
-}
-
-// Bounded wait on an mbarrier phase; false (and ST_TIMEOUT recorded) on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *status) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kSpinCycles) {
-      atomicExch(&status[ST_TIMEOUT], 1);
-      return false;
-    }
-  }
-  return true;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_t *bar, int x,
@@ -219,16 +179,6 @@ __host__ __device__ constexpr uint32_t bf16_idesc() {
          ((uint32_t)(kTileM >> 4) << 24);
 }
 
-// One 128 x BN x 16 BF16 product (32 bytes of K per operand row, like one TF32 step).
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
@@ -245,13 +195,6 @@ __device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
       " [%0], %1;" ::"r"(smem_u32(bar)),
       "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
       : "memory");
 }
 

@@ -183,3 +183,18 @@ def test_create_pattern_matches_create():
     out = C.c_void_p()
     o = gb.default_options()
     assert lib.ipm_create_pattern(4, 4, None, C.byref(o), None, C.byref(out)) == 1
+
+
+def test_fp64_tc_sizes_slice_storage(lib):
+    """options.fp64_tc makes kkt_analyze size FP64 storage plus the BF16 slice
+    planes (7 x 2 bytes per factor entry, rows padded to 8) and their exponents."""
+    lp = gen.grid_lp(9, seed=3)
+    perm = gen.nd_order_grid3d(9)
+    ws = []
+    for tc in (0, 1):
+        o = gb.default_options(storage_fp64=1, fp64_tc=tc)
+        ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u, options=o)
+        info = ctx.kkt_analyze(perm)
+        ws.append(info.workspace_bytes)
+    extra = (ws[1] - ws[0]) / info.factor_entries
+    assert 14.0 <= extra <= 15.0, extra
