@@ -210,6 +210,11 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
     run(c64, max_iter=1)  # first-touch of the workspace and graphs
     out["fp64"] = run(c64, max_iter=200)
     c64.close()
+    # the FP64 factor with its updates on the tensor cores (Ozaki slices)
+    c64 = mk(precision=gb.IPM_FP64, storage_fp64=1, fp64_tc=1)
+    run(c64, max_iter=1)
+    out["fp64_tc"] = run(c64, max_iter=200)
+    c64.close()
     ctx = mk(precision=gb.IPM_TF32X3, storage_fp64=0, learned_probes=4)
     run(ctx, max_iter=1, learned=0)
     out["tf32x3"] = run(ctx, max_iter=200, learned=0)
@@ -228,7 +233,7 @@ def forms_measure(G: int, train_seeds=(1001, 1002, 1003, 1004), seed: int = 1):
     out["tf32x3_stale_E0"] = run(ctx, max_iter=200, learned=2)
     ctx.close()
     ref = out["fp64"]["objective"]
-    for k in ("tf32x3", "tf32x3_learned", "tf32x3_stale_E0"):
+    for k in ("fp64_tc", "tf32x3", "tf32x3_learned", "tf32x3_stale_E0"):
         out[k]["objective_rel_diff_vs_fp64"] = float(
             f"{abs(out[k]['objective'] - ref) / max(1.0, abs(ref)):.2e}")
     out["flops"] = flops[0]
@@ -247,9 +252,10 @@ def nlp_measure(N: int, max_iter: int = 150):
     ut = torch.as_tensor(P.ut, dtype=torch.float64, device="cuda")
     out = {"workload": f"grid NLP {N}^2 (n = m = {P.n}), alpha 5e-3, |v| <= 1, seed 5",
            "max_iter": max_iter}
-    for name, prec in (("fp64", gb.IPM_FP64), ("tf32x3", gb.IPM_TF32X3), ("bf16", gb.IPM_BF16)):
+    for name, prec, tc in (("fp64", gb.IPM_FP64, 0), ("fp64_tc", gb.IPM_FP64, 1),
+                           ("tf32x3", gb.IPM_TF32X3, 0), ("bf16", gb.IPM_BF16, 0)):
         o = gb.default_options(precision=prec, tol=1e-6, max_iter=max_iter, storage_fp64=1,
-                               fallback_fp64=1)
+                               fallback_fp64=1, fp64_tc=tc)
         G = gb.GridNLP(N, perm=perm, options=o)
         n, mt = G.pat["n"], G.ctx.m_tot
         x = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -267,7 +273,7 @@ def nlp_measure(N: int, max_iter: int = 150):
                      "regularizations": int(r.regularizations), "refine_steps": int(r.refine_steps),
                      "factor_flops": G.info.flops}
         G.ctx.close()
-    for name in ("tf32x3", "bf16"):
+    for name in ("fp64_tc", "tf32x3", "bf16"):
         out[name]["objective_rel_diff_vs_fp64"] = float(
             f"{abs(out[name]['objective'] - out['fp64']['objective']) / max(1.0, abs(out['fp64']['objective'])):.2e}")
     return out
@@ -433,6 +439,40 @@ def tti_run(ctx, jv, b, c, x, s, lam, prec, ref_obj=None, cg_escalate=0):
     return out
 
 
+def tti_fp64_tc(lp, perm, jv, b, c, ref_obj):
+    """The FP64 path measured: cold start to KKT <= 1e-6 with every factorisation
+    in FP64, its dense updates on the tensor cores (Ozaki slices), in a context
+    of its own (FP64 storage plus the slices)."""
+    import torch
+    import paper_2508_16094_gb300 as gb
+    o = gb.default_options(precision=gb.IPM_FP64, storage_fp64=1, fp64_tc=1, tol=1e-6)
+    ctx = gb.IpmContext(lp.n, lp.m, lp.rowptr, lp.col, lp.l, lp.u, options=o)
+    try:
+        info = ctx.kkt_analyze(perm)
+        ctx.ipm_set_workspace()
+        x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+        s = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        lam = torch.empty(ctx.m_tot, dtype=torch.float64, device="cuda")
+        ctx.ipm_set_options(max_iter=1)  # first touch of the workspace
+        ctx.ipm_solve(jv, b, c, x, s, lam)
+        out = tti_run(ctx, jv, b, c, x, s, lam, gb.IPM_FP64, ref_obj)
+        # one more factorisation of the last assembled matrix, timed alone
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.kkt_factor(gb.IPM_FP64)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        out["factor_s_one"] = round(tf, 4)
+        out["factor_tflops_fp64_equiv"] = round(info.flops / tf / 1e12, 2)
+        out["workspace_gb"] = round(info.workspace_bytes / 1e9, 1)
+        return out
+    except Exception as e:  # e.g. the slices do not fit next to the main context
+        return {"error": str(e)[:160]}
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
+
+
 def run_ours(args, ws, rank):
     import torch
     import paper_2508_16094_gb300 as gb
@@ -594,6 +634,8 @@ def run_ours(args, ws, rank):
             except Exception as e:  # an unsupported precision is reported, not fatal
                 tti[name] = {"error": str(e)[:120]}
         ctx.ipm_set_options(cg_escalate=0)
+        if args.fp64_tc_tti:
+            tti["fp64_tc"] = tti_fp64_tc(lp, perm, jv, b, c, ref)
 
     mpc = mpc_measure() if not args.no_mpc else None
     forms = forms_measure(args.forms_grid) if args.forms_grid > 0 else None
@@ -655,6 +697,8 @@ def main():
     ap.add_argument("--learned-sweep", type=int, default=0, metavar="G",
                     help="only run the learned correction's seed sweep on the G^3 grid-LP family "
                          "(64 training and 16 held-out seeds) and print its JSON line")
+    ap.add_argument("--no-fp64-tc-tti", dest="fp64_tc_tti", action="store_false",
+                    help="skip the FP64 (tensor-core updates) time to 1e-6 on the bench grid")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

@@ -255,6 +255,12 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__re
     if (r >= c) Ad[r * ls + c] = A[(int64_t)r * F.ld + c];
   }
   __syncthreads();
+  // FP64 Cholesky (no signs): the column below the pivot is multiplied by one
+  // reciprocal instead of divided entry by entry (an FP64 division is a long
+  // sequence on the FP64 pipe); FP32 and signed factors keep the division.
+  const bool recip = sizeof(T) == 8 && !sg;
+  __shared__ T rl;  // 1 / (s_j L_jj) of the current column
+  const int tx = tid % 16, ty = tid / 16;  // 16 x 16 grid over the trailing block
   for (int j = 0; j < kb; j++) {
     const T sj = (sg && sg[j] < 0) ? T(-1) : T(1);
     if (tid == 0) {
@@ -268,16 +274,22 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan dp, const Task *__re
           d = T(1);
         }
       }
-      Ad[j * ls + j] = sqrt(d);
+      const T l = sqrt(d);
+      Ad[j * ls + j] = l;
+      if (recip) rl = T(1) / l;
     }
     __syncthreads();
-    const T ljj = sj * Ad[j * ls + j];
-    for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i * ls + j] /= ljj;
+    if (recip) {
+      const T r = rl;
+      for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i * ls + j] *= r;
+    } else {
+      const T ljj = sj * Ad[j * ls + j];
+      for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ad[i * ls + j] /= ljj;
+    }
     __syncthreads();
-    const int w = kb - j - 1;
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int i = j + 1 + e / w, c = j + 1 + e % w;
-      if (c <= i) Ad[i * ls + c] = fma(-sj * Ad[i * ls + j], Ad[c * ls + j], Ad[i * ls + c]);
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const T lij = -sj * Ad[i * ls + j];
+      for (int c = j + 1 + tx; c <= i; c += 16) Ad[i * ls + c] = fma(lij, Ad[c * ls + j], Ad[i * ls + c]);
     }
     __syncthreads();
   }
@@ -311,17 +323,28 @@ __global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, const Task 
     const int r = e / kb, c = e % kb;
     X[r * ls + c] = Xg[(int64_t)r * F.ld + c];
   }
-  __syncthreads();
   const int8_t *sg = dp.sgn ? dp.sgn + F.first + k : nullptr;
-  if (tid < rows) {
+  // FP64 without signs: the diagonal replaced by its reciprocal (no FP64
+  // division on the substitution's critical path); otherwise s_c L_cc, the
+  // signs also folded into the entries below the diagonal (s_c2 L_c,c2)
+  const bool recip = sizeof(T) == 8 && !sg;
+  __syncthreads();
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    if (r == c) {
+      const T d = (sg && sg[c] < 0) ? -Lk[r * ls + c] : Lk[r * ls + c];
+      Lk[r * ls + c] = recip ? T(1) / d : d;
+    } else if (r > c && sg && sg[c] < 0) {
+      Lk[r * ls + c] = -Lk[r * ls + c];
+    }
+  }
+  __syncthreads();
+  if (tid < rows) {  // column by column: the updates of one step are independent
     T *x = X + tid * ls;
     for (int c = 0; c < kb; c++) {
-      T v = x[c];
-      for (int c2 = 0; c2 < c; c2++) {
-        const T l = (sg && sg[c2] < 0) ? -Lk[c * ls + c2] : Lk[c * ls + c2];
-        v = fma(-x[c2], l, v);
-      }
-      x[c] = v / ((sg && sg[c] < 0) ? -Lk[c * ls + c] : Lk[c * ls + c]);
+      const T xc = recip ? x[c] * Lk[c * ls + c] : x[c] / Lk[c * ls + c];
+      x[c] = xc;
+      for (int c2 = c + 1; c2 < kb; c2++) x[c2] = fma(-xc, Lk[c2 * ls + c], x[c2]);
     }
   }
   __syncthreads();

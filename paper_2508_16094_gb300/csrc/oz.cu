@@ -6,22 +6,23 @@
 //
 // Splitting. Each finished row segment of 64 panel columns (a "window") gets
 // one exponent e (all its |x| < 2^e); every x of it is rounded to the integer
-// X = round(x 2^(54-e)) and written in balanced base 256,
-//   X = sum_{i<7} D_i 256^(6-i),  D_1..D_6 in [-128, 127], |D_0| <= 65,
+// X = round(x 2^(55-e)) and written in balanced base 256,
+//   X = sum_{i<7} D_i 256^(6-i),  D_1..D_6 in [-128, 127], |D_0| <= 129,
 // stored as the BF16 slices s_i = D_i 2^(-8i) (exact: at most 8 significant
-// bits). Then x = 2^(e-6) sum_i s_i up to 2^(e-55).
+// bits). Then x = 2^(e-7) sum_i s_i up to 2^(e-56).
 //
 // Products. For a 128 x 64 tile of C -= A B^T and one window, the products
 // s_i t_j with i + j = d <= 4 are summed over the window's 64 columns into
 // their own FP32 accumulator in tensor memory: every term is an integer
-// multiple of 2^(-8d) and the sum stays below 2^24 of those units, so the
+// multiple of 2^(-8d) and the sum stays below 2^23 of those units, so the
 // accumulation is exact whatever its order. Diagonals 5 and 6 share one
-// accumulator (they carry less than 2^-33 of the tile's scale, so FP32
-// rounding there costs less than 2^-53 of it). The epilogue turns the five
-// exact sums and the tail into one 64-bit fixed-point integer W per entry,
-// then adds W 2^(e_a + e_b - 52) in FP64. Terms i + j >= 7 are dropped: at
-// most 2^-49 of K max|a| max|b| for a 64-column window, below the rounding
-// bound of an FP64 dot product of that length.
+// accumulator, rounded in FP32. The epilogue turns the five exact sums and
+// the tail into one 64-bit fixed-point integer W per entry and adds
+// W 2^(e_a + e_b - 54) in FP64. Relative to K max|a| max|b| of the window
+// (K = 64), the tail's rounding costs at most about 2^-48 and the dropped
+// terms i + j >= 7 at most 2^-50: both below the worst-case rounding bound of
+// an FP64 dot product of that length (K u = 2^-47 relative to sum |a||b|),
+// and far below it for digits of mixed signs.
 //
 // Long K ranges of one tile are split over several CTAs whose results are
 // added with FP64 atomics (the sum of a few FP64 partials in any order).
@@ -98,28 +99,37 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr));
 }
 
-// 2^(ea + eb - 52): the weight of one unit of the fixed-point sum W.
-__device__ __forceinline__ double unit_scale(int ea, int eb) {
-  if (ea == kNanExp || eb == kNanExp) return __longlong_as_double(0x7FF8000000000000LL);
-  const int s = ea + eb - 52;
-  if (s < -1022) return 0.0;
-  return __longlong_as_double((long long)(min(s, 1023) + 1023) << 52);
+// The integer n held exactly by an FP32 accumulator as n / scale, |n| < 2^22:
+// adding 1.5 * 2^23 puts n in the low mantissa bits.
+__device__ __forceinline__ int exact_int(uint32_t bits, float scale) {
+  return __float_as_int(fmaf(__uint_as_float(bits), scale, 12582912.0f)) - 0x4B400000;
 }
 
-// X = round(x 2^(54 - e)) for the window exponent e = mx - 1022 (mx: the
+// W 2^(ea + eb - 54) as an FP64 value built from W's bits (rounded to 53
+// bits, ties away from zero; a carry out of the mantissa moves into the
+// exponent field); 0 below the normal range, NaN if either window held an
+// Inf or NaN.
+__device__ __forceinline__ double scaled_double(long long W, int ea, int eb) {
+  const unsigned long long a = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
+  const int lz = __clzll(a);
+  const int ex = 63 - lz + ea + eb - 54 + 1023;
+  const unsigned long long n = a << (lz & 63);  // leading one at bit 63
+  const unsigned long long bits = (W < 0 ? (1ull << 63) : 0ull) |
+                                  (((unsigned long long)min(ex, 2045) << 52) +
+                                   ((n >> 11) & 0xFFFFFFFFFFFFFull) + ((n >> 10) & 1ull));
+  if (ea == kNanExp || eb == kNanExp) return __longlong_as_double(0x7FF8000000000000LL);
+  return (a == 0 || ex <= 0) ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+// X = round(x 2^(55 - e)) for the window exponent e = mx - 1022 (mx: the
 // window's largest biased exponent), from the bits of x.
 __device__ __forceinline__ long long scaled_int(unsigned long long b, int mx) {
   const int ex = (int)((b >> 52) & 0x7FF);
   if (ex == 0) return 0;  // zero or subnormal
   const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = ex - mx + 1;  // <= 1
-  unsigned long long X;
-  if (sh >= 0) {
-    X = mant << sh;
-  } else {
-    const int rs = -sh;
-    X = rs >= 60 ? 0ull : (mant + (1ull << (rs - 1))) >> rs;
-  }
+  const int sh = ex - mx + 2;  // <= 2
+  const unsigned long long X =
+      sh >= 0 ? mant << sh : (-sh >= 60 ? 0ull : (mant + (1ull << (-sh - 1))) >> -sh);
   return (b >> 63) ? -(long long)X : (long long)X;
 }
 
@@ -296,35 +306,52 @@ __global__ void __launch_bounds__(kThreads, 1)
     int wi = 0;
     for (int w = wb; w < we && !*abort_flag; w++, wi++) {
       const int ea = arow_ok ? ea_row[w] : kZeroExp;
+      // lane c holds the exponent of this thread's column c0 + c (one load per
+      // lane; the additions below take it by shuffle)
+      const int eb_lane = lane < nb_rows ? eb_col[(int64_t)lane * Z.nwin + w] : kZeroExp;
       if (!mbar_wait(accfull, wi & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // W of all 32 entries first (cheap FP32/INT work), then free the
+      // accumulators for the next window, then the FP64 additions
+      long long Wv[32];
 #pragma unroll
-      for (int sub = 0; sub < 4; sub++) {  // 8 columns at a time
-        uint32_t v[kSlots][8];
+      for (int sub = 0; sub < 4; sub++) {  // 8 columns at a time, one sum at a time
         const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 8 * sub);
-#pragma unroll
-        for (int sl = 0; sl < kSlots; sl++) tmem_ld8(ta + (uint32_t)(sl * kN), v[sl]);
+        uint32_t v[8];
+        int hi[8];
+        tmem_ld8(ta, v);  // diagonal 0
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (sub == 3) {  // every sum of this window is in registers: free the accumulators
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(accempty);
-        }
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-          const int cc = 8 * sub + c;
-          const int eb = cc < nb_rows ? eb_col[(int64_t)cc * Z.nwin + w] : kZeroExp;
-          const int n0 = __float2int_rn(__uint_as_float(v[0][c]));
-          const int n1 = __float2int_rn(__uint_as_float(v[1][c]) * 0x1p8f);
-          const int n2 = __float2int_rn(__uint_as_float(v[2][c]) * 0x1p16f);
-          const int n3 = __float2int_rn(__uint_as_float(v[3][c]) * 0x1p24f);
-          const int n4 = __float2int_rn(__uint_as_float(v[4][c]) * 0x1p32f);
-          const int nt = __float2int_rn(__uint_as_float(v[5][c]) * 0x1p40f);
-          const long long W = ((long long)n0 << 40) + ((long long)n1 << 32) +
-                              ((long long)n2 << 24) + ((long long)n3 << 16) +
-                              ((long long)n4 << 8) + (long long)nt;
-          acc[cc] = fma((double)W, unit_scale(ea, eb), acc[cc]);
-        }
+        for (int c = 0; c < 8; c++) hi[c] = exact_int(v[c], 1.f) * 256;
+        tmem_ld8(ta + kN, v);  // diagonal 1
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; c++) Wv[8 * sub + c] = (long long)(hi[c] + exact_int(v[c], 0x1p8f)) << 32;
+        tmem_ld8(ta + 2 * kN, v);  // diagonal 2
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; c++) Wv[8 * sub + c] += (long long)exact_int(v[c], 0x1p16f) << 24;
+        tmem_ld8(ta + 3 * kN, v);  // diagonal 3
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; c++) hi[c] = __float2int_rn(__uint_as_float(v[c]) * 0x1p24f) * 256;
+        tmem_ld8(ta + 4 * kN, v);  // diagonal 4
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+          Wv[8 * sub + c] += (long long)(hi[c] + __float2int_rn(__uint_as_float(v[c]) * 0x1p32f)) << 8;
+        tmem_ld8(ta + 5 * kN, v);  // diagonals 5 and 6 (rounded), |.| < 2^23 units
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; c++) Wv[8 * sub + c] += __float2int_rn(__uint_as_float(v[c]) * 0x1p40f);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accempty);
+#pragma unroll
+      for (int c = 0; c < 32; c++) {
+        const int eb = __shfl_sync(0xFFFFFFFFu, eb_lane, c);
+        acc[c] += scaled_double(Wv[c], ea, eb);
       }
     }
     if (!*abort_flag) {
