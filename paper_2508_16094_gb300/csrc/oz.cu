@@ -4,7 +4,10 @@
 // multiplication and its applications", Numer. Algorithms 59, 2012; run on
 // tensor cores by Mukunoki, Ozaki, Ogita and Imamura, ICCS 2020).
 //
-// Splitting. Each finished row segment of 64 panel columns (a "window") gets
+// Splitting. The panel's columns are taken in windows of two 64-column blocks
+// (the last one of a range may be a single block): once a block is finished
+// its row segments are sliced, and when the second block of a window is, the
+// window's rows are sliced again as one. Each row segment of a window gets
 // one exponent e (all its |x| < 2^e); every x of it is rounded to the integer
 // X = round(x 2^(55-e)) and written in balanced base 256,
 //   X = sum_{i<7} D_i 256^(6-i),  D_1..D_6 in [-128, 127], |D_0| <= 129,
@@ -12,16 +15,16 @@
 // bits). Then x = 2^(e-7) sum_i s_i up to 2^(e-56).
 //
 // Products. For a 128 x 64 tile of C -= A B^T and one window, the products
-// s_i t_j with i + j = d <= 4 are summed over the window's 64 columns into
-// their own FP32 accumulator in tensor memory: every term is an integer
-// multiple of 2^(-8d) and the sum stays below 2^23 of those units, so the
-// accumulation is exact whatever its order. Diagonals 5 and 6 share one
+// s_i t_j with i + j = d <= 4 are summed over the window's (at most 128)
+// columns into their own FP32 accumulator in tensor memory: every term is an
+// integer multiple of 2^(-8d) and the sum stays below 2^24 of those units, so
+// the accumulation is exact whatever its order. Diagonals 5 and 6 share one
 // accumulator, rounded in FP32. The epilogue turns the five exact sums and
 // the tail into one 64-bit fixed-point integer W per entry and adds
 // W 2^(e_a + e_b - 54) in FP64. Relative to K max|a| max|b| of the window
-// (K = 64), the tail's rounding costs at most about 2^-48 and the dropped
-// terms i + j >= 7 at most 2^-50: both below the worst-case rounding bound of
-// an FP64 dot product of that length (K u = 2^-47 relative to sum |a||b|),
+// (K = 128), the tail's rounding costs at most about 2^-50 and the dropped
+// terms i + j >= 7 at most 2^-53: both below the worst-case rounding bound of
+// an FP64 dot product of that length (K u = 2^-46 relative to sum |a||b|),
 // and far below it for digits of mixed signs.
 //
 // Long K ranges of one tile are split over several CTAs whose results are
@@ -45,7 +48,7 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kP = OzPlan::kPlanes, kW = OzPlan::kWin;
+constexpr int kP = OzPlan::kPlanes, kBlk = OzPlan::kBlk;
 constexpr int kM = 128, kN = 64;   // tile rows and columns
 constexpr int kKs = 32;            // K per stage: 64-byte operand rows
 constexpr int kStages = 2;
@@ -104,6 +107,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 __device__ __forceinline__ int exact_int(uint32_t bits, float scale) {
   return __float_as_int(fmaf(__uint_as_float(bits), scale, 12582912.0f)) - 0x4B400000;
 }
+// The same for |n| < 2^31 (a conversion instruction).
+__device__ __forceinline__ int wide_int(uint32_t bits, float scale) {
+  return __float2int_rn(__uint_as_float(bits) * scale);
+}
 
 // W 2^(ea + eb - 54) as an FP64 value built from W's bits (rounded to 53
 // bits, ties away from zero; a carry out of the mantissa moves into the
@@ -133,8 +140,10 @@ __device__ __forceinline__ long long scaled_int(unsigned long long b, int mx) {
   return (b >> 63) ? -(long long)X : (long long)X;
 }
 
-// Slices of the finished block column k (one window) of one front, rows
-// [a, a + 128) past the diagonal block: one warp per row.
+// Slices of one window of a front: columns [b, b + c) (a finished 64-column
+// block, or that block and the one before it, sliced again with one
+// exponent), rows [a, a + 128) below the window's last diagonal block: one
+// warp per row.
 __global__ void __launch_bounds__(256) oz_slice_kernel(DevPlan dp, const OzFront *__restrict__ ozf,
                                                        const Task *__restrict__ tasks,
                                                        const double *__restrict__ L,
@@ -143,28 +152,28 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(DevPlan dp, const OzFront
   const Task tk = tasks[blockIdx.x];
   const FrontInfo F = dp.fronts[tk.front];
   const OzFront Z = ozf[tk.front];
-  const int nf = F.ncol + F.nrow, k = tk.b, kb = min(kW, F.ncol - k), w = k / kW;
+  const int nf = F.ncol + F.nrow, c0 = tk.b, width = tk.c, blk = c0 / kBlk;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t plane = (int64_t)nf * Z.lds;
   const int rend = min(nf, tk.a + 128);
   const float pw[kP] = {1.f, 0x1p-8f, 0x1p-16f, 0x1p-24f, 0x1p-32f, 0x1p-40f, 0x1p-48f};
   for (int row = tk.a + warp; row < rend; row += 8) {
-    const double *xr = L + F.loff + (int64_t)row * F.ld + k;
-    unsigned long long b[2];
+    const double *xr = L + F.loff + (int64_t)row * F.ld + c0;
+    unsigned long long b[4];
     int mx = 0;
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < 4; h++) {
       const int col = lane + 32 * h;
-      b[h] = col < kb ? (unsigned long long)__double_as_longlong(xr[col]) : 0ull;
+      b[h] = col < width ? (unsigned long long)__double_as_longlong(xr[col]) : 0ull;
       mx = max(mx, (int)((b[h] >> 52) & 0x7FF));
     }
     mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     const bool normal = mx > 0 && mx < 0x7FF;
-    uint16_t *out = S + Z.soff + (int64_t)row * Z.lds + k;
+    uint16_t *out = S + Z.soff + (int64_t)row * Z.lds + c0;
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < 4; h++) {
       const int col = lane + 32 * h;
-      if (col >= kb) continue;
+      if (col >= width) continue;
       long long X = normal ? scaled_int(b[h], mx) : 0ll;
       int D[kP];
 #pragma unroll
@@ -178,8 +187,8 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(DevPlan dp, const OzFront
       for (int i = 0; i < kP; i++)
         out[i * plane + col] = __bfloat16_as_ushort(__float2bfloat16_rn((float)D[i] * pw[i]));
     }
-    if (lane == 0)
-      E[Z.eoff + (int64_t)row * Z.nwin + w] =
+    if (lane < (width > kBlk ? 2 : 1))
+      E[Z.eoff + (int64_t)row * Z.nblk + blk + lane] =
           normal ? (int16_t)(mx - 1022) : (mx == 0 ? kZeroExp : kNanExp);
   }
 }
@@ -189,7 +198,9 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(DevPlan dp, const OzFront
 //    columns k..k+64; A = panel rows a.., B = panel rows k.., K = columns [0, k).
 //  Mode 1 (update-matrix SYRK): C = U rows a.., columns b..; A = panel rows
 //    ncol + a.., B = panel rows ncol + b.., K = all ncol columns.
-// c = mode | wb << 2 | we << 17.
+// Window w of the K range covers columns [128 w, 128 w + 128), the last one
+// only 64 when the range has an odd number of blocks; its exponent is that of
+// block 2 w. c = mode | wb << 2 | we << 17.
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(DevPlan dp, const OzFront *__restrict__ ozf, const Task *__restrict__ tasks,
                    const CUtensorMap *__restrict__ maps, const int16_t *__restrict__ E,
@@ -213,6 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nf = F.ncol + F.nrow;
   const int arow = mode == 0 ? tk.a : F.ncol + tk.a;  // operand rows (front-local)
   const int brow = mode == 0 ? tk.b : F.ncol + tk.b;
+  const int nblk = mode == 0 ? tk.b / kBlk : (F.ncol + kBlk - 1) / kBlk;  // blocks of K
+  const int npair = nblk / 2;  // windows of two blocks
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) {
@@ -242,13 +255,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const CUtensorMap *ma = maps + 2 * tk.front, *mb = ma + 1;
       uint32_t g = 0;
       for (int w = wb; w < we && !*abort_flag; w++)
-        for (int sub = 0; sub < 2; sub++, g++) {
+        for (int sub = 0; sub < (w < npair ? 4 : 2); sub++, g++) {
           const int s = g % kStages;
           const uint32_t round = g / kStages;
           if (!mbar_wait(&empty[s], (round & 1) ^ 1, status)) { *abort_flag = 1; break; }
           mbar_arrive_expect_tx(&full[s], kStageBytes);
           uint8_t *st = base + s * kStageBytes;
-          const int x = w * kW + sub * kKs;
+          const int x = w * 2 * kBlk + sub * kKs;
           tma_load_3d(st, ma, &full[s], x, arow, 0);
           tma_load_3d(st + kABytes, mb, &full[s], x, brow, 0);
         }
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(accempty, (wi & 1) ^ 1, status)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool fail = false;
-        for (int sub = 0; sub < 2; sub++, g++) {
+        for (int sub = 0; sub < (w < npair ? 4 : 2); sub++, g++) {
           const int s = g % kStages;
           const uint32_t round = g / kStages;
           if (!mbar_wait(&full[s], round & 1, status)) { *abort_flag = 1; fail = true; break; }
@@ -297,18 +310,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = 32 * q + lane;    // its row of the tile
     const OzFront Z = ozf[tk.front];
     const bool arow_ok = arow + r < nf;
-    const int16_t *ea_row = E + Z.eoff + (int64_t)(arow + r) * Z.nwin;
-    const int16_t *eb_col = E + Z.eoff + (int64_t)(brow + c0) * Z.nwin;
+    const int16_t *ea_row = E + Z.eoff + (int64_t)(arow + r) * Z.nblk;
+    const int16_t *eb_col = E + Z.eoff + (int64_t)(brow + c0) * Z.nblk;
     const int nb_rows = nf - (brow + c0);  // B rows of this thread's columns inside the front
     double acc[32];
 #pragma unroll
     for (int c = 0; c < 32; c++) acc[c] = 0.0;
     int wi = 0;
     for (int w = wb; w < we && !*abort_flag; w++, wi++) {
-      const int ea = arow_ok ? ea_row[w] : kZeroExp;
+      const int ea = arow_ok ? ea_row[2 * w] : kZeroExp;
       // lane c holds the exponent of this thread's column c0 + c (one load per
       // lane; the additions below take it by shuffle)
-      const int eb_lane = lane < nb_rows ? eb_col[(int64_t)lane * Z.nwin + w] : kZeroExp;
+      const int eb_lane = lane < nb_rows ? eb_col[(int64_t)lane * Z.nblk + 2 * w] : kZeroExp;
       if (!mbar_wait(accfull, wi & 1, status)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // W of all 32 entries first (cheap FP32/INT work), then free the
@@ -326,24 +339,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld8(ta + kN, v);  // diagonal 1
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 8; c++) Wv[8 * sub + c] = (long long)(hi[c] + exact_int(v[c], 0x1p8f)) << 32;
+        for (int c = 0; c < 8; c++) Wv[8 * sub + c] = (long long)(hi[c] + wide_int(v[c], 0x1p8f)) << 32;
         tmem_ld8(ta + 2 * kN, v);  // diagonal 2
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 8; c++) Wv[8 * sub + c] += (long long)exact_int(v[c], 0x1p16f) << 24;
+        for (int c = 0; c < 8; c++) Wv[8 * sub + c] += (long long)wide_int(v[c], 0x1p16f) << 24;
         tmem_ld8(ta + 3 * kN, v);  // diagonal 3
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 8; c++) hi[c] = __float2int_rn(__uint_as_float(v[c]) * 0x1p24f) * 256;
+        for (int c = 0; c < 8; c++) hi[c] = wide_int(v[c], 0x1p24f);
         tmem_ld8(ta + 4 * kN, v);  // diagonal 4
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 8; c++)
-          Wv[8 * sub + c] += (long long)(hi[c] + __float2int_rn(__uint_as_float(v[c]) * 0x1p32f)) << 8;
-        tmem_ld8(ta + 5 * kN, v);  // diagonals 5 and 6 (rounded), |.| < 2^23 units
+          Wv[8 * sub + c] += ((long long)hi[c] << 16) + ((long long)wide_int(v[c], 0x1p32f) << 8);
+        tmem_ld8(ta + 5 * kN, v);  // diagonals 5 and 6 (rounded), |.| < 2^24 units
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 8; c++) Wv[8 * sub + c] += __float2int_rn(__uint_as_float(v[c]) * 0x1p40f);
+        for (int c = 0; c < 8; c++) Wv[8 * sub + c] += wide_int(v[c], 0x1p40f);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t ldc;
       if (mode == 0) {
         M = min(kM, nf - tk.a);
-        N = min(kW, F.ncol - tk.b);
+        N = min(kBlk, F.ncol - tk.b);
         C = L + F.loff + (int64_t)tk.a * F.ld + tk.b;
         ldc = F.ld;
       } else {
@@ -414,10 +427,13 @@ void push_split(std::vector<Task> &out, int32_t front, int32_t a, int32_t b, int
   }
 }
 
+// Windows of a K range of nblk blocks: pairs, and a last single block.
+int windows(int nblk) { return nblk / 2 + nblk % 2; }
+
 }  // namespace
 
 void OzPlan::build(const Plan &plan) {
-  if (plan.nb != kW) throw std::runtime_error("the FP64 tensor-core factor needs 64-wide blocks");
+  if (plan.nb != kBlk) throw std::runtime_error("the FP64 tensor-core factor needs 64-wide blocks");
   gemm_.clear();
   slice_.clear();
   levels_.clear();
@@ -428,11 +444,11 @@ void OzPlan::build(const Plan &plan) {
     const FrontInfo &F = plan.fronts[f];
     const int nf = F.ncol + F.nrow;
     const int lds = (std::max(F.ncol, 1) + 7) / 8 * 8;
-    const int nwin = (F.ncol + kW - 1) / kW;
-    if (nwin >= 0x7FFF) throw std::runtime_error("front too wide for the FP64 tensor-core factor");
-    fr_[f] = OzFront{so, eo, lds, nwin, {0, 0}};
+    const int nblk = (F.ncol + kBlk - 1) / kBlk;
+    if (windows(nblk) >= 0x7FFF) throw std::runtime_error("front too wide for the FP64 tensor-core factor");
+    fr_[f] = OzFront{so, eo, lds, nblk, {0, 0}};
     so += (int64_t)kP * nf * lds;
-    eo += (int64_t)nf * nwin;
+    eo += (int64_t)nf * nblk;
   }
   slice_elems_ = so;
   exp_elems_ = eo;
@@ -440,7 +456,7 @@ void OzPlan::build(const Plan &plan) {
   for (size_t l = 0; l < plan.levels.size(); l++) {
     const LevelPlan &LP = plan.levels[l];
     Level &V = levels_[l];
-    for (int32_t k = 0; k < LP.max_ncol; k += kW) {
+    for (int32_t k = 0; k < LP.max_ncol; k += kBlk) {
       Step st{};
       st.gemm_b = (int)gemm_.size();
       if (k > 0) {
@@ -449,22 +465,27 @@ void OzPlan::build(const Plan &plan) {
           const FrontInfo &F = plan.fronts[plan.level_fronts[t]];
           if (F.ncol > k) tiles += (F.ncol + F.nrow - k + kM - 1) / kM;
         }
-        const int split = split_for(tiles, k / kW);
+        const int nw = windows(k / kBlk);
+        const int split = split_for(tiles, nw);
         for (int32_t t = LP.front_b; t < LP.front_e; t++) {
           const int32_t s = plan.level_fronts[t];
           const FrontInfo &F = plan.fronts[s];
           if (F.ncol <= k) continue;
-          for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kM) push_split(gemm_, s, i0, k, 0, k / kW, split);
+          for (int32_t i0 = k; i0 < F.ncol + F.nrow; i0 += kM) push_split(gemm_, s, i0, k, 0, nw, split);
         }
       }
       st.gemm_e = (int)gemm_.size();
+      // the finished block (an even block alone, an odd block with the one
+      // before it), rows below it
       st.slice_b = (int)slice_.size();
+      const bool odd = (k / kBlk) % 2 == 1;
       for (int32_t t = LP.front_b; t < LP.front_e; t++) {
         const int32_t s = plan.level_fronts[t];
         const FrontInfo &F = plan.fronts[s];
         if (F.ncol <= k) continue;
-        const int32_t kb = std::min(kW, F.ncol - k);
-        for (int32_t r0 = k + kb; r0 < F.ncol + F.nrow; r0 += 128) slice_.push_back({s, r0, k, 0});
+        const int32_t kb = std::min(kBlk, F.ncol - k);
+        const int32_t c0 = odd ? k - kBlk : k, width = odd ? kBlk + kb : kb;
+        for (int32_t r0 = k + kb; r0 < F.ncol + F.nrow; r0 += 128) slice_.push_back({s, r0, c0, width});
       }
       st.slice_e = (int)slice_.size();
       V.steps.push_back(st);
@@ -480,11 +501,11 @@ void OzPlan::build(const Plan &plan) {
       const int32_t s = plan.level_fronts[t];
       const FrontInfo &F = plan.fronts[s];
       if (F.nrow == 0) continue;
-      const int nwin = (F.ncol + kW - 1) / kW;
-      const int split = split_for(tiles, nwin);
+      const int nw = windows((F.ncol + kBlk - 1) / kBlk);
+      const int split = split_for(tiles, nw);
       for (int32_t i0 = 0; i0 < F.nrow; i0 += kM)
         for (int32_t j0 = 0; j0 < F.nrow && j0 < i0 + kM; j0 += kN)
-          push_split(gemm_, s, i0, j0, 1, nwin, split);
+          push_split(gemm_, s, i0, j0, 1, nw, split);
     }
     V.syrk_e = (int)gemm_.size();
   }

@@ -13,9 +13,9 @@ namespace gipm {
 // Per front: where its slice planes and exponent table live.
 struct OzFront {
   int64_t soff;  // first element of plane 0 (7 planes of nf x lds BF16 values)
-  int64_t eoff;  // first exponent (nf rows x nwin int16)
+  int64_t eoff;  // first exponent (nf rows x nblk int16)
   int32_t lds;   // row stride of a plane (elements, a multiple of 8)
-  int32_t nwin;  // 64-column windows of the panel
+  int32_t nblk;  // 64-column blocks of the panel
   int32_t pad[2];
 };
 static_assert(sizeof(OzFront) == 32, "OzFront layout");
@@ -23,11 +23,11 @@ static_assert(sizeof(OzFront) == 32, "OzFront layout");
 class OzPlan {
  public:
   static constexpr int kPlanes = 7;  // BF16 slices per FP64 value
-  static constexpr int kWin = 64;    // columns per exponent window (the plan's block width)
+  static constexpr int kBlk = 64;    // the plan's block width; windows are 1 or 2 blocks
   OzPlan() = default;
   OzPlan(const OzPlan &) = delete;
   OzPlan &operator=(const OzPlan &) = delete;
-  // Task lists and slice layout from the FP64 plan (block width kWin).
+  // Task lists and slice layout from the FP64 plan (block width kBlk).
   void build(const Plan &plan);
   // Carve device memory: tasks, per-front records and tensor maps, and (when
   // `storage` is set) the slice planes and exponent tables.
