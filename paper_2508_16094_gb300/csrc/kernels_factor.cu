@@ -354,6 +354,64 @@ __global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan dp, const Task 
   }
 }
 
+// FP64 rows below a diagonal block without pivot signs: X <- X L_kk^{-T}. A
+// full 64-wide block keeps each thread's row in registers (64 values) and
+// reads the block by broadcast from shared memory, its diagonal replaced by
+// reciprocals; the 2080 multiply-adds of a row then issue back to back on the
+// FP64 pipe. A narrower last block takes the shared-memory loop of trsm_kernel.
+// Same arithmetic, in the same order, as trsm_kernel<double> on such a block.
+__global__ void __launch_bounds__(kTrsmRows) trsm_f64_kernel(DevPlan dp, const Task *__restrict__ tasks,
+                                                             double *__restrict__ L) {
+  constexpr int NB = 64, LS = NB + 1;
+  const Task tk = tasks[blockIdx.x];
+  const FrontInfo F = dp.fronts[tk.front];
+  const int nf = F.ncol + F.nrow, i0 = tk.a, k = tk.b;
+  const int kb = min(NB, F.ncol - k), rows = min(kTrsmRows, nf - i0);
+  extern __shared__ unsigned char smem_raw[];
+  double *Lk = reinterpret_cast<double *>(smem_raw);  // [NB][LS]
+  double *X = Lk + NB * LS;                           // [kTrsmRows][LS]
+  const double *A = L + F.loff + (int64_t)k * F.ld + k;
+  double *Xg = L + F.loff + (int64_t)i0 * F.ld + k;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    const double v = A[(int64_t)r * F.ld + c];
+    Lk[r * LS + c] = r > c ? v : (r == c ? 1.0 / v : 0.0);
+  }
+  for (int e = tid; e < rows * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    X[r * LS + c] = Xg[(int64_t)r * F.ld + c];
+  }
+  __syncthreads();
+  if (tid < rows) {
+    double *xs = X + tid * LS;
+    if (kb == NB) {
+      double x[NB];
+#pragma unroll
+      for (int c = 0; c < NB; c++) x[c] = xs[c];
+#pragma unroll
+      for (int c = 0; c < NB; c++) {
+        x[c] *= Lk[c * LS + c];
+#pragma unroll
+        for (int c2 = c + 1; c2 < NB; c2++) x[c2] = fma(-x[c], Lk[c2 * LS + c], x[c2]);
+      }
+#pragma unroll
+      for (int c = 0; c < NB; c++) xs[c] = x[c];
+    } else {
+      for (int c = 0; c < kb; c++) {
+        const double xc = xs[c] * Lk[c * LS + c];
+        xs[c] = xc;
+        for (int c2 = c + 1; c2 < kb; c2++) xs[c2] = fma(-xc, Lk[c2 * LS + c], xs[c2]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * kb; e += blockDim.x) {
+    const int r = e / kb, c = e % kb;
+    Xg[(int64_t)r * F.ld + c] = X[r * LS + c];
+  }
+}
+
 template <typename T>
 __global__ void entries_kernel(DevPlan dp, const T *__restrict__ L, const int32_t *col2s,
                                int64_t count, const int32_t *rows, const int32_t *cols,
@@ -421,6 +479,17 @@ void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   { note_launch(); trsm_kernel<T><<<ntasks, kTrsmRows, smem, st>>>(dp, tasks, nb, L); }
+}
+
+void launch_trsm_f64(const DevPlan &dp, const Task *tasks, int ntasks, double *L, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)(64 + kTrsmRows) * 65 * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(trsm_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  { note_launch(); trsm_f64_kernel<<<ntasks, kTrsmRows, smem, st>>>(dp, tasks, L); }
 }
 
 template <typename T>

@@ -27,6 +27,8 @@ void launch_potrf(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L
                   bool perturb, cudaStream_t st);
 template <typename T>
 void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L, cudaStream_t st);
+// FP64 without pivot signs, 64-wide blocks: the panel solve with each row in registers.
+void launch_trsm_f64(const DevPlan &dp, const Task *tasks, int ntasks, double *L, cudaStream_t st);
 
 // Triangular solves with the factor: y (final numbering, length n) is
 // overwritten by L^{-T} L^{-1} y (L^{-T} S L^{-1} y for a signed factor,

@@ -586,7 +586,7 @@ void OzPlan::factor(const DevPlan &dp, const Plan &plan, const double *kval, dou
       gemm(Z.gemm_b, Z.gemm_e);
       launch_potrf<double>(dp, dp.potrf + R.potrf_b, R.potrf_e - R.potrf_b, plan.nb, L, status,
                            false, st);
-      launch_trsm<double>(dp, dp.trsm + R.trsm_b, R.trsm_e - R.trsm_b, plan.nb, L, st);
+      launch_trsm_f64(dp, dp.trsm + R.trsm_b, R.trsm_e - R.trsm_b, L, st);
       if (Z.slice_e > Z.slice_b) {
         note_launch();
         oz_slice_kernel<<<Z.slice_e - Z.slice_b, 256, 0, st>>>(dp, d_fr_, d_slice_ + Z.slice_b, L,
