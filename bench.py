@@ -473,6 +473,28 @@ def tti_fp64_tc(lp, perm, jv, b, c, ref_obj):
         torch.cuda.empty_cache()
 
 
+def summary(tti, forms, nlp, mpc):
+    """The headline figures, compact, for the end of the JSON line."""
+    def pick(d, key):
+        return {k: v[key] for k, v in d.items() if isinstance(v, dict) and key in v}
+    out = {"tti_1e-6_s": pick(tti, "s")}
+    if "fp64_extrapolated" in tti:
+        out["tti_1e-6_s"]["fp64_fma_extrapolated"] = tti["fp64_extrapolated"]["s_factor_only"]
+    t = out["tti_1e-6_s"]
+    if "fp64_tc" in t and "tf32_then_tf32x3" in t:
+        out["fp64_tc_over_ladder"] = round(t["fp64_tc"] / t["tf32_then_tf32x3"], 2)
+    if isinstance(tti.get("fp64_tc"), dict) and "factor_tflops_fp64_equiv" in tti["fp64_tc"]:
+        out["fp64_tc_factor_tflops"] = tti["fp64_tc"]["factor_tflops_fp64_equiv"]
+    if forms:
+        out["forms_48_s"] = pick(forms, "seconds")
+    if nlp:
+        out["grid_nlp_s"] = pick(nlp, "seconds")
+    if mpc:
+        out["mpc_solves_per_s"] = {k: v["solves_per_s"] for k, v in mpc.items()
+                                   if isinstance(v, dict) and "solves_per_s" in v}
+    return out
+
+
 def run_ours(args, ws, rank):
     import torch
     import paper_2508_16094_gb300 as gb
@@ -687,6 +709,7 @@ def run_ours(args, ws, rank):
                      "factor_ms": fac_ms / args.steps, "solve_ms": sol_ms / args.steps},
         "time_to_kkt_1e-6": tti,
     }
+    line["summary"] = summary(tti, forms, nlp, mpc)  # last: the headline figures in the line's tail
     print(json.dumps(line), flush=True)
     ctx.close()
 
