@@ -100,12 +100,15 @@ def _factor_entries(ctx, S, n):
     return rows, cols, ctx.kkt_factor_entries(rows, cols)
 
 
-@pytest.mark.parametrize("prec", [gb.IPM_FP64, gb.IPM_FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("prec,tc", [(gb.IPM_FP64, 0), (gb.IPM_FP32, 0), (gb.IPM_FP64, 1)],
+                         ids=["fp64", "fp32", "fp64_tc"])
 @pytest.mark.parametrize("form", ["dual", "augmented"])
 @pytest.mark.parametrize("name", ["grid7x9x5", "random600"])
-def test_factor_matches_oracle(form, name, prec):
+def test_factor_matches_oracle(form, name, prec, tc):
+    """fp64_tc: the SPD system of (6) takes the tensor-core FP64 updates; the
+    signed LDL^T of (4) keeps the FMA path."""
     lp, perm = _problem(name, form)
-    ctx, info = _ctx(lp, perm, form, storage_fp64=1)
+    ctx, info = _ctx(lp, perm, form, storage_fp64=1, fp64_tc=tc)
     x, s, lam = _point(lp, 4)
     _assemble(ctx, lp, s, lam)
     st, bad = ctx.kkt_factor(prec)
