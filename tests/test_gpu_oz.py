@@ -149,3 +149,17 @@ def test_fp64_tc_needs_analysis_with_the_option():
     with pytest.raises(gb.IpmError) as e:
         ctx.kkt_factor(gb.IPM_FP64)
     assert e.value.status == 10  # IPM_ERR_UNSUPPORTED
+
+
+def test_fp64_tc_nan_reaches_a_pivot():
+    """A NaN in K (one D entry) propagates through the slices (its window's
+    exponent marks it) into a pivot: the factor reports a failed pivot, as the
+    FMA-pipe FP64 factor does, instead of hiding it."""
+    lp, perm = _problem("grid15")
+    D = _state(lp, 2)
+    D[lp.m // 2] = np.nan
+    for tc in (0, 1):
+        ctx, info = _ctx(lp, perm, fp64_tc=tc)
+        ctx.kkt_assemble(dev(lp.val), dev(D), 1e-8)
+        st, bad = ctx.kkt_factor(gb.IPM_FP64, raise_on_error=False)
+        assert st == 5 and bad >= 0, (tc, st, bad)  # IPM_ERR_NOT_SPD
