@@ -18,6 +18,40 @@ namespace gipm {
 
 namespace {
 
+// Substitution with one diagonal block (jb <= 64, lower triangle in Lb) on one
+// warp: lane l holds y_l and y_{l+32}; each step finishes y_c on its lane,
+// broadcasts it by shuffle and updates the rows still open (forward: rows
+// below c with L_ic; backward, L^T: rows above c with L_ci). With `recip`
+// (FP64 without pivot signs) y_c is multiplied by 1 / L_cc formed before the
+// chain, otherwise divided by L_cc, keeping the FP32 and signed solves' rounding.
+template <typename V, bool FWD>
+__device__ __forceinline__ void diag_chain(const V (*Lb)[65], V *yb, int jb, int lane, bool recip) {
+  V y0 = lane < jb ? yb[lane] : V(0), y1 = lane + 32 < jb ? yb[lane + 32] : V(0);
+  V d0 = lane < jb ? Lb[lane][lane] : V(1), d1 = lane + 32 < jb ? Lb[lane + 32][lane + 32] : V(1);
+  if (recip) {
+    d0 = V(1) / d0;
+    d1 = V(1) / d1;
+  }
+  for (int s = 0; s < jb; s++) {
+    const int c = FWD ? s : jb - 1 - s, src = c & 31;
+    const bool hi = c >= 32;
+    if (lane == src) {
+      if (hi) y1 = recip ? y1 * d1 : y1 / d1;
+      else y0 = recip ? y0 * d0 : y0 / d0;
+    }
+    const V yc = __shfl_sync(0xFFFFFFFFu, hi ? y1 : y0, src);
+    if (FWD) {
+      if (lane > c && lane < jb) y0 = fma(-Lb[lane][c], yc, y0);
+      if (lane + 32 > c && lane + 32 < jb) y1 = fma(-Lb[lane + 32][c], yc, y1);
+    } else {
+      if (lane < c) y0 = fma(-Lb[c][lane], yc, y0);
+      if (lane + 32 < c) y1 = fma(-Lb[c][lane + 32], yc, y1);
+    }
+  }
+  if (lane < jb) yb[lane] = y0;
+  if (lane + 32 < jb) yb[lane + 32] = y1;
+}
+
 template <typename V>
 __global__ void __launch_bounds__(kGathPos) gather_fwd_kernel(DevPlan dp, int32_t task0,
                                                               V *__restrict__ y,
@@ -52,12 +86,8 @@ __global__ void __launch_bounds__(64) diag_fwd_kernel(DevPlan dp, int32_t task0,
   }
   if (tid < jb) yb[tid] = y[F.first + j + tid];
   __syncthreads();
-  for (int c = 0; c < jb; c++) {
-    if (tid == c) yb[c] /= Lb[c][c];
-    __syncthreads();
-    if (tid > c && tid < jb) yb[tid] = fma(-Lb[tid][c], yb[c], yb[tid]);
-    __syncthreads();
-  }
+  if (tid < 32) diag_chain<V, true>(Lb, yb, jb, tid, sizeof(V) == 8 && !dp.sgn);
+  __syncthreads();
   if (tid < jb) y[F.first + j + tid] = yb[tid];
 }
 
@@ -126,12 +156,8 @@ __global__ void __launch_bounds__(64) diag_bwd_kernel(DevPlan dp, int32_t task0,
   }
   if (tid < jb) yb[tid] = y[F.first + j + tid];
   __syncthreads();
-  for (int c = jb - 1; c >= 0; c--) {
-    if (tid == c) yb[c] /= Lb[c][c];
-    __syncthreads();
-    if (tid < c) yb[tid] = fma(-Lb[c][tid], yb[c], yb[tid]);
-    __syncthreads();
-  }
+  if (tid < 32) diag_chain<V, false>(Lb, yb, jb, tid, sizeof(V) == 8 && !dp.sgn);
+  __syncthreads();
   if (tid < jb) y[F.first + j + tid] = yb[tid];
 }
 
