@@ -271,6 +271,7 @@ def nlp_measure(N: int, max_iter: int = 150):
                      "dual": float(f"{r.dual_res:.3e}"), "fp64_fallbacks": int(r.fp64_fallbacks),
                      "factorizations": int(r.factorizations),
                      "regularizations": int(r.regularizations), "refine_steps": int(r.refine_steps),
+                     "fp64_tc_rechecks": int(r.fp64_tc_rechecks),
                      "factor_flops": G.info.flops}
         G.ctx.close()
     for name in ("fp64_tc", "tf32x3", "bf16"):
@@ -432,6 +433,7 @@ def tti_run(ctx, jv, b, c, x, s, lam, prec, ref_obj=None, cg_escalate=0):
     out = {"s": round(time.perf_counter() - t0, 4), "status": int(r.status),
            "iters": int(r.iterations), "pcg": int(r.pcg_steps), "kkt": float(f"{r.kkt:.3e}"),
            "fallbacks": int(r.fp64_fallbacks), "perturbed": int(r.perturbed_pivots),
+           "regularizations": int(r.regularizations), "fp64_tc_rechecks": int(r.fp64_tc_rechecks),
            "obj": r.objective, "factor_s": round(r.time_factor_ms / 1e3, 4),
            "solve_s": round(r.time_solve_ms / 1e3, 4)}
     if ref_obj is not None:
@@ -482,7 +484,8 @@ def tti_fp64_tc(lp, perm, jv, b, c, ref_obj, bf16_peak):
 def summary(tti, forms, nlp, mpc):
     """The headline figures, compact, for the end of the JSON line."""
     def pick(d, key):
-        return {k: v[key] for k, v in d.items() if isinstance(v, dict) and key in v}
+        return {k: v[key] for k, v in d.items()
+                if isinstance(v, dict) and key in v and k != "training"}
     out = {"tti_1e-6_s": pick(tti, "s")}
     if "fp64_extrapolated" in tti:
         out["tti_1e-6_s"]["fp64_fma_extrapolated"] = tti["fp64_extrapolated"]["s_factor_only"]

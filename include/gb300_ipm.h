@@ -141,7 +141,11 @@ typedef struct {
                             diagonal blocks stay on the FP64 pipe. Sizes FP64 storage plus 14
                             bytes per factor entry of slices. The signed LDL^T of (4) keeps the
                             FMA path. Long updates are split over CTAs and summed with FP64
-                            atomics, so results may differ between runs in the last bits (0) */
+                            atomics, so results may differ between runs in the last bits. The
+                            slices keep each 128-column row window to 56 bits of its largest
+                            entry, so a factorisation that meets a non-positive pivot is redone
+                            on the FMA pipe before the status is returned (counted in
+                            ipm_result.fp64_tc_rechecks) (0) */
 } ipm_options;
 
 typedef enum {
@@ -191,6 +195,8 @@ typedef struct {
   double time_total_ms, time_assemble_ms, time_factor_ms, time_solve_ms, time_other_ms;
   int32_t learned_skips;     /* iterations that reused the held factor (no factorisation) */
   int32_t learned_pcg_steps; /* PCG iterations spent with the held factor */
+  int32_t fp64_tc_rechecks;  /* FP64 tensor-core factorisations (options.fp64_tc) whose failed
+                                pivot was redone by the FMA-pipe FP64 factor of the same matrix */
 } ipm_result;
 
 /* Create a solver context for a problem with n variables and m general

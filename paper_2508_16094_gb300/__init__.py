@@ -79,7 +79,7 @@ class Result(C.Structure):
                 ("time_total_ms", C.c_double), ("time_assemble_ms", C.c_double),
                 ("time_factor_ms", C.c_double), ("time_solve_ms", C.c_double),
                 ("time_other_ms", C.c_double), ("learned_skips", C.c_int32),
-                ("learned_pcg_steps", C.c_int32)]
+                ("learned_pcg_steps", C.c_int32), ("fp64_tc_rechecks", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -71,6 +71,7 @@ struct ipm_ctx {
   TcPlan tcp;
   OzPlan ozp;          // FP64 factor on tensor cores (Ozaki slices), with options.fp64_tc
   bool oz_on = false;  // its task lists and slice storage were sized by kkt_analyze
+  int64_t oz_rechecks = 0;  // its failed pivots redone on the FMA pipe
   // formulations (4) and (6): `sys` is the context of that system's matrix
   // (its pattern, symbolic analysis, factor and solves); this context keeps
   // the interior-point vectors and builds sys's inputs with the map kernels
@@ -365,6 +366,20 @@ ipm_status do_factor(ipm_ctx *c, int prec, int32_t *bad_col) {
   int32_t out[ST_COUNT];
   CK(cudaMemcpyAsync(out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (prec == IPM_FP64 && c->opts.fp64_tc && !c->dp.sgn && out[ST_FAIL_COL] != INT32_MAX &&
+      !out[ST_TIMEOUT]) {
+    // The slices keep each 128-column window to 56 bits of its largest entry:
+    // where a row's entries span many decades within a window, a pivot that
+    // cancels to a small positive value can come out non-positive. The FMA-pipe
+    // FP64 factor of the same matrix decides before the caller regularises.
+    CK(cudaMemcpyAsync(c->status, init, sizeof(init), cudaMemcpyHostToDevice, c->st));
+    launch_factor_simt<double>(c->dp, c->plan, c->kval, (double *)c->L, (double *)c->U, c->status,
+                               false, c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->oz_rechecks++;
+  }
   c->last_perturbed = out[ST_PERTURBED];
   c->factor_prec = prec;
   c->have_stale = false;  // ipm_solve re-records what a new factor was computed from
@@ -705,10 +720,13 @@ ipm_status factor_with_retry(ipm_ctx *c, const double *wvals, const double *jval
   for (int tries = 0;; tries++) {
     assemble_any(c, wvals, jvals, c->vD, delta_p);
     int32_t bad = -1;
+    ipm_ctx *fc = c->sys ? c->sys : c;  // the context that factors
+    const int64_t rechecks = fc->oz_rechecks;
     ipm_status stt = factor_any(c, prec, &bad);
     if (res) {
       res->factorizations++;
       res->perturbed_pivots += c->last_perturbed;
+      res->fp64_tc_rechecks += (int32_t)(fc->oz_rechecks - rechecks);
     }
     if (stt == IPM_OK) return IPM_OK;
     if (stt != IPM_ERR_NOT_SPD || tries >= max_tries) return stt;

@@ -53,6 +53,23 @@ def test_fp64_matches_oracle(N):
     assert abs(res.iterations - ref["iterations"]) <= 2
 
 
+def test_fp64_tensor_core_factor_matches_oracle():
+    """FP64 factorisations with the updates on the tensor cores (fp64_tc): the
+    grid NLP's K spans many decades within a row, and a pivot the slices make
+    non-positive is redone on the FMA pipe before delta_p is raised, so the
+    regularisations stay those of the FMA-pipe FP64 solve and the optimum is the oracle's."""
+    P = gen.grid_nlp(40, seed=35)
+    out = []
+    for tc in (0, 1):
+        res, x, s, lam = _solve(P, tol=1e-7, fp64_tc=tc)
+        assert res.status == 0 and res.kkt <= 1e-7, res.as_dict()
+        out.append(res)
+    ref = _oracle(P, tol=1e-7)
+    assert out[1].objective == pytest.approx(ref["objective"], rel=1e-6)
+    assert out[1].regularizations <= out[0].regularizations + 2
+    assert out[0].fp64_tc_rechecks == 0
+
+
 def test_without_cubic_term_matches_equality_qp():
     P = gen.grid_nlp(20, seed=32, cubic=0, v_bounded=0)
     res, x, _, _ = _solve(P, tol=1e-9)

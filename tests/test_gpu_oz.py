@@ -158,8 +158,12 @@ def test_fp64_tc_nan_reaches_a_pivot():
     lp, perm = _problem("grid15")
     D = _state(lp, 2)
     D[lp.m // 2] = np.nan
+    bads = []
     for tc in (0, 1):
         ctx, info = _ctx(lp, perm, fp64_tc=tc)
         ctx.kkt_assemble(dev(lp.val), dev(D), 1e-8)
         st, bad = ctx.kkt_factor(gb.IPM_FP64, raise_on_error=False)
         assert st == 5 and bad >= 0, (tc, st, bad)  # IPM_ERR_NOT_SPD
+        bads.append(bad)
+    # a failed pivot of the tensor-core factor is redone on the FMA pipe, which decides
+    assert bads[0] == bads[1]
