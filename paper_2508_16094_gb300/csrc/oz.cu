@@ -25,7 +25,10 @@
 // (K = 128), the tail's rounding costs at most about 2^-50 and the dropped
 // terms i + j >= 7 at most 2^-53: both below the worst-case rounding bound of
 // an FP64 dot product of that length (K u = 2^-46 relative to sum |a||b|),
-// and far below it for digits of mixed signs.
+// and far below it for digits of mixed signs. The bound is normwise per
+// window: an entry far below its window's largest keeps fewer significant
+// bits (the caller redoes a factorisation on the FMA pipe when that turns a
+// pivot non-positive).
 //
 // Long K ranges of one tile are split over several CTAs whose results are
 // added with FP64 atomics (the sum of a few FP64 partials in any order).
