@@ -466,6 +466,18 @@ def tti_fp64_tc(lp, perm, jv, b, c, ref_obj, bf16_peak):
         tf = time.perf_counter() - t0
         out["factor_s_one"] = round(tf, 4)
         out["factor_tflops_fp64_equiv"] = round(info.flops / tf / 1e12, 2)
+        # the same matrix factored on the FMA pipe (the slices left unused): the
+        # FMA-pipe FP64 path's time to 1e-6 is this run's with each of its
+        # factorisations replaced by one of those (the same 10 iterations)
+        ctx.ipm_set_options(fp64_tc=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.kkt_factor(gb.IPM_FP64)
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        out["fma_factor_s_one"] = round(tm, 3)
+        out["fma_factor_tflops"] = round(info.flops / tm / 1e12, 3)
+        out["fma_path_s_estimate"] = round(out["s"] + out["iters"] * (tm - tf), 1)
         # its tensor work: 28 BF16 slice products per multiply-add, against the
         # measured BF16 burst peak (the factorisation timed alone)
         bp = 28 * info.flops / tf / 1e12
@@ -487,8 +499,8 @@ def summary(tti, forms, nlp, mpc):
         return {k: v[key] for k, v in d.items()
                 if isinstance(v, dict) and key in v and k != "training"}
     out = {"tti_1e-6_s": pick(tti, "s")}
-    if "fp64_extrapolated" in tti:
-        out["tti_1e-6_s"]["fp64_fma_extrapolated"] = tti["fp64_extrapolated"]["s_factor_only"]
+    if isinstance(tti.get("fp64_tc"), dict) and "fma_path_s_estimate" in tti["fp64_tc"]:
+        out["tti_1e-6_s"]["fp64_fma_estimate"] = tti["fp64_tc"]["fma_path_s_estimate"]
     t = out["tti_1e-6_s"]
     if "fp64_tc" in t and "tf32_then_tf32x3" in t:
         out["fp64_tc_over_ladder"] = round(t["fp64_tc"] / t["tf32_then_tf32x3"], 2)
@@ -648,7 +660,7 @@ def run_ours(args, ws, rank):
                                      "ms": round(t_as, 4), "bytes": ab}
 
     # time to a 1e-6 KKT residual from the cold start, every precision of the
-    # factor on the 100^3 grid (the FP64 factor by extrapolation, below)
+    # factor on the 100^3 grid (the FP64 path in a context of its own, below)
     tti = {"workload": f"grid LP {G}^3 cold start to KKT <= 1e-6"}
     if args.tti:
         tti[args.precision] = tti_run(ctx, jv, b, c, x, s, lam, prec)
@@ -670,16 +682,6 @@ def run_ours(args, ws, rank):
 
     mpc = mpc_measure() if not args.no_mpc else None
     forms = forms_measure(args.forms_grid) if args.forms_grid > 0 else None
-    if forms is not None and args.tti:
-        # FP64 factor at this grid, extrapolated from the FP64 factor's measured
-        # rate on the forms grid: iterations x flops / rate (factor time only)
-        f64 = forms["fp64"]
-        rate = forms["flops"] * f64["factorizations"] / max(f64["time_factor_s"], 1e-9)
-        it = tti.get(args.precision, {}).get("iters", T)
-        tti["fp64_extrapolated"] = {"s_factor_only": round(it * info.flops / rate, 2),
-                                    "fp64_factor_tflops": round(rate / 1e12, 4),
-                                    "basis": f"{args.forms_grid}^3 FP64 factor rate x "
-                                             f"{G}^3 flops x {it} iterations"}
     nlp = nlp_measure(args.nlp_grid) if args.nlp_grid > 0 else None
 
     cpu = None
