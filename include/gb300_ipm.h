@@ -65,7 +65,7 @@ typedef enum {
   IPM_ERR_MAXITER = 7,     /* interior-point iteration limit reached */
   IPM_ERR_TIMEOUT = 8,     /* a bounded device-side wait ran out */
   IPM_ERR_STALL = 9,       /* the interior-point method stopped making progress */
-  IPM_ERR_UNSUPPORTED = 10 /* feature not available in this build / configuration */
+  IPM_ERR_UNSUPPORTED = 10 /* feature not available for this configuration */
 } ipm_status;
 
 /* Arithmetic of the numeric factorisation (storage type in brackets). */

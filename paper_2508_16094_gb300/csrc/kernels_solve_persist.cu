@@ -128,7 +128,7 @@ struct PsShared {
   unsigned long long mbar;      // completion of the staging copy
   uint32_t parity;              // its phase
   int tk;                       // this CTA's current task
-  int ok;                       // verdict of the last wait
+  int ok;                       // outcome of the last wait
   int ready;                    // blocks of the running chain known to be published
   int nkids;                    // children of the task's front staged below
   int64_t kid_inv[kMaxKids];    // their child -> front map offsets
@@ -178,7 +178,7 @@ __device__ bool wait_dinv(const PsArgs &A, PsShared &S) {
       break;
     }
   }
-  ok = __syncthreads_and(ok) != 0;  // one verdict for the whole CTA
+  ok = __syncthreads_and(ok) != 0;  // one outcome for the whole CTA
   if (threadIdx.x == 0) S.parity = par ^ 1u;
   return ok;
 }
@@ -252,11 +252,11 @@ __device__ void diag_bwd(const PsArgs &A, PsShared &S, const FrontInfo &F, int j
 
 // Thread 0 polls *w until it reaches target (acquire), at most A.spins times
 // and only while no other wait of the launch has run out; the CTA then shares
-// the verdict (and, on success, S.ready = ready unless ready < -1). On expiry
+// the outcome (and, on success, S.ready = ready unless ready < -1). On expiry
 // the status word is set, and every later wait of the launch gives up at once.
 __device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsigned target,
                           int ready = -2) {
-  __syncthreads();  // every thread has read the previous verdict
+  __syncthreads();  // every thread has read the previous outcome
   if (threadIdx.x == 0) {
     unsigned v, spins = 0;
     int ok = 1;
@@ -290,7 +290,7 @@ __device__ bool wait_flag(const PsArgs &A, PsShared &S, const unsigned *w, unsig
 __device__ bool wait_chain(const PsArgs &A, PsShared &S, const unsigned *flags, int j, int last,
                            int step) {
   if ((step > 0 ? j <= S.ready : j >= S.ready) && S.ready >= 0) return true;
-  __syncthreads();  // every thread has read S.ready and the previous verdict
+  __syncthreads();  // every thread has read S.ready and the previous outcome
   if (threadIdx.x == 0) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flags + last) : "memory");
