@@ -484,11 +484,7 @@ void launch_trsm(const DevPlan &dp, const Task *tasks, int ntasks, int nb, T *L,
 void launch_trsm_f64(const DevPlan &dp, const Task *tasks, int ntasks, double *L, cudaStream_t st) {
   if (ntasks <= 0) return;
   const size_t smem = (size_t)(64 + kTrsmRows) * 65 * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(trsm_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  cudaFuncSetAttribute(trsm_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   { note_launch(); trsm_f64_kernel<<<ntasks, kTrsmRows, smem, st>>>(dp, tasks, L); }
 }
 
