@@ -263,3 +263,20 @@ def test_cg_escalation_moves_to_split_tf32_and_matches_oracle():
         ctx.close()
     assert out[2].fp64_fallbacks == 1
     assert out[2].pcg_steps < out[0].pcg_steps
+
+
+@pytest.mark.parametrize("where", ["c", "jvals"])
+def test_nan_in_the_data_is_reported_as_numeric(where):
+    """A NaN in the problem data makes the KKT residual NaN: ipm_solve stops
+    with IPM_ERR_NUMERIC at once instead of factoring."""
+    lp, perm = _problem("grid7x9x5")
+    ctx, info = _ctx(lp, perm, precision=gb.IPM_FP64, storage_fp64=1, tol=1e-8)
+    c, val = lp.c.copy(), lp.val.copy()
+    (c if where == "c" else val)[3] = np.nan
+    mt = lp.m + 2 * lp.n
+    x = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    s = torch.empty(mt, dtype=torch.float64, device="cuda")
+    lam = torch.empty(mt, dtype=torch.float64, device="cuda")
+    res = ctx.ipm_solve(dev(val), dev(lp.b), dev(c), x, s, lam)
+    assert res.status == 6, res.as_dict()  # IPM_ERR_NUMERIC
+    assert res.factorizations == 0
