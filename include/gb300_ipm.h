@@ -263,9 +263,14 @@ IPM_API ipm_status kkt_assemble(ipm_ctx *ctx, const double *d_wvals, const doubl
  * IPM_ERR_NOT_SPD with *bad_col = that column in the final ordering (the
  * smallest such column). Lower precisions replace a non-positive pivot by a
  * large value (static pivoting; counted in ipm_last_perturbed) and return
- * IPM_OK; refinement in kkt_solve corrects the perturbation.
+ * IPM_OK; refinement in kkt_solve corrects the perturbation. With
+ * options.fp64_tc (set before kkt_analyze), FP64 runs the dense updates on the
+ * tensor cores (BF16 slices, Sec. 6 on the precision of condensed systems);
+ * a factorisation that meets a non-positive pivot there is redone on the FMA
+ * pipe, whose first failing column is the one reported.
  * Errors: IPM_ERR_STATE before kkt_assemble; IPM_ERR_NOMEM if the storage was
- * sized for FP32 and FP64 is requested. */
+ * sized for FP32 and FP64 is requested; IPM_ERR_UNSUPPORTED if fp64_tc is set
+ * but was not at kkt_analyze (no slice storage). */
 IPM_API ipm_status kkt_factor(ipm_ctx *ctx, int32_t precision, int32_t *bad_col);
 
 /* Solve K x = b with the current factor: x = P^T L^{-T} L^{-1} P b, then FP64
