@@ -512,6 +512,58 @@ void OzPlan::build(const Plan &plan) {
     }
     V.syrk_e = (int)gemm_.size();
   }
+  validate(plan);
+}
+
+// Every task against the buffers it indexes, and the K chunks of each tile
+// against its window range (consecutive, no gap, no overlap): a violation is a
+// planning bug, reported before any launch.
+void OzPlan::validate(const Plan &plan) const {
+  auto need = [](bool ok, const char *what) {
+    if (!ok) throw std::runtime_error(std::string("FP64 tensor-core plan: ") + what);
+  };
+  const int nfr = (int)plan.fronts.size();
+  for (int f = 0; f < nfr; f++) {
+    const FrontInfo &F = plan.fronts[f];
+    const OzFront &Z = fr_[f];
+    const int64_t nf = F.ncol + F.nrow;
+    need(Z.lds >= F.ncol && Z.lds % 8 == 0 && Z.soff % 8 == 0, "slice row stride");
+    need(Z.soff + (int64_t)kP * nf * Z.lds <= slice_elems_, "slice planes past the storage");
+    need(Z.eoff + nf * Z.nblk <= exp_elems_, "exponents past the storage");
+  }
+  int cur_f = -1, cur_a = -1, cur_b = -1, cur_mode = -1, next_w = 0, cur_W = 0;
+  auto close_tile = [&]() { need(cur_f < 0 || next_w == cur_W, "a tile's chunks miss windows"); };
+  for (const Task &t : gemm_) {
+    need(t.front >= 0 && t.front < nfr, "task front");
+    const FrontInfo &F = plan.fronts[t.front];
+    const int mode = t.c & 3, w0 = (t.c >> 2) & 0x7FFF, w1 = (t.c >> 17) & 0x7FFF;
+    int W;
+    if (mode == 0) {
+      need(t.b > 0 && t.b % kBlk == 0 && t.b < F.ncol, "update: block column");
+      need(t.a >= t.b && t.a < F.ncol + F.nrow && (t.a - t.b) % kM == 0, "update: row tile");
+      W = windows(t.b / kBlk);
+    } else {
+      need(mode == 1 && F.nrow > 0, "task mode");
+      need(t.a >= 0 && t.a < F.nrow && t.a % kM == 0, "SYRK: row tile");
+      need(t.b >= 0 && t.b < F.nrow && t.b % kN == 0 && t.b < t.a + kM, "SYRK: column tile");
+      W = windows((F.ncol + kBlk - 1) / kBlk);
+    }
+    need(0 <= w0 && w0 < w1 && w1 <= W, "window range");
+    if (t.front != cur_f || t.a != cur_a || t.b != cur_b || mode != cur_mode || w0 == 0) {
+      close_tile();
+      need(w0 == 0, "a tile's first chunk starts past window 0");
+      cur_f = t.front, cur_a = t.a, cur_b = t.b, cur_mode = mode, cur_W = W, next_w = 0;
+    }
+    need(w0 == next_w, "a tile's chunks are not consecutive");
+    next_w = w1;
+  }
+  close_tile();
+  for (const Task &t : slice_) {
+    need(t.front >= 0 && t.front < nfr, "slice front");
+    const FrontInfo &F = plan.fronts[t.front];
+    need(t.b % kBlk == 0 && t.c > 0 && t.c <= 2 * kBlk && t.b + t.c <= F.ncol, "slice columns");
+    need(t.a >= t.b + t.c && t.a < F.ncol + F.nrow, "slice rows");
+  }
 }
 
 void OzPlan::layout(Carve &cv, cudaStream_t st, bool storage) {

@@ -42,6 +42,7 @@ class OzPlan {
               int32_t *status, cudaStream_t st);
 
  private:
+  void validate(const Plan &plan) const;
   struct Step { int gemm_b, gemm_e, slice_b, slice_e; };
   struct Level { std::vector<Step> steps; int syrk_b = 0, syrk_e = 0; };
   std::vector<Task> gemm_, slice_;
