@@ -44,6 +44,7 @@
 #include "launch.h"
 #include "oz.h"
 #include "ptx.cuh"
+#include "tmap.h"
 
 namespace gipm {
 
@@ -400,20 +401,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                  "r"(kTmemCols));
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    cudaDriverEntryPointQueryResult q;
-    void *p = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !p)
-      throw std::runtime_error("cuTensorMapEncodeTiled unavailable");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 // Chunks of the K range of each tile: enough CTAs for the launch, at least
 // kMinSplitWin windows each.
 int split_for(int64_t tiles, int nwin) {
@@ -588,7 +575,7 @@ void OzPlan::layout(Carve &cv, cudaStream_t st, bool storage) {
 void OzPlan::encode(const Plan &plan, cudaStream_t st) {
   ready_ = false;
   if (!sized_ || !S_) return;
-  PFN_cuTensorMapEncodeTiled_v12000 enc = oz_encode_fn();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   const size_t nfr = plan.fronts.size();
   std::vector<CUtensorMap> maps(2 * nfr);
   for (size_t f = 0; f < nfr; f++) {

@@ -28,6 +28,7 @@
 #include "launch.h"
 #include "ptx.cuh"
 #include "tc.h"
+#include "tmap.h"
 
 #include <cstring>
 
@@ -831,7 +832,9 @@ __global__ void __launch_bounds__(256, 1) potrf_inv_kernel(DevPlan dp, const Tas
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -844,8 +847,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   }
   return fn;
 }
-
-}  // namespace
 
 void TcPlan::build(const Plan &plan) {
   gemm_.clear();
@@ -1018,7 +1019,7 @@ void TcPlan::layout(Carve &cv, cudaStream_t st) {
 }
 
 void TcPlan::encode(const Plan &plan, float *L, float *Llo, float *U, cudaStream_t st) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!side_) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
