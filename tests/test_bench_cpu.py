@@ -49,3 +49,27 @@ def test_reference_arm_under_torchrun_prints_once():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check(lines[0], 2)
+
+
+def test_summary_carries_the_headline_figures():
+    """The compact key that ends the own arm's line: every form's time to
+    1e-6, the FP64 tensor-core path against the ladder, and the other
+    workloads, without the training record."""
+    sys.path.insert(0, ROOT)
+    import bench
+    tti = {"workload": "w", "tf32x3": {"s": 3.67, "iters": 10},
+           "tf32_then_tf32x3": {"s": 3.49}, "bf16": {"error": "x"},
+           "fp64_tc": {"s": 26.0, "factor_tflops_fp64_equiv": 20.7, "fma_path_s_estimate": 464.5}}
+    forms = {"workload": "w", "fp64": {"seconds": 8.06}, "training": {"seconds": 2.7},
+             "flops": 1.0}
+    nlp = {"workload": "w", "max_iter": 150, "fp64_tc": {"seconds": 7.2}}
+    mpc = {"fp64": {"solves_per_s": 33800.0}}
+    s = bench.summary(tti, forms, nlp, mpc)
+    assert s["tti_1e-6_s"] == {"tf32x3": 3.67, "tf32_then_tf32x3": 3.49, "fp64_tc": 26.0,
+                               "fp64_fma_estimate": 464.5}
+    assert s["fp64_tc_over_ladder"] == round(26.0 / 3.49, 2)
+    assert s["fp64_tc_factor_tflops"] == 20.7
+    assert s["forms_48_s"] == {"fp64": 8.06}
+    assert s["grid_nlp_s"] == {"fp64_tc": 7.2}
+    assert s["mpc_solves_per_s"] == {"fp64": 33800.0}
+    assert len(json.dumps(s)) < 1000  # fits the end of the line the driver keeps
